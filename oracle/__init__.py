@@ -1,0 +1,142 @@
+"""TEST INFRASTRUCTURE ONLY -- the CPU oracle for matrix products over small fields.
+
+Boothby & Bradshaw, "Bitslicing and the Method of Four Russians Over Larger
+Finite Fields".  This package is the plain, slow, obviously correct statement of
+what the library computes; the CUDA path is checked against it bit for bit.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import it.  It imports nothing from the library and the
+library imports nothing from it.
+
+* ``matmul(q, A, B)``: C = AB over F_q (q = 2, 3, 5, 7) or GF(4) (q = 4), on
+  residue matrices (uint8, entries in [0, q)), computed in C as the row
+  combination C_i = sum_j a_ij B_j of Section 2 (``fq_oracle.c``).
+* ``gf4_karatsuba(A, B)``: the matrix-level GF(4) formula of Section 4.3 over
+  three F_2 products, a second GF(4) oracle.
+* ``encoding``: the bitsliced representation (Sections 3-4).
+* ``bitslice``: the paper's element formulas.
+* ``m4rm``: the Section 2 method itself, step by step, for small sizes.
+* ``freivalds`` / ``matmul_rows``: checks for sizes too large for the full
+  product (a randomized identity test and exact sampled rows).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import bitslice, encoding  # noqa: F401
+from .build import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build()
+        lib = ctypes.CDLL(path)
+        i64 = ctypes.c_int64
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        lib.fq_oracle_matmul_fp.argtypes = [ctypes.c_int, i64, i64, i64, u8p, i64, u8p, i64, u8p, i64,
+                                            ctypes.c_int]
+        lib.fq_oracle_matmul_fp.restype = ctypes.c_int
+        lib.fq_oracle_matmul_gf4.argtypes = [i64, i64, i64, u8p, i64, u8p, i64, u8p, i64, ctypes.c_int]
+        lib.fq_oracle_matmul_gf4.restype = ctypes.c_int
+        lib.fq_oracle_threads.argtypes = [ctypes.c_int]
+        lib.fq_oracle_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+FIELDS = (2, 3, 4, 5, 7)
+
+
+def threads_used(threads: int = 0) -> int:
+    """Number of host threads ``matmul`` uses for a given request (0 = all)."""
+    return int(_load().fq_oracle_threads(int(threads)))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def matmul(q: int, A: np.ndarray, B: np.ndarray, threads: int = 0) -> np.ndarray:
+    """C = A B over F_q (q prime <= 7) or GF(4) (q = 4); residues in, residues out."""
+    if q not in FIELDS:
+        raise ValueError("unsupported field size %r" % (q,))
+    A = np.ascontiguousarray(A, dtype=np.uint8)
+    B = np.ascontiguousarray(B, dtype=np.uint8)
+    if A.ndim != 2 or B.ndim != 2 or A.shape[1] != B.shape[0]:
+        raise ValueError("shape mismatch")
+    if A.size and A.max() >= q or B.size and B.max() >= q:
+        raise ValueError("residue out of range")
+    m, l = A.shape
+    n = B.shape[1]
+    C = np.zeros((m, n), dtype=np.uint8)
+    lib = _load()
+    if q == 4:
+        rc = lib.fq_oracle_matmul_gf4(m, l, n, _ptr(A), l, _ptr(B), n, _ptr(C), n, int(threads))
+    else:
+        rc = lib.fq_oracle_matmul_fp(q, m, l, n, _ptr(A), l, _ptr(B), n, _ptr(C), n, int(threads))
+    if rc != 0:
+        raise RuntimeError("oracle failed with status %d" % rc)
+    return C
+
+
+def matmul_rows(q: int, A: np.ndarray, B: np.ndarray, rows, threads: int = 0) -> np.ndarray:
+    """Exact rows ``rows`` of A B (each row is C_i = A_i B, independent of the rest)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    return matmul(q, np.asarray(A)[rows], B, threads)
+
+
+def gf4_karatsuba(A: np.ndarray, B: np.ndarray, threads: int = 0) -> np.ndarray:
+    """GF(4) product by Section 4.3: with A = A0 + alpha A1 and B = B0 + alpha B1,
+    AB = (A0 B0 + A1 B1) + alpha ((A0 + A1)(B0 + B1) + A0 B0), three F_2 products."""
+    A = np.asarray(A, dtype=np.uint8)
+    B = np.asarray(B, dtype=np.uint8)
+    A0, A1 = A & 1, (A >> 1) & 1
+    B0, B1 = B & 1, (B >> 1) & 1
+    P00 = matmul(2, A0, B0, threads)
+    P11 = matmul(2, A1, B1, threads)
+    Pss = matmul(2, A0 ^ A1, B0 ^ B1, threads)
+    c0 = P00 ^ P11
+    c1 = Pss ^ P00
+    return (c0 | (c1 << 1)).astype(np.uint8)
+
+
+def _gf4_matvec(M: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = M x over GF(4) via the Section 4.3 decomposition on F_2 mat-vecs."""
+    M0, M1 = (M & 1).astype(np.int64), ((M >> 1) & 1).astype(np.int64)
+    x0, x1 = (x & 1).astype(np.int64), ((x >> 1) & 1).astype(np.int64)
+    p00 = (M0 @ x0) & 1
+    p11 = (M1 @ x1) & 1
+    pss = ((M0 ^ M1) @ (x0 ^ x1)) & 1
+    return ((p00 ^ p11) | ((pss ^ p00) << 1)).astype(np.int64)
+
+
+def freivalds(q: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, trials: int = 32,
+              seed: int = 0) -> bool:
+    """Randomized check that C = A B: for random x, A (B x) == C x over F_q.
+
+    A wrong C passes one trial with probability at most 1/q (Freivalds), so the
+    false-pass probability is at most q^-trials.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    A = np.asarray(A)
+    B = np.asarray(B)
+    C = np.asarray(C)
+    n = B.shape[1]
+    for _ in range(trials):
+        x = rng.integers(0, q, size=n, dtype=np.int64)
+        if q == 4:
+            lhs = _gf4_matvec(A, _gf4_matvec(B, x))
+            rhs = _gf4_matvec(C, x)
+        else:
+            bx = (B.astype(np.int64) @ x) % q
+            lhs = (A.astype(np.int64) @ bx) % q
+            rhs = (C.astype(np.int64) @ x) % q
+        if not np.array_equal(lhs, rhs):
+            return False
+    return True

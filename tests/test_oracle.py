@@ -1,0 +1,226 @@
+"""The CPU oracle, pinned by checks that do not restate its own formula."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import encoding, m4rm
+from tests import pins
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+FIELDS = (2, 3, 4, 5, 7)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_oracle_passes_all_pins(q):
+    assert pins.run_all(oracle.matmul, q, seed=q, karatsuba=oracle.gf4_karatsuba) == []
+
+
+# --- planted mistakes: each mutant of the oracle must fail at least one pin ---
+
+def _mut_dropped_term(q, A, B):          # the last term a_{i,l-1} B_{l-1} is lost
+    A = np.array(A, copy=True)
+    if A.shape[1]:
+        A[:, -1] = 0
+    return oracle.matmul(q, A, B)
+
+
+def _mut_wrong_index(q, A, B):           # row j of B paired with a_{i,j+1}
+    return oracle.matmul(q, A, np.ascontiguousarray(np.roll(B, 1, axis=0)))
+
+
+def _mut_transposed(q, A, B):            # A^T B whenever the shapes allow it
+    if A.shape[0] == A.shape[1]:
+        return oracle.matmul(q, np.ascontiguousarray(A.T), B)
+    return oracle.matmul(q, A, B)
+
+
+def _mut_sign(q, A, B):                  # first term subtracted instead of added
+    C = oracle.matmul(q, A, B).astype(np.int64)
+    if q == 4:
+        return C.astype(np.uint8)            # (char 2: -x = x, no sign to flip)
+    first = np.outer(A[:, 0].astype(np.int64), B[0].astype(np.int64)) if A.shape[1] else 0
+    return ((C - 2 * first) % q).astype(np.uint8)
+
+
+def _mut_narrow_accumulator(q, A, B):    # int8-wide accumulation that wraps
+    if q == 4:
+        return oracle.matmul(q, A, B)
+    acc = (A.astype(np.uint8) @ B.astype(np.uint8)).astype(np.uint8)
+    return (acc % q).astype(np.uint8)
+
+
+def _mut_gf4_wrong_poly(q, A, B):        # GF(4) reduced with x^2 = 1 instead of x + 1
+    if q != 4:
+        return oracle.matmul(q, A, B)
+    A0, A1 = A & 1, (A >> 1) & 1
+    B0, B1 = B & 1, (B >> 1) & 1
+    e0 = oracle.matmul(2, A0, B0) ^ oracle.matmul(2, A1, B1)
+    e1 = oracle.matmul(2, A0, B1) ^ oracle.matmul(2, A1, B0)
+    return (e0 | (e1 << 1)).astype(np.uint8)
+
+
+MUTANTS = {
+    "dropped_term": _mut_dropped_term,
+    "wrong_index": _mut_wrong_index,
+    "transposed": _mut_transposed,
+    "sign": _mut_sign,
+    "narrow_accumulator": _mut_narrow_accumulator,
+    "gf4_wrong_poly": _mut_gf4_wrong_poly,
+}
+
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistakes(q, name):
+    if (q == 4 and name in ("sign", "narrow_accumulator")) or (q != 4 and name == "gf4_wrong_poly"):
+        pytest.skip("mutant is the identity for this field")
+    if q == 2 and name == "sign":
+        pytest.skip("char 2: -x = x")
+    if q == 2 and name == "narrow_accumulator":
+        pytest.skip("a wrap mod 256 preserves parity: the mutant is correct over F_2")
+    fails = pins.run_all(MUTANTS[name], q, seed=q, karatsuba=oracle.gf4_karatsuba)
+    assert fails, "mutant %s survived every pin for q=%d" % (name, q)
+
+
+# --- the paper's method, step by step, reaches the plain product ---
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("k", [1, 3, 4, 8])
+def test_m4rm_method_matches_plain_product(q, k):
+    rng = np.random.default_rng(100 + q * 10 + k)
+    m, l, n = 9, 23, 70                      # k does not divide l; n spans two words
+    A, B = pins.rand(rng, q, m, l), pins.rand(rng, q, l, n)
+    assert np.array_equal(m4rm.m4rm(q, A, B, k), oracle.matmul(q, A, B))
+
+
+def test_m4rm_method_zero_and_degenerate():
+    A = np.zeros((4, 5), np.uint8)
+    B = np.zeros((5, 3), np.uint8)
+    assert not m4rm.m4rm(3, A, B, 2).any()
+    assert m4rm.m4rm(5, np.zeros((0, 5), np.uint8), B, 2).shape == (0, 3)
+
+
+# --- GF(4): the two oracles agree; brute force over every 2x2 product ---
+
+def test_gf4_karatsuba_agrees_with_polynomial_oracle():
+    rng = np.random.default_rng(4)
+    for m, l, n in ((1, 1, 1), (17, 65, 31), (64, 128, 64)):
+        A, B = pins.rand(rng, 4, m, l), pins.rand(rng, 4, l, n)
+        assert np.array_equal(oracle.matmul(4, A, B), oracle.gf4_karatsuba(A, B))
+
+
+@pytest.mark.parametrize("q", [3, 4])
+def test_brute_force_all_2x2_products(q):
+    """Every pair of 2x2 matrices (q^8 products) against the Section 4.3
+    Karatsuba form (GF(4)) or numpy (F_3), batched as one block-diagonal product."""
+    vals = np.array(np.meshgrid(*[np.arange(q)] * 4, indexing="ij")).reshape(4, -1).T.astype(np.uint8)
+    mats = vals.reshape(-1, 2, 2)
+    N = len(mats)
+    Astack = np.repeat(mats, N, axis=0)          # pair (a, b) -> A = mats[a], B = mats[b]
+    Bstack = np.tile(mats, (N, 1, 1))
+    # one product per pair: rows of A_pair against B_pair, computed pair by pair in bulk
+    # by the oracle on a (2, 2) x (2, 2N^2)-wide layout per A
+    got = np.empty_like(Astack)
+    for a in range(N):
+        Bwide = np.ascontiguousarray(np.concatenate(list(Bstack[a * N:(a + 1) * N]), axis=1))
+        got[a * N:(a + 1) * N] = oracle.matmul(q, mats[a], Bwide).reshape(2, N, 2).transpose(1, 0, 2)
+    if q == 3:
+        ref = np.einsum("pij,pjk->pik", Astack.astype(np.int64), Bstack.astype(np.int64)) % 3
+    else:
+        ref = np.stack([oracle.gf4_karatsuba(x, y) for x, y in zip(Astack[::97], Bstack[::97])])
+        got = got[::97]
+    assert np.array_equal(got, ref)
+
+
+# --- checks used at sizes the full oracle cannot reach ---
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_freivalds_accepts_product_and_rejects_one_wrong_entry(q):
+    rng = np.random.default_rng(7)
+    A, B = pins.rand(rng, q, 40, 50), pins.rand(rng, q, 50, 30)
+    C = oracle.matmul(q, A, B)
+    assert oracle.freivalds(q, A, B, C, trials=16)
+    bad = C.copy()
+    bad[13, 17] = (int(bad[13, 17]) + 1) % q
+    assert not oracle.freivalds(q, A, B, bad, trials=16)
+
+
+def test_matmul_rows_is_a_slice():
+    rng = np.random.default_rng(8)
+    A, B = pins.rand(rng, 5, 30, 20), pins.rand(rng, 5, 20, 10)
+    rows = [0, 7, 29]
+    assert np.array_equal(oracle.matmul_rows(5, A, B, rows), oracle.matmul(5, A, B)[rows])
+
+
+def test_thread_count_does_not_change_result():
+    rng = np.random.default_rng(9)
+    A, B = pins.rand(rng, 7, 100, 90), pins.rand(rng, 7, 90, 80)
+    assert np.array_equal(oracle.matmul(7, A, B, threads=1), oracle.matmul(7, A, B, threads=4))
+    assert oracle.threads_used(3) == 3
+
+
+def test_oracle_rejects_bad_input():
+    with pytest.raises(ValueError):
+        oracle.matmul(6, np.zeros((2, 2), np.uint8), np.zeros((2, 2), np.uint8))
+    with pytest.raises(ValueError):
+        oracle.matmul(3, np.full((2, 2), 3, np.uint8), np.zeros((2, 2), np.uint8))
+    with pytest.raises(ValueError):
+        oracle.matmul(3, np.zeros((2, 3), np.uint8), np.zeros((2, 2), np.uint8))
+
+
+def test_empty_dimensions():
+    for m, l, n in ((0, 5, 3), (4, 0, 3), (4, 5, 0)):
+        C = oracle.matmul(3, np.zeros((m, l), np.uint8), np.zeros((l, n), np.uint8))
+        assert C.shape == (m, n) and not C.any()
+
+
+# --- the representation (Sections 3 and 4.1) ---
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def test_worked_example_planes_section3():
+    g = {r[0]: r[1:] for r in _read_golden("z4_worked_example.txt")}
+    values = np.array([int(v) for v in g["values"]], np.uint8)
+    # Z/4 codes are the values' binary digits; use the generic binary planes.
+    bits = [(values >> i) & 1 for i in range(2)]
+    display = lambda b: "".join(str(int(x)) for x in b)   # element 0 at the left
+    assert display(bits[1]) == g["plane1"][0]
+    assert display(bits[0]) == g["plane0"][0]
+    words = encoding._bits_to_words(np.stack(bits))
+    assert encoding._words_to_bits(words, 8).tolist() == [list(b) for b in bits]
+
+
+def test_f3_representation_section41():
+    for value, code in _read_golden("f3_representation.txt"):
+        x0, x1 = encoding.codes_to_bits(3, np.array([int(value)]))
+        assert "%d%d" % (x0[0], x1[0]) == code
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_pack_unpack_round_trip(q):
+    rng = np.random.default_rng(q)
+    for r, c in ((1, 1), (3, 64), (5, 65), (7, 200)):
+        R = pins.rand(rng, q, r, c)
+        Pl = encoding.pack(q, R)
+        assert Pl.shape == (encoding.planes(q), r, (c + 63) // 64)
+        assert np.array_equal(encoding.unpack(q, Pl, c), R)
+
+
+def test_pack_bit_order():
+    R = np.zeros((1, 130), np.uint8)
+    R[0, 0] = 1
+    R[0, 65] = 2
+    R[0, 129] = 1
+    Pl = encoding.pack(3, R)
+    assert Pl[0, 0].tolist() == [1, 2, 2]             # unit plane: bits 0, 65, 129
+    assert Pl[1, 0].tolist() == [0, 2, 0]             # sign plane: element 65 is -1
