@@ -1,0 +1,121 @@
+/*
+ * fq.h -- exact dense matrix products over small finite fields on GB300 (sm_103a).
+ *
+ * Boothby & Bradshaw, "Bitslicing and the Method of Four Russians Over Larger
+ * Finite Fields".  Matrices are stored bitsliced (Section 3): bit i of every
+ * element's code lives in bit-plane i, 64 elements per 64-bit word.  Products use
+ * the Method of Four Russians with an additive basis (Section 2).
+ *
+ * Fields (argument q):
+ *   q = 3  F_3,  2 planes, codes (x0, x1): 0 = (0,0), 1 = (1,0), -1 = (1,1)
+ *          (Section 4.1), additive basis {1, -1};
+ *   q = 5  F_5,  3 planes, binary digits of the residue (Section 4.2), basis {1,2,4};
+ *   q = 7  F_7,  3 planes, binary digits of the residue (Section 4.2), basis {1,2,4};
+ *   q = 4  GF(4) = F_2[x]/(x^2+x+1), 2 planes, element a0 + alpha*a1 has code
+ *          a0 + 2*a1 (Section 4.3), basis {1, alpha}.
+ *
+ * Packed layout ("planes buffer") of a rows x cols matrix: plane-major,
+ *   word(p, r, w) = buf[(p * rows + r) * pitch + w],  pitch = fq_pitch_words(cols),
+ * element c of row r is bit (c mod 64) of word floor(c / 64) of each plane.
+ * Words past the last column (padding) must be zero in inputs and are zero in
+ * outputs; fq_pack writes them.  Planes buffers must be 16-byte aligned device
+ * memory (cudaMalloc and PyTorch allocations are).  Output codes are canonical
+ * (F_5 and F_7 codes are reduced to [0, p)).
+ *
+ * Conventions: every function is asynchronous on `stream` (a cudaStream_t, or
+ * NULL for the legacy default stream) unless it says otherwise; the caller owns
+ * all device buffers; argument errors are returned before anything is
+ * enqueued.  Errors a kernel detects while running (a residue >= q in fq_pack, a
+ * bounded device wait that gave up) are recorded on the device and returned by
+ * fq_status().
+ */
+#ifndef FQ_H
+#define FQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define FQ_OK 0
+#define FQ_EINVAL 1    /* bad q, shape, pointer, alignment or option              */
+#define FQ_EVALUE 2    /* a residue >= q was passed to fq_pack (device-detected)   */
+#define FQ_ECUDA 3     /* a CUDA call failed; see fq_last_cuda_error()            */
+#define FQ_ETIMEOUT 4  /* a bounded device wait gave up (device-detected)          */
+#define FQ_ENOTSUP 5   /* valid request this build does not support               */
+#define FQ_ENOMEM 6    /* host allocation failed                                   */
+
+/* ---- product paths (fq_options.path) --------------------------------------- */
+#define FQ_PATH_AUTO 0 /* planner's choice                                         */
+#define FQ_PATH_M4RM 1 /* bitsliced Method of Four Russians (Sections 2-4)         */
+#define FQ_PATH_MMA 2  /* exact integer tensor-core contraction, mod p per l-chunk */
+
+/* Number of bit-planes of a field element (2 for q = 3, 4; 3 for q = 5, 7), or 0
+ * for an unsupported q.  Section 4 fixes the widths. */
+int fq_planes(int q);
+
+/* Row pitch in 64-bit words of a planes buffer with `cols` columns:
+ * ceil(cols / 64) rounded up to a multiple of 16 (128 bytes).  -1 if cols < 0. */
+int64_t fq_pitch_words(int64_t cols);
+
+/* Total 64-bit words of a planes buffer: fq_planes(q) * rows * fq_pitch_words(cols);
+ * -1 on bad arguments. */
+int64_t fq_planes_words(int q, int64_t rows, int64_t cols);
+
+/* Pack residues into bit-planes (Section 3; codes of Sections 4.1-4.3).
+ * res:    device, rows x cols uint8 residues in [0, q), row-major, leading
+ *         dimension ld >= cols (elements).
+ * planes: device planes buffer (layout above), written entirely, padding zeroed.
+ * A residue >= q is stored as 0 and recorded for fq_status() (FQ_EVALUE). */
+int fq_pack(int q, int64_t rows, int64_t cols, const uint8_t *res, int64_t ld,
+            uint64_t *planes, void *stream);
+
+/* Unpack bit-planes into residues in [0, q).  Any 3-bit code is accepted for
+ * F_5/F_7 and read mod p (codes are not unique, Section 4.2).
+ * planes: device planes buffer; res: device rows x cols uint8, leading dim ld. */
+int fq_unpack(int q, int64_t rows, int64_t cols, const uint64_t *planes,
+              uint8_t *res, int64_t ld, void *stream);
+
+/* Elementwise Z = X + Y (sub = 0) or Z = X - Y (sub = 1) of packed matrices with
+ * the bitsliced formulas of Sections 4.1-4.3 -- the row additions the product is
+ * built from.  X, Y, Z: device planes buffers of the same shape (Z may alias X or
+ * Y).  F_5/F_7 outputs may be non-canonical codes (fq_unpack reduces them). */
+int fq_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t *Y,
+           uint64_t *Z, int sub, void *stream);
+
+/* Options for fq_matmul_ex; zero-initialise for defaults. */
+typedef struct fq_options {
+  int path;      /* FQ_PATH_*                                                     */
+  int k;         /* M4RM block size: 0 = planner, else 6..10 (Section 2's k)       */
+  int64_t chunk; /* MMA path: l-chunk length between mod-p reductions; 0 = largest */
+  int variant;   /* M4RM tile variant: 0 = planner, else an index >= 1             */
+  int reserved[5];
+} fq_options;
+
+/* C = A B over F_q (Section 2: C_i = sum_s sum_d alpha_d T_s[phi_d(A_i, block s)]).
+ * A: device planes buffer m x l; B: l x n; C: m x n (written entirely; must not
+ * alias A or B).  m, l, n >= 0; l = 0 gives C = 0.  The product is exact. */
+int fq_matmul(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
+              const uint64_t *B, uint64_t *C, void *stream);
+
+/* fq_matmul with explicit options (path, k, l-chunk, tile variant); opt may be NULL. */
+int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
+                 const uint64_t *B, uint64_t *C, void *stream, const fq_options *opt);
+
+/* Wait for `stream`, then return and clear the first error kernels recorded on
+ * the current device (FQ_EVALUE, FQ_ETIMEOUT), or FQ_OK.  Synchronous. */
+int fq_status(void *stream);
+
+/* Static text for a status code. */
+const char *fq_error_string(int status);
+
+/* Text of the last CUDA error seen by this library in the calling thread. */
+const char *fq_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FQ_H */

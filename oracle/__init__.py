@@ -116,6 +116,15 @@ def _gf4_matvec(M: np.ndarray, x: np.ndarray) -> np.ndarray:
     return ((p00 ^ p11) | ((pss ^ p00) << 1)).astype(np.int64)
 
 
+def _matvec_mod(q: int, M: np.ndarray, x: np.ndarray, rows_per_chunk: int = 2048) -> np.ndarray:
+    """M x over F_q (or GF(4)), row chunk by row chunk to bound memory."""
+    out = np.empty(M.shape[0], dtype=np.int64)
+    for r in range(0, M.shape[0], rows_per_chunk):
+        blk = M[r:r + rows_per_chunk]
+        out[r:r + rows_per_chunk] = _gf4_matvec(blk, x) if q == 4 else (blk.astype(np.int64) @ x) % q
+    return out
+
+
 def freivalds(q: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, trials: int = 32,
               seed: int = 0) -> bool:
     """Randomized check that C = A B: for random x, A (B x) == C x over F_q.
@@ -130,13 +139,8 @@ def freivalds(q: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, trials: int =
     n = B.shape[1]
     for _ in range(trials):
         x = rng.integers(0, q, size=n, dtype=np.int64)
-        if q == 4:
-            lhs = _gf4_matvec(A, _gf4_matvec(B, x))
-            rhs = _gf4_matvec(C, x)
-        else:
-            bx = (B.astype(np.int64) @ x) % q
-            lhs = (A.astype(np.int64) @ bx) % q
-            rhs = (C.astype(np.int64) @ x) % q
+        lhs = _matvec_mod(q, A, _matvec_mod(q, B, x))
+        rhs = _matvec_mod(q, C, x)
         if not np.array_equal(lhs, rhs):
             return False
     return True

@@ -1,0 +1,163 @@
+// The C ABI of include/fq.h: argument checks, the per-device status word and
+// dispatch to the kernels.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "fq_common.cuh"
+#include "fq_internal.h"
+
+namespace fqk {
+
+namespace {
+
+// Errors kernels detect while running; read and cleared by fq_status().
+__device__ unsigned g_status;
+
+thread_local char t_last_cuda_error[256] = "no CUDA error";
+
+constexpr int kMaxDevices = 64;
+unsigned *g_status_ptr[kMaxDevices];
+std::mutex g_mu;
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool valid_q(int q) { return q == 3 || q == 4 || q == 5 || q == 7; }
+
+}  // namespace
+
+int record_cuda_error(cudaError_t e) {
+  snprintf(t_last_cuda_error, sizeof(t_last_cuda_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return FQ_ECUDA;
+}
+
+int status_word(unsigned **out) {
+  int dev = 0;
+  FQ_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return FQ_ENOTSUP;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_status_ptr[dev]) {
+    void *p = nullptr;
+    FQ_CUDA_TRY(cudaGetSymbolAddress(&p, g_status));
+    g_status_ptr[dev] = static_cast<unsigned *>(p);
+  }
+  *out = g_status_ptr[dev];
+  return FQ_OK;
+}
+
+int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000 *out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    FQ_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return FQ_ENOTSUP;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  *out = g_encode;
+  return FQ_OK;
+}
+
+}  // namespace fqk
+
+using fqk::aligned16;
+using fqk::valid_q;
+
+extern "C" {
+
+int fq_planes(int q) {
+  switch (q) {
+    case 3: case 4: return 2;
+    case 5: case 7: return 3;
+    default: return 0;
+  }
+}
+
+int64_t fq_pitch_words(int64_t cols) {
+  if (cols < 0) return -1;
+  const int64_t words = (cols + 63) / 64;
+  return (words + 15) / 16 * 16;
+}
+
+int64_t fq_planes_words(int q, int64_t rows, int64_t cols) {
+  if (!valid_q(q) || rows < 0 || cols < 0) return -1;
+  return int64_t(fq_planes(q)) * rows * fq_pitch_words(cols);
+}
+
+int fq_pack(int q, int64_t rows, int64_t cols, const uint8_t *res, int64_t ld, uint64_t *planes, void *stream) {
+  if (!valid_q(q) || rows < 0 || cols < 0 || ld < cols) return FQ_EINVAL;
+  if (rows == 0) return FQ_OK;
+  if (!planes || !aligned16(planes) || (cols > 0 && !res)) return FQ_EINVAL;
+  return fqk::launch_pack(q, rows, cols, res, ld, planes, static_cast<cudaStream_t>(stream));
+}
+
+int fq_unpack(int q, int64_t rows, int64_t cols, const uint64_t *planes, uint8_t *res, int64_t ld, void *stream) {
+  if (!valid_q(q) || rows < 0 || cols < 0 || ld < cols) return FQ_EINVAL;
+  if (rows == 0 || cols == 0) return FQ_OK;
+  if (!planes || !res || !aligned16(planes)) return FQ_EINVAL;
+  return fqk::launch_unpack(q, rows, cols, planes, res, ld, static_cast<cudaStream_t>(stream));
+}
+
+int fq_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t *Y, uint64_t *Z, int sub,
+           void *stream) {
+  if (!valid_q(q) || rows < 0 || cols < 0 || (sub != 0 && sub != 1)) return FQ_EINVAL;
+  if (rows == 0) return FQ_OK;
+  if (!X || !Y || !Z || !aligned16(X) || !aligned16(Y) || !aligned16(Z)) return FQ_EINVAL;
+  return fqk::launch_add(q, rows, cols, X, Y, Z, sub, static_cast<cudaStream_t>(stream));
+}
+
+int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+                 void *stream, const fq_options *opt) {
+  if (!valid_q(q) || m < 0 || l < 0 || n < 0) return FQ_EINVAL;
+  if (m == 0 || n == 0) return FQ_OK;
+  if (!C || !aligned16(C)) return FQ_EINVAL;
+  if (l > 0 && (!A || !B || !aligned16(A) || !aligned16(B))) return FQ_EINVAL;
+  if (l > 0 && (A == C || B == C)) return FQ_EINVAL;
+  if (l >= (int64_t(1) << 31) || m >= (int64_t(1) << 40) || n >= (int64_t(1) << 36)) return FQ_ENOTSUP;
+  fq_options o;
+  memset(&o, 0, sizeof(o));
+  if (opt) o = *opt;
+  if (o.path < FQ_PATH_AUTO || o.path > FQ_PATH_MMA) return FQ_EINVAL;
+  if (o.k != 0 && (o.k < 6 || o.k > 10)) return FQ_EINVAL;
+  if (o.chunk < 0 || o.variant < 0) return FQ_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (o.path == FQ_PATH_MMA) return FQ_ENOTSUP;
+  return fqk::launch_m4rm(q, m, l, n, A, B, C, o.k, o.variant, s);
+}
+
+int fq_matmul(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+              void *stream) {
+  return fq_matmul_ex(q, m, l, n, A, B, C, stream, nullptr);
+}
+
+int fq_status(void *stream) {
+  unsigned *err = nullptr;
+  if (int rc = fqk::status_word(&err)) return rc;
+  FQ_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  unsigned h = 0;
+  FQ_CUDA_TRY(cudaMemcpy(&h, err, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    const unsigned zero = 0;
+    FQ_CUDA_TRY(cudaMemcpy(err, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+  }
+  return int(h);
+}
+
+const char *fq_error_string(int status) {
+  switch (status) {
+    case FQ_OK: return "ok";
+    case FQ_EINVAL: return "invalid argument";
+    case FQ_EVALUE: return "residue out of range for the field";
+    case FQ_ECUDA: return "CUDA error";
+    case FQ_ETIMEOUT: return "bounded device wait timed out";
+    case FQ_ENOTSUP: return "not supported";
+    case FQ_ENOMEM: return "out of host memory";
+    default: return "unknown status";
+  }
+}
+
+const char *fq_last_cuda_error(void) { return fqk::t_last_cuda_error; }
+
+}  // extern "C"

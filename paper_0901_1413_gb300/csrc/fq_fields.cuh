@@ -1,0 +1,198 @@
+// Bitsliced field arithmetic on 32-bit plane words (Sections 3-4 of Boothby &
+// Bradshaw).  One call works on 32 elements: bit b of word p is bit p of the
+// code of element b.
+//
+// Each field type gives P (planes), D (size of the additive basis, Section 2),
+// add / sub on one column word, `accumulate` (acc += sum_d alpha_d t_d, the
+// Four-Russians inner step), `canon` (canonical codes) and `phi` (the binary
+// maps phi_d of Section 2 on 64-bit words of A's planes).
+#pragma once
+
+#include "fq_common.cuh"
+
+namespace fqk {
+
+// ------------------------------------------------------------------ F_3 ----
+// Codes (x0, x1): 0 = (0,0), 1 = (1,0), -1 = (1,1) (Section 4.1); basis {1, -1},
+// phi_0(a) = [a = 1], phi_1(a) = [a = -1].
+struct F3 {
+  static constexpr int Q = 3, P = 2, D = 2;
+
+  // x += y.  Section 4.1's six-gate add, with its outputs in the order that
+  // makes it exact (x0 = unit, x1 = sign), fused into four LOP3s:
+  //   u = x0 ^ y1, t = x1 ^ y0 ^ y1, x0' = (u ^ x1) | t, x1' = u & (x1 ^ y0).
+  __device__ __forceinline__ static void add(uint32_t &x0, uint32_t &x1, uint32_t y0, uint32_t y1) {
+    const uint32_t u = x0 ^ y1;
+    const uint32_t t = lop3<0x96>(x1, y0, y1);
+    const uint32_t r0 = lop3<0xBE>(u, x1, t);
+    const uint32_t r1 = lop3<0x60>(u, x1, y0);
+    x0 = r0;
+    x1 = r1;
+  }
+  // x -= y: the add above applied to -y = (y0, y0 ^ y1) (Section 4.1 negation),
+  // still four LOP3s.
+  __device__ __forceinline__ static void sub(uint32_t &x0, uint32_t &x1, uint32_t y0, uint32_t y1) {
+    const uint32_t u = lop3<0x96>(x0, y0, y1);
+    const uint32_t t = x1 ^ y1;
+    const uint32_t r0 = lop3<0xBE>(u, x1, t);
+    const uint32_t r1 = lop3<0x60>(u, x1, y0);
+    x0 = r0;
+    x1 = r1;
+  }
+  __device__ __forceinline__ static void add(uint32_t (&x)[P], const uint32_t (&y)[P]) {
+    add(x[0], x[1], y[0], y[1]);
+  }
+  __device__ __forceinline__ static void sub(uint32_t (&x)[P], const uint32_t (&y)[P]) {
+    sub(x[0], x[1], y[0], y[1]);
+  }
+  // acc += 1 * t[0] + (-1) * t[1]
+  __device__ __forceinline__ static void accumulate(uint32_t (&acc)[P], const uint32_t (&t)[D][P]) {
+    add(acc[0], acc[1], t[0][0], t[0][1]);
+    sub(acc[0], acc[1], t[1][0], t[1][1]);
+  }
+  __device__ __forceinline__ static void canon(uint32_t (&)[P]) {}
+  __device__ __forceinline__ static void phi(const uint64_t (&a)[P], uint64_t (&ph)[D]) {
+    ph[0] = a[0] & ~a[1];
+    ph[1] = a[0] & a[1];
+  }
+};
+
+// ---------------------------------------------------------------- GF(4) ----
+// GF(4) = F_2[x]/(x^2+x+1), element a0 + alpha a1, codes (a0, a1) (Section 4.3);
+// basis {1, alpha}, phi_d(a) = a_d; addition is XOR.
+struct GF4 {
+  static constexpr int Q = 4, P = 2, D = 2;
+  __device__ __forceinline__ static void add(uint32_t (&x)[P], const uint32_t (&y)[P]) {
+    x[0] ^= y[0];
+    x[1] ^= y[1];
+  }
+  __device__ __forceinline__ static void sub(uint32_t (&x)[P], const uint32_t (&y)[P]) { add(x, y); }
+  // acc += t[0] + alpha * t[1], alpha (b0 + alpha b1) = b1 + alpha (b0 + b1).
+  __device__ __forceinline__ static void accumulate(uint32_t (&acc)[P], const uint32_t (&t)[D][P]) {
+    acc[0] = lop3<0x96>(acc[0], t[0][0], t[1][1]);
+    acc[1] = lop3<0x96>(acc[1], t[0][1], t[1][0]) ^ t[1][1];
+  }
+  __device__ __forceinline__ static void canon(uint32_t (&)[P]) {}
+  __device__ __forceinline__ static void phi(const uint64_t (&a)[P], uint64_t (&ph)[D]) {
+    ph[0] = a[0];
+    ph[1] = a[1];
+  }
+};
+
+// ------------------------------------------------------- F_5 and F_7 shared --
+// Plain binary codes a2 a1 a0 read mod p, not unique (Section 4.2); basis {1,2,4}.
+
+// Grade-school add of two 3-bit codes into s3 s2 s1 s0 (Section 4.2's `add`).
+__device__ __forceinline__ void ripple3(const uint32_t (&x)[3], const uint32_t (&y)[3], uint32_t &s0,
+                                        uint32_t &s1, uint32_t &s2, uint32_t &s3) {
+  s0 = x[0] ^ y[0];
+  const uint32_t c0 = x[0] & y[0];
+  s1 = x[1] ^ y[1] ^ c0;
+  const uint32_t c1 = (x[1] & y[1]) | (c0 & (x[1] ^ y[1]));
+  s2 = x[2] ^ y[2] ^ c1;
+  s3 = (x[2] & y[2]) | (c1 & (x[2] ^ y[2]));
+}
+
+// ------------------------------------------------------------------ F_7 ----
+struct F7 {
+  static constexpr int Q = 7, P = 3, D = 3;
+  // x += y: s = add(x, y); x = add(s2 s1 s0, s3) -- the carry out of bit 2 is the
+  // unit bit mod 7 (Section 4.2); the second add never carries out.
+  __device__ __forceinline__ static void add(uint32_t (&x)[P], const uint32_t (&y)[P]) {
+    uint32_t s0, s1, s2, s3;
+    ripple3(x, y, s0, s1, s2, s3);
+    const uint32_t d0 = s0 & s3;
+    x[0] = s0 ^ s3;
+    x[1] = s1 ^ d0;
+    x[2] = s2 ^ (s1 & d0);
+  }
+  // x -= y: add the complement (negation is plane-wise NOT, Section 4.2).
+  __device__ __forceinline__ static void sub(uint32_t (&x)[P], const uint32_t (&y)[P]) {
+    const uint32_t n[P] = {~y[0], ~y[1], ~y[2]};
+    add(x, n);
+  }
+  // acc += t0 + 2 t1 + 4 t2; doubling is a rotation of the planes (Section 4.2).
+  __device__ __forceinline__ static void accumulate(uint32_t (&acc)[P], const uint32_t (&t)[D][P]) {
+    add(acc, t[0]);
+    const uint32_t d1[P] = {t[1][2], t[1][0], t[1][1]};
+    add(acc, d1);
+    const uint32_t d2[P] = {t[2][1], t[2][2], t[2][0]};
+    add(acc, d2);
+  }
+  // Canonical code: 7 (111) -> 0, others unchanged (Section 4.2's reduce with the
+  // common term read as a0 & a1 & a2).
+  __device__ __forceinline__ static void canon(uint32_t (&x)[P]) {
+    const uint32_t c = x[0] & x[1] & x[2];
+    x[0] ^= c;
+    x[1] ^= c;
+    x[2] ^= c;
+  }
+  __device__ __forceinline__ static void phi(const uint64_t (&a)[P], uint64_t (&ph)[D]) {
+    const uint64_t c = a[0] & a[1] & a[2];
+    ph[0] = a[0] ^ c;
+    ph[1] = a[1] ^ c;
+    ph[2] = a[2] ^ c;
+  }
+};
+
+// ------------------------------------------------------------------ F_5 ----
+struct F5 {
+  static constexpr int Q = 5, P = 3, D = 3;
+  // fold5: the 4-bit s3 s2 s1 s0 folded to three bits with the same value mod 5
+  // (Section 4.2, its eight-operation form).
+  __device__ __forceinline__ static void fold5(uint32_t s0, uint32_t s1, uint32_t s2, uint32_t s3,
+                                               uint32_t (&r)[P]) {
+    const uint32_t t = s2 | s1;
+    const uint32_t r2 = s0 ^ t;
+    const uint32_t r1 = (r2 & s0) ^ (s3 ^ s1);
+    r[0] = (t ^ s2) | (r1 & s3);
+    r[1] = r1;
+    r[2] = r2;
+  }
+  __device__ __forceinline__ static void add(uint32_t (&x)[P], const uint32_t (&y)[P]) {
+    uint32_t s0, s1, s2, s3;
+    ripple3(x, y, s0, s1, s2, s3);
+    fold5(s0, s1, s2, s3, x);
+  }
+  // 2x = fold5(x2 x1 x0 0)
+  __device__ __forceinline__ static void dbl(const uint32_t (&x)[P], uint32_t (&r)[P]) {
+    fold5(0u, x[0], x[1], x[2], r);
+  }
+  // -x = 4x = fold5(x1 x0 0 x2)
+  __device__ __forceinline__ static void neg(const uint32_t (&x)[P], uint32_t (&r)[P]) {
+    fold5(x[2], 0u, x[0], x[1], r);
+  }
+  __device__ __forceinline__ static void sub(uint32_t (&x)[P], const uint32_t (&y)[P]) {
+    uint32_t n[P];
+    neg(y, n);
+    add(x, n);
+  }
+  // acc += t0 + 2 t1 + 4 t2, with 4 = -1 mod 5.
+  __device__ __forceinline__ static void accumulate(uint32_t (&acc)[P], const uint32_t (&t)[D][P]) {
+    add(acc, t[0]);
+    uint32_t u[P];
+    dbl(t[1], u);
+    add(acc, u);
+    neg(t[2], u);
+    add(acc, u);
+  }
+  // Canonical code: 5, 6, 7 -> 0, 1, 2 (c marks codes >= 5).  Section 4.2's
+  // printed reduce is not a reduction; this one is derived from the code table.
+  __device__ __forceinline__ static void canon(uint32_t (&x)[P]) {
+    const uint32_t c = x[2] & (x[0] | x[1]);
+    const uint32_t r0 = (x[0] & ~c) | (c & x[1] & ~x[0]);
+    const uint32_t r1 = x[1] & (~c | x[0]);
+    const uint32_t r2 = x[2] & ~c;
+    x[0] = r0;
+    x[1] = r1;
+    x[2] = r2;
+  }
+  __device__ __forceinline__ static void phi(const uint64_t (&a)[P], uint64_t (&ph)[D]) {
+    const uint64_t c = a[2] & (a[0] | a[1]);
+    ph[0] = (a[0] & ~c) | (c & a[1] & ~a[0]);
+    ph[1] = a[1] & (~c | a[0]);
+    ph[2] = a[2] & ~c;
+  }
+};
+
+}  // namespace fqk

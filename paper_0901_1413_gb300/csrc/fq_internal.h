@@ -1,0 +1,18 @@
+// Internal launchers shared between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fqk {
+
+int launch_pack(int q, int64_t rows, int64_t cols, const uint8_t *res, int64_t ld, uint64_t *planes,
+                cudaStream_t s);
+int launch_unpack(int q, int64_t rows, int64_t cols, const uint64_t *planes, uint8_t *res, int64_t ld,
+                  cudaStream_t s);
+int launch_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t *Y, uint64_t *Z, int sub,
+               cudaStream_t s);
+int launch_m4rm(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+                int k, int variant, cudaStream_t s);
+
+}  // namespace fqk

@@ -1,0 +1,222 @@
+// Packing residues into bit-planes and back (Section 3, codes of Section 4), and
+// elementwise bitsliced add/sub.  All three are bandwidth-bound: one thread per
+// 64-element word of a row, grid-stride over rows x pitch.
+#include "fq_fields.cuh"
+#include "fq_internal.h"
+
+namespace fqk {
+
+namespace {
+
+constexpr uint32_t kLsb = 0x01010101u;
+
+// Gathers bit 0 of each byte of x (bits 0, 8, 16, 24) into bits 0..3.  The
+// partial products of x * 0x204081 land on distinct bit positions, so bits
+// 21..24 are exactly those four bits.
+__device__ __forceinline__ uint32_t gather_nibble(uint32_t x) { return ((x * 0x204081u) >> 21) & 0xFu; }
+
+// Inverse: bits 0..3 of n spread to bit 0 of each byte.
+__device__ __forceinline__ uint32_t spread_nibble(uint32_t n) { return (n * 0x204081u) & kLsb; }
+
+// Encodes 4 residues (bytes of v, element e at byte 0) into the plane words.
+template <int Q, int P>
+__device__ __forceinline__ void encode4(uint32_t v, uint64_t (&out)[P], int e, uint32_t &bad) {
+  // bytes >= Q: bit 7 of the byte set in m
+  const uint32_t m = (v & 0x80808080u) | (((v | 0x80808080u) - uint32_t(Q) * kLsb) & 0x80808080u);
+  bad |= m;
+  v &= ~((m >> 7) * 0xFFu);  // invalid residues are stored as 0
+  if (Q == 3) {
+    const uint32_t unit = (v | (v >> 1)) & kLsb;
+    const uint32_t sign = (v >> 1) & kLsb;
+    out[0] |= uint64_t(gather_nibble(unit)) << e;
+    out[1] |= uint64_t(gather_nibble(sign)) << e;
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) out[p] |= uint64_t(gather_nibble((v >> p) & kLsb)) << e;
+  }
+}
+
+template <int Q, int P>
+__global__ void pack_kernel(int64_t rows, int64_t cols, const uint8_t *__restrict__ res, int64_t ld,
+                            uint64_t *__restrict__ planes, int64_t pitch, unsigned *err, int vec16) {
+  const int64_t total = rows * pitch;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / pitch;
+    const int64_t w = i - r * pitch;
+    const int64_t c0 = w * 64;
+    uint64_t out[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) out[p] = 0;
+    uint32_t bad = 0;
+    if (c0 < cols) {
+      const uint8_t *src = res + r * ld + c0;
+      const int cnt = int(cols - c0 < 64 ? cols - c0 : 64);
+      if (vec16 && cnt == 64) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint4 v = __ldg(s4 + j);
+          encode4<Q, P>(v.x, out, 16 * j + 0, bad);
+          encode4<Q, P>(v.y, out, 16 * j + 4, bad);
+          encode4<Q, P>(v.z, out, 16 * j + 8, bad);
+          encode4<Q, P>(v.w, out, 16 * j + 12, bad);
+        }
+      } else {
+        for (int e = 0; e < cnt; e += 4) {
+          uint32_t v = 0;
+          for (int b = 0; b < 4 && e + b < cnt; ++b) v |= uint32_t(src[e + b]) << (8 * b);
+          encode4<Q, P>(v, out, e, bad);
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) planes[(p * rows + r) * pitch + w] = out[p];
+    if (bad) record_error(err, FQ_EVALUE);
+  }
+}
+
+// Residues of 4 elements (bytes) from the four code bits starting at element e.
+template <int Q, int P>
+__device__ __forceinline__ uint32_t decode4(const uint64_t (&in)[P], int e) {
+  uint32_t x[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) x[p] = spread_nibble(uint32_t(in[p] >> e) & 0xFu);
+  if (Q == 3) return x[0] + (x[0] & x[1]);          // (1,0) -> 1, (1,1) -> 2
+  if (Q == 4) return x[0] | (x[1] << 1);            // a0 + 2 a1
+  const uint32_t code = x[0] | (x[1] << 1) | (x[2] << 2);
+  if (Q == 7) {
+    const uint32_t seven = ((code + kLsb) >> 3) & kLsb;        // code == 7
+    return code - 7u * seven;
+  }
+  const uint32_t ge5 = ((code + 3u * kLsb) >> 3) & kLsb;       // code >= 5
+  return code - 5u * ge5;
+}
+
+template <int Q, int P>
+__global__ void unpack_kernel(int64_t rows, int64_t cols, const uint64_t *__restrict__ planes, int64_t pitch,
+                              uint8_t *__restrict__ res, int64_t ld, int vec16) {
+  const int64_t words = (cols + 63) / 64;
+  const int64_t total = rows * words;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / words;
+    const int64_t w = i - r * words;
+    uint64_t in[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) in[p] = __ldg(planes + (p * rows + r) * pitch + w);
+    const int64_t c0 = w * 64;
+    uint8_t *dst = res + r * ld + c0;
+    const int cnt = int(cols - c0 < 64 ? cols - c0 : 64);
+    if (vec16 && cnt == 64) {
+      uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint4 v;
+        v.x = decode4<Q, P>(in, 16 * j + 0);
+        v.y = decode4<Q, P>(in, 16 * j + 4);
+        v.z = decode4<Q, P>(in, 16 * j + 8);
+        v.w = decode4<Q, P>(in, 16 * j + 12);
+        d4[j] = v;
+      }
+    } else {
+      for (int e = 0; e < cnt; e += 4) {
+        const uint32_t v = decode4<Q, P>(in, e);
+        for (int b = 0; b < 4 && e + b < cnt; ++b) dst[e + b] = uint8_t(v >> (8 * b));
+      }
+    }
+  }
+}
+
+template <class F>
+__global__ void add_kernel(int64_t rows, int64_t pitch, const uint64_t *X, const uint64_t *Y, uint64_t *Z,
+                           int sub) {
+  constexpr int P = F::P;
+  const int64_t total = rows * pitch;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    uint32_t lo[P], hi[P], ylo[P], yhi[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const uint64_t x = X[p * total + i], y = Y[p * total + i];
+      lo[p] = uint32_t(x);
+      hi[p] = uint32_t(x >> 32);
+      ylo[p] = uint32_t(y);
+      yhi[p] = uint32_t(y >> 32);
+    }
+    if (sub) {
+      F::sub(lo, ylo);
+      F::sub(hi, yhi);
+    } else {
+      F::add(lo, ylo);
+      F::add(hi, yhi);
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) Z[p * total + i] = uint64_t(lo[p]) | (uint64_t(hi[p]) << 32);
+  }
+}
+
+inline int grid_for(int64_t total, int threads) {
+  const int64_t want = cdiv(total, threads);
+  const int64_t cap = 152 * 32;
+  return int(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+}  // namespace
+
+int launch_pack(int q, int64_t rows, int64_t cols, const uint8_t *res, int64_t ld, uint64_t *planes,
+                cudaStream_t s) {
+  unsigned *err = nullptr;
+  if (int rc = status_word(&err)) return rc;
+  const int64_t pitch = fq_pitch_words(cols);
+  const int64_t total = rows * pitch;
+  if (total == 0) return FQ_OK;
+  const int vec16 = (reinterpret_cast<uintptr_t>(res) % 16 == 0) && (ld % 16 == 0);
+  const int th = 256, gr = grid_for(total, th);
+  switch (q) {
+    case 3: pack_kernel<3, 2><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err, vec16); break;
+    case 4: pack_kernel<4, 2><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err, vec16); break;
+    case 5: pack_kernel<5, 3><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err, vec16); break;
+    case 7: pack_kernel<7, 3><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err, vec16); break;
+    default: return FQ_EINVAL;
+  }
+  FQ_LAUNCH_CHECK();
+  return FQ_OK;
+}
+
+int launch_unpack(int q, int64_t rows, int64_t cols, const uint64_t *planes, uint8_t *res, int64_t ld,
+                  cudaStream_t s) {
+  const int64_t pitch = fq_pitch_words(cols);
+  const int64_t total = rows * cdiv(cols, 64);
+  if (total == 0) return FQ_OK;
+  const int vec16 = (reinterpret_cast<uintptr_t>(res) % 16 == 0) && (ld % 16 == 0);
+  const int th = 256, gr = grid_for(total, th);
+  switch (q) {
+    case 3: unpack_kernel<3, 2><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld, vec16); break;
+    case 4: unpack_kernel<4, 2><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld, vec16); break;
+    case 5: unpack_kernel<5, 3><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld, vec16); break;
+    case 7: unpack_kernel<7, 3><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld, vec16); break;
+    default: return FQ_EINVAL;
+  }
+  FQ_LAUNCH_CHECK();
+  return FQ_OK;
+}
+
+int launch_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t *Y, uint64_t *Z, int sub,
+               cudaStream_t s) {
+  const int64_t pitch = fq_pitch_words(cols);
+  const int64_t total = rows * pitch;
+  if (total == 0) return FQ_OK;
+  const int th = 256, gr = grid_for(total, th);
+  switch (q) {
+    case 3: add_kernel<F3><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;
+    case 4: add_kernel<GF4><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;
+    case 5: add_kernel<F5><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;
+    case 7: add_kernel<F7><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;
+    default: return FQ_EINVAL;
+  }
+  FQ_LAUNCH_CHECK();
+  return FQ_OK;
+}
+
+}  // namespace fqk

@@ -1,0 +1,159 @@
+"""Python binding of the C ABI in ``include/fq.h`` (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libfq_gb300.so``; PyTorch is
+used only for device memory and streams.  There is no CPU path: if the library
+cannot be built or loaded, ``load()`` raises.
+
+A packed matrix is a ``Packed``: field size q, shape (rows, cols) and a flat
+int64 CUDA tensor holding the plane-major bit-planes (``fq_planes(q) * rows *
+fq_pitch_words(cols)`` 64-bit words).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+OK, EINVAL, EVALUE, ECUDA, ETIMEOUT, ENOTSUP, ENOMEM = range(7)
+PATH_AUTO, PATH_M4RM, PATH_MMA = 0, 1, 2
+
+_lib = None
+
+
+class FqError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = "%s failed: %s" % (what, _lib.fq_error_string(status).decode() if _lib else status)
+        if status == ECUDA and _lib is not None:
+            msg += " (%s)" % _lib.fq_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("k", ctypes.c_int), ("chunk", ctypes.c_int64),
+                ("variant", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+def load():
+    """Build (if stale) and load the CUDA library; returns the ctypes handle."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        sig = {
+            "fq_planes": (i32, [i32]),
+            "fq_pitch_words": (i64, [i64]),
+            "fq_planes_words": (i64, [i32, i64, i64]),
+            "fq_pack": (i32, [i32, i64, i64, vp, i64, vp, vp]),
+            "fq_unpack": (i32, [i32, i64, i64, vp, vp, i64, vp]),
+            "fq_add": (i32, [i32, i64, i64, vp, vp, vp, i32, vp]),
+            "fq_matmul": (i32, [i32, i64, i64, i64, vp, vp, vp, vp]),
+            "fq_matmul_ex": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, ctypes.POINTER(Options)]),
+            "fq_status": (i32, [vp]),
+            "fq_error_string": (ctypes.c_char_p, [i32]),
+            "fq_last_cuda_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise FqError(rc, what)
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def planes(q: int) -> int:
+    return load().fq_planes(q)
+
+
+def pitch_words(cols: int) -> int:
+    return load().fq_pitch_words(cols)
+
+
+@dataclass
+class Packed:
+    q: int
+    rows: int
+    cols: int
+    data: torch.Tensor  # flat int64, device
+
+    @property
+    def pitch(self) -> int:
+        return pitch_words(self.cols)
+
+    def planes_view(self) -> torch.Tensor:
+        """(planes, rows, pitch) view of the words."""
+        return self.data.view(planes(self.q), self.rows, self.pitch)
+
+
+def empty(q: int, rows: int, cols: int, device=None) -> Packed:
+    words = load().fq_planes_words(q, rows, cols)
+    if words < 0:
+        raise FqError(EINVAL, "fq_planes_words")
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    return Packed(q, rows, cols, torch.empty(max(words, 1), dtype=torch.int64, device=dev))
+
+
+def pack(q: int, res: torch.Tensor, out: Packed | None = None, stream=None) -> Packed:
+    """fq_pack: (rows, cols) uint8 CUDA tensor of residues -> Packed."""
+    if res.dtype != torch.uint8 or res.dim() != 2 or not res.is_cuda:
+        raise ValueError("expected a 2-D uint8 CUDA tensor")
+    if res.stride(1) != 1:
+        res = res.contiguous()
+    rows, cols = res.shape
+    out = empty(q, rows, cols, res.device) if out is None else out
+    _check(load().fq_pack(q, rows, cols, ctypes.c_void_p(res.data_ptr()), res.stride(0),
+                          ctypes.c_void_p(out.data.data_ptr()), _stream(stream)), "fq_pack")
+    return out
+
+
+def unpack(x: Packed, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """fq_unpack: Packed -> (rows, cols) uint8 residues on the same device."""
+    if out is None:
+        out = torch.empty((x.rows, x.cols), dtype=torch.uint8, device=x.data.device)
+    _check(load().fq_unpack(x.q, x.rows, x.cols, ctypes.c_void_p(x.data.data_ptr()),
+                            ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream(stream)), "fq_unpack")
+    return out
+
+
+def add(x: Packed, y: Packed, sub: bool = False, out: Packed | None = None, stream=None) -> Packed:
+    """fq_add: elementwise x + y (or x - y) with the bitsliced formulas."""
+    if (x.q, x.rows, x.cols) != (y.q, y.rows, y.cols):
+        raise ValueError("shape mismatch")
+    out = empty(x.q, x.rows, x.cols, x.data.device) if out is None else out
+    _check(load().fq_add(x.q, x.rows, x.cols, ctypes.c_void_p(x.data.data_ptr()),
+                         ctypes.c_void_p(y.data.data_ptr()), ctypes.c_void_p(out.data.data_ptr()),
+                         int(sub), _stream(stream)), "fq_add")
+    return out
+
+
+def matmul(a: Packed, b: Packed, out: Packed | None = None, path: int = PATH_AUTO, k: int = 0,
+           chunk: int = 0, variant: int = 0, stream=None) -> Packed:
+    """fq_matmul_ex: C = A B over F_q."""
+    if a.q != b.q or a.cols != b.rows:
+        raise ValueError("shape mismatch")
+    m, l, n = a.rows, a.cols, b.cols
+    out = empty(a.q, m, n, a.data.device) if out is None else out
+    opt = Options(path=path, k=k, chunk=chunk, variant=variant)
+    _check(load().fq_matmul_ex(a.q, m, l, n, ctypes.c_void_p(a.data.data_ptr()),
+                               ctypes.c_void_p(b.data.data_ptr()), ctypes.c_void_p(out.data.data_ptr()),
+                               _stream(stream), ctypes.byref(opt)), "fq_matmul")
+    return out
+
+
+def status(stream=None) -> int:
+    """fq_status: synchronize and return (and clear) device-detected errors."""
+    return load().fq_status(_stream(stream))

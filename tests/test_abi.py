@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every function include/fq.h declares, and the host-only calls behave.  No
+kernel is launched (this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fq.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fq_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0901_1413_gb300 import fq
+    return fq.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("fq_pack", "fq_unpack", "fq_matmul", "fq_matmul_ex", "fq_add", "fq_status"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_layout_helpers(lib):
+    assert [lib.fq_planes(q) for q in (2, 3, 4, 5, 6, 7, 8)] == [0, 2, 2, 3, 0, 3, 0]
+    assert lib.fq_pitch_words(0) == 0
+    assert lib.fq_pitch_words(1) == 16
+    assert lib.fq_pitch_words(1024) == 16
+    assert lib.fq_pitch_words(1025) == 32
+    assert lib.fq_pitch_words(-1) == -1
+    assert lib.fq_planes_words(5, 3, 65) == 3 * 3 * 16
+    assert lib.fq_planes_words(6, 3, 65) == -1
+
+
+def test_argument_errors_return_before_any_launch(lib):
+    from paper_0901_1413_gb300 import fq
+    vp = ctypes.c_void_p
+    # bad field, negative sizes, null or misaligned pointers: all EINVAL, no CUDA call
+    assert lib.fq_matmul(6, 4, 4, 4, vp(16), vp(32), vp(48), None) == fq.EINVAL
+    assert lib.fq_matmul(3, -1, 4, 4, vp(16), vp(32), vp(48), None) == fq.EINVAL
+    assert lib.fq_matmul(3, 4, 4, 4, None, vp(32), vp(48), None) == fq.EINVAL
+    assert lib.fq_matmul(3, 4, 4, 4, vp(16), vp(32), vp(8), None) == fq.EINVAL
+    assert lib.fq_matmul(3, 4, 4, 4, vp(16), vp(32), vp(16), None) == fq.EINVAL   # C aliases A
+    assert lib.fq_pack(3, 2, 70, vp(16), 69, vp(16), None) == fq.EINVAL           # ld < cols
+    assert lib.fq_unpack(5, 2, 3, None, vp(16), 3, None) == fq.EINVAL
+    assert lib.fq_add(3, 2, 3, vp(16), vp(16), vp(16), 2, None) == fq.EINVAL      # sub flag
+    opt = fq.Options(path=7)
+    assert lib.fq_matmul_ex(3, 4, 4, 4, vp(16), vp(32), vp(48), None, ctypes.byref(opt)) == fq.EINVAL
+    opt = fq.Options(k=11)
+    assert lib.fq_matmul_ex(3, 4, 4, 4, vp(16), vp(32), vp(48), None, ctypes.byref(opt)) == fq.EINVAL
+    # empty products are no-ops
+    assert lib.fq_matmul(3, 0, 4, 4, None, None, None, None) == fq.OK
+    assert lib.fq_matmul(3, 4, 4, 0, None, None, None, None) == fq.OK
+
+
+def test_error_strings(lib):
+    assert lib.fq_error_string(0) == b"ok"
+    assert lib.fq_error_string(4) == b"bounded device wait timed out"
+    assert lib.fq_error_string(99) == b"unknown status"

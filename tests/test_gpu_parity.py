@@ -1,0 +1,226 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Integer work: every comparison is bit-exact (zero tolerance)."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import encoding
+from paper_0901_1413_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = (3, 4, 5, 7)
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def gpu_pack(fq, q, R):
+    return fq.pack(q, to_dev(R))
+
+
+def gpu_product(fq, q, A, B, **kw):
+    a, b = gpu_pack(fq, q, A), gpu_pack(fq, q, B)
+    c = fq.matmul(a, b, **kw)
+    out = fq.unpack(c).cpu().numpy()
+    assert fq.status() == fq.OK
+    return out, c
+
+
+def packed_words(x):
+    """(planes, rows, ceil(cols/64)) uint64 from a Packed, plus its padding words."""
+    v = x.planes_view().cpu().numpy().view(np.uint64)
+    w = (x.cols + 63) // 64
+    return v[:, :, :w], v[:, :, w:]
+
+
+# ----------------------------------------------------------- pack / unpack --
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("shape", [(1, 1), (3, 63), (5, 64), (7, 65), (33, 1000), (2, 1100)])
+def test_pack_matches_oracle_encoding(fq, q, shape):
+    R = inputs.uniform(q, *shape, seed=11, stream=q)
+    x = gpu_pack(fq, q, R)
+    words, pad = packed_words(x)
+    assert np.array_equal(words, encoding.pack(q, R))
+    assert not pad.any()
+    assert np.array_equal(fq.unpack(x).cpu().numpy(), R)
+    assert fq.status() == fq.OK
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_pack_strided_and_unaligned_rows(fq, q):
+    R = inputs.uniform(q, 9, 203, seed=3, stream=0)
+    big = torch.zeros((9, 211), dtype=torch.uint8, device="cuda")
+    big[:, 5:208] = to_dev(R)
+    view = big[:, 5:208]                           # ld = 211, base not 16-byte aligned
+    x = fq.pack(q, view)
+    assert np.array_equal(packed_words(x)[0], encoding.pack(q, R))
+    out = torch.full((9, 300), 255, dtype=torch.uint8, device="cuda")
+    fq.unpack(x, out=out[:, 3:206])
+    o = out.cpu().numpy()
+    assert np.array_equal(o[:, 3:206], R)
+    assert (o[:, :3] == 255).all() and (o[:, 206:] == 255).all()
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_pack_rejects_out_of_range_residues(fq, q):
+    R = inputs.uniform(q, 4, 100, seed=5, stream=0)
+    R[2, 17] = q
+    R[3, 99] = 200
+    x = gpu_pack(fq, q, R)
+    assert fq.status() == fq.EVALUE
+    assert fq.status() == fq.OK                    # cleared
+    R2 = R.copy()
+    R2[2, 17] = 0
+    R2[3, 99] = 0
+    assert np.array_equal(fq.unpack(x).cpu().numpy(), R2)
+
+
+@pytest.mark.parametrize("q", [5, 7])
+def test_unpack_reduces_every_code(fq, q):
+    """Any 3-bit code is read mod p (Section 4.2: codes are not unique)."""
+    codes = np.arange(64, dtype=np.uint8) % 8
+    planes = np.zeros((3, 1, 16), np.uint64)
+    for p in range(3):
+        planes[p, 0, 0] = np.uint64(sum(int((c >> p) & 1) << j for j, c in enumerate(codes)))
+    x = fq.empty(q, 1, 64)
+    x.data.copy_(torch.from_numpy(planes.reshape(-1).view(np.int64)))
+    assert np.array_equal(fq.unpack(x).cpu().numpy()[0], codes % q)
+
+
+# ---------------------------------------- bitsliced add/sub, every code pair --
+
+def _code_planes(q, codes):
+    P = encoding.planes(q)
+    pl = np.zeros((P, 1, 16), np.uint64)
+    for p in range(P):
+        pl[p, 0, 0] = np.uint64(sum(int((int(c) >> p) & 1) << j for j, c in enumerate(codes)))
+    return pl
+
+
+def _value(q, code):
+    if q == 3:
+        return {0: 0, 1: 1, 3: 2}[code]
+    return code % q if q != 4 else code
+
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("sub", [False, True])
+def test_add_sub_every_code_pair(fq, q, sub):
+    codes = [0, 1, 3] if q == 3 else list(range(4 if q == 4 else 8))
+    pairs = list(itertools.product(codes, repeat=2))
+    assert len(pairs) <= 64
+    X = fq.empty(q, 1, 64)
+    Y = fq.empty(q, 1, 64)
+    X.data.copy_(torch.from_numpy(_code_planes(q, [a for a, _ in pairs]).reshape(-1).view(np.int64)))
+    Y.data.copy_(torch.from_numpy(_code_planes(q, [b for _, b in pairs]).reshape(-1).view(np.int64)))
+    Z = fq.add(X, Y, sub=sub)
+    got = fq.unpack(Z).cpu().numpy()[0, :len(pairs)]
+    for (a, b), g in zip(pairs, got):
+        va, vb = _value(q, a), _value(q, b)
+        if q == 4:
+            want = va ^ vb
+        else:
+            want = (va - vb) % q if sub else (va + vb) % q
+        assert g == want, (a, b)
+    if q == 3:   # F_3 codes stay valid: never (x0, x1) = (0, 1)
+        w = Z.planes_view().cpu().numpy().view(np.uint64)[:, 0, 0]
+        assert int(~w[0] & w[1] & np.uint64((1 << len(pairs)) - 1)) == 0
+
+
+# -------------------------------------------------------------- products --
+
+def _check_product(fq, q, m, l, n, seed, sparse=False, **kw):
+    A = (inputs.sparse if sparse else inputs.uniform)(q, m, l, seed=seed, stream=inputs.STREAM_A)
+    B = inputs.uniform(q, l, n, seed=seed, stream=inputs.STREAM_B)
+    got, c = gpu_product(fq, q, A, B, **kw)
+    want = oracle.matmul(q, A, B)
+    assert np.array_equal(got, want), "first mismatch at %s" % (np.argwhere(got != want)[:3].tolist(),)
+    # output planes are canonical codes with zero padding
+    words, pad = packed_words(c)
+    assert np.array_equal(words, encoding.pack(q, want))
+    assert not pad.any()
+
+
+def test_config1_f3_512(fq):
+    """F_3, A and B 512 x 512 uniform, k = 8, basis {1, -1}."""
+    _check_product(fq, 3, 512, 512, 512, seed=0, k=8)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("mln", [(1, 1, 1), (3, 7, 5), (37, 100, 70), (300, 64, 1024),
+                                 (513, 257, 1025), (1100, 520, 600)])
+def test_product_matches_oracle(fq, q, mln):
+    _check_product(fq, q, *mln, seed=sum(mln) + q)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_product_sparse_a(fq, q):
+    _check_product(fq, q, 700, 900, 600, seed=9, sparse=True)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_product_all_max_closed_form(fq, q):
+    """A, B filled with q-1: every entry is l (q-1)^2 mod q (GF(4): (alpha+1)^2 = alpha
+    summed l times)."""
+    m, l, n = 70, 1001, 130
+    A = np.full((m, l), q - 1, np.uint8)
+    B = np.full((l, n), q - 1, np.uint8)
+    got, _ = gpu_product(fq, q, A, B)
+    if q == 4:
+        want = 2 if l % 2 else 0
+    else:
+        want = (l * (q - 1) ** 2) % q
+    assert (got == want).all()
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_product_degenerate_shapes(fq, q):
+    # l = 0: C = 0
+    a = fq.empty(q, 5, 0)
+    b = fq.empty(q, 0, 70)
+    c = fq.empty(q, 5, 70)
+    c.data.fill_(-1)
+    fq.matmul(a, b, out=c)
+    assert not fq.unpack(c).cpu().numpy().any()
+    assert not c.data.cpu().numpy().any()
+    # m = 0 and n = 0 are no-ops
+    fq.matmul(fq.empty(q, 0, 9), fq.empty(q, 9, 4))
+    fq.matmul(fq.empty(q, 3, 9), fq.empty(q, 9, 0))
+    assert fq.status() == fq.OK
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_identity_and_permutation(fq, q):
+    n = 300
+    B = inputs.uniform(q, n, 200, seed=1, stream=1)
+    perm = np.random.default_rng(q).permutation(n)
+    Pm = np.zeros((n, n), np.uint8)
+    Pm[np.arange(n), perm] = 1
+    got, _ = gpu_product(fq, q, Pm, B)
+    assert np.array_equal(got, B[perm])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("q", FIELDS)
+def test_product_4096_full_oracle(fq, q):
+    _check_product(fq, q, 4096, 4096, 4096, seed=q)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n", [8192, 16384])
+def test_f3_large_sampled_rows_and_freivalds(fq, n):
+    """F_3 at n = 8192 and 16384: exact oracle rows for a sample, plus Freivalds."""
+    q = 3
+    A = inputs.uniform(q, n, n, seed=0, stream=inputs.STREAM_A)
+    B = inputs.uniform(q, n, n, seed=0, stream=inputs.STREAM_B)
+    got, _ = gpu_product(fq, q, A, B)
+    rows = np.random.default_rng(n).choice(n, size=24, replace=False)
+    assert np.array_equal(got[rows], oracle.matmul_rows(q, A, B, rows))
+    assert oracle.freivalds(q, A, B, got, trials=4)
