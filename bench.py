@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput of exact F_q matrix products on GB300: one JSON line on stdout.
+
+Workload (one step): the F_3 square products n = 4096, 8192 and 16384 with
+entries uniform on {0, 1, 2}, and n = 8192 with A 90% zeros (i.i.d.), by the
+bitsliced Method of Four Russians.  Metric: field operations per second,
+2 m l n / t (the paper's normalisation of a classical product's work).
+
+* ``value``: packed inputs resident in HBM, kernel time only (CUDA events on the
+  launching stream), L2 flushed before every step.
+* ``e2e``: the same products through the public API from pinned host residues:
+  host->device copy, fq_pack, fq_matmul, fq_unpack, device->host copy.
+* ``roofline``: the M4RM kernel against the integer-logic (LOP3) issue rate.
+* ``cpu_baseline``: the CPU oracle on a bounded sample of rows of the same
+  products, all host cores.
+
+``--impl reference`` times the oracle alone (the reference arm).  Under
+torchrun with N > 1 ranks every rank runs the whole workload on its own GPU
+(independent replicas, weak scaling) and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "F_q matmul 2mln/s: bitsliced M4RM vs INT8-TC path; batched products/s"
+UNIT = "field-ops/s (2mln/t)"
+Q = 3
+K_BLOCK = 8
+# (m, l, n, A law)
+PRODUCTS = [(4096, 4096, 4096, "uniform"), (8192, 8192, 8192, "uniform"),
+            (16384, 16384, 16384, "uniform"), (8192, 8192, 8192, "sparse90")]
+WORKLOAD = "F_3 square products n=4096, 8192, 16384 uniform + n=8192 with A 90% zeros"
+
+# Integer-logic issue rate: 64 LOP3 lane-ops per clock per SM (the ALU pipe;
+# measured 63.99 on this GPU), 152 SMs, 2070 MHz maximum SM clock.
+ALU_PEAK_TLOPS = 64 * 152 * 2.070e9 / 1e12
+LOP3_PER_ADD = 4     # F_3 add and subtract are four LOP3s per 32-element word pair
+BASIS = 2            # F_3 additive basis {1, -1}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def cdiv(a, b):
+    return -(-a // b)
+
+
+def algorithmic_lop3(m, l, n, k=K_BLOCK):
+    """LOP3 lane-ops of one F_3 product by M4RM: every (row, block, basis element)
+    lookup adds one table row (ceil(n/32) word pairs), and every block's table of
+    2^k - 1 nonzero combinations is built once."""
+    words = cdiv(n, 32)
+    blocks = cdiv(l, k)
+    return LOP3_PER_ADD * words * blocks * (m * BASIS + (2 ** k - 1))
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sizes", type=str, default="",
+                    help="comma-separated n list (uniform square products) instead of the workload")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=48, help="oracle rows sampled per product")
+    return ap.parse_args()
+
+
+def products_for(args):
+    if args.sizes:
+        return [(n, n, n, "uniform") for n in (int(x) for x in args.sizes.split(","))]
+    return PRODUCTS
+
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float, device) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def done(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="fq_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 7:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_sources_digest():
+    h = hashlib.sha256()
+    for name in ("fq_m4rm.cu", "fq_fields.cuh", "fq_common.cuh"):
+        with open(os.path.join(ROOT, "paper_0901_1413_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the M4RM kernel from the committed ncu summary,
+    if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "m4rm_f3_dram_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_sources_sha256_16") != kernel_sources_digest():
+        return None
+    return rec
+
+
+def make_inputs(torch, inputs, prods, seed=0):
+    out = []
+    for (m, l, n, law) in prods:
+        gen = inputs.sparse_torch if law == "sparse90" else inputs.uniform_torch
+        A = gen(Q, m, l, seed=seed, stream=inputs.STREAM_A, device="cuda")
+        B = inputs.uniform_torch(Q, l, n, seed=seed, stream=inputs.STREAM_B, device="cuda")
+        out.append((A, B))
+    return out
+
+
+def cpu_baseline(prods, rows_per_product, seed=0, steps=1):
+    """The oracle (as it stands) on the first rows_per_product rows of every product."""
+    import numpy as np
+
+    import oracle
+    from paper_0901_1413_gb300 import inputs
+    work = []
+    for (m, l, n, law) in prods:
+        r = min(rows_per_product, m)
+        A = (inputs.sparse if law == "sparse90" else inputs.uniform)(Q, r, l, seed=seed, stream=inputs.STREAM_A)
+        B = inputs.uniform(Q, l, n, seed=seed, stream=inputs.STREAM_B)
+        work.append((A, B, r, l, n))
+    oracle.matmul(Q, work[0][0][:1], work[0][1])          # load and warm
+    times = []
+    ops = sum(2.0 * r * l * n for (_, _, r, l, n) in work)
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        for (A, B, _, _, _) in work:
+            C = oracle.matmul(Q, A, B)
+            assert C.dtype == np.uint8
+        times.append(time.perf_counter() - t0)
+    return ops, times, oracle.threads_used(0), sum(r for (_, _, r, _, _) in work)
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    prods = products_for(args)
+    rows = max(1, min(args.cpu_rows, 16))
+    ops, times, cores, nrows = cpu_baseline(prods, rows, steps=args.warmup + args.steps)
+    t = times[args.warmup:]
+    mean = sum(t) / len(t)
+    value = ops / mean
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if not args.sizes else "F_3 square n=" + args.sizes, "q": Q,
+                   "sample": "first %d rows of each product" % rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "first %d rows of each of the %d products (%d rows total)"
+                                   % (rows, len(prods), nrows)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        dist.init("gloo")
+        run_reference(args, dist)
+        dist.done()
+        return
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+
+    import torch
+
+    from paper_0901_1413_gb300 import fq, inputs
+
+    torch.cuda.set_device(dist.local)
+    dist.init("nccl")
+    dev = torch.device("cuda", dist.local)
+    fq.load()
+    prods = products_for(args)
+
+    # ---- inputs, packed and resident -------------------------------------
+    res = make_inputs(torch, inputs, prods)
+    packed = []
+    for (A, B), (m, l, n, _) in zip(res, prods):
+        a, b = fq.pack(Q, A), fq.pack(Q, B)
+        packed.append((a, b, fq.empty(Q, m, n)))
+    if fq.status() != fq.OK:
+        raise SystemExit("device error while packing")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        for j, (a, b, c) in enumerate(packed):
+            if evs is not None:
+                evs[j][0].record(stream)
+            fq.matmul(a, b, out=c, k=K_BLOCK)
+            if evs is not None:
+                evs[j][1].record(stream)
+
+    for w in range(args.warmup):
+        flush.fill_(w)
+        step()
+    torch.cuda.synchronize()
+    if fq.status() != fq.OK:
+        raise SystemExit("device error during warm-up")
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "")) or str(dist.local)
+    clocks = ClockSampler(uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if len(uuid) > 30 else uuid))
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in packed]
+           for _ in range(args.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for s in range(args.steps):
+        flush.fill_(s + 1)
+        step(evs[s])
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    if fq.status() != fq.OK:
+        raise SystemExit("device error in the timed region")
+
+    per_launch = [[evs[s][j][0].elapsed_time(evs[s][j][1]) for j in range(len(packed))]
+                  for s in range(args.steps)]
+    step_ms = [evs[s][0][0].elapsed_time(evs[s][-1][1]) for s in range(args.steps)]
+    mean_ms = dist.max(sum(step_ms) / len(step_ms), dev)
+    ops_step = sum(2.0 * m * l * n for (m, l, n, _) in prods)
+    value = ops_step * dist.world / (mean_ms * 1e-3)
+
+    kernel_ms = sum(sum(r) for r in per_launch) / args.steps
+    lop3_step = sum(algorithmic_lop3(m, l, n) for (m, l, n, _) in prods)
+    achieved = lop3_step / (kernel_ms * 1e-3) / 1e12
+    traffic_rec = measured_traffic()
+    traffic = None
+    if traffic_rec is not None:
+        per = traffic_rec.get("bytes_per_launch", {})
+        vals = [per.get("%dx%dx%d" % (m, l, n)) for (m, l, n, _) in prods]
+        if all(v is not None for v in vals):
+            traffic = sum(vals) / len(vals)
+
+    # ---- end to end through the public API, host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        host = []
+        for (A, B), (m, l, n, _) in zip(res, prods):
+            host.append((A.cpu().pin_memory(), B.cpu().pin_memory(),
+                         torch.empty((m, n), dtype=torch.uint8).pin_memory()))
+        dbuf = [(torch.empty_like(A), torch.empty_like(B)) for (A, B) in res]
+        pk = [(fq.empty(Q, m, l), fq.empty(Q, l, n), fq.empty(Q, m, n), torch.empty((m, n), dtype=torch.uint8,
+                                                                                   device=dev))
+              for (m, l, n, _) in prods]
+
+        def e2e_step():
+            for (hA, hB, hC), (dA, dB), (a, b, c, dC) in zip(host, dbuf, pk):
+                dA.copy_(hA, non_blocking=True)
+                dB.copy_(hB, non_blocking=True)
+                fq.pack(Q, dA, out=a)
+                fq.pack(Q, dB, out=b)
+                fq.matmul(a, b, out=c, k=K_BLOCK)
+                fq.unpack(c, out=dC)
+                hC.copy_(dC, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_steps = max(3, min(args.steps, 10))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        if fq.status() != fq.OK:
+            raise SystemExit("device error in the end-to-end region")
+        e_ms = dist.max(e0.elapsed_time(e1) / e_steps, dev)
+        e2e = {"value": ops_step * dist.world / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": sum(m * l + l * n for (m, l, n, _) in prods),
+               "d2h_bytes_per_step": sum(m * n for (m, l, n, _) in prods),
+               "ms_per_step": e_ms, "steps": e_steps}
+
+    base = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        ops, times, cores, nrows = cpu_baseline(prods, args.cpu_rows)
+        base = {"value": ops / times[0], "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": "first %d rows of each of the %d products (%d rows), one pass"
+                          % (args.cpu_rows, len(prods), nrows)}
+
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if not args.sizes else "F_3 square n=" + args.sizes,
+                       "q": Q, "k": K_BLOCK, "products": [list(p) for p in prods],
+                       "path": "m4rm", "l2": "flushed (256 MiB write) before every step",
+                       "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TLOPS, "unit": "Tlop3/s",
+                         "frac": achieved / ALU_PEAK_TLOPS, "traffic": traffic,
+                         "peak_note": "derived: 64 LOP3 lanes/clk/SM x 152 SMs x 2070 MHz",
+                         "kernel_ms_per_step": kernel_ms},
+            "per_product_ms": [sum(r[j] for r in per_launch) / args.steps for j in range(len(prods))],
+            "e2e": e2e,
+            "cpu_baseline": base,
+            "clocks": clk,
+            "gpu_launches": args.steps * len(prods),
+        }
+        print(json.dumps(line), flush=True)
+    dist.done()
+
+
+if __name__ == "__main__":
+    main()

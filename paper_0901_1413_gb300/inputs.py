@@ -115,3 +115,67 @@ def batch_shapes(count: int, seed: int, lo: int = 64, hi: int = 1024, step: int 
     choices = (hi - lo) // step + 1
     h = hashes(seed, STREAM_SHAPES, 0, 3 * count)
     return (lo + step * _scale(h, choices).astype(np.int64)).reshape(count, 3)
+
+
+# ------------------------------------------------------ same draws, on a GPU --
+# The definitions above, evaluated with torch int64 arithmetic (wrapping
+# multiplication; logical shifts by masking), for large benchmark inputs.
+
+def _t_lsr(x, s: int):
+    import torch
+    return (x >> s) & torch.tensor((1 << (64 - s)) - 1, dtype=torch.int64, device=x.device)
+
+
+def _t_mix64(z):
+    import torch
+    c1 = torch.tensor(0xBF58476D1CE4E5B9 - (1 << 64), dtype=torch.int64, device=z.device)
+    c2 = torch.tensor(0x94D049BB133111EB - (1 << 64), dtype=torch.int64, device=z.device)
+    z = (z ^ _t_lsr(z, 30)) * c1
+    z = (z ^ _t_lsr(z, 27)) * c2
+    return z ^ _t_lsr(z, 31)
+
+
+def _as_i64(v: int) -> int:
+    v &= _MASK64
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _t_hashes(seed: int, stream: int, start: int, count: int, device):
+    import torch
+    s0 = stream_start(seed, stream)
+    i = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    g = torch.tensor(_as_i64(int(GAMMA)), dtype=torch.int64, device=device)
+    return _t_mix64(torch.tensor(_as_i64(s0), dtype=torch.int64, device=device) + i * g)
+
+
+def _t_scale(h, q: int):
+    hi = _t_lsr(h, 32)
+    lo = h & 0xFFFFFFFF
+    return (hi * q + _t_lsr(lo * q, 32)) >> 32
+
+
+def uniform_torch(q: int, rows: int, cols: int, seed: int, stream: int, device="cuda"):
+    """``uniform`` evaluated on a torch device; identical values."""
+    import torch
+    out = torch.empty((rows, cols), dtype=torch.uint8, device=device)
+    step = max(1, (1 << 24) // max(cols, 1))
+    for r in range(0, rows, step):
+        rr = min(step, rows - r)
+        h = _t_hashes(seed, stream, r * cols, rr * cols, device)
+        out[r:r + rr] = _t_scale(h, q).to(torch.uint8).view(rr, cols)
+    return out
+
+
+def sparse_torch(q: int, rows: int, cols: int, seed: int, stream: int, device="cuda"):
+    """``sparse`` evaluated on a torch device; identical values."""
+    import torch
+    out = torch.empty((rows, cols), dtype=torch.uint8, device=device)
+    step = max(1, (1 << 24) // max(cols, 1))
+    for r in range(0, rows, step):
+        rr = min(step, rows - r)
+        hm = _t_hashes(seed, stream, r * cols, rr * cols, device)
+        hv = _t_hashes(seed, stream + 1000, r * cols, rr * cols, device)
+        zero = _t_scale(hm, 10) < 9
+        val = (1 + _t_scale(hv, q - 1)).to(torch.uint8)
+        out[r:r + rr] = torch.where(zero, torch.zeros_like(val), val).view(rr, cols)
+    return out

@@ -45,3 +45,14 @@ def test_batch_shapes():
     assert sh.shape == (4096, 3)
     assert sh.min() == 64 and sh.max() == 1024 and np.all(sh % 64 == 0)
     assert abs(sh.mean() - 544) < 10
+
+
+def test_torch_generator_matches_numpy():
+    torch = __import__("torch")
+    for q in (3, 5, 7, 4):
+        a = inputs.uniform(q, 17, 301, seed=4, stream=1)
+        b = inputs.uniform_torch(q, 17, 301, seed=4, stream=1, device="cpu").numpy()
+        assert np.array_equal(a, b)
+    s = inputs.sparse(5, 9, 777, seed=3, stream=0)
+    assert np.array_equal(s, inputs.sparse_torch(5, 9, 777, seed=3, stream=0, device="cpu").numpy())
+    assert torch is not None
