@@ -1,0 +1,434 @@
+// Warp-specialised Four-Russians kernel for the two-plane fields (F_3, GF(4)).
+//
+// Same product as fq_m4rm.cuh (Section 2 of Boothby & Bradshaw):
+//   C_i = sum_s sum_d alpha_d T_s[phi_d(A_i, block s)],  T_s[b] = sum_t b_t B_{sk+t},
+// but the work of one block is split between two kinds of warps so that the
+// lookups -- the part that scales with the rows -- never wait for the rest:
+//
+//  * 4 producer warps (one warpgroup, few registers): stage A's words one chunk
+//    of NB blocks ahead (cp.async), turn the k-bit fields phi_d(A_i, block s) of
+//    a whole chunk into table byte offsets for every row of the tile (two 16-bit
+//    offsets per word), and build T_s in shared memory from the TMA-loaded B
+//    block (16 builder groups, each walking 2^(k-4) entries with one bitsliced
+//    add per entry).
+//  * 12 consumer warps (three warpgroups, most registers): for every block,
+//    gather D table entries per row and add them into register accumulators.
+//
+// Tables are double-buffered by block and offsets by chunk: while consumers
+// read table s & 1, producers fill table (s + 1) & 1, and the offsets of chunk
+// c + 1 are written while chunk c is consumed.  Hand-over is by mbarriers (tfull: 128
+// producer arrivals; tempty: 384 consumer arrivals).  Every wait is bounded;
+// on a timeout the CTA records FQ_ETIMEOUT, stops waiting and runs out its
+// loops without further synchronisation hazards.
+#pragma once
+
+#include <cstring>
+
+#include "fq_fields.cuh"
+#include "fq_internal.h"
+
+namespace fqk {
+
+namespace ws {
+
+__host__ __device__ constexpr int popc(int x) { return x == 0 ? 0 : (x & 1) + popc(x >> 1); }
+__host__ __device__ constexpr int ctz(int x) { return (x & 1) ? 0 : 1 + ctz(x >> 1); }
+constexpr int round128(int x) { return (x + 127) / 128 * 128; }
+
+template <class F, int K_, int RS_>
+struct Cfg {
+  using Field = F;
+  static_assert(F::P == 2 && F::D == 2, "two planes, basis of two");
+  static constexpr int K = K_;        // block size
+  static constexpr int RS = RS_;      // row slots per consumer warp (even)
+  static_assert(RS % 2 == 0, "slots are read in pairs");
+  static constexpr int P = 2, D = 2;
+  static constexpr int LPR = 8, GPW = 4, WPL = 2, PW = 4;  // 8-lane groups, 2 words per plane
+  static constexpr int NPW = 4, NCW = 12;                   // producer / consumer warps
+  static constexpr int NT = (NPW + NCW) * 32;
+  static constexpr int NPT = NPW * 32;                      // producer threads
+  static constexpr int PREG = 80, CREG = 144;               // registers after setmaxnreg
+  static_assert(NPT * PREG + NCW * 32 * CREG == 65536, "register split");
+  static constexpr int ENTRY = 128;                         // bytes per table entry
+  static constexpr int ENTRIES = 1 << K;
+  static constexpr int CT = 512, CTW = 8;                   // columns (words) per tile
+  static constexpr int ROWS_PER_SLOT = NCW * GPW;           // 48
+  static constexpr int MT = RS * ROWS_PER_SLOT;             // rows per CTA
+  static constexpr int NBUILD = NPW * GPW;                  // 16 builder groups
+  static constexpr int LB = K - 4, HB = 4, EPB = 1 << LB;
+  static_assert(K >= 6 && K <= 9, "k in 6..9 (offsets idx * 128 fit 16 bits)");
+  static constexpr int NB = 64 / K;                         // blocks per A chunk
+  static constexpr int STAGE_BYTES = P * K * CTW * 8;
+  static constexpr int STAGE_STRIDE = round128(STAGE_BYTES);
+  static constexpr int TABLE_BYTES = ENTRIES * ENTRY;
+  static constexpr int OFFS_BYTES = NB * MT * 4;            // one chunk: [b][pair][48][2] uint32
+  static constexpr int ASTAGE_BYTES = P * MT * 16;          // [p][r][2] uint64
+  static constexpr int TABLE_OFF = 0;
+  static constexpr int OFFS_OFF = 2 * TABLE_BYTES;
+  static constexpr int BSTAGE_OFF = OFFS_OFF + 2 * OFFS_BYTES;
+  static constexpr int ASTAGE_OFF = BSTAGE_OFF + 2 * STAGE_STRIDE;
+  static constexpr int BAR_OFF = ASTAGE_OFF + ASTAGE_BYTES;  // bfull[2], tfull[2], tempty[2]
+  static constexpr int ABORT_OFF = BAR_OFF + 48;
+  static constexpr int SMEM = ABORT_OFF + 16;
+  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+};
+
+struct Params {
+  const uint64_t *A;
+  uint64_t *C;
+  int64_t m, l;
+  int64_t pa, pc;   // row pitches (words) of A and of B, C
+  int64_t nblocks;  // ceil(l / K)
+  int mt;           // rows per CTA (<= MT)
+  uint32_t one;     // the constant 1 as data: address adds stay on IMAD
+  unsigned *err;
+};
+
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ int64_t cdiv_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void lds128(uint32_t addr, uint32_t (&v)[4]) {
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(addr));
+}
+__device__ __forceinline__ void sts128(uint32_t addr, const uint32_t (&v)[4]) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+
+// Bounded wait that also gives up at once when the CTA has aborted.
+__device__ __forceinline__ void wait_or_abort(uint32_t bar, uint32_t parity, volatile int &abort_flag,
+                                              unsigned *err) {
+  if (abort_flag) return;
+  if (!mbar_wait_bounded(bar, parity)) {
+    abort_flag = 1;
+    record_error(err, FQ_ETIMEOUT);
+  }
+}
+
+// ------------------------------------------------------------- producers --
+
+// Stage words wlo, wlo + 1 of both planes of the tile's rows, layout [p][r][2].
+template <class C>
+__device__ __forceinline__ void stage_a(const Params &prm, uint32_t astage, int64_t row0, int rows_here,
+                                        int64_t wlo, int ptid) {
+  for (int e = ptid; e < C::P * C::MT * 2; e += C::NPT) {
+    const int j = e & 1;
+    const int r = (e >> 1) % C::MT;
+    const int p = (e >> 1) / C::MT;
+    const int64_t w = wlo + j;
+    if (r < rows_here && w < prm.pa) cp_async8(astage + uint32_t(e) * 8u, prm.A + (p * prm.m + row0 + r) * prm.pa + w);
+  }
+  cp_async_commit();
+}
+
+// Offsets of phi_d(A_r, block s) for the blocks s = c0 .. c0 + nb - 1 of a
+// chunk and every row of the tile, packed off0 | off1 << 16 (off = idx * 128).
+// Layout [b][slot pair][48 rows][2 slots] so that a consumer warp reads two
+// slots of its four row groups in one 32-byte wavefront.
+template <class C>
+__device__ __forceinline__ void build_offsets(const Params &prm, const unsigned char *astage, uint32_t *offs,
+                                              int rows_here, int64_t c0, int nb, int ptid) {
+  using F = typename C::Field;
+  const int64_t bit0 = c0 * C::K;
+  const int sh = int(bit0 & 63);
+  const uint64_t *as = reinterpret_cast<const uint64_t *>(astage);
+  for (int r = ptid; r < C::MT; r += C::NPT) {
+    uint64_t win[2];
+    if (r < rows_here) {
+      uint64_t f[2];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const uint64_t w0 = as[(p * C::MT + r) * 2 + 0];
+        const uint64_t w1 = as[(p * C::MT + r) * 2 + 1];
+        f[p] = sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;   // the chunk's 64 bits
+      }
+      F::phi(f, win);
+      // bits past column l (and past the staged words) are not part of A
+      const int64_t valid = prm.l - bit0;
+      if (valid < 64) {
+        const uint64_t keep = (uint64_t(1) << valid) - 1u;
+        win[0] &= keep;
+        win[1] &= keep;
+      }
+    } else {
+      win[0] = win[1] = 0ull;
+    }
+    const int i = r / C::ROWS_PER_SLOT, rem = r % C::ROWS_PER_SLOT;
+    uint32_t *dst = offs + ((i >> 1) * C::ROWS_PER_SLOT + rem) * 2 + (i & 1);
+    const uint32_t mask = (1u << C::K) - 1u;
+#pragma unroll
+    for (int b = 0; b < C::NB; ++b) {
+      if (b < nb) {
+        const uint32_t i0 = uint32_t(win[0] >> (b * C::K)) & mask;
+        const uint32_t i1 = uint32_t(win[1] >> (b * C::K)) & mask;
+        dst[b * (C::MT)] = (i0 * uint32_t(C::ENTRY)) | ((i1 * uint32_t(C::ENTRY)) << 16);
+      }
+    }
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void load_brow(uint32_t stage, int t, int gl, uint32_t (&v)[4]) {
+  // stage layout [p][row][16 x 32-bit]; lane gl's words of plane p at gl * 2
+  const uint32_t a0 = stage + uint32_t((0 * C::K + t) * 64 + gl * 8);
+  const uint32_t a1 = stage + uint32_t((1 * C::K + t) * 64 + gl * 8);
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v[0]), "=r"(v[1]) : "r"(a0));
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v[2]), "=r"(v[3]) : "r"(a1));
+}
+
+// entry layout (per lane, 16 bytes): plane 0 words 0..1, plane 1 words 0..1
+template <class F>
+__device__ __forceinline__ void add_lane(uint32_t (&x)[4], const uint32_t (&y)[4]) {
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    uint32_t a[2] = {x[w], x[2 + w]}, b[2] = {y[w], y[2 + w]};
+    F::add(a, b);
+    x[w] = a[0];
+    x[2 + w] = a[1];
+  }
+}
+
+template <class C, int X>
+__device__ __forceinline__ void build_walk(uint32_t (&S)[C::LB + 1][4], const uint32_t (&rows)[C::LB][4],
+                                           uint32_t tbl_lane, int e0) {
+  if constexpr (X < C::EPB) {
+    constexpr int pc = popc(X), tz = ctz(X);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) S[pc][j] = S[pc - 1][j];
+    add_lane<typename C::Field>(S[pc], rows[tz]);
+    sts128(tbl_lane + uint32_t((e0 + X) * C::ENTRY), S[pc]);
+    build_walk<C, X + 1>(S, rows, tbl_lane, e0);
+  }
+}
+
+// Builder j (0..15) fills entries [j EPB, (j + 1) EPB): high bits j over rows
+// LB..K-1 summed once, then the LB low rows walked (entry x = parent
+// x & (x - 1) plus row ctz(x); the parent is the last entry with one bit less).
+template <class C>
+__device__ __forceinline__ void build_table(uint32_t tbl_lane, uint32_t stage, int builder, int gl) {
+  uint32_t rows[C::LB][4];
+#pragma unroll
+  for (int t = 0; t < C::LB; ++t) load_brow<C>(stage, t, gl, rows[t]);
+  uint32_t S[C::LB + 1][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) S[0][j] = 0u;
+#pragma unroll
+  for (int t = 0; t < C::HB; ++t) {
+    if ((builder >> t) & 1) {
+      uint32_t r[4];
+      load_brow<C>(stage, C::LB + t, gl, r);
+      add_lane<typename C::Field>(S[0], r);
+    }
+  }
+  const int e0 = builder * C::EPB;
+  sts128(tbl_lane + uint32_t(e0 * C::ENTRY), S[0]);
+  build_walk<C, 1>(S, rows, tbl_lane, e0);
+}
+
+// ------------------------------------------------------------- consumers --
+
+template <class C>
+__device__ __forceinline__ void lookup_block(uint32_t (&acc)[C::RS][4], uint32_t tbl_lane, uint32_t offs_s, int cw,
+                                             int grp, uint32_t one) {
+  using F = typename C::Field;
+#pragma unroll
+  for (int j = 0; j < C::RS / 2; ++j) {
+    uint32_t o[2];
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                 : "=r"(o[0]), "=r"(o[1]) : "r"(offs_s + uint32_t(((j * C::ROWS_PER_SLOT) + cw * C::GPW + grp) * 8)));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * j + h;
+      // off1 = o >> 16 and off0 = o - off1 * 2^16, both as IMADs
+      const uint32_t hi = __umulhi(o[h], 65536u);
+      const uint32_t a1 = imad(hi, one, tbl_lane);
+      const uint32_t a0 = imad(hi, 0xFFFF0000u, imad(o[h], one, tbl_lane));
+      uint32_t t0[4], t1[4];
+      lds128(a0, t0);
+      lds128(a1, t1);
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        uint32_t a[2] = {acc[i][w], acc[i][2 + w]};
+        const uint32_t tt[2][2] = {{t0[w], t0[2 + w]}, {t1[w], t1[2 + w]}};
+        F::accumulate(a, tt);
+        acc[i][w] = a[0];
+        acc[i][2 + w] = a[1];
+      }
+    }
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant__ CUtensorMap tmB, const Params prm) {
+  using F = typename C::Field;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = lane >> 3, gl = lane & 7;
+  const int64_t row0 = int64_t(blockIdx.y) * prm.mt;
+  const int rows_here = int(prm.m - row0 < prm.mt ? prm.m - row0 : prm.mt);
+  const int64_t w0 = int64_t(blockIdx.x) * C::CTW;
+
+  const uint32_t base = smem_u32(smem);
+  const uint32_t bfull = base + C::BAR_OFF, tfull = bfull + 16, tempty = bfull + 32;
+  volatile int &abort_flag = *reinterpret_cast<int *>(smem + C::ABORT_OFF);
+
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(bfull, 1);
+    mbar_init(bfull + 8, 1);
+    mbar_init(tfull, C::NPT);
+    mbar_init(tfull + 8, C::NPT);
+    mbar_init(tempty, C::NCW * 32);
+    mbar_init(tempty + 8, C::NCW * 32);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp < C::NPW) {
+    // ------------------------------------------------------- producers
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(C::PREG));
+    const int ptid = tid;
+    const int builder = warp * C::GPW + grp;
+    const uint32_t tbl_lane0 = base + C::TABLE_OFF + uint32_t(gl * 16);
+    if (ptid == 0) {
+      for (int64_t s = 0; s < 2 && s < prm.nblocks; ++s) {
+        mbar_expect_tx(bfull + 8 * uint32_t(s), C::STAGE_BYTES);
+        tma_load_3d(base + C::BSTAGE_OFF + uint32_t(s) * C::STAGE_STRIDE, &tmB, bfull + 8 * uint32_t(s), int(w0),
+                    int(s * C::K), 0);
+      }
+    }
+    const uint32_t astage = base + C::ASTAGE_OFF;
+    const unsigned char *astage_p = smem + C::ASTAGE_OFF;
+    const int64_t nchunks = cdiv_dev(prm.nblocks, C::NB);
+    uint32_t *const offs0 = reinterpret_cast<uint32_t *>(smem + C::OFFS_OFF);  // chunk buffers 0, 1
+    // prologue: offsets of chunk 0, A words of chunk 1 in flight
+    if (prm.nblocks > 0) {
+      stage_a<C>(prm, astage, row0, rows_here, 0, ptid);
+      cp_async_wait_all();
+      producer_sync();
+      build_offsets<C>(prm, astage_p, offs0, rows_here, 0, int(prm.nblocks < C::NB ? prm.nblocks : C::NB), ptid);
+      producer_sync();
+      if (nchunks > 1) stage_a<C>(prm, astage, row0, rows_here, (C::NB * C::K) >> 6, ptid);
+    }
+    for (int64_t s = 0; s < prm.nblocks; ++s) {
+      const int buf = int(s & 1);
+      const uint32_t use = uint32_t(s >> 1);
+      if (s % C::NB == 0) {
+        // start of chunk c: write the offsets of chunk c + 1 into the buffer
+        // chunk c - 1 used (free once block s - 1 is consumed), then prefetch
+        // the A words of chunk c + 2
+        const int64_t c = s / C::NB;
+        if (c + 1 < nchunks) {
+          if (s >= 1) wait_or_abort(tempty + 8 * ((s - 1) & 1), uint32_t((s - 1) >> 1) & 1, abort_flag, prm.err);
+          cp_async_wait_all();
+          producer_sync();
+          const int64_t c1 = (c + 1) * C::NB;
+          build_offsets<C>(prm, astage_p, offs0 + ((c + 1) & 1) * (C::OFFS_BYTES / 4), rows_here, c1,
+                           int(prm.nblocks - c1 < C::NB ? prm.nblocks - c1 : C::NB), ptid);
+          producer_sync();
+          if (c + 2 < nchunks) stage_a<C>(prm, astage, row0, rows_here, (((c + 2) * C::NB) * C::K) >> 6, ptid);
+        }
+      }
+      if (s >= 2) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
+      wait_or_abort(bfull + 8 * buf, use & 1, abort_flag, prm.err);
+      build_table<C>(tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), base + C::BSTAGE_OFF + buf * C::STAGE_STRIDE,
+                     builder, gl);
+      producer_sync();  // every producer is done with this B stage
+      if (ptid == 0 && s + 2 < prm.nblocks && !abort_flag) {
+        fence_proxy_async_smem();
+        mbar_expect_tx(bfull + 8 * buf, C::STAGE_BYTES);
+        tma_load_3d(base + C::BSTAGE_OFF + buf * C::STAGE_STRIDE, &tmB, bfull + 8 * buf, int(w0),
+                    int((s + 2) * C::K), 0);
+      }
+      mbar_arrive(tfull + 8 * buf);
+    }
+    cp_async_wait_all();
+  } else {
+    // ------------------------------------------------------- consumers
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(C::CREG));
+    const int cw = warp - C::NPW;
+    const uint32_t tbl_lane0 = base + C::TABLE_OFF + uint32_t(gl * 16);
+    uint32_t acc[C::RS][4];
+#pragma unroll
+    for (int i = 0; i < C::RS; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0u;
+    for (int64_t s = 0; s < prm.nblocks; ++s) {
+      const int buf = int(s & 1);
+      wait_or_abort(tfull + 8 * buf, uint32_t(s >> 1) & 1, abort_flag, prm.err);
+      const int64_t c = s / C::NB;
+      const uint32_t offs_s =
+          base + C::OFFS_OFF + uint32_t(c & 1) * C::OFFS_BYTES + uint32_t((s - c * C::NB) * C::MT) * 4u;
+      lookup_block<C>(acc, tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), offs_s, cw, grp, prm.one);
+      mbar_arrive(tempty + 8 * buf);
+    }
+    // epilogue: canonical codes (F_3 and GF(4) codes are already canonical)
+#pragma unroll
+    for (int i = 0; i < C::RS; ++i) {
+      const int r = i * C::ROWS_PER_SLOT + cw * C::GPW + grp;
+      if (r < rows_here) {
+        const int64_t row = row0 + r;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          uint32_t *dst = reinterpret_cast<uint32_t *>(prm.C + (p * prm.m + row) * prm.pc + w0) + gl * 2;
+          *reinterpret_cast<uint2 *>(dst) = make_uint2(acc[i][2 * p + 0], acc[i][2 * p + 1]);
+        }
+      }
+    }
+  }
+}
+
+template <class C>
+int launch(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *Cm, int mt,
+           cudaStream_t s) {
+  unsigned *err = nullptr;
+  if (int rc = status_word(&err)) return rc;
+  if (mt < 1 || mt > C::MT) return FQ_EINVAL;
+  Params prm;
+  prm.A = A;
+  prm.C = Cm;
+  prm.m = m;
+  prm.l = l;
+  prm.pa = fq_pitch_words(l);
+  prm.pc = fq_pitch_words(n);
+  prm.nblocks = cdiv(l, C::K);
+  prm.mt = mt;
+  prm.one = 1u;
+  prm.err = err;
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  if (l > 0) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (int rc = tensor_map_encoder(&encode)) return rc;
+    const cuuint64_t dims[3] = {cuuint64_t(prm.pc), cuuint64_t(l), cuuint64_t(C::P)};
+    const cuuint64_t strides[2] = {cuuint64_t(prm.pc) * 8u, cuuint64_t(prm.pc) * 8u * cuuint64_t(l)};
+    const cuuint32_t box[3] = {cuuint32_t(C::CTW), cuuint32_t(C::K), cuuint32_t(C::P)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<uint64_t *>(B), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return FQ_EINVAL;
+  }
+  FQ_CUDA_TRY(cudaFuncSetAttribute(m4rm_ws_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  const dim3 grid(unsigned(prm.pc / C::CTW), unsigned(cdiv(m, mt)));
+  if (grid.y > 65535u) return FQ_ENOTSUP;
+  m4rm_ws_kernel<C><<<grid, C::NT, C::SMEM, s>>>(map, prm);
+  FQ_LAUNCH_CHECK();
+  return FQ_OK;
+}
+
+}  // namespace ws
+
+}  // namespace fqk

@@ -224,3 +224,32 @@ def test_f3_large_sampled_rows_and_freivalds(fq, n):
     rows = np.random.default_rng(n).choice(n, size=24, replace=False)
     assert np.array_equal(got[rows], oracle.matmul_rows(q, A, B, rows))
     assert oracle.freivalds(q, A, B, got, trials=4)
+
+
+@pytest.mark.parametrize("q,k", [(3, 6), (3, 7), (3, 9), (3, 10), (4, 6), (4, 9), (4, 10),
+                                 (5, 6), (5, 7), (7, 6), (7, 7)])
+def test_every_block_size(fq, q, k):
+    """k = 6, 7, 9, 10 do not divide 64: indices straddle A's words."""
+    _check_product(fq, q, 333, 777, 600, seed=k, k=k)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("mt", [1, 5, 33, 200])
+def test_forced_rows_per_cta(fq, q, mt):
+    """Tiles of any height, including partial row slots."""
+    _check_product(fq, q, 410, 300, 520, seed=mt, variant=mt)
+
+
+@pytest.mark.parametrize("q,kmax", [(3, 10), (5, 8)])
+def test_unsupported_block_size_is_reported(fq, q, kmax):
+    a = fq.empty(q, 4, 4)
+    b = fq.empty(q, 4, 4)
+    a.data.zero_()
+    b.data.zero_()
+    if kmax < 10:
+        with pytest.raises(fq.FqError) as e:
+            fq.matmul(a, b, k=kmax + 1)
+        assert e.value.status == fq.ENOTSUP
+    with pytest.raises(fq.FqError) as e:
+        fq.matmul(a, b, variant=100000)
+    assert e.value.status == fq.EINVAL
