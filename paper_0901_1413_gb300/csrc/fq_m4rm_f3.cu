@@ -22,7 +22,7 @@ const Variant kVariants[] = {
     {8, 12, &run_ws<ws::Cfg<F3, 8, 12>>, 48},
     {8, 8, &run_ws<ws::Cfg<F3, 8, 8>>, 48},
     {8, 4, &run_ws<ws::Cfg<F3, 8, 4>>, 48},
-    {9, 22, &run_ws<ws::Cfg<F3, 9, 22>>, 48},
+    {9, 16, &run_ws<ws::Cfg<F3, 9, 16>>, 48},
     {7, 24, &run_ws<ws::Cfg<F3, 7, 24>>, 48},
     {6, 24, &run_ws<ws::Cfg<F3, 6, 24>>, 48},
     {10, 16, &run<M4rmCfg<F3, 10, 8, 2, 16, 16>>, 64},

@@ -22,7 +22,7 @@ const Variant kVariants[] = {
     {8, 12, &run_ws<ws::Cfg<GF4, 8, 12>>, 48},
     {8, 8, &run_ws<ws::Cfg<GF4, 8, 8>>, 48},
     {8, 4, &run_ws<ws::Cfg<GF4, 8, 4>>, 48},
-    {9, 22, &run_ws<ws::Cfg<GF4, 9, 22>>, 48},
+    {9, 16, &run_ws<ws::Cfg<GF4, 9, 16>>, 48},
     {7, 24, &run_ws<ws::Cfg<GF4, 7, 24>>, 48},
     {6, 24, &run_ws<ws::Cfg<GF4, 6, 24>>, 48},
     {10, 16, &run<M4rmCfg<GF4, 10, 8, 2, 16, 16>>, 64},

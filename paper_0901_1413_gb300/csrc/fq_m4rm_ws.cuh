@@ -6,7 +6,7 @@
 // lookups -- the part that scales with the rows -- never wait for the rest:
 //
 //  * 4 producer warps (one warpgroup, few registers): stage A's words one chunk
-//    of NB blocks ahead (cp.async), turn the k-bit fields phi_d(A_i, block s) of
+//    of NB blocks ahead (TMA boxes of 4 words x 96 rows x 2 planes), turn the k-bit fields phi_d(A_i, block s) of
 //    a whole chunk into table byte offsets for every row of the tile (two 16-bit
 //    offsets per word), and build T_s in shared memory from the TMA-loaded B
 //    block (16 builder groups, each walking 2^(k-4) entries with one bitsliced
@@ -62,13 +62,18 @@ struct Cfg {
   static constexpr int STAGE_STRIDE = round128(STAGE_BYTES);
   static constexpr int TABLE_BYTES = ENTRIES * ENTRY;
   static constexpr int OFFS_BYTES = NB * MT * 4;            // one chunk: [b][pair][48][2] uint32
-  static constexpr int ASTAGE_BYTES = P * MT * 16;          // [p][r][2] uint64
+  static constexpr int ABOX_ROWS = 96;                      // TMA box rows for A
+  static constexpr int ABOX_WORDS = 4;
+  static constexpr int ABOXES = MT / ABOX_ROWS;
+  static_assert(MT % ABOX_ROWS == 0, "whole A boxes");
+  static constexpr int ABOX_BYTES = ABOX_WORDS * ABOX_ROWS * P * 8;
+  static constexpr int ASTAGE_BYTES = ABOXES * ABOX_BYTES;  // [box][p][96][4] uint64
   static constexpr int TABLE_OFF = 0;
   static constexpr int OFFS_OFF = 2 * TABLE_BYTES;
   static constexpr int BSTAGE_OFF = OFFS_OFF + 2 * OFFS_BYTES;
   static constexpr int ASTAGE_OFF = BSTAGE_OFF + 2 * STAGE_STRIDE;
-  static constexpr int BAR_OFF = ASTAGE_OFF + ASTAGE_BYTES;  // bfull[2], tfull[2], tempty[2]
-  static constexpr int ABORT_OFF = BAR_OFF + 48;
+  static constexpr int BAR_OFF = ASTAGE_OFF + ASTAGE_BYTES;  // bfull[2], tfull[2], tempty[2], afull
+  static constexpr int ABORT_OFF = BAR_OFF + 56;
   static constexpr int SMEM = ABORT_OFF + 16;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -119,63 +124,67 @@ __device__ __forceinline__ void wait_or_abort(uint32_t bar, uint32_t parity, vol
 
 // ------------------------------------------------------------- producers --
 
-// Stage words wlo, wlo + 1 of both planes of the tile's rows, layout [p][r][2].
+// Stage A's words x .. x + 3 (x = the chunk's first word rounded down to even,
+// so the copy starts on a 16-byte boundary) of both planes of the tile's rows:
+// ABOXES TMA boxes completing on `afull`.  Rows past m and words past the
+// pitch read as zero.
 template <class C>
-__device__ __forceinline__ void stage_a(const Params &prm, uint32_t astage, int64_t row0, int rows_here,
-                                        int64_t wlo, int ptid) {
-  for (int e = ptid; e < C::P * C::MT * 2; e += C::NPT) {
-    const int j = e & 1;
-    const int r = (e >> 1) % C::MT;
-    const int p = (e >> 1) / C::MT;
-    const int64_t w = wlo + j;
-    if (r < rows_here && w < prm.pa) cp_async8(astage + uint32_t(e) * 8u, prm.A + (p * prm.m + row0 + r) * prm.pa + w);
-  }
-  cp_async_commit();
+__device__ __forceinline__ void stage_a(const CUtensorMap *tmA, uint32_t astage, uint32_t afull, int64_t row0,
+                                        int64_t c0) {
+  const int x = int(((c0 * C::K) >> 6) & ~int64_t(1));
+  mbar_expect_tx(afull, C::ASTAGE_BYTES);
+  for (int j = 0; j < C::ABOXES; ++j)
+    tma_load_3d(astage + uint32_t(j * C::ABOX_BYTES), tmA, afull, x, int(row0 + j * C::ABOX_ROWS), 0);
 }
 
 // Offsets of phi_d(A_r, block s) for the blocks s = c0 .. c0 + nb - 1 of a
 // chunk and every row of the tile, packed off0 | off1 << 16 (off = idx * 128).
-// Layout [b][slot pair][48 rows][2 slots] so that a consumer warp reads two
-// slots of its four row groups in one 32-byte wavefront.
+// Layout [b][slot pair][48 rows][2 slots]: a consumer warp reads two slots of
+// its four row groups in one wavefront; a producer thread handles the two rows
+// of one slot pair and writes them with one 8-byte store.
 template <class C>
 __device__ __forceinline__ void build_offsets(const Params &prm, const unsigned char *astage, uint32_t *offs,
                                               int rows_here, int64_t c0, int nb, int ptid) {
   using F = typename C::Field;
   const int64_t bit0 = c0 * C::K;
-  const int sh = int(bit0 & 63);
+  const int o = int(bit0 - 64 * (((bit0 >> 6)) & ~int64_t(1)));  // 0 .. 127 within the staged words
+  const int wi = o >> 6, sh = o & 63;
+  const int64_t valid = prm.l - bit0;
+  const uint64_t keep = valid < 64 ? (uint64_t(1) << valid) - 1u : ~uint64_t(0);
+  const uint32_t mask = (1u << C::K) - 1u;
   const uint64_t *as = reinterpret_cast<const uint64_t *>(astage);
-  for (int r = ptid; r < C::MT; r += C::NPT) {
-    uint64_t win[2];
-    if (r < rows_here) {
-      uint64_t f[2];
+  for (int pr = ptid; pr < C::MT / 2; pr += C::NPT) {
+    const int j = pr / C::ROWS_PER_SLOT, rem = pr % C::ROWS_PER_SLOT;  // slots 2j, 2j + 1
+    uint32_t packed[2][C::NB];
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const uint64_t w0 = as[(p * C::MT + r) * 2 + 0];
-        const uint64_t w1 = as[(p * C::MT + r) * 2 + 1];
-        f[p] = sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;   // the chunk's 64 bits
-      }
-      F::phi(f, win);
-      // bits past column l (and past the staged words) are not part of A
-      const int64_t valid = prm.l - bit0;
-      if (valid < 64) {
-        const uint64_t keep = (uint64_t(1) << valid) - 1u;
+    for (int h = 0; h < 2; ++h) {
+      const int r = (2 * j + h) * C::ROWS_PER_SLOT + rem;
+      uint64_t win[2] = {0ull, 0ull};
+      if (r < rows_here) {
+        const uint64_t *rowp = as + (r / C::ABOX_ROWS) * (C::ABOX_BYTES / 8) + (r % C::ABOX_ROWS) * C::ABOX_WORDS;
+        uint64_t f[2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const uint64_t *wp = rowp + p * (C::ABOX_ROWS * C::ABOX_WORDS);
+          const uint64_t w0 = wi ? wp[1] : wp[0];
+          const uint64_t w1 = wi ? wp[2] : wp[1];
+          f[p] = sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;   // the chunk's 64 bits
+        }
+        F::phi(f, win);
         win[0] &= keep;
         win[1] &= keep;
       }
-    } else {
-      win[0] = win[1] = 0ull;
-    }
-    const int i = r / C::ROWS_PER_SLOT, rem = r % C::ROWS_PER_SLOT;
-    uint32_t *dst = offs + ((i >> 1) * C::ROWS_PER_SLOT + rem) * 2 + (i & 1);
-    const uint32_t mask = (1u << C::K) - 1u;
 #pragma unroll
-    for (int b = 0; b < C::NB; ++b) {
-      if (b < nb) {
+      for (int b = 0; b < C::NB; ++b) {
         const uint32_t i0 = uint32_t(win[0] >> (b * C::K)) & mask;
         const uint32_t i1 = uint32_t(win[1] >> (b * C::K)) & mask;
-        dst[b * (C::MT)] = (i0 * uint32_t(C::ENTRY)) | ((i1 * uint32_t(C::ENTRY)) << 16);
+        packed[h][b] = (i0 * uint32_t(C::ENTRY)) | ((i1 * uint32_t(C::ENTRY)) << 16);
       }
     }
+    uint2 *dst = reinterpret_cast<uint2 *>(offs) + j * C::ROWS_PER_SLOT + rem;
+#pragma unroll
+    for (int b = 0; b < C::NB; ++b)
+      if (b < nb) dst[b * (C::MT / 2)] = make_uint2(packed[0][b], packed[1][b]);
   }
 }
 
@@ -271,7 +280,8 @@ __device__ __forceinline__ void lookup_block(uint32_t (&acc)[C::RS][4], uint32_t
 }
 
 template <class C>
-__global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant__ CUtensorMap tmB, const Params prm) {
+__global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmA,
+                                                          const Params prm) {
   using F = typename C::Field;
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
   const int64_t w0 = int64_t(blockIdx.x) * C::CTW;
 
   const uint32_t base = smem_u32(smem);
-  const uint32_t bfull = base + C::BAR_OFF, tfull = bfull + 16, tempty = bfull + 32;
+  const uint32_t bfull = base + C::BAR_OFF, tfull = bfull + 16, tempty = bfull + 32, afull = bfull + 48;
   volatile int &abort_flag = *reinterpret_cast<int *>(smem + C::ABORT_OFF);
 
   if (tid == 0) {
@@ -292,6 +302,7 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
     mbar_init(tfull + 8, C::NPT);
     mbar_init(tempty, C::NCW * 32);
     mbar_init(tempty + 8, C::NCW * 32);
+    mbar_init(afull, 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -313,14 +324,18 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
     const unsigned char *astage_p = smem + C::ASTAGE_OFF;
     const int64_t nchunks = cdiv_dev(prm.nblocks, C::NB);
     uint32_t *const offs0 = reinterpret_cast<uint32_t *>(smem + C::OFFS_OFF);  // chunk buffers 0, 1
+    uint32_t aphase = 0;  // completed uses of afull
     // prologue: offsets of chunk 0, A words of chunk 1 in flight
     if (prm.nblocks > 0) {
-      stage_a<C>(prm, astage, row0, rows_here, 0, ptid);
-      cp_async_wait_all();
-      producer_sync();
+      if (ptid == 0) stage_a<C>(&tmA, astage, afull, row0, 0);
+      wait_or_abort(afull, aphase & 1, abort_flag, prm.err);
+      ++aphase;
       build_offsets<C>(prm, astage_p, offs0, rows_here, 0, int(prm.nblocks < C::NB ? prm.nblocks : C::NB), ptid);
-      producer_sync();
-      if (nchunks > 1) stage_a<C>(prm, astage, row0, rows_here, (C::NB * C::K) >> 6, ptid);
+      producer_sync();  // the A stage is free
+      if (ptid == 0 && nchunks > 1 && !abort_flag) {
+        fence_proxy_async_smem();
+        stage_a<C>(&tmA, astage, afull, row0, C::NB);
+      }
     }
     for (int64_t s = 0; s < prm.nblocks; ++s) {
       const int buf = int(s & 1);
@@ -332,13 +347,16 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
         const int64_t c = s / C::NB;
         if (c + 1 < nchunks) {
           if (s >= 1) wait_or_abort(tempty + 8 * ((s - 1) & 1), uint32_t((s - 1) >> 1) & 1, abort_flag, prm.err);
-          cp_async_wait_all();
-          producer_sync();
+          wait_or_abort(afull, aphase & 1, abort_flag, prm.err);
+          ++aphase;
           const int64_t c1 = (c + 1) * C::NB;
           build_offsets<C>(prm, astage_p, offs0 + ((c + 1) & 1) * (C::OFFS_BYTES / 4), rows_here, c1,
                            int(prm.nblocks - c1 < C::NB ? prm.nblocks - c1 : C::NB), ptid);
-          producer_sync();
-          if (c + 2 < nchunks) stage_a<C>(prm, astage, row0, rows_here, (((c + 2) * C::NB) * C::K) >> 6, ptid);
+          producer_sync();  // the A stage is free
+          if (ptid == 0 && c + 2 < nchunks && !abort_flag) {
+            fence_proxy_async_smem();
+            stage_a<C>(&tmA, astage, afull, row0, (c + 2) * C::NB);
+          }
         }
       }
       if (s >= 2) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
@@ -354,7 +372,6 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
       }
       mbar_arrive(tfull + 8 * buf);
     }
-    cp_async_wait_all();
   } else {
     // ------------------------------------------------------- consumers
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(C::CREG));
@@ -407,11 +424,22 @@ int launch(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B
   prm.mt = mt;
   prm.one = 1u;
   prm.err = err;
-  CUtensorMap map;
+  CUtensorMap map, amap;
   memset(&map, 0, sizeof(map));
+  memset(&amap, 0, sizeof(amap));
   if (l > 0) {
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (int rc = tensor_map_encoder(&encode)) return rc;
+    {
+      const cuuint64_t adims[3] = {cuuint64_t(prm.pa), cuuint64_t(m), cuuint64_t(C::P)};
+      const cuuint64_t astr[2] = {cuuint64_t(prm.pa) * 8u, cuuint64_t(prm.pa) * 8u * cuuint64_t(m)};
+      const cuuint32_t abox[3] = {cuuint32_t(C::ABOX_WORDS), cuuint32_t(C::ABOX_ROWS), cuuint32_t(C::P)};
+      const cuuint32_t aestr[3] = {1, 1, 1};
+      CUresult cr = encode(&amap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<uint64_t *>(A), adims, astr, abox,
+                           aestr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (cr != CUDA_SUCCESS) return FQ_EINVAL;
+    }
     const cuuint64_t dims[3] = {cuuint64_t(prm.pc), cuuint64_t(l), cuuint64_t(C::P)};
     const cuuint64_t strides[2] = {cuuint64_t(prm.pc) * 8u, cuuint64_t(prm.pc) * 8u * cuuint64_t(l)};
     const cuuint32_t box[3] = {cuuint32_t(C::CTW), cuuint32_t(C::K), cuuint32_t(C::P)};
@@ -424,7 +452,7 @@ int launch(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B
   FQ_CUDA_TRY(cudaFuncSetAttribute(m4rm_ws_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   const dim3 grid(unsigned(prm.pc / C::CTW), unsigned(cdiv(m, mt)));
   if (grid.y > 65535u) return FQ_ENOTSUP;
-  m4rm_ws_kernel<C><<<grid, C::NT, C::SMEM, s>>>(map, prm);
+  m4rm_ws_kernel<C><<<grid, C::NT, C::SMEM, s>>>(map, amap, prm);
   FQ_LAUNCH_CHECK();
   return FQ_OK;
 }

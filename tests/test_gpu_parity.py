@@ -253,3 +253,13 @@ def test_unsupported_block_size_is_reported(fq, q, kmax):
     with pytest.raises(fq.FqError) as e:
         fq.matmul(a, b, variant=100000)
     assert e.value.status == fq.EINVAL
+
+
+@pytest.mark.parametrize("q", [3, 4, 5, 7])
+@pytest.mark.parametrize("k", [6, 7, 9])
+def test_last_block_reaches_past_the_pitch(fq, q, k):
+    """l = 1024 is a whole pitch: with k not dividing 64 the last block's index
+    field extends past the row's last word."""
+    if q in (5, 7) and k == 9:
+        pytest.skip("three-plane tables stop at k = 8")
+    _check_product(fq, q, 200, 1024, 130, seed=k, k=k)
