@@ -90,8 +90,9 @@ typedef struct fq_options {
   int path;      /* FQ_PATH_*                                                     */
   int k;         /* M4RM block size: 0 = planner, else 6..10 (Section 2's k)       */
   int64_t chunk; /* MMA path: l-chunk length between mod-p reductions; 0 = largest */
-  int variant;   /* M4RM tile variant: 0 = planner, else an index >= 1             */
-  int reserved[5];
+  int variant;   /* M4RM rows per CTA: 0 = planner, else 1 .. the kernel's maximum */
+  int kernel;    /* M4RM kernel: 0 = planner, i + 1 = compiled kernel i of field q  */
+  int reserved[4];
 } fq_options;
 
 /* C = A B over F_q (Section 2: C_i = sum_s sum_d alpha_d T_s[phi_d(A_i, block s)]).
@@ -103,6 +104,13 @@ int fq_matmul(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
 /* fq_matmul with explicit options (path, k, l-chunk, tile variant); opt may be NULL. */
 int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
                  const uint64_t *B, uint64_t *C, void *stream, const fq_options *opt);
+
+/* Compiled M4RM kernels for field q (planner candidates).  fq_kernel_count
+ * returns their number (0 for a bad q); fq_kernel_info describes kernel idx:
+ * block size k, the most rows one CTA holds, columns per CTA and warps per CTA.
+ * Host-only; returns FQ_EINVAL for a bad q or idx. */
+int fq_kernel_count(int q);
+int fq_kernel_info(int q, int idx, int *k, int *max_rows, int *cols, int *warps);
 
 /* Wait for `stream`, then return and clear the first error kernels recorded on
  * the current device (FQ_EVALUE, FQ_ETIMEOUT), or FQ_OK.  Synchronous. */

@@ -124,12 +124,30 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, cons
   if (o.chunk < 0 || o.variant < 0) return FQ_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (o.path == FQ_PATH_MMA) return FQ_ENOTSUP;
-  return fqk::launch_m4rm(q, m, l, n, A, B, C, o.k, o.variant, s);
+  if (o.kernel < 0) return FQ_EINVAL;
+  return fqk::launch_m4rm(q, m, l, n, A, B, C, o.k, o.variant, o.kernel, s);
 }
 
 int fq_matmul(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
               void *stream) {
   return fq_matmul_ex(q, m, l, n, A, B, C, stream, nullptr);
+}
+
+int fq_kernel_count(int q) {
+  int count = 0;
+  fqk::m4rm_variants(q, &count);
+  return count;
+}
+
+int fq_kernel_info(int q, int idx, int *k, int *max_rows, int *cols, int *warps) {
+  int count = 0;
+  const fqk::Variant *vs = fqk::m4rm_variants(q, &count);
+  if (!vs || idx < 0 || idx >= count) return FQ_EINVAL;
+  if (k) *k = vs[idx].k;
+  if (max_rows) *max_rows = vs[idx].rs * vs[idx].rows_per_slot;
+  if (cols) *cols = vs[idx].cols;
+  if (warps) *warps = vs[idx].warps;
+  return FQ_OK;
 }
 
 int fq_status(void *stream) {

@@ -13,6 +13,16 @@ int launch_unpack(int q, int64_t rows, int64_t cols, const uint64_t *planes, uin
 int launch_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t *Y, uint64_t *Z, int sub,
                cudaStream_t s);
 int launch_m4rm(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
-                int k, int variant, cudaStream_t s);
+                int k, int variant, int kernel, cudaStream_t s);
+
+// One compiled M4RM kernel shape of a field (the planner's candidates).
+struct Variant {
+  int k, rs;
+  int (*launch)(int64_t, int64_t, int64_t, const uint64_t *, const uint64_t *, uint64_t *, int, cudaStream_t);
+  int rows_per_slot;
+  int cols, warps;
+};
+// The variant table of field q (nullptr and 0 for a bad q).
+const Variant *m4rm_variants(int q, int *count);
 
 }  // namespace fqk

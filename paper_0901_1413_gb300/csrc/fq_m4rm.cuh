@@ -463,24 +463,23 @@ int launch_cfg(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_
   return FQ_OK;
 }
 
-// One compiled kernel shape: block size k and row slots per warp.
-struct Variant {
-  int k, rs;
-  int (*launch)(int64_t, int64_t, int64_t, const uint64_t *, const uint64_t *, uint64_t *, int, cudaStream_t);
-  int rows_per_slot;
-};
-
 // Picks (k, rows per CTA) for a product.  Without a request, every compiled
 // variant is costed: one CTA per SM, waves of CTAs, and per CTA ceil(l/k)
 // blocks of (about 1.2 * 2^k table adds + D adds per row).  A requested k
 // narrows the choice; a requested height (tests) takes the tallest variant of
 // that k and runs it with `mt` rows per CTA.
-inline int plan_and_launch(const Variant *vs, int nv, int d, int ctw, int64_t m, int64_t l, int64_t n,
-                           const uint64_t *A, const uint64_t *B, uint64_t *C, int k, int mt, cudaStream_t s) {
+inline int plan_and_launch(const Variant *vs, int nv, int d, int64_t m, int64_t l, int64_t n,
+                           const uint64_t *A, const uint64_t *B, uint64_t *C, int k, int mt, int kernel,
+                           cudaStream_t s) {
+  if (kernel > 0) {
+    if (kernel > nv) return FQ_EINVAL;
+    const Variant &v = vs[kernel - 1];
+    if (k != 0 && k != v.k) return FQ_EINVAL;
+    return v.launch(m, l, n, A, B, C, mt > 0 ? mt : v.rs * v.rows_per_slot, s);
+  }
   int dev = 0, sms = 152;
   FQ_CUDA_TRY(cudaGetDevice(&dev));
   FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t col_tiles = fq_pitch_words(n) / ctw;
   const Variant *pick = nullptr;
   if (mt > 0) {
     for (int i = 0; i < nv; ++i)
@@ -492,7 +491,7 @@ inline int plan_and_launch(const Variant *vs, int nv, int d, int ctw, int64_t m,
   for (int i = 0; i < nv; ++i) {
     if (k != 0 && vs[i].k != k) continue;
     const int64_t rows = int64_t(vs[i].rs) * vs[i].rows_per_slot;
-    const int64_t ctas = cdiv(m, rows) * col_tiles;
+    const int64_t ctas = cdiv(m, rows) * (fq_pitch_words(n) / (vs[i].cols / 64));
     const int64_t waves = cdiv(ctas, sms);
     const double cost =
         double(waves) * double(cdiv(l, vs[i].k)) * (1.2 * double(1 << vs[i].k) + double(rows) * d);

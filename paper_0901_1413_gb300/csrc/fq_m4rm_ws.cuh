@@ -5,13 +5,13 @@
 // but the work of one block is split between two kinds of warps so that the
 // lookups -- the part that scales with the rows -- never wait for the rest:
 //
-//  * 4 producer warps (one warpgroup, few registers): stage A's words one chunk
+//  * NPW = 4 or 8 producer warps (one or two warpgroups, few registers): stage A's words one chunk
 //    of NB blocks ahead (TMA boxes of 4 words x 96 rows x 2 planes), turn the k-bit fields phi_d(A_i, block s) of
 //    a whole chunk into table byte offsets for every row of the tile (two 16-bit
 //    offsets per word), and build T_s in shared memory from the TMA-loaded B
 //    block (16 builder groups, each walking 2^(k-4) entries with one bitsliced
 //    add per entry).
-//  * 12 consumer warps (three warpgroups, most registers): for every block,
+//  * 16 - NPW consumer warps (the other warpgroups, most registers): for every block,
 //    gather D table entries per row and add them into register accumulators.
 //
 // Tables are double-buffered by block and offsets by chunk: while consumers
@@ -35,7 +35,7 @@ __host__ __device__ constexpr int popc(int x) { return x == 0 ? 0 : (x & 1) + po
 __host__ __device__ constexpr int ctz(int x) { return (x & 1) ? 0 : 1 + ctz(x >> 1); }
 constexpr int round128(int x) { return (x + 127) / 128 * 128; }
 
-template <class F, int K_, int RS_>
+template <class F, int K_, int RS_, int NPW_ = 4>
 struct Cfg {
   using Field = F;
   static_assert(F::P == 2 && F::D == 2, "two planes, basis of two");
@@ -44,30 +44,32 @@ struct Cfg {
   static_assert(RS % 2 == 0, "slots are read in pairs");
   static constexpr int P = 2, D = 2;
   static constexpr int LPR = 8, GPW = 4, WPL = 2, PW = 4;  // 8-lane groups, 2 words per plane
-  static constexpr int NPW = 4, NCW = 12;                   // producer / consumer warps
+  static constexpr int NPW = NPW_, NCW = 16 - NPW;         // producer / consumer warps
+  static_assert(NPW == 4 || NPW == 8, "one or two producer warpgroups");
   static constexpr int NT = (NPW + NCW) * 32;
   static constexpr int NPT = NPW * 32;                      // producer threads
-  static constexpr int PREG = 80, CREG = 144;               // registers after setmaxnreg
+  static constexpr int PREG = NPW == 4 ? 80 : 64;           // registers after setmaxnreg
+  static constexpr int CREG = NPW == 4 ? 144 : 192;
   static_assert(NPT * PREG + NCW * 32 * CREG == 65536, "register split");
   static constexpr int ENTRY = 128;                         // bytes per table entry
   static constexpr int ENTRIES = 1 << K;
   static constexpr int CT = 512, CTW = 8;                   // columns (words) per tile
-  static constexpr int ROWS_PER_SLOT = NCW * GPW;           // 48
+  static constexpr int ROWS_PER_SLOT = NCW * GPW;
   static constexpr int MT = RS * ROWS_PER_SLOT;             // rows per CTA
-  static constexpr int NBUILD = NPW * GPW;                  // 16 builder groups
-  static constexpr int LB = K - 4, HB = 4, EPB = 1 << LB;
+  static constexpr int NBUILD = NPW * GPW;                  // builder groups
+  static constexpr int HB = NPW == 4 ? 4 : 5, LB = K - HB, EPB = 1 << LB;
   static_assert(K >= 6 && K <= 9, "k in 6..9 (offsets idx * 128 fit 16 bits)");
   static constexpr int NB = 64 / K;                         // blocks per A chunk
   static constexpr int STAGE_BYTES = P * K * CTW * 8;
   static constexpr int STAGE_STRIDE = round128(STAGE_BYTES);
   static constexpr int TABLE_BYTES = ENTRIES * ENTRY;
-  static constexpr int OFFS_BYTES = NB * MT * 4;            // one chunk: [b][pair][48][2] uint32
-  static constexpr int ABOX_ROWS = 96;                      // TMA box rows for A
+  static constexpr int OFFS_BYTES = NB * MT * 4;            // one chunk: [b][pair][rows/slot][2] uint32
+  static constexpr int ABOX_ROWS = 2 * ROWS_PER_SLOT;       // TMA box rows for A
   static constexpr int ABOX_WORDS = 4;
   static constexpr int ABOXES = MT / ABOX_ROWS;
   static_assert(MT % ABOX_ROWS == 0, "whole A boxes");
   static constexpr int ABOX_BYTES = ABOX_WORDS * ABOX_ROWS * P * 8;
-  static constexpr int ASTAGE_BYTES = ABOXES * ABOX_BYTES;  // [box][p][96][4] uint64
+  static constexpr int ASTAGE_BYTES = ABOXES * ABOX_BYTES;  // [box][p][rows][4] uint64
   static constexpr int TABLE_OFF = 0;
   static constexpr int OFFS_OFF = 2 * TABLE_BYTES;
   static constexpr int BSTAGE_OFF = OFFS_OFF + 2 * OFFS_BYTES;
@@ -100,7 +102,8 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ int64_t cdiv_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
-__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -222,7 +225,7 @@ __device__ __forceinline__ void build_walk(uint32_t (&S)[C::LB + 1][4], const ui
   }
 }
 
-// Builder j (0..15) fills entries [j EPB, (j + 1) EPB): high bits j over rows
+// Builder j (0 .. NBUILD-1) fills entries [j EPB, (j + 1) EPB): high bits j over rows
 // LB..K-1 summed once, then the LB low rows walked (entry x = parent
 // x & (x - 1) plus row ctz(x); the parent is the last entry with one bit less).
 template <class C>
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
       wait_or_abort(afull, aphase & 1, abort_flag, prm.err);
       ++aphase;
       build_offsets<C>(prm, astage_p, offs0, rows_here, 0, int(prm.nblocks < C::NB ? prm.nblocks : C::NB), ptid);
-      producer_sync();  // the A stage is free
+      producer_sync<C::NPT>();  // the A stage is free
       if (ptid == 0 && nchunks > 1 && !abort_flag) {
         fence_proxy_async_smem();
         stage_a<C>(&tmA, astage, afull, row0, C::NB);
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
           const int64_t c1 = (c + 1) * C::NB;
           build_offsets<C>(prm, astage_p, offs0 + ((c + 1) & 1) * (C::OFFS_BYTES / 4), rows_here, c1,
                            int(prm.nblocks - c1 < C::NB ? prm.nblocks - c1 : C::NB), ptid);
-          producer_sync();  // the A stage is free
+          producer_sync<C::NPT>();  // the A stage is free
           if (ptid == 0 && c + 2 < nchunks && !abort_flag) {
             fence_proxy_async_smem();
             stage_a<C>(&tmA, astage, afull, row0, (c + 2) * C::NB);
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
       wait_or_abort(bfull + 8 * buf, use & 1, abort_flag, prm.err);
       build_table<C>(tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), base + C::BSTAGE_OFF + buf * C::STAGE_STRIDE,
                      builder, gl);
-      producer_sync();  // every producer is done with this B stage
+      producer_sync<C::NPT>();  // every producer is done with this B stage
       if (ptid == 0 && s + 2 < prm.nblocks && !abort_flag) {
         fence_proxy_async_smem();
         mbar_expect_tx(bfull + 8 * buf, C::STAGE_BYTES);

@@ -34,7 +34,7 @@ class FqError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("k", ctypes.c_int), ("chunk", ctypes.c_int64),
-                ("variant", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("variant", ctypes.c_int), ("kernel", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 def load():
@@ -54,6 +54,9 @@ def load():
             "fq_matmul": (i32, [i32, i64, i64, i64, vp, vp, vp, vp]),
             "fq_matmul_ex": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, ctypes.POINTER(Options)]),
             "fq_status": (i32, [vp]),
+            "fq_kernel_count": (i32, [i32]),
+            "fq_kernel_info": (i32, [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i32)]),
             "fq_error_string": (ctypes.c_char_p, [i32]),
             "fq_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -141,16 +144,28 @@ def add(x: Packed, y: Packed, sub: bool = False, out: Packed | None = None, stre
 
 
 def matmul(a: Packed, b: Packed, out: Packed | None = None, path: int = PATH_AUTO, k: int = 0,
-           chunk: int = 0, variant: int = 0, stream=None) -> Packed:
+           chunk: int = 0, variant: int = 0, kernel: int = 0, stream=None) -> Packed:
     """fq_matmul_ex: C = A B over F_q."""
     if a.q != b.q or a.cols != b.rows:
         raise ValueError("shape mismatch")
     m, l, n = a.rows, a.cols, b.cols
     out = empty(a.q, m, n, a.data.device) if out is None else out
-    opt = Options(path=path, k=k, chunk=chunk, variant=variant)
+    opt = Options(path=path, k=k, chunk=chunk, variant=variant, kernel=kernel)
     _check(load().fq_matmul_ex(a.q, m, l, n, ctypes.c_void_p(a.data.data_ptr()),
                                ctypes.c_void_p(b.data.data_ptr()), ctypes.c_void_p(out.data.data_ptr()),
                                _stream(stream), ctypes.byref(opt)), "fq_matmul")
+    return out
+
+
+def kernels(q: int) -> list[dict]:
+    """The compiled M4RM kernels of field q: k, rows and columns per CTA, warps."""
+    lib = load()
+    out = []
+    for i in range(lib.fq_kernel_count(q)):
+        k, rows, cols, warps = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.fq_kernel_info(q, i, ctypes.byref(k), ctypes.byref(rows), ctypes.byref(cols), ctypes.byref(warps)),
+               "fq_kernel_info")
+        out.append({"index": i, "k": k.value, "max_rows": rows.value, "cols": cols.value, "warps": warps.value})
     return out
 
 

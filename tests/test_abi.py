@@ -70,3 +70,13 @@ def test_error_strings(lib):
     assert lib.fq_error_string(0) == b"ok"
     assert lib.fq_error_string(4) == b"bounded device wait timed out"
     assert lib.fq_error_string(99) == b"unknown status"
+
+
+def test_kernel_table(lib):
+    from paper_0901_1413_gb300 import fq
+    for q in (3, 4, 5, 7):
+        ks = fq.kernels(q)
+        assert ks and all(6 <= k["k"] <= 10 and k["max_rows"] > 0 and k["cols"] % 512 == 0 for k in ks)
+    assert lib.fq_kernel_count(6) == 0
+    k = ctypes.c_int()
+    assert lib.fq_kernel_info(3, 10_000, ctypes.byref(k), None, None, None) == fq.EINVAL

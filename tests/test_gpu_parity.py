@@ -263,3 +263,19 @@ def test_last_block_reaches_past_the_pitch(fq, q, k):
     if q in (5, 7) and k == 9:
         pytest.skip("three-plane tables stop at k = 8")
     _check_product(fq, q, 200, 1024, 130, seed=k, k=k)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_every_compiled_kernel(fq, q):
+    """Each compiled M4RM kernel (block size, tile shape, warp layout) on a ragged
+    product, bit-exact against the oracle."""
+    ks = fq.kernels(q)
+    assert len(ks) >= 5
+    A = inputs.uniform(q, 333, 777, seed=q, stream=inputs.STREAM_A)
+    B = inputs.uniform(q, 777, 600, seed=q, stream=inputs.STREAM_B)
+    want = oracle.matmul(q, A, B)
+    a, b = gpu_pack(fq, q, A), gpu_pack(fq, q, B)
+    for info in ks:
+        got = fq.unpack(fq.matmul(a, b, kernel=info["index"] + 1)).cpu().numpy()
+        assert np.array_equal(got, want), info
+    assert fq.status() == fq.OK
