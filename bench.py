@@ -161,9 +161,14 @@ class ClockSampler:
 
 
 def kernel_sources_digest():
+    """Digest of the sources the M4RM kernels are compiled from."""
+    import glob
     h = hashlib.sha256()
-    for name in ("fq_m4rm.cu", "fq_fields.cuh", "fq_common.cuh"):
-        with open(os.path.join(ROOT, "paper_0901_1413_gb300", "csrc", name), "rb") as f:
+    csrc = os.path.join(ROOT, "paper_0901_1413_gb300", "csrc")
+    names = sorted(glob.glob(os.path.join(csrc, "fq_m4rm*")) +
+                   [os.path.join(csrc, n) for n in ("fq_fields.cuh", "fq_common.cuh")])
+    for name in names:
+        with open(name, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
