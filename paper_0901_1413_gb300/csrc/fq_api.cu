@@ -123,8 +123,8 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, cons
   if (o.k != 0 && (o.k < 6 || o.k > 10)) return FQ_EINVAL;
   if (o.chunk < 0 || o.variant < 0) return FQ_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (o.path == FQ_PATH_MMA) return FQ_ENOTSUP;
   if (o.kernel < 0) return FQ_EINVAL;
+  if (o.path == FQ_PATH_MMA) return fqk::launch_mma(q, m, l, n, A, B, C, o.chunk, s);
   return fqk::launch_m4rm(q, m, l, n, A, B, C, o.k, o.variant, o.kernel, s);
 }
 

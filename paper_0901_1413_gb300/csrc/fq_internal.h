@@ -15,6 +15,9 @@ int launch_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint6
 int launch_m4rm(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                 int k, int variant, int kernel, cudaStream_t s);
 
+int launch_mma(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+               int64_t chunk, cudaStream_t s);
+
 // One compiled M4RM kernel shape of a field (the planner's candidates).
 struct Variant {
   int k, rs;

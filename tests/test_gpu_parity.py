@@ -279,3 +279,48 @@ def test_every_compiled_kernel(fq, q):
         got = fq.unpack(fq.matmul(a, b, kernel=info["index"] + 1)).cpu().numpy()
         assert np.array_equal(got, want), info
     assert fq.status() == fq.OK
+
+
+# ------------------------------------------------ exact tensor-core path --
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("mln", [(1, 1, 1), (37, 100, 70), (300, 500, 260), (513, 257, 1025)])
+def test_mma_path_matches_oracle(fq, q, mln):
+    _check_product(fq, q, *mln, seed=sum(mln) + 7 * q, path=fq.PATH_MMA)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("chunk", [64, 128, 1000])
+def test_mma_path_reduces_between_chunks(fq, q, chunk):
+    """A forced short l-chunk runs the mod-p reduction between chunks many times."""
+    _check_product(fq, q, 130, 1100, 200, seed=chunk, path=fq.PATH_MMA, chunk=chunk)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_mma_path_all_max(fq, q):
+    m, l, n = 70, 3001, 130
+    A = np.full((m, l), q - 1, np.uint8)
+    B = np.full((l, n), q - 1, np.uint8)
+    got, _ = gpu_product(fq, q, A, B, path=fq.PATH_MMA, chunk=64)
+    want = (2 if l % 2 else 0) if q == 4 else (l * (q - 1) ** 2) % q
+    assert (got == want).all()
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_paths_agree_bit_for_bit(fq, q):
+    """M4RM and the tensor-core form give identical planes."""
+    n = 1536
+    A = inputs.uniform(q, n, n, seed=q, stream=inputs.STREAM_A)
+    B = inputs.uniform(q, n, n, seed=q, stream=inputs.STREAM_B)
+    a, b = gpu_pack(fq, q, A), gpu_pack(fq, q, B)
+    c1 = fq.matmul(a, b, path=fq.PATH_M4RM)
+    c2 = fq.matmul(a, b, path=fq.PATH_MMA)
+    assert torch.equal(c1.data, c2.data)
+    assert fq.status() == fq.OK
+
+
+def test_mma_path_degenerate(fq):
+    c = fq.empty(5, 4, 70)
+    c.data.fill_(-1)
+    fq.matmul(fq.empty(5, 4, 0), fq.empty(5, 0, 70), out=c, path=fq.PATH_MMA)
+    assert not c.data.cpu().numpy().any()
