@@ -105,6 +105,39 @@ int fq_matmul(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
 int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
                  const uint64_t *B, uint64_t *C, void *stream, const fq_options *opt);
 
+/* ---- many products in one launch ------------------------------------------
+ * A plan splits `count` products C_p = A_p B_p (shapes m[p] x l[p] times
+ * l[p] x n[p], all over the same field q) into work items (rows x a column
+ * tile of one product) with a block size k chosen per item by the planner's
+ * cost model, longest first.  The plan is host memory owned by the library. */
+typedef struct fq_batch_plan fq_batch_plan;
+
+/* Build a plan (host only).  m, l, n: host arrays of `count` sizes (each >= 0;
+ * l, m < 2^31).  Returns FQ_EINVAL on bad sizes, FQ_ENOMEM on allocation failure. */
+int fq_batched_plan_create(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n,
+                           fq_batch_plan **plan);
+
+/* Bytes of device workspace the plan needs (64-byte aligned, caller-owned),
+ * and the number of work items it holds; -1 for a NULL plan. */
+int64_t fq_batched_workspace_bytes(const fq_batch_plan *plan);
+int64_t fq_batched_items(const fq_batch_plan *plan);
+
+/* Copy the plan's work list into `workspace` (synchronous on `stream`).  Once
+ * per plan and workspace, before any fq_matmul_batched on them. */
+int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *stream);
+
+/* All products of the plan in one persistent launch (Section 2's method on
+ * every product).  A, B, C: DEVICE arrays of `count` device pointers to planes
+ * buffers (A_p m x l, B_p l x n, C_p m x n; C_p must not alias A_p or B_p);
+ * workspace: the uploaded workspace.  Enqueues one memset and one kernel on
+ * `stream`; allocates nothing and never synchronises, so it may be captured in
+ * a CUDA graph.  Launches sharing a workspace must not overlap on the GPU. */
+int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
+                      uint64_t *const *C, void *workspace, void *stream);
+
+/* Free a plan (NULL is fine). */
+int fq_batched_plan_destroy(fq_batch_plan *plan);
+
 /* Compiled M4RM kernels for field q (planner candidates).  fq_kernel_count
  * returns their number (0 for a bad q); fq_kernel_info describes kernel idx:
  * block size k, the most rows one CTA holds, columns per CTA and warps per CTA.

@@ -57,6 +57,12 @@ def load():
             "fq_kernel_count": (i32, [i32]),
             "fq_kernel_info": (i32, [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(i32)]),
+            "fq_batched_plan_create": (i32, [i32, i32, vp, vp, vp, ctypes.POINTER(vp)]),
+            "fq_batched_workspace_bytes": (i64, [vp]),
+            "fq_batched_items": (i64, [vp]),
+            "fq_batched_plan_upload": (i32, [vp, vp, vp]),
+            "fq_matmul_batched": (i32, [vp, vp, vp, vp, vp, vp]),
+            "fq_batched_plan_destroy": (i32, [vp]),
             "fq_error_string": (ctypes.c_char_p, [i32]),
             "fq_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -167,6 +173,45 @@ def kernels(q: int) -> list[dict]:
                "fq_kernel_info")
         out.append({"index": i, "k": k.value, "max_rows": rows.value, "cols": cols.value, "warps": warps.value})
     return out
+
+
+class BatchPlan:
+    """fq_batched_plan_*: a plan for many products over one field, with its
+    device workspace (a torch buffer) already uploaded."""
+
+    def __init__(self, q: int, shapes, device=None, stream=None):
+        import numpy as np
+        lib = load()
+        sh = np.ascontiguousarray(np.asarray(shapes, dtype=np.int64).reshape(-1, 3))
+        self.q = q
+        self.shapes = sh
+        m, l, n = (np.ascontiguousarray(sh[:, i]) for i in range(3))
+        h = ctypes.c_void_p()
+        _check(lib.fq_batched_plan_create(q, len(sh), m.ctypes.data_as(ctypes.c_void_p),
+                                          l.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
+                                          ctypes.byref(h)), "fq_batched_plan_create")
+        self._h = h
+        nbytes = lib.fq_batched_workspace_bytes(h)
+        self.items = lib.fq_batched_items(h)
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.workspace = torch.empty((nbytes + 63) // 64 * 8 + 8, dtype=torch.int64, device=dev)
+        _check(lib.fq_batched_plan_upload(h, ctypes.c_void_p(self._ws_ptr()), _stream(stream)),
+               "fq_batched_plan_upload")
+
+    def _ws_ptr(self) -> int:
+        p = self.workspace.data_ptr()
+        return (p + 63) // 64 * 64
+
+    def run(self, A_ptrs: torch.Tensor, B_ptrs: torch.Tensor, C_ptrs: torch.Tensor, stream=None):
+        """fq_matmul_batched; *_ptrs are int64 CUDA tensors of device pointers."""
+        _check(load().fq_matmul_batched(self._h, ctypes.c_void_p(A_ptrs.data_ptr()),
+                                        ctypes.c_void_p(B_ptrs.data_ptr()), ctypes.c_void_p(C_ptrs.data_ptr()),
+                                        ctypes.c_void_p(self._ws_ptr()), _stream(stream)), "fq_matmul_batched")
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fq_batched_plan_destroy(self._h)
+            self._h = None
 
 
 def status(stream=None) -> int:

@@ -80,3 +80,26 @@ def test_kernel_table(lib):
     assert lib.fq_kernel_count(6) == 0
     k = ctypes.c_int()
     assert lib.fq_kernel_info(3, 10_000, ctypes.byref(k), None, None, None) == fq.EINVAL
+
+
+def test_batch_plan_host_side(lib):
+    """Plan creation is host-only: sizes, item count, workspace bytes, errors."""
+    import numpy as np
+    from paper_0901_1413_gb300 import fq
+    i64p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    m = np.array([100, 2000, 0, 64], np.int64)
+    l = np.array([70, 64, 5, 0], np.int64)
+    n = np.array([600, 64, 9, 1100], np.int64)
+    h = ctypes.c_void_p()
+    assert lib.fq_batched_plan_create(3, 4, i64p(m), i64p(l), i64p(n), ctypes.byref(h)) == fq.OK
+    # items: one per row tile x column tile of the pitch (512-column tiles;
+    # tiles of padding only are zero-fill items): 1 x 2, 2 x 2, 0, 1 x 4
+    assert lib.fq_batched_items(h) == 2 + 4 + 0 + 4
+    assert lib.fq_batched_workspace_bytes(h) == 64 + 128 + 10 * 32
+    assert lib.fq_batched_plan_upload(h, ctypes.c_void_p(8), None) == fq.EINVAL      # misaligned
+    assert lib.fq_matmul_batched(h, None, None, None, ctypes.c_void_p(64), None) == fq.EINVAL
+    assert lib.fq_batched_plan_destroy(h) == fq.OK
+    bad = np.array([-1], np.int64)
+    assert lib.fq_batched_plan_create(3, 1, i64p(bad), i64p(bad), i64p(bad), ctypes.byref(h)) == fq.EINVAL
+    assert lib.fq_batched_plan_create(6, 1, i64p(m), i64p(l), i64p(n), ctypes.byref(h)) == fq.EINVAL
+    assert lib.fq_batched_workspace_bytes(None) == -1

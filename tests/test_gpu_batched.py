@@ -1,0 +1,103 @@
+"""Many products in one persistent launch (fq_matmul_batched), bit-exact
+against the oracle, including under CUDA-graph capture and replay."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_0901_1413_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = (3, 4, 5, 7)
+
+
+def make_batch(fq, q, shapes, seed):
+    A, B, a, b, c = [], [], [], [], []
+    for p, (m, l, n) in enumerate(shapes):
+        Ap = inputs.uniform(q, m, l, seed=seed, stream=100 + 2 * p)
+        Bp = inputs.uniform(q, l, n, seed=seed, stream=101 + 2 * p)
+        A.append(Ap)
+        B.append(Bp)
+        a.append(fq.pack(q, torch.from_numpy(Ap).cuda()) if m and l else fq.empty(q, m, l))
+        b.append(fq.pack(q, torch.from_numpy(Bp).cuda()) if l and n else fq.empty(q, l, n))
+        out = fq.empty(q, m, n)
+        out.data.fill_(-1)
+        c.append(out)
+    ptr = lambda xs: torch.tensor([x.data.data_ptr() for x in xs], dtype=torch.int64, device="cuda")
+    return A, B, a, b, c, ptr(a), ptr(b), ptr(c)
+
+
+def check(fq, q, A, B, c):
+    for p in range(len(A)):
+        m, n = A[p].shape[0], B[p].shape[1]
+        if m == 0 or n == 0:
+            continue
+        got = fq.unpack(c[p]).cpu().numpy()
+        assert np.array_equal(got, oracle.matmul(q, A[p], B[p])), "product %d %s" % (p, (m, A[p].shape[1], n))
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_batched_matches_oracle(fq, q):
+    rng = np.random.default_rng(q)
+    shapes = [tuple(int(x) for x in rng.choice(np.arange(64, 577, 64), 3)) for _ in range(20)]
+    shapes += [(1, 1, 1), (7, 100, 70), (300, 65, 1100), (1200, 130, 90), (5, 0, 9), (0, 5, 9), (4, 9, 0)]
+    A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=q)
+    plan = fq.BatchPlan(q, shapes)
+    assert plan.items >= 24
+    plan.run(pa, pb, pc)
+    assert fq.status() == fq.OK
+    check(fq, q, A, B, c)
+    # l = 0: C = 0
+    assert not c[len(shapes) - 3].data.cpu().numpy()[: 2 * 5 * 16].any()
+
+
+@pytest.mark.parametrize("q", [3, 5])
+def test_batched_graph_capture_and_replay(fq, q):
+    rng = np.random.default_rng(10 + q)
+    shapes = [tuple(int(x) for x in rng.choice(np.arange(64, 449, 64), 3)) for _ in range(12)]
+    A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=1)
+    plan = fq.BatchPlan(q, shapes)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        plan.run(pa, pb, pc, stream=stream)          # warm up outside capture
+    torch.cuda.current_stream().wait_stream(stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        plan.run(pa, pb, pc, stream=stream)
+    for c_ in c:
+        c_.data.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    assert fq.status() == fq.OK
+    check(fq, q, A, B, c)
+    # new inputs behind the same pointers, replay again
+    A2, B2 = [], []
+    for p, (m, l, n) in enumerate(shapes):
+        A2.append(inputs.uniform(q, m, l, seed=99, stream=2 * p))
+        B2.append(inputs.uniform(q, l, n, seed=99, stream=2 * p + 1))
+        fq.pack(q, torch.from_numpy(A2[-1]).cuda(), out=a[p])
+        fq.pack(q, torch.from_numpy(B2[-1]).cuda(), out=b[p])
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    check(fq, q, A2, B2, c)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("q", [3, 5])
+def test_batched_4096_products(fq, q):
+    """4096 products with m, l, n uniform over multiples of 64 in [64, 1024];
+    a sample of products against the oracle, and all of them by Freivalds."""
+    shapes = [tuple(int(x) for x in s) for s in inputs.batch_shapes(4096, seed=q)]
+    A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=q)
+    plan = fq.BatchPlan(q, shapes)
+    plan.run(pa, pb, pc)
+    assert fq.status() == fq.OK
+    sample = list(range(0, 4096, 97))
+    check(fq, q, [A[i] for i in sample], [B[i] for i in sample], [c[i] for i in sample])
+    for p in range(0, 4096, 7):
+        got = fq.unpack(c[p]).cpu().numpy()
+        assert oracle.freivalds(q, A[p], B[p], got, trials=2, seed=p)
