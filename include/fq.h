@@ -138,6 +138,29 @@ int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const
 /* Free a plan (NULL is fine). */
 int fq_batched_plan_destroy(fq_batch_plan *plan);
 
+/* Size of the fixed device array fq_matmul_batched_static works in. */
+#define FQ_BATCH_STATIC_BYTES (1 << 20)
+
+/* fq_matmul_batched for callers that cannot allocate device memory -- for
+ * example code running inside a framework whose allocator owns all of the
+ * GPU's memory, or a plug-in that must not call cudaMalloc because it would
+ * synchronise the device under its host.  No workspace argument: the work list
+ * and queue counter live in one FQ_BATCH_STATIC_BYTES array the library keeps
+ * on every GPU that loads it (until the process exits), and no call allocates
+ * or frees device memory.
+ *   - A plan needing more than FQ_BATCH_STATIC_BYTES of workspace
+ *     (fq_batched_workspace_bytes) is refused with FQ_ENOTSUP.
+ *   - Each call copies the plan's work list into the array on `stream` before
+ *     its launch (the array keeps the previous call's contents otherwise).
+ *   - All calls on a GPU share the one array: calls whose work overlaps on the
+ *     GPU (for example on two streams) race and give wrong results.
+ *   - The first call on a device looks up the array's device address; make that
+ *     first call before capturing any stream into a graph.
+ * The paper has no counterpart: this is an interface for allocation-free
+ * callers, with the arguments and results of fq_matmul_batched. */
+int fq_matmul_batched_static(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
+                             uint64_t *const *C, void *stream);
+
 /* Compiled M4RM kernels for field q (planner candidates).  fq_kernel_count
  * returns their number (0 for a bad q); fq_kernel_info describes kernel idx:
  * block size k, the most rows one CTA holds, columns per CTA and warps per CTA.

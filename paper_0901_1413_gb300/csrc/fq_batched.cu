@@ -11,6 +11,7 @@
 // in a CUDA graph and replayed.
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -363,3 +364,71 @@ int fq_batched_plan_destroy(fq_batch_plan *plan) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------- batched products without allocation --
+//
+// fq_matmul_batched_static runs the same persistent kernel as fq_matmul_batched,
+// but its work list and queue counter live in this file-scope device array
+// instead of a workspace the caller allocates.  The array exists once per GPU
+// that loads the library and stays until the process exits.
+
+namespace {
+
+constexpr int64_t kStaticScratchBytes = FQ_BATCH_STATIC_BYTES;
+static __device__ __align__(256) unsigned char g_batch_scratch[kStaticScratchBytes];
+
+constexpr int kMaxStaticDevices = 64;
+unsigned char *g_scratch_addr[kMaxStaticDevices];
+std::mutex g_scratch_mu;
+
+// Device address of g_batch_scratch on the current device.  In host code the
+// array's name is only a host-side handle, so the address is looked up once per
+// device (with that device current) and reused.
+int static_scratch(unsigned char **out) {
+  int dev = 0;
+  FQ_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxStaticDevices) return FQ_ENOTSUP;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_batch_scratch);
+    if (e != cudaSuccess) return fqk::record_cuda_error(e);
+    g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return FQ_OK;
+}
+
+}  // namespace
+
+extern "C" int fq_matmul_batched_static(const fq_batch_plan *plan, const uint64_t *const *A,
+                                        const uint64_t *const *B, uint64_t *const *C, void *stream) {
+  using namespace fqk::batched;
+  if (!plan) return FQ_EINVAL;
+  if (plan->items.empty()) return FQ_OK;
+  if (!A || !B || !C) return FQ_EINVAL;
+  if (plan->workspace_bytes > kStaticScratchBytes) return FQ_ENOTSUP;  // does not fit the fixed array
+  unsigned char *ws = nullptr;
+  if (int rc = static_scratch(&ws)) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The array holds whatever the previous call left: write this plan's header
+  // (queue counter 0), shapes and items before the launch, in stream order.
+  Header h{};
+  h.next = 0;
+  h.count = uint32_t(plan->count);
+  h.nitems = uint32_t(plan->items.size());
+  h.q = uint32_t(plan->q);
+  FQ_CUDA_TRY(cudaMemcpyAsync(ws, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  if (plan->count)
+    FQ_CUDA_TRY(cudaMemcpyAsync(ws + sizeof(Header), plan->shapes.data(), plan->shapes.size() * sizeof(Shape),
+                                cudaMemcpyHostToDevice, s));
+  FQ_CUDA_TRY(cudaMemcpyAsync(ws + sizeof(Header) + shapes_bytes(plan->count), plan->items.data(),
+                              plan->items.size() * sizeof(Item), cudaMemcpyHostToDevice, s));
+  switch (plan->q) {
+    case 3: return launch_field<fqk::F3>(ws, A, B, C, s);
+    case 4: return launch_field<fqk::GF4>(ws, A, B, C, s);
+    case 5: return launch_field<fqk::F5>(ws, A, B, C, s);
+    case 7: return launch_field<fqk::F7>(ws, A, B, C, s);
+    default: return FQ_EINVAL;
+  }
+}
