@@ -212,41 +212,61 @@ __device__ __forceinline__ void add_lane(uint32_t (&x)[4], const uint32_t (&y)[4
   }
 }
 
-template <class C, int X>
-__device__ __forceinline__ void build_walk(uint32_t (&S)[C::LB + 1][4], const uint32_t (&rows)[C::LB][4],
-                                           uint32_t tbl_lane, int e0) {
-  if constexpr (X < C::EPB) {
-    constexpr int pc = popc(X), tz = ctz(X);
+// Entries of a builder's run in breadth-first order: by number of set bits,
+// then by value.  Entry x is built from x without its highest bit, which sits
+// one level up, so all adds of a level are independent.
+__host__ __device__ constexpr int bfs_entry(int lb, int i) {
+  int seen = 0;
+  for (int pc = 0; pc <= lb; ++pc)
+    for (int x = 0; x < (1 << lb); ++x)
+      if (popc(x) == pc) {
+        if (seen == i) return x;
+        ++seen;
+      }
+  return -1;
+}
+__host__ __device__ constexpr int top_bit(int x) { return x <= 1 ? 0 : 1 + top_bit(x >> 1); }
+
+template <class C, int I>
+__device__ __forceinline__ void build_bfs(uint32_t (&V)[C::EPB][4], const uint32_t (&rows)[C::LB][4],
+                                          uint32_t tbl_lane, int e0) {
+  if constexpr (I < C::EPB) {
+    constexpr int x = bfs_entry(C::LB, I), hb = top_bit(x), parent = x ^ (1 << hb);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) S[pc][j] = S[pc - 1][j];
-    add_lane<typename C::Field>(S[pc], rows[tz]);
-    sts128(tbl_lane + uint32_t((e0 + X) * C::ENTRY), S[pc]);
-    build_walk<C, X + 1>(S, rows, tbl_lane, e0);
+    for (int j = 0; j < 4; ++j) V[x][j] = V[parent][j];
+    add_lane<typename C::Field>(V[x], rows[hb]);
+    sts128(tbl_lane + uint32_t((e0 + x) * C::ENTRY), V[x]);
+    build_bfs<C, I + 1>(V, rows, tbl_lane, e0);
   }
 }
 
-// Builder j (0 .. NBUILD-1) fills entries [j EPB, (j + 1) EPB): high bits j over rows
-// LB..K-1 summed once, then the LB low rows walked (entry x = parent
-// x & (x - 1) plus row ctz(x); the parent is the last entry with one bit less).
+// Builder j (0 .. NBUILD-1) fills entries [j EPB, (j + 1) EPB): its high index
+// bits j select rows LB.. of the block, summed as a tree (adding a zero row
+// leaves a value unchanged); the LB low rows then build the run breadth-first.
 template <class C>
 __device__ __forceinline__ void build_table(uint32_t tbl_lane, uint32_t stage, int builder, int gl) {
+  using F = typename C::Field;
   uint32_t rows[C::LB][4];
 #pragma unroll
   for (int t = 0; t < C::LB; ++t) load_brow<C>(stage, t, gl, rows[t]);
-  uint32_t S[C::LB + 1][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) S[0][j] = 0u;
+  uint32_t hi[C::HB][4];
 #pragma unroll
   for (int t = 0; t < C::HB; ++t) {
-    if ((builder >> t) & 1) {
-      uint32_t r[4];
-      load_brow<C>(stage, C::LB + t, gl, r);
-      add_lane<typename C::Field>(S[0], r);
-    }
+    load_brow<C>(stage, C::LB + t, gl, hi[t]);
+    const uint32_t keep = ((builder >> t) & 1) ? 0xFFFFFFFFu : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hi[t][j] &= keep;
   }
+#pragma unroll
+  for (int w = 1; w < C::HB; w *= 2)
+#pragma unroll
+    for (int t = 0; t + w < C::HB; t += 2 * w) add_lane<F>(hi[t], hi[t + w]);
+  uint32_t V[C::EPB][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) V[0][j] = hi[0][j];
   const int e0 = builder * C::EPB;
-  sts128(tbl_lane + uint32_t(e0 * C::ENTRY), S[0]);
-  build_walk<C, 1>(S, rows, tbl_lane, e0);
+  sts128(tbl_lane + uint32_t(e0 * C::ENTRY), V[0]);
+  build_bfs<C, 1>(V, rows, tbl_lane, e0);
 }
 
 // ------------------------------------------------------------- consumers --
@@ -343,13 +363,14 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
     for (int64_t s = 0; s < prm.nblocks; ++s) {
       const int buf = int(s & 1);
       const uint32_t use = uint32_t(s >> 1);
-      if (s % C::NB == 0) {
-        // start of chunk c: write the offsets of chunk c + 1 into the buffer
-        // chunk c - 1 used (free once block s - 1 is consumed), then prefetch
-        // the A words of chunk c + 2
+      if (s % C::NB == 1) {
+        // second block of chunk c: write the offsets of chunk c + 1 into the
+        // buffer chunk c - 1 used -- consumers are done with it once block
+        // s - 2 is consumed, the same wait the table buffer needs below -- then
+        // prefetch the A words of chunk c + 2
         const int64_t c = s / C::NB;
         if (c + 1 < nchunks) {
-          if (s >= 1) wait_or_abort(tempty + 8 * ((s - 1) & 1), uint32_t((s - 1) >> 1) & 1, abort_flag, prm.err);
+          if (s >= 2) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
           wait_or_abort(afull, aphase & 1, abort_flag, prm.err);
           ++aphase;
           const int64_t c1 = (c + 1) * C::NB;
