@@ -161,6 +161,27 @@ int fq_batched_plan_destroy(fq_batch_plan *plan);
 int fq_matmul_batched_static(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
                              uint64_t *const *C, void *stream);
 
+/* ---- measured autotuning -----------------------------------------------------
+ * fq_autotune times, on the caller's operands and stream (synchronously), the
+ * M4RM planner's choice, every compiled M4RM kernel of field q and the
+ * tensor-core path, and remembers the fastest for this exact (q, m, l, n):
+ * later fq_matmul / fq_matmul_ex calls with FQ_PATH_AUTO, k = 0 and kernel = 0
+ * on that shape use it.  C holds the product when it returns.  The cache is
+ * process-wide host memory; fq_autotune_clear empties it. */
+typedef struct fq_tune_result {
+  int path;           /* FQ_PATH_M4RM or FQ_PATH_MMA                        */
+  int kernel;         /* 1-based compiled M4RM kernel, 0 = the M4RM planner   */
+  float ms;           /* time of the chosen candidate                         */
+  float ms_planner;   /* time of the M4RM planner's choice                    */
+  float ms_mma;       /* time of the tensor-core path (0 if not run)          */
+} fq_tune_result;
+
+int fq_autotune(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+                void *stream, fq_tune_result *out);
+/* FQ_OK and the remembered choice for (q, m, l, n), or FQ_ENOTSUP if none. */
+int fq_autotune_lookup(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel);
+int fq_autotune_clear(void);
+
 /* Compiled M4RM kernels for field q (planner candidates).  fq_kernel_count
  * returns their number (0 for a bad q); fq_kernel_info describes kernel idx:
  * block size k, the most rows one CTA holds, columns per CTA and warps per CTA.

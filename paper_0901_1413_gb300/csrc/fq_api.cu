@@ -124,6 +124,13 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, cons
   if (o.chunk < 0 || o.variant < 0) return FQ_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (o.kernel < 0) return FQ_EINVAL;
+  if (o.path == FQ_PATH_AUTO && o.k == 0 && o.kernel == 0 && o.variant == 0) {
+    int path = 0, kernel = 0;
+    if (fqk::tuned_choice(q, m, l, n, &path, &kernel)) {
+      o.path = path;
+      o.kernel = kernel;
+    }
+  }
   if (o.path == FQ_PATH_MMA) return fqk::launch_mma(q, m, l, n, A, B, C, o.chunk, s);
   return fqk::launch_m4rm(q, m, l, n, A, B, C, o.k, o.variant, o.kernel, s);
 }

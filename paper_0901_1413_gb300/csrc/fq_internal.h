@@ -28,4 +28,7 @@ struct Variant {
 // The variant table of field q (nullptr and 0 for a bad q).
 const Variant *m4rm_variants(int q, int *count);
 
+// The autotuned (path, kernel) for a shape, if fq_autotune measured one.
+bool tuned_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel);
+
 }  // namespace fqk

@@ -1,0 +1,102 @@
+// Measured autotuning of fq_matmul: time every compiled Four-Russians kernel of
+// the field and the tensor-core path on the caller's operands, keep the
+// fastest per (q, m, l, n), and let FQ_PATH_AUTO calls of that shape use it.
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "fq_common.cuh"
+#include "fq_internal.h"
+
+namespace fqk {
+
+namespace {
+
+struct Choice {
+  int path;    // FQ_PATH_M4RM or FQ_PATH_MMA
+  int kernel;  // 1-based compiled kernel for M4RM, 0 for the planner
+};
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int64_t, int64_t>, Choice> g_tuned;
+
+}  // namespace
+
+bool tuned_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(std::make_tuple(q, m, l, n));
+  if (it == g_tuned.end()) return false;
+  *path = it->second.path;
+  *kernel = it->second.kernel;
+  return true;
+}
+
+}  // namespace fqk
+
+extern "C" {
+
+int fq_autotune(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+                void *stream, fq_tune_result *out) {
+  if (!(q == 3 || q == 4 || q == 5 || q == 7) || m <= 0 || l <= 0 || n <= 0 || !A || !B || !C) return FQ_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int nk = 0;
+  fqk::m4rm_variants(q, &nk);
+  cudaEvent_t e0, e1;
+  FQ_CUDA_TRY(cudaEventCreate(&e0));
+  FQ_CUDA_TRY(cudaEventCreate(&e1));
+  fq_tune_result best{};
+  best.ms = -1.0f;
+  int rc = FQ_OK;
+  // candidates: 0 = M4RM planner, 1..nk = compiled M4RM kernels, nk + 1 = MMA
+  for (int c = 0; c <= nk + 1 && rc == FQ_OK; ++c) {
+    fq_options o{};
+    o.path = c == nk + 1 ? FQ_PATH_MMA : FQ_PATH_M4RM;
+    o.kernel = (c >= 1 && c <= nk) ? c : 0;
+    int r = fq_matmul_ex(q, m, l, n, A, B, C, stream, &o);  // warm-up (and applicability)
+    if (r == FQ_ENOTSUP || r == FQ_EINVAL) continue;
+    if (r != FQ_OK) {
+      rc = r;
+      break;
+    }
+    float ms = 0.0f;
+    if (cudaEventRecord(e0, s) != cudaSuccess || fq_matmul_ex(q, m, l, n, A, B, C, stream, &o) != FQ_OK ||
+        cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = fqk::record_cuda_error(cudaGetLastError());
+      break;
+    }
+    if (c == 0) best.ms_planner = ms;
+    if (c == nk + 1) best.ms_mma = ms;
+    if (best.ms < 0 || ms < best.ms) {
+      best.ms = ms;
+      best.path = o.path;
+      best.kernel = o.kernel;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != FQ_OK) return rc;
+  if (best.ms < 0) return FQ_ENOTSUP;
+  {
+    std::lock_guard<std::mutex> lock(fqk::g_tune_mu);
+    fqk::g_tuned[std::make_tuple(q, m, l, n)] = fqk::Choice{best.path, best.kernel};
+  }
+  if (out) *out = best;
+  return FQ_OK;
+}
+
+int fq_autotune_lookup(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel) {
+  int p = 0, k = 0;
+  if (!fqk::tuned_choice(q, m, l, n, &p, &k)) return FQ_ENOTSUP;
+  if (path) *path = p;
+  if (kernel) *kernel = k;
+  return FQ_OK;
+}
+
+int fq_autotune_clear(void) {
+  std::lock_guard<std::mutex> lock(fqk::g_tune_mu);
+  fqk::g_tuned.clear();
+  return FQ_OK;
+}
+
+}  // extern "C"

@@ -63,6 +63,9 @@ def load():
             "fq_batched_plan_upload": (i32, [vp, vp, vp]),
             "fq_matmul_batched": (i32, [vp, vp, vp, vp, vp, vp]),
             "fq_batched_plan_destroy": (i32, [vp]),
+            "fq_autotune": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, vp]),
+            "fq_autotune_lookup": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "fq_autotune_clear": (i32, []),
             "fq_error_string": (ctypes.c_char_p, [i32]),
             "fq_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -173,6 +176,22 @@ def kernels(q: int) -> list[dict]:
                "fq_kernel_info")
         out.append({"index": i, "k": k.value, "max_rows": rows.value, "cols": cols.value, "warps": warps.value})
     return out
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("kernel", ctypes.c_int), ("ms", ctypes.c_float),
+                ("ms_planner", ctypes.c_float), ("ms_mma", ctypes.c_float)]
+
+
+def autotune(a: Packed, b: Packed, out: Packed | None = None, stream=None) -> dict:
+    """fq_autotune: time every candidate on these operands; later AUTO products of
+    this shape use the fastest.  Returns the measurement."""
+    m, l, n = a.rows, a.cols, b.cols
+    out = empty(a.q, m, n, a.data.device) if out is None else out
+    r = TuneResult()
+    _check(load().fq_autotune(a.q, m, l, n, ctypes.c_void_p(a.data.data_ptr()), ctypes.c_void_p(b.data.data_ptr()),
+                              ctypes.c_void_p(out.data.data_ptr()), _stream(stream), ctypes.byref(r)), "fq_autotune")
+    return {"path": r.path, "kernel": r.kernel, "ms": r.ms, "ms_planner": r.ms_planner, "ms_mma": r.ms_mma}
 
 
 class BatchPlan:

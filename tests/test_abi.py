@@ -103,3 +103,10 @@ def test_batch_plan_host_side(lib):
     assert lib.fq_batched_plan_create(3, 1, i64p(bad), i64p(bad), i64p(bad), ctypes.byref(h)) == fq.EINVAL
     assert lib.fq_batched_plan_create(6, 1, i64p(m), i64p(l), i64p(n), ctypes.byref(h)) == fq.EINVAL
     assert lib.fq_batched_workspace_bytes(None) == -1
+
+
+def test_autotune_cache_host_side(lib):
+    from paper_0901_1413_gb300 import fq
+    assert lib.fq_autotune_clear() == fq.OK
+    assert lib.fq_autotune_lookup(3, 10, 10, 10, None, None) == fq.ENOTSUP
+    assert lib.fq_autotune(6, 10, 10, 10, None, None, None, None, None) == fq.EINVAL

@@ -1,6 +1,7 @@
 """CUDA path vs the CPU oracle, element by element, through the C ABI.
 
 Integer work: every comparison is bit-exact (zero tolerance)."""
+import ctypes
 import itertools
 
 import numpy as np
@@ -324,3 +325,57 @@ def test_mma_path_degenerate(fq):
     c.data.fill_(-1)
     fq.matmul(fq.empty(5, 4, 0), fq.empty(5, 0, 70), out=c, path=fq.PATH_MMA)
     assert not c.data.cpu().numpy().any()
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_autotune_picks_a_candidate_and_auto_uses_it(fq, q):
+    lib = fq.load()
+    lib.fq_autotune_clear()
+    m, l, n = 700, 900, 600
+    A = inputs.uniform(q, m, l, seed=21, stream=inputs.STREAM_A)
+    B = inputs.uniform(q, l, n, seed=21, stream=inputs.STREAM_B)
+    a, b = gpu_pack(fq, q, A), gpu_pack(fq, q, B)
+    c = fq.empty(q, m, n)
+    res = fq.autotune(a, b, out=c)
+    want = oracle.matmul(q, A, B)
+    assert np.array_equal(fq.unpack(c).cpu().numpy(), want)          # C holds the product
+    assert res["path"] in (fq.PATH_M4RM, fq.PATH_MMA) and res["ms"] > 0
+    assert res["ms"] <= res["ms_planner"] + 1e-6 and res["ms"] <= res["ms_mma"] + 1e-6
+    path, kernel = ctypes.c_int(), ctypes.c_int()
+    assert lib.fq_autotune_lookup(q, m, l, n, ctypes.byref(path), ctypes.byref(kernel)) == fq.OK
+    assert (path.value, kernel.value) == (res["path"], res["kernel"])
+    got = fq.unpack(fq.matmul(a, b)).cpu().numpy()                       # AUTO: the tuned choice
+    assert np.array_equal(got, want)
+    lib.fq_autotune_clear()
+    assert lib.fq_autotune_lookup(q, m, l, n, None, None) == fq.ENOTSUP
+
+
+def _large_case(fq, q, m, l, n, rows=16):
+    """M4RM and the tensor-core path on a large product: the two agree bit for
+    bit, sampled rows equal the oracle, and Freivalds accepts the whole result."""
+    A = inputs.uniform_torch(q, m, l, seed=5, stream=inputs.STREAM_A)
+    B = inputs.uniform_torch(q, l, n, seed=5, stream=inputs.STREAM_B)
+    a, b = fq.pack(q, A), fq.pack(q, B)
+    c1 = fq.matmul(a, b, path=fq.PATH_M4RM)
+    c2 = fq.matmul(a, b, path=fq.PATH_MMA)
+    assert fq.status() == fq.OK
+    assert torch.equal(c1.data, c2.data)
+    del c2
+    C = fq.unpack(c1).cpu().numpy()
+    Bh = B.cpu().numpy()
+    sample = np.random.default_rng(m + n).choice(m, size=rows, replace=False)
+    Ah = inputs.uniform(q, 1, l, seed=5, stream=inputs.STREAM_A, row0=0)  # row 0 drawn on the host
+    assert np.array_equal(Ah[0], A[0].cpu().numpy())                      # same draws as on the GPU
+    Arows = A[torch.from_numpy(sample).cuda()].cpu().numpy()
+    assert np.array_equal(C[sample], oracle.matmul(q, Arows, Bh))
+    assert oracle.freivalds(q, A.cpu().numpy(), Bh, C, trials=1, seed=q)
+
+
+@pytest.mark.slow
+def test_large_f5_32768_both_paths(fq):
+    _large_case(fq, 5, 32768, 32768, 32768)
+
+
+@pytest.mark.slow
+def test_large_f3_rectangular_65536_4096_4096(fq):
+    _large_case(fq, 3, 65536, 4096, 4096, rows=32)
