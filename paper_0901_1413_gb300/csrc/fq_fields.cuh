@@ -111,13 +111,31 @@ struct F7 {
     const uint32_t n[P] = {~y[0], ~y[1], ~y[2]};
     add(x, n);
   }
-  // acc += t0 + 2 t1 + 4 t2; doubling is a rotation of the planes (Section 4.2).
+  // acc += t0 + 2 t1 + 4 t2.  Doubling is a rotation of the planes (Section
+  // 4.2); because 8 = 1 mod 7 a carry-save adder works mod 7 too (its carry
+  // vector rotates instead of shifting), so the four operands are compressed
+  // to two with two carry-save adders and finished with one add.
+  __device__ __forceinline__ static void csa(const uint32_t (&x)[P], const uint32_t (&y)[P], const uint32_t (&z)[P],
+                                             uint32_t (&s)[P], uint32_t (&c)[P]) {
+    uint32_t m[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      s[i] = lop3<0x96>(x[i], y[i], z[i]);
+      m[i] = lop3<0xE8>(x[i], y[i], z[i]);
+    }
+    c[0] = m[2];  // carry out of bit 2 has weight 8 = 1 mod 7
+    c[1] = m[0];
+    c[2] = m[1];
+  }
   __device__ __forceinline__ static void accumulate(uint32_t (&acc)[P], const uint32_t (&t)[D][P]) {
-    add(acc, t[0]);
     const uint32_t d1[P] = {t[1][2], t[1][0], t[1][1]};
-    add(acc, d1);
     const uint32_t d2[P] = {t[2][1], t[2][2], t[2][0]};
-    add(acc, d2);
+    uint32_t s1[P], c1[P], s2[P], c2[P];
+    csa(t[0], d1, d2, s1, c1);
+    csa(acc, s1, c1, s2, c2);
+#pragma unroll
+    for (int i = 0; i < P; ++i) acc[i] = s2[i];
+    add(acc, c2);
   }
   // Canonical code: 7 (111) -> 0, others unchanged (Section 4.2's reduce with the
   // common term read as a0 & a1 & a2).
@@ -167,14 +185,51 @@ struct F5 {
     neg(y, n);
     add(x, n);
   }
-  // acc += t0 + 2 t1 + 4 t2, with 4 = -1 mod 5.
+  // acc += t0 + 2 t1 + 4 t2, computed mod 15 = 3 * 5 and folded back to F_5.
+  // Mod 15 (16 = 1) doubling a 4-bit number rotates it and carry-save adders
+  // wrap their carry, as for F_7 mod 7: 2 t1 = (0, t1_0, t1_1, t1_2) and
+  // 4 t2 = (t2_2, 0, t2_0, t2_1) as 4-bit numbers.  Two carry-save adders take
+  // acc, t0, 2 t1, 4 t2 to two 4-bit numbers, one end-around add to one, and
+  // fold5 (Section 4.2) to a 3-bit code with the same value mod 5.
   __device__ __forceinline__ static void accumulate(uint32_t (&acc)[P], const uint32_t (&t)[D][P]) {
-    add(acc, t[0]);
-    uint32_t u[P];
-    dbl(t[1], u);
-    add(acc, u);
-    neg(t[2], u);
-    add(acc, u);
+    // first carry-save adder on x = t0, y = 2 t1, z = 4 t2 (zero bits dropped)
+    uint32_t s[4], m[4];
+    s[0] = t[0][0] ^ t[2][2];
+    m[0] = t[0][0] & t[2][2];
+    s[1] = t[0][1] ^ t[1][0];
+    m[1] = t[0][1] & t[1][0];
+    s[2] = lop3<0x96>(t[0][2], t[1][1], t[2][0]);
+    m[2] = lop3<0xE8>(t[0][2], t[1][1], t[2][0]);
+    s[3] = t[1][2] ^ t[2][1];
+    m[3] = t[1][2] & t[2][1];
+    // carry vector rotated: weight 16 = 1 mod 15
+    const uint32_t c[4] = {m[3], m[0], m[1], m[2]};
+    // second carry-save adder with acc (3 bits)
+    uint32_t u[4], v[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      u[i] = lop3<0x96>(acc[i], s[i], c[i]);
+      v[i] = lop3<0xE8>(acc[i], s[i], c[i]);
+    }
+    u[3] = s[3] ^ c[3];
+    v[3] = s[3] & c[3];
+    const uint32_t w[4] = {v[3], v[0], v[1], v[2]};
+    // u + w mod 15: 4-bit add, then the carry out added back at bit 0
+    uint32_t r[4];
+    r[0] = u[0] ^ w[0];
+    uint32_t k = u[0] & w[0];
+#pragma unroll
+    for (int i = 1; i < 4; ++i) {
+      r[i] = lop3<0x96>(u[i], w[i], k);
+      k = lop3<0xE8>(u[i], w[i], k);
+    }
+    const uint32_t a0 = r[0] & k;
+    const uint32_t b0 = r[1] & a0;
+    const uint32_t q0 = r[0] ^ k;
+    const uint32_t q1 = r[1] ^ a0;
+    const uint32_t q2 = r[2] ^ b0;
+    const uint32_t q3 = r[3] ^ (r[2] & b0);
+    fold5(q0, q1, q2, q3, acc);
   }
   // Canonical code: 5, 6, 7 -> 0, 1, 2 (c marks codes >= 5).  Section 4.2's
   // printed reduce is not a reduction; this one is derived from the code table.
