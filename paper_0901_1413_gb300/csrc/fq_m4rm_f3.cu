@@ -16,22 +16,22 @@ int run(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, u
 
 // {k, row slots, launcher, rows per slot, columns per CTA, warps per CTA}
 const Variant kVariants[] = {
-    {8, 24, &run_ws<ws::Cfg<F3, 8, 24, 4>>, 48, 512, 16},
-    {8, 20, &run_ws<ws::Cfg<F3, 8, 20, 4>>, 48, 512, 16},
-    {8, 16, &run_ws<ws::Cfg<F3, 8, 16, 4>>, 48, 512, 16},
-    {8, 12, &run_ws<ws::Cfg<F3, 8, 12, 4>>, 48, 512, 16},
-    {8, 8, &run_ws<ws::Cfg<F3, 8, 8, 4>>, 48, 512, 16},
-    {8, 4, &run_ws<ws::Cfg<F3, 8, 4, 4>>, 48, 512, 16},
-    {7, 24, &run_ws<ws::Cfg<F3, 7, 24, 4>>, 48, 512, 16},
-    {6, 24, &run_ws<ws::Cfg<F3, 6, 24, 4>>, 48, 512, 16},
-    {9, 16, &run_ws<ws::Cfg<F3, 9, 16, 4>>, 48, 512, 16},
-    {8, 32, &run_ws<ws::Cfg<F3, 8, 32, 8>>, 32, 512, 16},
-    {8, 24, &run_ws<ws::Cfg<F3, 8, 24, 8>>, 32, 512, 16},
-    {8, 16, &run_ws<ws::Cfg<F3, 8, 16, 8>>, 32, 512, 16},
-    {8, 8, &run_ws<ws::Cfg<F3, 8, 8, 8>>, 32, 512, 16},
-    {7, 32, &run_ws<ws::Cfg<F3, 7, 32, 8>>, 32, 512, 16},
-    {6, 32, &run_ws<ws::Cfg<F3, 6, 32, 8>>, 32, 512, 16},
-    {9, 16, &run_ws<ws::Cfg<F3, 9, 16, 8>>, 32, 512, 16},
+    {8, 20, &run_ws<ws::Cfg<F3, 8, 20, 4, 3>>, 48, 512, 16},
+    {8, 16, &run_ws<ws::Cfg<F3, 8, 16, 4, 3>>, 48, 512, 16},
+    {8, 12, &run_ws<ws::Cfg<F3, 8, 12, 4, 3>>, 48, 512, 16},
+    {8, 8, &run_ws<ws::Cfg<F3, 8, 8, 4, 3>>, 48, 512, 16},
+    {8, 4, &run_ws<ws::Cfg<F3, 8, 4, 4, 3>>, 48, 512, 16},
+    {8, 24, &run_ws<ws::Cfg<F3, 8, 24, 4, 2>>, 48, 512, 16},
+    {7, 24, &run_ws<ws::Cfg<F3, 7, 24, 4, 2>>, 48, 512, 16},
+    {6, 24, &run_ws<ws::Cfg<F3, 6, 24, 4, 2>>, 48, 512, 16},
+    {9, 16, &run_ws<ws::Cfg<F3, 9, 16, 4, 2>>, 48, 512, 16},
+    {8, 32, &run_ws<ws::Cfg<F3, 8, 32, 8, 2>>, 32, 512, 16},
+    {8, 24, &run_ws<ws::Cfg<F3, 8, 24, 8, 2>>, 32, 512, 16},
+    {8, 16, &run_ws<ws::Cfg<F3, 8, 16, 8, 2>>, 32, 512, 16},
+    {8, 8, &run_ws<ws::Cfg<F3, 8, 8, 8, 2>>, 32, 512, 16},
+    {7, 32, &run_ws<ws::Cfg<F3, 7, 32, 8, 2>>, 32, 512, 16},
+    {6, 32, &run_ws<ws::Cfg<F3, 6, 32, 8, 2>>, 32, 512, 16},
+    {9, 16, &run_ws<ws::Cfg<F3, 9, 16, 8, 2>>, 32, 512, 16},
     {10, 16, &run<M4rmCfg<F3, 10, 8, 2, 16, 16>>, 64, 512, 16},
 };
 }  // namespace

@@ -14,9 +14,10 @@
 //  * 16 - NPW consumer warps (the other warpgroups, most registers): for every block,
 //    gather D table entries per row and add them into register accumulators.
 //
-// Tables are double-buffered by block and offsets by chunk: while consumers
-// read table s & 1, producers fill table (s + 1) & 1, and the offsets of chunk
-// c + 1 are written while chunk c is consumed.  Hand-over is by mbarriers (tfull: 128
+// Tables are double- or triple-buffered by block (NBUF) and offsets
+// double-buffered by chunk: while consumers read table s mod NBUF, producers
+// fill the next ones, and the offsets of chunk c + 1 are written while chunk c
+// is consumed.  Hand-over is by mbarriers (tfull: 128
 // producer arrivals; tempty: 384 consumer arrivals).  Every wait is bounded;
 // on a timeout the CTA records FQ_ETIMEOUT, stops waiting and runs out its
 // loops without further synchronisation hazards.
@@ -35,7 +36,7 @@ __host__ __device__ constexpr int popc(int x) { return x == 0 ? 0 : (x & 1) + po
 __host__ __device__ constexpr int ctz(int x) { return (x & 1) ? 0 : 1 + ctz(x >> 1); }
 constexpr int round128(int x) { return (x + 127) / 128 * 128; }
 
-template <class F, int K_, int RS_, int NPW_ = 4>
+template <class F, int K_, int RS_, int NPW_ = 4, int NBUF_ = 2>
 struct Cfg {
   using Field = F;
   static_assert(F::P == 2 && F::D == 2, "two planes, basis of two");
@@ -45,13 +46,15 @@ struct Cfg {
   static constexpr int P = 2, D = 2;
   static constexpr int LPR = 8, GPW = 4, WPL = 2, PW = 4;  // 8-lane groups, 2 words per plane
   static constexpr int NPW = NPW_, NCW = 16 - NPW;         // producer / consumer warps
+  static constexpr int NBUF = NBUF_;                        // table (and B stage) buffers
+  static_assert(NBUF == 2 || NBUF == 3, "double or triple buffering");
   static_assert(NPW == 4 || NPW == 8, "one or two producer warpgroups");
   static constexpr int NT = (NPW + NCW) * 32;
   static constexpr int NPT = NPW * 32;                      // producer threads
   static constexpr int PREG = NPW == 4 ? 80 : 64;           // registers after setmaxnreg
   static constexpr int CREG = NPW == 4 ? 144 : 192;
   static_assert(NPT * PREG + NCW * 32 * CREG == 65536, "register split");
-  static constexpr int ENTRY = 128;                         // bytes per table entry
+  static constexpr int ENTRY = 128;                         // bytes per table entry (idx * 128 below)
   static constexpr int ENTRIES = 1 << K;
   static constexpr int CT = 512, CTW = 8;                   // columns (words) per tile
   static constexpr int ROWS_PER_SLOT = NCW * GPW;
@@ -71,11 +74,11 @@ struct Cfg {
   static constexpr int ABOX_BYTES = ABOX_WORDS * ABOX_ROWS * P * 8;
   static constexpr int ASTAGE_BYTES = ABOXES * ABOX_BYTES;  // [box][p][rows][4] uint64
   static constexpr int TABLE_OFF = 0;
-  static constexpr int OFFS_OFF = 2 * TABLE_BYTES;
+  static constexpr int OFFS_OFF = NBUF * TABLE_BYTES;
   static constexpr int BSTAGE_OFF = OFFS_OFF + 2 * OFFS_BYTES;
-  static constexpr int ASTAGE_OFF = BSTAGE_OFF + 2 * STAGE_STRIDE;
-  static constexpr int BAR_OFF = ASTAGE_OFF + ASTAGE_BYTES;  // bfull[2], tfull[2], tempty[2], afull
-  static constexpr int ABORT_OFF = BAR_OFF + 56;
+  static constexpr int ASTAGE_OFF = BSTAGE_OFF + NBUF * STAGE_STRIDE;
+  static constexpr int BAR_OFF = ASTAGE_OFF + ASTAGE_BYTES;  // bfull[NBUF], tfull[NBUF], tempty[NBUF], afull
+  static constexpr int ABORT_OFF = BAR_OFF + 8 * (3 * NBUF + 1);
   static constexpr int SMEM = ABORT_OFF + 16;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -177,11 +180,22 @@ __device__ __forceinline__ void build_offsets(const Params &prm, const unsigned 
         win[0] &= keep;
         win[1] &= keep;
       }
+      if constexpr (C::K == 8) {
+        // byte b of each map: one byte permute, then idx * 128 in both halves
 #pragma unroll
-      for (int b = 0; b < C::NB; ++b) {
-        const uint32_t i0 = uint32_t(win[0] >> (b * C::K)) & mask;
-        const uint32_t i1 = uint32_t(win[1] >> (b * C::K)) & mask;
-        packed[h][b] = (i0 * uint32_t(C::ENTRY)) | ((i1 * uint32_t(C::ENTRY)) << 16);
+        for (int b = 0; b < 8; ++b) {
+          const uint32_t x = uint32_t(win[0] >> (32 * (b >> 2)));
+          const uint32_t y = uint32_t(win[1] >> (32 * (b >> 2)));
+          const uint32_t r = __byte_perm(x, y, uint32_t(b & 3) | (uint32_t(4 + (b & 3)) << 4));
+          packed[h][b] = ((r & 0xFFu) << 7) | ((r & 0xFF00u) << 15);
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < C::NB; ++b) {
+          const uint32_t i0 = uint32_t(win[0] >> (b * C::K)) & mask;
+          const uint32_t i1 = uint32_t(win[1] >> (b * C::K)) & mask;
+          packed[h][b] = (i0 * uint32_t(C::ENTRY)) | ((i1 * uint32_t(C::ENTRY)) << 16);
+        }
       }
     }
     uint2 *dst = reinterpret_cast<uint2 *>(offs) + j * C::ROWS_PER_SLOT + rem;
@@ -314,17 +328,17 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
   const int64_t w0 = int64_t(blockIdx.x) * C::CTW;
 
   const uint32_t base = smem_u32(smem);
-  const uint32_t bfull = base + C::BAR_OFF, tfull = bfull + 16, tempty = bfull + 32, afull = bfull + 48;
+  const uint32_t bfull = base + C::BAR_OFF, tfull = bfull + 8 * C::NBUF, tempty = bfull + 16 * C::NBUF,
+                 afull = bfull + 24 * C::NBUF;
   volatile int &abort_flag = *reinterpret_cast<int *>(smem + C::ABORT_OFF);
 
   if (tid == 0) {
     abort_flag = 0;
-    mbar_init(bfull, 1);
-    mbar_init(bfull + 8, 1);
-    mbar_init(tfull, C::NPT);
-    mbar_init(tfull + 8, C::NPT);
-    mbar_init(tempty, C::NCW * 32);
-    mbar_init(tempty + 8, C::NCW * 32);
+    for (int i = 0; i < C::NBUF; ++i) {
+      mbar_init(bfull + 8 * i, 1);
+      mbar_init(tfull + 8 * i, C::NPT);
+      mbar_init(tempty + 8 * i, C::NCW * 32);
+    }
     mbar_init(afull, 1);
     fence_mbar_init();
   }
@@ -337,7 +351,7 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
     const int builder = warp * C::GPW + grp;
     const uint32_t tbl_lane0 = base + C::TABLE_OFF + uint32_t(gl * 16);
     if (ptid == 0) {
-      for (int64_t s = 0; s < 2 && s < prm.nblocks; ++s) {
+      for (int64_t s = 0; s < C::NBUF && s < prm.nblocks; ++s) {
         mbar_expect_tx(bfull + 8 * uint32_t(s), C::STAGE_BYTES);
         tma_load_3d(base + C::BSTAGE_OFF + uint32_t(s) * C::STAGE_STRIDE, &tmB, bfull + 8 * uint32_t(s), int(w0),
                     int(s * C::K), 0);
@@ -361,16 +375,16 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
       }
     }
     for (int64_t s = 0; s < prm.nblocks; ++s) {
-      const int buf = int(s & 1);
-      const uint32_t use = uint32_t(s >> 1);
-      if (s % C::NB == 1) {
-        // second block of chunk c: write the offsets of chunk c + 1 into the
+      const int buf = int(s % C::NBUF);
+      const uint32_t use = uint32_t(s / C::NBUF);
+      if (s % C::NB == C::NBUF - 1) {
+        // block NBUF - 1 of chunk c: write the offsets of chunk c + 1 into the
         // buffer chunk c - 1 used -- consumers are done with it once block
-        // s - 2 is consumed, the same wait the table buffer needs below -- then
-        // prefetch the A words of chunk c + 2
+        // s - NBUF is consumed, the same wait the table buffer needs below --
+        // then prefetch the A words of chunk c + 2
         const int64_t c = s / C::NB;
         if (c + 1 < nchunks) {
-          if (s >= 2) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
+          if (s >= C::NBUF) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
           wait_or_abort(afull, aphase & 1, abort_flag, prm.err);
           ++aphase;
           const int64_t c1 = (c + 1) * C::NB;
@@ -383,16 +397,16 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
           }
         }
       }
-      if (s >= 2) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
+      if (s >= C::NBUF) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
       wait_or_abort(bfull + 8 * buf, use & 1, abort_flag, prm.err);
       build_table<C>(tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), base + C::BSTAGE_OFF + buf * C::STAGE_STRIDE,
                      builder, gl);
       producer_sync<C::NPT>();  // every producer is done with this B stage
-      if (ptid == 0 && s + 2 < prm.nblocks && !abort_flag) {
+      if (ptid == 0 && s + C::NBUF < prm.nblocks && !abort_flag) {
         fence_proxy_async_smem();
         mbar_expect_tx(bfull + 8 * buf, C::STAGE_BYTES);
         tma_load_3d(base + C::BSTAGE_OFF + buf * C::STAGE_STRIDE, &tmB, bfull + 8 * buf, int(w0),
-                    int((s + 2) * C::K), 0);
+                    int((s + C::NBUF) * C::K), 0);
       }
       mbar_arrive(tfull + 8 * buf);
     }
@@ -407,8 +421,8 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0u;
     for (int64_t s = 0; s < prm.nblocks; ++s) {
-      const int buf = int(s & 1);
-      wait_or_abort(tfull + 8 * buf, uint32_t(s >> 1) & 1, abort_flag, prm.err);
+      const int buf = int(s % C::NBUF);
+      wait_or_abort(tfull + 8 * buf, uint32_t(s / C::NBUF) & 1, abort_flag, prm.err);
       const int64_t c = s / C::NB;
       const uint32_t offs_s =
           base + C::OFFS_OFF + uint32_t(c & 1) * C::OFFS_BYTES + uint32_t((s - c * C::NB) * C::MT) * 4u;
