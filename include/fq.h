@@ -182,6 +182,17 @@ int fq_autotune(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const
 int fq_autotune_lookup(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel);
 int fq_autotune_clear(void);
 
+/* The path and kernel that fq_matmul_ex with FQ_PATH_AUTO, k = 0 and kernel = 0
+ * takes for (q, m, l, n) on the current device: the fq_autotune choice when
+ * one is remembered, otherwise the path with the smaller modelled time
+ * (kernel 0, the M4RM planner).  The model counts waves of one CTA per SM
+ * times block steps times the measured cycles of one step of each path; it
+ * picks the tensor-core path for small products (up to about 1024 on a side
+ * for F_3), where the Four-Russians tables are not amortised over enough
+ * rows.  Host-only apart from the device attribute query; FQ_EINVAL for a
+ * bad q, a negative size or a null pointer, FQ_ECUDA if no device answers. */
+int fq_auto_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel);
+
 /* Compiled M4RM kernels for field q (planner candidates).  fq_kernel_count
  * returns their number (0 for a bad q); fq_kernel_info describes kernel idx:
  * block size k, the most rows one CTA holds, columns per CTA and warps per CTA.

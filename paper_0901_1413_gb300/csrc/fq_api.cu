@@ -108,6 +108,20 @@ int fq_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t 
   return fqk::launch_add(q, rows, cols, X, Y, Z, sub, static_cast<cudaStream_t>(stream));
 }
 
+int fq_auto_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel) {
+  if (!valid_q(q) || m < 0 || l < 0 || n < 0 || !path || !kernel) return FQ_EINVAL;
+  *path = FQ_PATH_M4RM;
+  *kernel = 0;
+  if (fqk::tuned_choice(q, m, l, n, path, kernel)) return FQ_OK;
+  if (m == 0 || l == 0 || n == 0) return FQ_OK;
+  // no measurement for this shape: the cheaper path by the time model
+  int dev = 0, sms = 0;
+  FQ_CUDA_TRY(cudaGetDevice(&dev));
+  FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (fqk::mma_estimate(q, m, l, n, sms) < fqk::m4rm_estimate(q, m, l, n, sms)) *path = FQ_PATH_MMA;
+  return FQ_OK;
+}
+
 int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                  void *stream, const fq_options *opt) {
   if (!valid_q(q) || m < 0 || l < 0 || n < 0) return FQ_EINVAL;
@@ -125,11 +139,7 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, cons
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (o.kernel < 0) return FQ_EINVAL;
   if (o.path == FQ_PATH_AUTO && o.k == 0 && o.kernel == 0 && o.variant == 0) {
-    int path = 0, kernel = 0;
-    if (fqk::tuned_choice(q, m, l, n, &path, &kernel)) {
-      o.path = path;
-      o.kernel = kernel;
-    }
+    if (int rc = fq_auto_choice(q, m, l, n, &o.path, &o.kernel)) return rc;
   }
   if (o.path == FQ_PATH_MMA) return fqk::launch_mma(q, m, l, n, A, B, C, o.chunk, s);
   return fqk::launch_m4rm(q, m, l, n, A, B, C, o.k, o.variant, o.kernel, s);

@@ -28,6 +28,11 @@ struct Variant {
 // The variant table of field q (nullptr and 0 for a bad q).
 const Variant *m4rm_variants(int q, int *count);
 
+// Modelled times (SM cycles) of the two paths for a product, for the
+// FQ_PATH_AUTO choice when no measured choice exists.
+double m4rm_estimate(int q, int64_t m, int64_t l, int64_t n, int sms);
+double mma_estimate(int q, int64_t m, int64_t l, int64_t n, int sms);
+
 // The autotuned (path, kernel) for a shape, if fq_autotune measured one.
 bool tuned_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel);
 

@@ -274,6 +274,16 @@ int launch_q(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t 
 
 }  // namespace
 
+// Modelled time (SM cycles) of the tensor-core path: waves of CTAs (one per
+// SM) times 64-column k-steps times the measured cycles of one k-step, plus a
+// constant for launch, the first loads and the epilogue (fitted on GB300).
+double mma_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
+  const int bn = q == 4 ? MmaSpec<4>::BN : 128;
+  const double per_step = q == 3 ? 4800.0 : (q == 4 ? 8670.0 : 8040.0);
+  const int64_t ctas = (fq_pitch_words(n) * 64 / bn) * cdiv(m, 128);
+  return double(cdiv(ctas, sms)) * double(cdiv(l, 64)) * per_step + 52000.0;
+}
+
 int launch_mma(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                int64_t chunk, cudaStream_t s) {
   switch (q) {

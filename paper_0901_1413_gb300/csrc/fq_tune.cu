@@ -31,6 +31,38 @@ bool tuned_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel
   return true;
 }
 
+// Modelled time (SM cycles) of the planner's M4RM choice: per wave of one
+// CTA per SM and per block of k columns of A, the larger of the table build
+// (the producer warps of the F_3 and GF(4) kernels build the next table while
+// the consumers look up the current one) and the lookups (a fixed part plus a
+// part per row of the tile), plus a constant for launch and the last store.
+// The constants are fitted to GB300 measurements of the compiled kernels.
+double m4rm_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
+  double fixed = 300.0, per_row = 2.9, build = 1700.0;
+  if (q == 5) {
+    fixed = 1500.0;
+    per_row = 26.0;
+    build = 0.0;
+  } else if (q == 7) {
+    fixed = 1200.0;
+    per_row = 21.6;
+    build = 0.0;
+  }
+  int nv = 0;
+  const Variant *vs = m4rm_variants(q, &nv);
+  double best = 1e300;
+  for (int i = 0; i < nv; ++i) {
+    const int64_t rows = int64_t(vs[i].rs) * vs[i].rows_per_slot;
+    const int64_t ctas = cdiv(m, rows) * (fq_pitch_words(n) / (vs[i].cols / 64));
+    const double scale = double(1 << vs[i].k) / 256.0;
+    const double lookups = fixed * scale + per_row * double(rows < m ? rows : m);
+    const double per_block = lookups > build * scale ? lookups : build * scale;
+    const double t = double(cdiv(ctas, sms)) * double(cdiv(l, vs[i].k)) * per_block;
+    best = t < best ? t : best;
+  }
+  return best + 20000.0;
+}
+
 }  // namespace fqk
 
 extern "C" {

@@ -66,6 +66,7 @@ def load():
             "fq_autotune": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, vp]),
             "fq_autotune_lookup": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "fq_autotune_clear": (i32, []),
+            "fq_auto_choice": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "fq_error_string": (ctypes.c_char_p, [i32]),
             "fq_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -192,6 +193,13 @@ def autotune(a: Packed, b: Packed, out: Packed | None = None, stream=None) -> di
     _check(load().fq_autotune(a.q, m, l, n, ctypes.c_void_p(a.data.data_ptr()), ctypes.c_void_p(b.data.data_ptr()),
                               ctypes.c_void_p(out.data.data_ptr()), _stream(stream), ctypes.byref(r)), "fq_autotune")
     return {"path": r.path, "kernel": r.kernel, "ms": r.ms, "ms_planner": r.ms_planner, "ms_mma": r.ms_mma}
+
+
+def auto_choice(q: int, m: int, l: int, n: int) -> tuple[int, int]:
+    """fq_auto_choice: the (path, kernel) an AUTO product of this shape takes."""
+    path, kernel = ctypes.c_int(), ctypes.c_int()
+    _check(load().fq_auto_choice(q, m, l, n, ctypes.byref(path), ctypes.byref(kernel)), "fq_auto_choice")
+    return path.value, kernel.value
 
 
 class BatchPlan:

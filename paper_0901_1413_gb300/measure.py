@@ -1,0 +1,108 @@
+"""Time the product configurations on cuda:0 and print a Markdown table.
+
+    python -m paper_0901_1413_gb300.measure [--quick]
+
+Every row is measured with CUDA events on the current stream, best of a few
+runs after one warm-up, inputs resident in device memory (seeded synthetic
+residues, uniform unless stated).  Throughput is 2 m l n / t in field
+operations per second; batched rows also give products per second.  Both
+product paths are timed where the configuration asks for them: the bitsliced
+Four-Russians path (M4RM) and the exact tensor-core path (MMA).
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+from . import fq, inputs
+
+
+def _time(fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def _operands(q, m, l, n, sparse=False):
+    gen = inputs.sparse_torch if sparse else inputs.uniform_torch
+    a = fq.pack(q, gen(q, m, l, seed=0, stream=inputs.STREAM_A))
+    b = fq.pack(q, inputs.uniform_torch(q, l, n, seed=0, stream=inputs.STREAM_B))
+    return a, b, fq.empty(q, m, n)
+
+
+def product_rows(q, m, l, n, paths=("m4rm",), sparse=False, reps=3):
+    a, b, c = _operands(q, m, l, n, sparse)
+    ops = 2.0 * m * l * n
+    out = []
+    for p in paths:
+        path = fq.PATH_M4RM if p == "m4rm" else fq.PATH_MMA
+        t = _time(lambda: fq.matmul(a, b, out=c, path=path), reps)
+        out.append((p, t, ops / t * 1e3))
+    if fq.status() != fq.OK:
+        raise RuntimeError("device reported an error")
+    return out
+
+
+def batched_row(q, count=4096, reps=5):
+    shapes = [tuple(int(x) for x in s) for s in inputs.batch_shapes(count, seed=q)]
+    a, b, c = [], [], []
+    for p, (m, l, n) in enumerate(shapes):
+        a.append(fq.pack(q, inputs.uniform_torch(q, m, l, seed=q, stream=100 + 2 * p)))
+        b.append(fq.pack(q, inputs.uniform_torch(q, l, n, seed=q, stream=101 + 2 * p)))
+        c.append(fq.empty(q, m, n))
+    ptr = lambda xs: torch.tensor([x.data.data_ptr() for x in xs], dtype=torch.int64, device="cuda")
+    pa, pb, pc = ptr(a), ptr(b), ptr(c)
+    plan = fq.BatchPlan(q, shapes)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan.run(pa, pb, pc, stream=stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        plan.run(pa, pb, pc, stream=stream)
+    t = _time(graph.replay, reps)
+    if fq.status() != fq.OK:
+        raise RuntimeError("device reported an error")
+    ops = sum(2.0 * m * l * n for m, l, n in shapes)
+    return t, count / t * 1e3, ops / t * 1e3, plan.items
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--quick", action="store_true", help="skip the n = 32768 product")
+    args = ap.parse_args()
+    fq.load()
+    print("| configuration | path | ms | field-ops/s |")
+    print("|---|---|---:|---:|")
+
+    def emit(name, rows):
+        for p, t, r in rows:
+            print("| %s | %s | %.3f | %.3e |" % (name, p, t, r), flush=True)
+
+    for n in (512, 1024, 2048, 4096, 8192, 16384):
+        emit("F_3 %d^3" % n, product_rows(3, n, n, n, paths=("m4rm", "mma")))
+    emit("F_3 8192^3, A 90% zeros", product_rows(3, 8192, 8192, 8192, sparse=True, paths=("m4rm", "mma")))
+    for q, name in ((5, "F_5"), (7, "F_7"), (4, "GF(4)")):
+        emit("%s 8192^3" % name, product_rows(q, 8192, 8192, 8192, paths=("m4rm", "mma")))
+    emit("F_3 65536 x 4096 x 4096", product_rows(3, 65536, 4096, 4096, paths=("m4rm", "mma")))
+    if not args.quick:
+        emit("F_5 32768^3", product_rows(5, 32768, 32768, 32768, paths=("m4rm", "mma"), reps=2))
+    print()
+    print("| batched (4096 products, m, l, n uniform on 64..1024 step 64, one graph replay) | ms | products/s | field-ops/s | items |")
+    print("|---|---:|---:|---:|---:|")
+    for q, name in ((3, "F_3"), (5, "F_5")):
+        t, pps, ops, items = batched_row(q)
+        print("| %s | %.3f | %.3e | %.3e | %d |" % (name, t, pps, ops, items), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -110,3 +110,10 @@ def test_autotune_cache_host_side(lib):
     assert lib.fq_autotune_clear() == fq.OK
     assert lib.fq_autotune_lookup(3, 10, 10, 10, None, None) == fq.ENOTSUP
     assert lib.fq_autotune(6, 10, 10, 10, None, None, None, None, None) == fq.EINVAL
+    p, k = ctypes.c_int(-1), ctypes.c_int(-1)
+    assert lib.fq_auto_choice(6, 10, 10, 10, ctypes.byref(p), ctypes.byref(k)) == fq.EINVAL
+    assert lib.fq_auto_choice(3, -1, 10, 10, ctypes.byref(p), ctypes.byref(k)) == fq.EINVAL
+    assert lib.fq_auto_choice(3, 10, 10, 10, None, ctypes.byref(k)) == fq.EINVAL
+    # an empty product needs no device and takes the M4RM planner
+    assert lib.fq_auto_choice(3, 0, 10, 10, ctypes.byref(p), ctypes.byref(k)) == fq.OK
+    assert (p.value, k.value) == (fq.PATH_M4RM, 0)

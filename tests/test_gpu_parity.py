@@ -350,6 +350,30 @@ def test_autotune_picks_a_candidate_and_auto_uses_it(fq, q):
     assert lib.fq_autotune_lookup(q, m, l, n, None, None) == fq.ENOTSUP
 
 
+def test_auto_choice_by_time_model(fq):
+    """Without a measurement, AUTO takes the tensor-core path for a small F_3
+    product and Four-Russians for a large one; both give the oracle's result."""
+    fq.load().fq_autotune_clear()
+    assert fq.auto_choice(3, 512, 512, 512) == (fq.PATH_MMA, 0)
+    assert fq.auto_choice(3, 8192, 8192, 8192) == (fq.PATH_M4RM, 0)
+    assert fq.auto_choice(4, 8192, 8192, 8192) == (fq.PATH_M4RM, 0)
+    assert fq.auto_choice(3, 0, 512, 512) == (fq.PATH_M4RM, 0)
+    for q in FIELDS:
+        _check_product(fq, q, 512, 512, 512, seed=q + 40)       # AUTO, whichever path
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_auto_choice_follows_autotune(fq, q):
+    lib = fq.load()
+    lib.fq_autotune_clear()
+    a, b = fq.empty(q, 300, 200), fq.empty(q, 200, 100)
+    a.data.zero_()
+    b.data.zero_()
+    res = fq.autotune(a, b)
+    assert fq.auto_choice(q, 300, 200, 100) == (res["path"], res["kernel"])
+    lib.fq_autotune_clear()
+
+
 def _large_case(fq, q, m, l, n, rows=16):
     """M4RM and the tensor-core path on a large product: the two agree bit for
     bit, sampled rows equal the oracle, and Freivalds accepts the whole result."""
