@@ -8,6 +8,9 @@ codes:
   any 3-bit code is accepted on decode and read mod p (codes are not unique).
 * GF(4) (Section 4.3): element a0 + alpha a1 has code a0 + 2 a1, planes (a0, a1).
 * F_2: one plane.
+* F_{p^n} (``fields.EXTENSIONS``; Section 4.3's matrix-level view A = sum_j A_j
+  x^j): code sum_j c_j p^j; the planes of coefficient matrix A_0 (F_p codes
+  above), then those of A_1, and so on.  GF(4) is the case p = 2, n = 2.
 
 Word layout (a choice of this library; the paper's display puts element 0 at the
 left): element j of a row is bit (j mod 64) of 64-bit word floor(j / 64).
@@ -17,10 +20,15 @@ from __future__ import annotations
 
 import numpy as np
 
+from .fields import EXTENSIONS
+
 PLANES = {2: 1, 3: 2, 4: 2, 5: 3, 7: 3}
 
 
 def planes(q: int) -> int:
+    if q in EXTENSIONS:
+        p, n, _ = EXTENSIONS[q]
+        return n * PLANES[p]
     if q not in PLANES:
         raise ValueError("unsupported field size %r" % (q,))
     return PLANES[q]
@@ -31,6 +39,12 @@ def codes_to_bits(q: int, values: np.ndarray) -> list[np.ndarray]:
     v = np.asarray(values).astype(np.uint8)
     if np.any(v >= q):
         raise ValueError("residue out of range for q=%d" % q)
+    if q in EXTENSIONS and q != 4:
+        p, n, _ = EXTENSIONS[q]
+        out = []
+        for j in range(n):
+            out += codes_to_bits(p, (v.astype(np.int64) // p ** j) % p)
+        return out
     if q == 3:
         unit = (v != 0).astype(np.uint8)
         sign = (v == 2).astype(np.uint8)
@@ -41,6 +55,11 @@ def codes_to_bits(q: int, values: np.ndarray) -> list[np.ndarray]:
 def bits_to_values(q: int, bits: list[np.ndarray]) -> np.ndarray:
     """Decode per-element code bits to residues in [0, q)."""
     b = [np.asarray(x).astype(np.int64) for x in bits]
+    if q in EXTENSIONS and q != 4:
+        p, n, _ = EXTENSIONS[q]
+        P = PLANES[p]
+        return sum(bits_to_values(p, b[j * P:(j + 1) * P]).astype(np.int64) * p ** j
+                   for j in range(n)).astype(np.uint8)
     if q == 3:
         x0, x1 = b
         if np.any((x0 == 0) & (x1 == 1)):

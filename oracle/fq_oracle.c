@@ -1,5 +1,6 @@
 /*
- * TEST INFRASTRUCTURE ONLY -- the CPU oracle for C = AB over F_p and GF(4).
+ * TEST INFRASTRUCTURE ONLY -- the CPU oracle for C = AB over F_p, GF(4) and
+ * the extension fields F_{p^n}.
  *
  * Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
  * load this code.  It shares nothing with the CUDA path: no headers, no helpers,
@@ -17,6 +18,13 @@
  *  - GF(4) = F_2[x]/(x^2 + x + 1) (Section 4.3): element code c = c0 + 2*c1 is
  *    the polynomial c0 + c1*x; a product is polynomial multiplication over F_2
  *    followed by the substitution x^2 = x + 1; addition is XOR of codes.
+ *  - F_{p^n} = F_p[x]/(f) for a monic f of degree n (Section 4.3, "non-prime
+ *    fields"): element code c = sum_j c_j p^j is the polynomial sum_j c_j x^j.
+ *    Addition is coefficientwise mod p; a product is schoolbook polynomial
+ *    multiplication followed by the substitution x^n = r_0 + r_1 x + ... +
+ *    r_{n-1} x^{n-1} (f = x^n - sum_j r_j x^j), highest degree first.  Both
+ *    operations are tabulated once per call from that definition; the row
+ *    combination then reads the tables.
  *
  * Rows are independent, so an OpenMP loop over i is the only parallelism; it
  * changes no arithmetic.
@@ -115,4 +123,96 @@ int fq_oracle_matmul_gf4(int64_t m, int64_t l, int64_t n,
     }
   }
   return ORACLE_OK;
+}
+
+/* Coefficients (base p digits) of an F_{p^n} code. */
+static void ext_digits(int p, int n, unsigned c, int *d) {
+  for (int j = 0; j < n; ++j) {
+    d[j] = (int)(c % (unsigned)p);
+    c /= (unsigned)p;
+  }
+}
+
+static unsigned ext_code(int p, int n, const int *d) {
+  unsigned c = 0;
+  for (int j = n - 1; j >= 0; --j) c = c * (unsigned)p + (unsigned)d[j];
+  return c;
+}
+
+/* a * b in F_p[x]/(x^n - sum_j r_j x^j): schoolbook product, then each x^k with
+ * k >= n (highest first) replaced by x^(k-n) * sum_j r_j x^j. */
+static unsigned ext_mul(int p, int n, const int *r, unsigned a, unsigned b) {
+  int da[8], db[8];
+  int64_t e[16];
+  ext_digits(p, n, a, da);
+  ext_digits(p, n, b, db);
+  for (int k = 0; k < 2 * n - 1; ++k) e[k] = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) e[i + j] += (int64_t)da[i] * db[j];
+  for (int k = 2 * n - 2; k >= n; --k) {
+    for (int j = 0; j < n; ++j) e[k - n + j] += e[k] * r[j];
+    e[k] = 0;
+  }
+  int d[8];
+  for (int j = 0; j < n; ++j) d[j] = (int)(e[j] % p);
+  return ext_code(p, n, d);
+}
+
+static unsigned ext_add(int p, int n, unsigned a, unsigned b) {
+  int da[8], db[8], d[8];
+  ext_digits(p, n, a, da);
+  ext_digits(p, n, b, db);
+  for (int j = 0; j < n; ++j) d[j] = (da[j] + db[j]) % p;
+  return ext_code(p, n, d);
+}
+
+/* C = A * B over F_{p^n} with x^n = sum_j r[j] x^j, codes in [0, p^n) <= 255. */
+int fq_oracle_matmul_ext(int p, int n, const int *r, int64_t m, int64_t l, int64_t nn,
+                         const uint8_t *A, int64_t lda,
+                         const uint8_t *B, int64_t ldb,
+                         uint8_t *C, int64_t ldc, int threads) {
+  if (p < 2 || n < 1 || n > 7 || !r || m < 0 || l < 0 || nn < 0) return ORACLE_EINVAL;
+  int q = 1;
+  for (int j = 0; j < n; ++j) q *= p;
+  if (q > 256) return ORACLE_EINVAL;
+  for (int j = 0; j < n; ++j)
+    if (r[j] < 0 || r[j] >= p) return ORACLE_EINVAL;
+  if (m == 0 || nn == 0) return ORACLE_OK;
+  if (!A || !B || !C || lda < l || ldb < nn || ldc < nn) return ORACLE_EINVAL;
+  uint8_t *mul = (uint8_t *)malloc((size_t)q * (size_t)q);
+  uint8_t *add = (uint8_t *)malloc((size_t)q * (size_t)q);
+  if (!mul || !add) {
+    free(mul);
+    free(add);
+    return ORACLE_ENOMEM;
+  }
+  for (int a = 0; a < q; ++a)
+    for (int b = 0; b < q; ++b) {
+      mul[a * q + b] = (uint8_t)ext_mul(p, n, r, (unsigned)a, (unsigned)b);
+      add[a * q + b] = (uint8_t)ext_add(p, n, (unsigned)a, (unsigned)b);
+    }
+  int status = ORACLE_OK;
+  for (int64_t i = 0; i < m && status == ORACLE_OK; ++i)
+    for (int64_t j = 0; j < l; ++j)
+      if (A[i * lda + j] >= q) status = ORACLE_EINVAL;
+  for (int64_t j = 0; j < l && status == ORACLE_OK; ++j)
+    for (int64_t t = 0; t < nn; ++t)
+      if (B[j * ldb + t] >= q) status = ORACLE_EINVAL;
+  if (status == ORACLE_OK) {
+    int nt = set_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t i = 0; i < m; ++i) {
+      uint8_t *Ci = C + i * ldc;
+      memset(Ci, 0, (size_t)nn);
+      const uint8_t *Ai = A + i * lda;
+      for (int64_t j = 0; j < l; ++j) {          /* C_i += a_ij * B_j */
+        const uint8_t *mrow = mul + (size_t)Ai[j] * (size_t)q;
+        const uint8_t *Bj = B + j * ldb;
+        for (int64_t t = 0; t < nn; ++t) Ci[t] = add[(size_t)Ci[t] * (size_t)q + mrow[Bj[t]]];
+      }
+    }
+  }
+  free(mul);
+  free(add);
+  return status;
 }

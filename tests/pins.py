@@ -1,10 +1,13 @@
 """Pins for a matrix-product function over F_q: checks that fix the product by
 something other than its own formula (library routines, closed forms, algebraic
-identities, the GF(4) defining polynomial).  Each check takes ``mm(q, A, B)``
+identities, field axioms, the Frobenius automorphism, the defining polynomials
+and the paper's matrix-level Karatsuba forms).  Each check takes ``mm(q, A, B)``
 and returns True when the function passes."""
 from __future__ import annotations
 
 import numpy as np
+
+from oracle.fields import EXTENSIONS
 
 
 def rand(rng, q, r, c):
@@ -18,6 +21,10 @@ def gf4_add(X, Y):
 def fadd(q, X, Y):
     if q == 4:
         return gf4_add(X, Y)
+    if q in EXTENSIONS:                      # coefficientwise mod p
+        p, n, _ = EXTENSIONS[q]
+        X, Y = np.asarray(X).astype(np.int64), np.asarray(Y).astype(np.int64)
+        return sum((((X // p ** j) + (Y // p ** j)) % p) * p ** j for j in range(n)).astype(np.uint8)
     return ((X.astype(np.int64) + Y) % q).astype(np.uint8)
 
 
@@ -123,7 +130,74 @@ def check_gf4_karatsuba(mm, rng, karatsuba):
     return True
 
 
-def run_all(mm, q, seed=0, karatsuba=None):
+def mul_table(mm, q):
+    """The q x q element products as 1 x 1 matrix products (one outer product)."""
+    e = np.arange(q, dtype=np.uint8)
+    return np.asarray(mm(q, e.reshape(q, 1), e.reshape(1, q))).astype(np.int64)
+
+
+def check_field_axioms(mm, q, rng, samples=4000):
+    """The element products of mm make F_q a field: 1 is the unit, 0 absorbs,
+    products commute, every nonzero element has an inverse (so there are no
+    zero divisors: the defining polynomial is irreducible), and products
+    associate and distribute over coefficientwise addition (all triples for
+    q <= 27, `samples` random triples above)."""
+    T = mul_table(mm, q)
+    e = np.arange(q)
+    if not (np.array_equal(T[1], e) and not T[0].any() and np.array_equal(T, T.T)):
+        return False
+    if not all(1 in T[a, 1:] for a in range(1, q)):
+        return False
+    if q <= 27:
+        a, b, c = (x.ravel() for x in np.meshgrid(e, e, e, indexing="ij"))
+    else:
+        a, b, c = (rng.integers(0, q, samples) for _ in range(3))
+    if not np.array_equal(T[T[a, b], c], T[a, T[b, c]]):
+        return False
+    bc = fadd(q, b.astype(np.uint8), c.astype(np.uint8)).astype(np.int64)
+    return np.array_equal(T[a, bc], fadd(q, T[a, b].astype(np.uint8), T[a, c].astype(np.uint8)))
+
+
+def check_primitive(mm, q):
+    """x (code p, the class of the polynomial variable) has multiplicative order
+    q - 1: the defining polynomial is primitive, which singles it out among the
+    irreducible ones a mistyped coefficient would give for most fields."""
+    p, n, _ = EXTENSIONS[q]
+    T = mul_table(mm, q)
+    x, y = p, p
+    for k in range(1, q):
+        if y == 1:
+            return k == q - 1
+        y = int(T[y, x])
+    return False
+
+
+def check_frobenius(mm, q, rng):
+    """The Frobenius map s(a) = a^p is a field automorphism, so applied to every
+    entry it commutes with matrix products: s(AB) = s(A) s(B)."""
+    p, n, _ = EXTENSIONS[q]
+    T = mul_table(mm, q)
+    frob = np.arange(q)
+    for _ in range(p - 1):
+        frob = T[frob, np.arange(q)]
+    if len(set(frob.tolist())) != q or np.array_equal(frob, np.arange(q)):
+        return False                          # a bijection other than the identity
+    A, B = rand(rng, q, 9, 14), rand(rng, q, 14, 6)
+    s = lambda X: frob[X.astype(np.int64)].astype(np.uint8)
+    return np.array_equal(s(mm(q, A, B)), mm(q, s(A), s(B)))
+
+
+def check_ext_karatsuba(mm, q, rng, karatsuba):
+    """The product equals Section 4.3's matrix-level form over base-field products
+    (Karatsuba for degree 2, the paper's trinomial formula for degree 3)."""
+    for m, l, n in ((5, 9, 7), (33, 70, 40)):
+        A, B = rand(rng, q, m, l), rand(rng, q, l, n)
+        if not np.array_equal(mm(q, A, B), karatsuba(q, A, B)):
+            return False
+    return True
+
+
+def run_all(mm, q, seed=0, karatsuba=None, ext_karatsuba=None):
     """All pins that apply to q; returns the names of the failing ones."""
     rng = np.random.default_rng(seed)
     fails = []
@@ -131,11 +205,17 @@ def run_all(mm, q, seed=0, karatsuba=None):
               ("units", lambda: check_units(mm, q)),
               ("identities", lambda: check_identities(mm, q, rng)),
               ("scalar", lambda: check_scalar(mm, q, rng))]
+    if q in EXTENSIONS:
+        checks.append(("field_axioms", lambda: check_field_axioms(mm, q, rng)))
+        checks.append(("primitive", lambda: check_primitive(mm, q)))
+        checks.append(("frobenius", lambda: check_frobenius(mm, q, rng)))
+        if ext_karatsuba is not None:
+            checks.append(("ext_karatsuba", lambda: check_ext_karatsuba(mm, q, rng, ext_karatsuba)))
     if q == 4:
         checks.append(("gf4_polynomial", lambda: check_gf4_polynomial(mm)))
         if karatsuba is not None:
             checks.append(("gf4_karatsuba", lambda: check_gf4_karatsuba(mm, rng, karatsuba)))
-    else:
+    elif q not in EXTENSIONS:
         checks.append(("numpy", lambda: check_numpy(mm, q, rng)))
         checks.append(("all_max", lambda: check_all_max(mm, q)))
     for name, fn in checks:

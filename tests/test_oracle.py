@@ -4,17 +4,25 @@ import os
 import numpy as np
 import pytest
 
+import ctypes
+
 import oracle
 from oracle import encoding, m4rm
+from oracle.fields import EXTENSIONS
 from tests import pins
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-FIELDS = (2, 3, 4, 5, 7)
+FIELDS = oracle.FIELDS
+BASE_FIELDS = (2, 3, 4, 5, 7)
+
+
+def run_pins(mm, q):
+    return pins.run_all(mm, q, seed=q, karatsuba=oracle.gf4_karatsuba, ext_karatsuba=oracle.ext_karatsuba)
 
 
 @pytest.mark.parametrize("q", FIELDS)
 def test_oracle_passes_all_pins(q):
-    assert pins.run_all(oracle.matmul, q, seed=q, karatsuba=oracle.gf4_karatsuba) == []
+    assert run_pins(oracle.matmul, q) == []
 
 
 # --- planted mistakes: each mutant of the oracle must fail at least one pin ---
@@ -38,14 +46,20 @@ def _mut_transposed(q, A, B):            # A^T B whenever the shapes allow it
 
 def _mut_sign(q, A, B):                  # first term subtracted instead of added
     C = oracle.matmul(q, A, B).astype(np.int64)
-    if q == 4:
+    if q == 4 or q == 8:
         return C.astype(np.uint8)            # (char 2: -x = x, no sign to flip)
+    if q in EXTENSIONS:
+        p = EXTENSIONS[q][0]
+        first = oracle.matmul(q, np.ascontiguousarray(A[:, :1]), np.ascontiguousarray(B[:1])) \
+            if A.shape[1] else np.zeros_like(C)
+        c, f = oracle.digits(q, C), oracle.digits(q, first)
+        return oracle.compose(q, [(x.astype(np.int64) - 2 * y) % p for x, y in zip(c, f)])
     first = np.outer(A[:, 0].astype(np.int64), B[0].astype(np.int64)) if A.shape[1] else 0
     return ((C - 2 * first) % q).astype(np.uint8)
 
 
 def _mut_narrow_accumulator(q, A, B):    # int8-wide accumulation that wraps
-    if q == 4:
+    if q in EXTENSIONS:
         return oracle.matmul(q, A, B)
     acc = (A.astype(np.uint8) @ B.astype(np.uint8)).astype(np.uint8)
     return (acc % q).astype(np.uint8)
@@ -61,6 +75,22 @@ def _mut_gf4_wrong_poly(q, A, B):        # GF(4) reduced with x^2 = 1 instead of
     return (e0 | (e1 << 1)).astype(np.uint8)
 
 
+def _mut_ext_wrong_poly(q, A, B):       # reduced with r_0 + 1 in place of r_0
+    if q not in EXTENSIONS:
+        return oracle.matmul(q, A, B)
+    p, n, r = EXTENSIONS[q]
+    bad = list(r)
+    bad[0] = (bad[0] + 1) % p
+    A = np.ascontiguousarray(A, dtype=np.uint8)
+    B = np.ascontiguousarray(B, dtype=np.uint8)
+    C = np.zeros((A.shape[0], B.shape[1]), np.uint8)
+    u8 = lambda X: X.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    rc = oracle._load().fq_oracle_matmul_ext(p, n, (ctypes.c_int * n)(*bad), A.shape[0], A.shape[1], B.shape[1],
+                                             u8(A), A.shape[1], u8(B), B.shape[1], u8(C), B.shape[1], 1)
+    assert rc == 0
+    return C
+
+
 MUTANTS = {
     "dropped_term": _mut_dropped_term,
     "wrong_index": _mut_wrong_index,
@@ -68,25 +98,27 @@ MUTANTS = {
     "sign": _mut_sign,
     "narrow_accumulator": _mut_narrow_accumulator,
     "gf4_wrong_poly": _mut_gf4_wrong_poly,
+    "ext_wrong_poly": _mut_ext_wrong_poly,
 }
 
 
 @pytest.mark.parametrize("q", FIELDS)
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_planted_mistakes(q, name):
-    if (q == 4 and name in ("sign", "narrow_accumulator")) or (q != 4 and name == "gf4_wrong_poly"):
+    if (q in EXTENSIONS and name == "narrow_accumulator") or (q != 4 and name == "gf4_wrong_poly") \
+            or (q not in EXTENSIONS and name == "ext_wrong_poly"):
         pytest.skip("mutant is the identity for this field")
-    if q == 2 and name == "sign":
+    if q in (2, 4, 8) and name == "sign":
         pytest.skip("char 2: -x = x")
     if q == 2 and name == "narrow_accumulator":
         pytest.skip("a wrap mod 256 preserves parity: the mutant is correct over F_2")
-    fails = pins.run_all(MUTANTS[name], q, seed=q, karatsuba=oracle.gf4_karatsuba)
+    fails = run_pins(MUTANTS[name], q)
     assert fails, "mutant %s survived every pin for q=%d" % (name, q)
 
 
 # --- the paper's method, step by step, reaches the plain product ---
 
-@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("q", BASE_FIELDS)
 @pytest.mark.parametrize("k", [1, 3, 4, 8])
 def test_m4rm_method_matches_plain_product(q, k):
     rng = np.random.default_rng(100 + q * 10 + k)
@@ -132,6 +164,43 @@ def test_brute_force_all_2x2_products(q):
         ref = np.stack([oracle.gf4_karatsuba(x, y) for x, y in zip(Astack[::97], Bstack[::97])])
         got = got[::97]
     assert np.array_equal(got, ref)
+
+
+# --- extension fields: the two oracles, the polynomials, the codes ---
+
+def test_extension_oracle_equals_gf4_oracle():
+    """The tabulated extension-field oracle at (p, n) = (2, 2) and the separate
+    GF(4) routine are independent codes for the same field."""
+    rng = np.random.default_rng(44)
+    for m, l, n in ((1, 1, 1), (19, 67, 33), (64, 130, 64)):
+        A, B = pins.rand(rng, 4, m, l), pins.rand(rng, 4, l, n)
+        assert np.array_equal(oracle.matmul_ext(4, A, B), oracle.matmul(4, A, B))
+
+
+@pytest.mark.parametrize("q", sorted(EXTENSIONS))
+def test_defining_polynomial_of_x(q):
+    """x^n in the oracle's arithmetic is r_0 + r_1 x + ... (the stated
+    polynomial), and no lower power of x reduces (x^j has code p^j, j < n)."""
+    p, n, r = EXTENSIONS[q]
+    T = pins.mul_table(oracle.matmul, q)
+    y = 1
+    for j in range(n):
+        assert y == p ** j
+        y = int(T[y, p])
+    assert y == sum(c * p ** j for j, c in enumerate(r))
+
+
+@pytest.mark.parametrize("q", sorted(EXTENSIONS))
+def test_extension_codes_round_trip(q):
+    rng = np.random.default_rng(q)
+    R = pins.rand(rng, q, 7, 130)
+    planes = encoding.pack(q, R)
+    assert planes.shape == (encoding.planes(q), 7, 3)
+    assert np.array_equal(encoding.unpack(q, planes, 130), R)
+    p, n, _ = EXTENSIONS[q]
+    P = encoding.planes(p)
+    for j, d in enumerate(oracle.digits(q, R)):           # coefficient j's planes
+        assert np.array_equal(planes[j * P:(j + 1) * P], encoding.pack(p, d))
 
 
 # --- checks used at sizes the full oracle cannot reach ---
