@@ -7,12 +7,23 @@
  * the Method of Four Russians with an additive basis (Section 2).
  *
  * Fields (argument q):
+ *   q = 2  F_2,  1 plane, the element itself (Section 2's binary case), basis {1};
  *   q = 3  F_3,  2 planes, codes (x0, x1): 0 = (0,0), 1 = (1,0), -1 = (1,1)
  *          (Section 4.1), additive basis {1, -1};
  *   q = 5  F_5,  3 planes, binary digits of the residue (Section 4.2), basis {1,2,4};
  *   q = 7  F_7,  3 planes, binary digits of the residue (Section 4.2), basis {1,2,4};
  *   q = 4  GF(4) = F_2[x]/(x^2+x+1), 2 planes, element a0 + alpha*a1 has code
- *          a0 + 2*a1 (Section 4.3), basis {1, alpha}.
+ *          a0 + 2*a1 (Section 4.3), basis {1, alpha};
+ *   q = 8, 9, 25, 27, 49, 125: the extension fields F_{p^n} = F_p[x]/(f) of
+ *          Section 4.3 ("non-prime fields"), with f = x^3 + x + 1, x^2 + 2x + 2,
+ *          x^2 + 4x + 2, x^3 + 2x + 1, x^2 + 6x + 3, x^3 + 3x + 3 (monic,
+ *          irreducible and primitive).  Element c_0 + c_1 x + ... has code
+ *          sum_j c_j p^j; a matrix is stored as its coefficient matrices
+ *          A = A_0 + A_1 x + ..., the planes of A_0 (as an F_p matrix), then
+ *          those of A_1, ... -- n * fq_planes(p) planes.  GF(4) is the same
+ *          layout for p = 2, n = 2.  Products are Section 4.3's matrix-level
+ *          products: Karatsuba (3 base-field products) for n = 2, the paper's
+ *          trinomial formula (6 products) for n = 3, then reduction by f.
  *
  * Packed layout ("planes buffer") of a rows x cols matrix: plane-major,
  *   word(p, r, w) = buf[(p * rows + r) * pitch + w],  pitch = fq_pitch_words(cols),
@@ -51,9 +62,11 @@ extern "C" {
 #define FQ_PATH_AUTO 0 /* planner's choice                                         */
 #define FQ_PATH_M4RM 1 /* bitsliced Method of Four Russians (Sections 2-4)         */
 #define FQ_PATH_MMA 2  /* exact integer tensor-core contraction, mod p per l-chunk */
+#define FQ_PATH_KARATSUBA 3 /* GF(4) only: Section 4.3's three F_2 products        */
 
-/* Number of bit-planes of a field element (2 for q = 3, 4; 3 for q = 5, 7), or 0
- * for an unsupported q.  Section 4 fixes the widths. */
+/* Number of bit-planes of a field element (1 for q = 2; 2 for q = 3, 4; 3 for
+ * q = 5, 7; n * fq_planes(p) for q = p^n), or 0 for an unsupported q.  Section 4
+ * fixes the widths. */
 int fq_planes(int q);
 
 /* Row pitch in 64-bit words of a planes buffer with `cols` columns:
@@ -64,8 +77,9 @@ int64_t fq_pitch_words(int64_t cols);
  * -1 on bad arguments. */
 int64_t fq_planes_words(int q, int64_t rows, int64_t cols);
 
-/* Pack residues into bit-planes (Section 3; codes of Sections 4.1-4.3).
- * res:    device, rows x cols uint8 residues in [0, q), row-major, leading
+/* Pack residues (element codes) into bit-planes (Section 3; codes of Sections
+ * 4.1-4.3).
+ * res:    device, rows x cols uint8 codes in [0, q), row-major, leading
  *         dimension ld >= cols (elements).
  * planes: device planes buffer (layout above), written entirely, padding zeroed.
  * A residue >= q is stored as 0 and recorded for fq_status() (FQ_EVALUE). */
@@ -87,7 +101,7 @@ int fq_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t 
 
 /* Options for fq_matmul_ex; zero-initialise for defaults. */
 typedef struct fq_options {
-  int path;      /* FQ_PATH_*                                                     */
+  int path;      /* FQ_PATH_*; for q = 8 .. 125 the base-field products' path      */
   int k;         /* M4RM block size: 0 = planner, else 6..10 (Section 2's k)       */
   int64_t chunk; /* MMA path: l-chunk length between mod-p reductions; 0 = largest */
   int variant;   /* M4RM rows per CTA: 0 = planner, else 1 .. the kernel's maximum */
@@ -97,7 +111,16 @@ typedef struct fq_options {
 
 /* C = A B over F_q (Section 2: C_i = sum_s sum_d alpha_d T_s[phi_d(A_i, block s)]).
  * A: device planes buffer m x l; B: l x n; C: m x n (written entirely; must not
- * alias A or B).  m, l, n >= 0; l = 0 gives C = 0.  The product is exact. */
+ * alias A or B).  m, l, n >= 0; l = 0 gives C = 0.  The product is exact.
+ * Extension fields (q = 8 .. 125, and GF(4) with FQ_PATH_KARATSUBA) run
+ * Section 4.3's matrix-level product: the base-field operand sums with fq_add's
+ * formulas, 3 or 6 base-field products (each on fq_options.path: AUTO, M4RM or
+ * MMA; k, variant and kernel refer to the base field's kernels) and one
+ * elementwise combination kernel.  Their scratch (the operand sums and the
+ * products beyond n, about (3 or 6 - n) x the base-field size of A, B and C)
+ * is taken from and returned to the device's stream-ordered memory pool on
+ * `stream` (cudaMallocAsync / cudaFreeAsync), which a CUDA graph capture
+ * records as allocation nodes. */
 int fq_matmul(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
               const uint64_t *B, uint64_t *C, void *stream);
 
@@ -112,8 +135,9 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
  * cost model, longest first.  The plan is host memory owned by the library. */
 typedef struct fq_batch_plan fq_batch_plan;
 
-/* Build a plan (host only).  m, l, n: host arrays of `count` sizes (each >= 0;
- * l, m < 2^31).  Returns FQ_EINVAL on bad sizes, FQ_ENOMEM on allocation failure. */
+/* Build a plan (host only).  q = 3, 4, 5 or 7.  m, l, n: host arrays of `count`
+ * sizes (each >= 0; l, m < 2^31).  Returns FQ_EINVAL on a bad q or bad sizes,
+ * FQ_ENOMEM on allocation failure. */
 int fq_batched_plan_create(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n,
                            fq_batch_plan **plan);
 
@@ -167,7 +191,7 @@ int fq_matmul_batched_static(const fq_batch_plan *plan, const uint64_t *const *A
  * tensor-core path, and remembers the fastest for this exact (q, m, l, n):
  * later fq_matmul / fq_matmul_ex calls with FQ_PATH_AUTO, k = 0 and kernel = 0
  * on that shape use it.  C holds the product when it returns.  The cache is
- * process-wide host memory; fq_autotune_clear empties it. */
+ * process-wide host memory; fq_autotune_clear empties it.  q = 2, 3, 4, 5 or 7. */
 typedef struct fq_tune_result {
   int path;           /* FQ_PATH_M4RM or FQ_PATH_MMA                        */
   int kernel;         /* 1-based compiled M4RM kernel, 0 = the M4RM planner   */
@@ -183,9 +207,10 @@ int fq_autotune_lookup(int q, int64_t m, int64_t l, int64_t n, int *path, int *k
 int fq_autotune_clear(void);
 
 /* The path and kernel that fq_matmul_ex with FQ_PATH_AUTO, k = 0 and kernel = 0
- * takes for (q, m, l, n) on the current device: the fq_autotune choice when
- * one is remembered, otherwise the path with the smaller modelled time
- * (kernel 0, the M4RM planner).  The model counts waves of one CTA per SM
+ * takes for (q, m, l, n) on the current device: FQ_PATH_KARATSUBA for the
+ * extension fields q = 8 .. 125, else the fq_autotune choice when one is
+ * remembered, otherwise the path with the smaller modelled time (kernel 0, the
+ * M4RM planner).  The model counts waves of one CTA per SM
  * times block steps times the measured cycles of one step of each path; it
  * picks the tensor-core path for small products (up to about 1024 on a side
  * for F_3), where the Four-Russians tables are not amortised over enough

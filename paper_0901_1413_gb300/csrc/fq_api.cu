@@ -24,7 +24,10 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-bool valid_q(int q) { return q == 3 || q == 4 || q == 5 || q == 7; }
+// Fields with their own kernels: F_2, F_3, F_5, F_7 and GF(4).
+bool base_q(int q) { return q == 2 || q == 3 || q == 4 || q == 5 || q == 7; }
+// ... and the extension fields built on them (fq_ext.cu).
+bool valid_q(int q) { return base_q(q) || ext_field(q) != nullptr; }
 
 }  // namespace
 
@@ -63,15 +66,20 @@ int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000 *out) {
 }  // namespace fqk
 
 using fqk::aligned16;
+using fqk::base_q;
 using fqk::valid_q;
 
 extern "C" {
 
 int fq_planes(int q) {
   switch (q) {
+    case 2: return 1;
     case 3: case 4: return 2;
     case 5: case 7: return 3;
-    default: return 0;
+    default: {
+      const fqk::ExtField *f = fqk::ext_field(q);
+      return f ? f->n * fq_planes(f->p) : 0;
+    }
   }
 }
 
@@ -105,13 +113,22 @@ int fq_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t 
   if (!valid_q(q) || rows < 0 || cols < 0 || (sub != 0 && sub != 1)) return FQ_EINVAL;
   if (rows == 0) return FQ_OK;
   if (!X || !Y || !Z || !aligned16(X) || !aligned16(Y) || !aligned16(Z)) return FQ_EINVAL;
-  return fqk::launch_add(q, rows, cols, X, Y, Z, sub, static_cast<cudaStream_t>(stream));
+  if (base_q(q)) return fqk::launch_add(q, rows, cols, X, Y, Z, sub, static_cast<cudaStream_t>(stream));
+  // extension field: coefficientwise over the base field
+  const fqk::ExtField *f = fqk::ext_field(q);
+  const int64_t block = int64_t(fq_planes(f->p)) * rows * fq_pitch_words(cols);
+  for (int j = 0; j < f->n; ++j)
+    if (int rc = fqk::launch_add(f->p, rows, cols, X + j * block, Y + j * block, Z + j * block, sub,
+                                 static_cast<cudaStream_t>(stream)))
+      return rc;
+  return FQ_OK;
 }
 
 int fq_auto_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel) {
   if (!valid_q(q) || m < 0 || l < 0 || n < 0 || !path || !kernel) return FQ_EINVAL;
-  *path = FQ_PATH_M4RM;
+  *path = base_q(q) ? FQ_PATH_M4RM : FQ_PATH_KARATSUBA;
   *kernel = 0;
+  if (!base_q(q)) return FQ_OK;
   if (fqk::tuned_choice(q, m, l, n, path, kernel)) return FQ_OK;
   if (m == 0 || l == 0 || n == 0) return FQ_OK;
   // no measurement for this shape: the cheaper path by the time model
@@ -133,11 +150,23 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, cons
   fq_options o;
   memset(&o, 0, sizeof(o));
   if (opt) o = *opt;
-  if (o.path < FQ_PATH_AUTO || o.path > FQ_PATH_MMA) return FQ_EINVAL;
+  if (o.path < FQ_PATH_AUTO || o.path > FQ_PATH_KARATSUBA) return FQ_EINVAL;
+  if (o.path == FQ_PATH_KARATSUBA && base_q(q) && q != 4) return FQ_EINVAL;
   if (o.k != 0 && (o.k < 6 || o.k > 10)) return FQ_EINVAL;
   if (o.chunk < 0 || o.variant < 0) return FQ_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (o.kernel < 0) return FQ_EINVAL;
+  if (!base_q(q) || o.path == FQ_PATH_KARATSUBA) {
+    // Section 4.3's matrix-level product; `path` picks the base products' path
+    fqk::ExtOptions e;
+    e.path = o.path == FQ_PATH_KARATSUBA ? FQ_PATH_AUTO : o.path;
+    if (e.path == FQ_PATH_AUTO && (o.k || o.kernel || o.variant)) e.path = FQ_PATH_M4RM;
+    e.k = o.k;
+    e.variant = o.variant;
+    e.kernel = o.kernel;
+    e.chunk = o.chunk;
+    return fqk::launch_ext(q, m, l, n, A, B, C, e, s);
+  }
   if (o.path == FQ_PATH_AUTO && o.k == 0 && o.kernel == 0 && o.variant == 0) {
     if (int rc = fq_auto_choice(q, m, l, n, &o.path, &o.kernel)) return rc;
   }

@@ -1,6 +1,6 @@
 // Residue <-> code-bit conversions, four elements (bytes of a 32-bit word) at a
 // time, shared by fq_pack/fq_unpack and the tensor-core path's epilogue.
-// Codes: Section 4.1 (F_3), 4.2 (F_5, F_7), 4.3 (GF(4)).
+// Codes: Section 4.1 (F_3), 4.2 (F_5, F_7), 4.3 (GF(4)); F_2 is one bit.
 #pragma once
 
 #include "fq_common.cuh"
@@ -24,7 +24,7 @@ __device__ __forceinline__ void encode4(uint32_t v, uint64_t (&out)[P], int e, u
   const uint32_t m = (v & 0x80808080u) | (((v | 0x80808080u) - uint32_t(Q) * kLsb) & 0x80808080u);
   bad |= m;
   v &= ~((m >> 7) * 0xFFu);  // invalid residues are stored as 0
-  if (Q == 3) {
+  if constexpr (Q == 3) {
     const uint32_t unit = (v | (v >> 1)) & kLsb;
     const uint32_t sign = (v >> 1) & kLsb;
     out[0] |= uint64_t(gather_nibble(unit)) << e;
@@ -41,15 +41,22 @@ __device__ __forceinline__ uint32_t decode4(const uint64_t (&in)[P], int e) {
   uint32_t x[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) x[p] = spread_nibble(uint32_t(in[p] >> e) & 0xFu);
-  if (Q == 3) return x[0] + (x[0] & x[1]);          // (1,0) -> 1, (1,1) -> 2
-  if (Q == 4) return x[0] | (x[1] << 1);            // a0 + 2 a1
-  const uint32_t code = x[0] | (x[1] << 1) | (x[2] << 2);
-  if (Q == 7) {
-    const uint32_t seven = ((code + kLsb) >> 3) & kLsb;        // code == 7
-    return code - 7u * seven;
+  if constexpr (Q == 2) {
+    return x[0];
+  } else if constexpr (Q == 3) {
+    return x[0] + (x[0] & x[1]);                    // (1,0) -> 1, (1,1) -> 2
+  } else if constexpr (Q == 4) {
+    return x[0] | (x[1] << 1);                      // a0 + 2 a1
+  } else {
+    const uint32_t code = x[0] | (x[1] << 1) | (x[2] << 2);
+    if constexpr (Q == 7) {
+      const uint32_t seven = ((code + kLsb) >> 3) & kLsb;      // code == 7
+      return code - 7u * seven;
+    } else {
+      const uint32_t ge5 = ((code + 3u * kLsb) >> 3) & kLsb;   // code >= 5
+      return code - 5u * ge5;
+    }
   }
-  const uint32_t ge5 = ((code + 3u * kLsb) >> 3) & kLsb;       // code >= 5
-  return code - 5u * ge5;
 }
 
 }  // namespace fqk

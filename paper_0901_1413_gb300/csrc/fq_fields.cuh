@@ -12,6 +12,21 @@
 
 namespace fqk {
 
+// ------------------------------------------------------------------ F_2 ----
+// One plane; the binary Four-Russians case of Section 2 (basis {1}, phi_0 = the
+// element itself); addition is XOR.  The base field of GF(4) and F_8 in the
+// matrix-level products of Section 4.3.
+struct F2 {
+  static constexpr int Q = 2, P = 1, D = 1;
+  __device__ __forceinline__ static void add(uint32_t (&x)[P], const uint32_t (&y)[P]) { x[0] ^= y[0]; }
+  __device__ __forceinline__ static void sub(uint32_t (&x)[P], const uint32_t (&y)[P]) { x[0] ^= y[0]; }
+  __device__ __forceinline__ static void accumulate(uint32_t (&acc)[P], const uint32_t (&t)[D][P]) {
+    acc[0] ^= t[0][0];
+  }
+  __device__ __forceinline__ static void canon(uint32_t (&)[P]) {}
+  __device__ __forceinline__ static void phi(const uint64_t (&a)[P], uint64_t (&ph)[D]) { ph[0] = a[0]; }
+};
+
 // ------------------------------------------------------------------ F_3 ----
 // Codes (x0, x1): 0 = (0,0), 1 = (1,0), -1 = (1,1) (Section 4.1); basis {1, -1},
 // phi_0(a) = [a = 1], phi_1(a) = [a = -1].

@@ -33,6 +33,22 @@ const Variant *m4rm_variants(int q, int *count);
 double m4rm_estimate(int q, int64_t m, int64_t l, int64_t n, int sms);
 double mma_estimate(int q, int64_t m, int64_t l, int64_t n, int sms);
 
+// Extension fields F_{p^n} = F_p[x]/(f), f = x^n - (r_0 + r_1 x + r_2 x^2)
+// (fq_ext.cu): the field of code size q, or nullptr.
+struct ExtField {
+  int q, p, n;
+  int r[3];
+};
+const ExtField *ext_field(int q);
+// Base-product options of an extension-field product.
+struct ExtOptions {
+  int path, k, variant, kernel;
+  int64_t chunk;
+};
+int64_t ext_workspace_words(int q, int64_t m, int64_t l, int64_t n);
+int launch_ext(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+               const ExtOptions &o, cudaStream_t s);
+
 // The autotuned (path, kernel) for a shape, if fq_autotune measured one.
 bool tuned_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel);
 

@@ -9,6 +9,7 @@ namespace fqk {
   int launch_m4rm_##name(int64_t, int64_t, int64_t, const uint64_t *, const uint64_t *, uint64_t *, int, int, \
                          int, cudaStream_t);                                                                  \
   const Variant *m4rm_variants_##name(int *count);
+FQ_FIELD_DECL(f2)
 FQ_FIELD_DECL(f3)
 FQ_FIELD_DECL(gf4)
 FQ_FIELD_DECL(f5)
@@ -19,6 +20,7 @@ int launch_m4rm(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const
                 int variant, int kernel, cudaStream_t s) {
   // variant > 0 forces the rows per CTA, kernel > 0 the compiled kernel
   switch (q) {
+    case 2: return launch_m4rm_f2(m, l, n, A, B, C, k, variant, kernel, s);
     case 3: return launch_m4rm_f3(m, l, n, A, B, C, k, variant, kernel, s);
     case 4: return launch_m4rm_gf4(m, l, n, A, B, C, k, variant, kernel, s);
     case 5: return launch_m4rm_f5(m, l, n, A, B, C, k, variant, kernel, s);
@@ -30,6 +32,7 @@ int launch_m4rm(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const
 const Variant *m4rm_variants(int q, int *count) {
   *count = 0;
   switch (q) {
+    case 2: return m4rm_variants_f2(count);
     case 3: return m4rm_variants_f3(count);
     case 4: return m4rm_variants_gf4(count);
     case 5: return m4rm_variants_f5(count);

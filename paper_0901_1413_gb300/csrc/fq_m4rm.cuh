@@ -68,7 +68,9 @@ struct M4rmCfg {
   static constexpr int LB = K - 5, HB = 5, EPB = 1 << LB;
   static_assert(K >= 6 && K <= 10, "k in 6..10");
   static constexpr int NB = 64 / K;              // blocks per A chunk (<= 64 bits)
-  using Off = std::conditional_t<(D == 3), uint4, uint2>;
+  // table byte offsets of one row and block: one per basis element
+  using Off = std::conditional_t<(D >= 3), uint4, std::conditional_t<(D == 2), uint2, uint32_t>>;
+  static_assert(D <= 4, "at most four basis elements");
   static constexpr int STAGE_BYTES = P * K * CTW * 8;
   static constexpr int STAGE_STRIDE = round128(STAGE_BYTES);
   static constexpr int TABLE_OFF = 0;
@@ -185,10 +187,14 @@ __device__ __forceinline__ void build_offsets(const M4rmParams &prm, const unsig
         for (int d = 0; d < D; ++d)
           off[d] = uint32_t((win[d] >> (b * K)) & ((1u << K) - 1u)) * uint32_t(Cfg::ENTRY);
         typename Cfg::Off o;
-        if constexpr (D == 3) {
+        if constexpr (D == 4) {
+          o = make_uint4(off[0], off[1], off[2], off[3]);
+        } else if constexpr (D == 3) {
           o = make_uint4(off[0], off[1], off[2], 0u);
-        } else {
+        } else if constexpr (D == 2) {
           o = make_uint2(off[0], off[1]);
+        } else {
+          o = off[0];
         }
         offs[b * Cfg::MT + r] = o;
       }
@@ -286,10 +292,14 @@ __device__ __forceinline__ void lookup_block(uint32_t (&acc)[Cfg::RS][Cfg::PW], 
       const int r = i * Cfg::ROWS_PER_SLOT + warp * Cfg::GPW + grp;
       const typename Cfg::Off o = offs_b[r];
       uint32_t od[D];
-      if constexpr (D == 3) {
+      if constexpr (D == 4) {
+        od[0] = o.x; od[1] = o.y; od[2] = o.z; od[3] = o.w;
+      } else if constexpr (D == 3) {
         od[0] = o.x; od[1] = o.y; od[2] = o.z;
-      } else {
+      } else if constexpr (D == 2) {
         od[0] = o.x; od[1] = o.y;
+      } else {
+        od[0] = o;
       }
       uint32_t t[D][PW];
 #pragma unroll

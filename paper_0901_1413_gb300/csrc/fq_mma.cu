@@ -2,9 +2,9 @@
 //
 // The same product C = A B as the Four-Russians path, as a dense integer
 // contraction: residues of A and B enter warp-level mma.sync.m16n8k32 s8 x s8
-// -> s32 as balanced int8 (F_3: {-1, 0, 1}; F_5: {-2..2}; F_7: {-3..3}), the
-// int32 accumulators are reduced mod p every `chunk` columns of A, and the
-// result is packed back into bit-planes.  GF(4) follows Section 4.3 at matrix
+// -> s32 as balanced int8 (F_2: {0, 1}; F_3: {-1, 0, 1}; F_5: {-2..2}; F_7:
+// {-3..3}), the int32 accumulators are reduced mod p every `chunk` columns of
+// A, and the result is packed back into bit-planes.  GF(4) follows Section 4.3 at matrix
 // level: with A = A0 + alpha A1, B = B0 + alpha B1,
 //   AB = (A0 B0 + A1 B1) + alpha ((A0 + A1)(B0 + B1) + A0 B0),
 // three integer products of 0/1 matrices, each read mod 2.
@@ -24,7 +24,7 @@ namespace {
 
 template <int Q>
 struct MmaSpec {
-  static constexpr int P = (Q == 5 || Q == 7) ? 3 : 2;
+  static constexpr int P = (Q == 5 || Q == 7) ? 3 : (Q == 2 ? 1 : 2);
   static constexpr int NPROD = Q == 4 ? 3 : 1;  // integer products per tile
   static constexpr int MOD = Q == 4 ? 2 : Q;
   static constexpr int BM = 128, BK = 64, BN = Q == 4 ? 64 : 128;
@@ -36,7 +36,7 @@ struct MmaSpec {
   static constexpr int LDC = BN + 16;
   static_assert(BM * LDC <= SMEM, "C tile reuses the operand tiles");
   // largest |balanced residue|
-  static constexpr int BMAX = Q == 4 ? 1 : (Q - 1) / 2;
+  static constexpr int BMAX = (Q == 2 || Q == 4) ? 1 : (Q - 1) / 2;
 };
 
 // Canonical codes for the three-plane fields (any 3-bit code is accepted).
@@ -59,7 +59,9 @@ __device__ __forceinline__ void to_i8(const uint32_t (&w)[P], int j, uint32_t (&
 #pragma unroll
     for (int p = 0; p < P; ++p) x[p] = spread_nibble((w[p] >> (4 * i)) & 0xFu);
     uint32_t v;
-    if constexpr (Q == 3) {                         // unit, sign -> 0, 1, -1
+    if constexpr (Q == 2) {                         // 0/1 operands, read mod 2
+      v = x[0];
+    } else if constexpr (Q == 3) {                  // unit, sign -> 0, 1, -1
       v = (x[0] & ~x[1]) | ((x[0] & x[1]) * 0xFFu);
     } else if constexpr (Q == 4) {                  // a0, a1, a0 + a1 as 0/1
       v = j == 0 ? x[0] : (j == 1 ? x[1] : (x[0] ^ x[1]));
@@ -279,7 +281,7 @@ int launch_q(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t 
 // constant for launch, the first loads and the epilogue (fitted on GB300).
 double mma_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
   const int bn = q == 4 ? MmaSpec<4>::BN : 128;
-  const double per_step = q == 3 ? 4800.0 : (q == 4 ? 8670.0 : 8040.0);
+  const double per_step = (q == 2 || q == 3) ? 4800.0 : (q == 4 ? 8670.0 : 8040.0);
   const int64_t ctas = (fq_pitch_words(n) * 64 / bn) * cdiv(m, 128);
   return double(cdiv(ctas, sms)) * double(cdiv(l, 64)) * per_step + 52000.0;
 }
@@ -287,6 +289,7 @@ double mma_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
 int launch_mma(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                int64_t chunk, cudaStream_t s) {
   switch (q) {
+    case 2: return launch_q<2>(m, l, n, A, B, C, chunk, s);
     case 3: return launch_q<3>(m, l, n, A, B, C, chunk, s);
     case 4: return launch_q<4>(m, l, n, A, B, C, chunk, s);
     case 5: return launch_q<5>(m, l, n, A, B, C, chunk, s);

@@ -1,5 +1,6 @@
-// Packing residues into bit-planes and back (Section 3, codes of Section 4), and
-// elementwise bitsliced add/sub.  All three are bandwidth-bound: one thread per
+// Packing residues into bit-planes and back (Section 3, codes of Section 4; the
+// extension fields' coefficient planes of Section 4.3), and elementwise
+// bitsliced add/sub over the base fields and GF(4).  All three are bandwidth-bound: one thread per
 // 64-element word of a row, grid-stride over rows x pitch.
 #include "fq_codes.cuh"
 #include "fq_fields.cuh"
@@ -84,6 +85,99 @@ __global__ void unpack_kernel(int64_t rows, int64_t cols, const uint64_t *__rest
   }
 }
 
+// Extension fields F_{p^n}: code c = sum_j c_j p^j; coefficient j's planes are
+// those of a packed F_p matrix (planes j P_p .. (j + 1) P_p - 1).  One element at
+// a time: packing is outside the product.
+template <int PB>
+__host__ __device__ constexpr int base_planes() { return PB == 2 ? 1 : (PB == 3 ? 2 : 3); }
+
+template <int PB, int N>
+__global__ void ext_pack_kernel(int64_t rows, int64_t cols, const uint8_t *__restrict__ res, int64_t ld,
+                                uint64_t *__restrict__ planes, int64_t pitch, unsigned *err) {
+  constexpr int PP = base_planes<PB>();
+  constexpr int Q = PB * PB * (N == 3 ? PB : 1);
+  const int64_t total = rows * pitch;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / pitch;
+    const int64_t w = i - r * pitch;
+    const int64_t c0 = w * 64;
+    uint64_t out[N][PP];
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+      for (int p = 0; p < PP; ++p) out[j][p] = 0;
+    bool bad = false;
+    if (c0 < cols) {
+      const uint8_t *src = res + r * ld + c0;
+      const int cnt = int(cols - c0 < 64 ? cols - c0 : 64);
+      for (int e = 0; e < cnt; ++e) {
+        unsigned v = src[e];
+        if (v >= unsigned(Q)) {
+          bad = true;
+          v = 0;
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const unsigned d = v % PB;
+          v /= PB;
+          if constexpr (PB == 3) {             // unit, sign (Section 4.1)
+            out[j][0] |= uint64_t(d != 0) << e;
+            out[j][1] |= uint64_t(d == 2) << e;
+          } else {
+#pragma unroll
+            for (int p = 0; p < PP; ++p) out[j][p] |= uint64_t((d >> p) & 1u) << e;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+      for (int p = 0; p < PP; ++p) planes[((j * PP + p) * rows + r) * pitch + w] = out[j][p];
+    if (bad) record_error(err, FQ_EVALUE);
+  }
+}
+
+template <int PB, int N>
+__global__ void ext_unpack_kernel(int64_t rows, int64_t cols, const uint64_t *__restrict__ planes, int64_t pitch,
+                                  uint8_t *__restrict__ res, int64_t ld) {
+  constexpr int PP = base_planes<PB>();
+  const int64_t words = (cols + 63) / 64;
+  const int64_t total = rows * words;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / words;
+    const int64_t w = i - r * words;
+    uint64_t in[N][PP];
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+      for (int p = 0; p < PP; ++p) in[j][p] = __ldg(planes + ((j * PP + p) * rows + r) * pitch + w);
+    const int64_t c0 = w * 64;
+    uint8_t *dst = res + r * ld + c0;
+    const int cnt = int(cols - c0 < 64 ? cols - c0 : 64);
+    for (int e = 0; e < cnt; ++e) {
+      unsigned v = 0;
+#pragma unroll
+      for (int j = N - 1; j >= 0; --j) {
+        unsigned d;
+        if constexpr (PB == 3) {
+          const unsigned unit = unsigned(in[j][0] >> e) & 1u, sign = unsigned(in[j][1] >> e) & 1u;
+          d = unit + (unit & sign);
+        } else {
+          d = 0;
+#pragma unroll
+          for (int p = 0; p < PP; ++p) d |= (unsigned(in[j][p] >> e) & 1u) << p;
+          d = d >= unsigned(PB) ? d - PB : d;    // F_5, F_7 codes read mod p
+        }
+        v = v * PB + d;
+      }
+      dst[e] = uint8_t(v);
+    }
+  }
+}
+
 template <class F>
 __global__ void add_kernel(int64_t rows, int64_t pitch, const uint64_t *X, const uint64_t *Y, uint64_t *Z,
                            int sub) {
@@ -130,10 +224,17 @@ int launch_pack(int q, int64_t rows, int64_t cols, const uint8_t *res, int64_t l
   const int vec16 = (reinterpret_cast<uintptr_t>(res) % 16 == 0) && (ld % 16 == 0);
   const int th = 256, gr = grid_for(total, th);
   switch (q) {
+    case 2: pack_kernel<2, 1><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err, vec16); break;
     case 3: pack_kernel<3, 2><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err, vec16); break;
     case 4: pack_kernel<4, 2><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err, vec16); break;
     case 5: pack_kernel<5, 3><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err, vec16); break;
     case 7: pack_kernel<7, 3><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err, vec16); break;
+    case 8: ext_pack_kernel<2, 3><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err); break;
+    case 9: ext_pack_kernel<3, 2><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err); break;
+    case 25: ext_pack_kernel<5, 2><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err); break;
+    case 27: ext_pack_kernel<3, 3><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err); break;
+    case 49: ext_pack_kernel<7, 2><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err); break;
+    case 125: ext_pack_kernel<5, 3><<<gr, th, 0, s>>>(rows, cols, res, ld, planes, pitch, err); break;
     default: return FQ_EINVAL;
   }
   FQ_LAUNCH_CHECK();
@@ -148,10 +249,17 @@ int launch_unpack(int q, int64_t rows, int64_t cols, const uint64_t *planes, uin
   const int vec16 = (reinterpret_cast<uintptr_t>(res) % 16 == 0) && (ld % 16 == 0);
   const int th = 256, gr = grid_for(total, th);
   switch (q) {
+    case 2: unpack_kernel<2, 1><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld, vec16); break;
     case 3: unpack_kernel<3, 2><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld, vec16); break;
     case 4: unpack_kernel<4, 2><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld, vec16); break;
     case 5: unpack_kernel<5, 3><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld, vec16); break;
     case 7: unpack_kernel<7, 3><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld, vec16); break;
+    case 8: ext_unpack_kernel<2, 3><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld); break;
+    case 9: ext_unpack_kernel<3, 2><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld); break;
+    case 25: ext_unpack_kernel<5, 2><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld); break;
+    case 27: ext_unpack_kernel<3, 3><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld); break;
+    case 49: ext_unpack_kernel<7, 2><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld); break;
+    case 125: ext_unpack_kernel<5, 3><<<gr, th, 0, s>>>(rows, cols, planes, pitch, res, ld); break;
     default: return FQ_EINVAL;
   }
   FQ_LAUNCH_CHECK();
@@ -165,6 +273,7 @@ int launch_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint6
   if (total == 0) return FQ_OK;
   const int th = 256, gr = grid_for(total, th);
   switch (q) {
+    case 2: add_kernel<F2><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;
     case 3: add_kernel<F3><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;
     case 4: add_kernel<GF4><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;
     case 5: add_kernel<F5><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;

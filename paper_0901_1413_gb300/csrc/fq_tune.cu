@@ -39,7 +39,11 @@ bool tuned_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel
 // The constants are fitted to GB300 measurements of the compiled kernels.
 double m4rm_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
   double fixed = 300.0, per_row = 2.9, build = 1700.0;
-  if (q == 5) {
+  if (q == 2) {  // all-warps kernel, one 128-byte gather per row and block
+    fixed = 600.0;
+    per_row = 1.0;
+    build = 0.0;
+  } else if (q == 5) {
     fixed = 1500.0;
     per_row = 26.0;
     build = 0.0;
@@ -69,7 +73,7 @@ extern "C" {
 
 int fq_autotune(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                 void *stream, fq_tune_result *out) {
-  if (!(q == 3 || q == 4 || q == 5 || q == 7) || m <= 0 || l <= 0 || n <= 0 || !A || !B || !C) return FQ_EINVAL;
+  if (!(q == 2 || q == 3 || q == 4 || q == 5 || q == 7) || m <= 0 || l <= 0 || n <= 0 || !A || !B || !C) return FQ_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int nk = 0;
   fqk::m4rm_variants(q, &nk);

@@ -18,7 +18,7 @@ import torch
 from . import build as _build
 
 OK, EINVAL, EVALUE, ECUDA, ETIMEOUT, ENOTSUP, ENOMEM = range(7)
-PATH_AUTO, PATH_M4RM, PATH_MMA = 0, 1, 2
+PATH_AUTO, PATH_M4RM, PATH_MMA, PATH_KARATSUBA = 0, 1, 2, 3
 
 _lib = None
 

@@ -7,7 +7,10 @@ runs after one warm-up, inputs resident in device memory (seeded synthetic
 residues, uniform unless stated).  Throughput is 2 m l n / t in field
 operations per second; batched rows also give products per second.  Both
 product paths are timed where the configuration asks for them: the bitsliced
-Four-Russians path (M4RM) and the exact tensor-core path (MMA).
+Four-Russians path (M4RM) and the exact tensor-core path (MMA); for the
+extension fields these name the path of the base-field products inside
+Section 4.3's matrix-level product, and "karatsuba" is GF(4) by three F_2
+products.
 """
 from __future__ import annotations
 
@@ -44,7 +47,7 @@ def product_rows(q, m, l, n, paths=("m4rm",), sparse=False, reps=3):
     ops = 2.0 * m * l * n
     out = []
     for p in paths:
-        path = fq.PATH_M4RM if p == "m4rm" else fq.PATH_MMA
+        path = {"m4rm": fq.PATH_M4RM, "mma": fq.PATH_MMA, "karatsuba": fq.PATH_KARATSUBA}[p]
         t = _time(lambda: fq.matmul(a, b, out=c, path=path), reps)
         out.append((p, t, ops / t * 1e3))
     if fq.status() != fq.OK:
@@ -93,6 +96,10 @@ def main():
     emit("F_3 8192^3, A 90% zeros", product_rows(3, 8192, 8192, 8192, sparse=True, paths=("m4rm", "mma")))
     for q, name in ((5, "F_5"), (7, "F_7"), (4, "GF(4)")):
         emit("%s 8192^3" % name, product_rows(q, 8192, 8192, 8192, paths=("m4rm", "mma")))
+    emit("F_2 8192^3", product_rows(2, 8192, 8192, 8192, paths=("m4rm", "mma")))
+    emit("GF(4) 8192^3, three F_2 products", product_rows(4, 8192, 8192, 8192, paths=("karatsuba",)))
+    for q, name in ((8, "F_8"), (9, "F_9"), (25, "F_25"), (27, "F_27"), (49, "F_49"), (125, "F_125")):
+        emit("%s 8192^3 (base products on each path)" % name, product_rows(q, 8192, 8192, 8192, paths=("m4rm", "mma")))
     emit("F_3 65536 x 4096 x 4096", product_rows(3, 65536, 4096, 4096, paths=("m4rm", "mma")))
     if not args.quick:
         emit("F_5 32768^3", product_rows(5, 32768, 32768, 32768, paths=("m4rm", "mma"), reps=2))

@@ -35,7 +35,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_layout_helpers(lib):
-    assert [lib.fq_planes(q) for q in (2, 3, 4, 5, 6, 7, 8)] == [0, 2, 2, 3, 0, 3, 0]
+    assert [lib.fq_planes(q) for q in (2, 3, 4, 5, 6, 7, 8)] == [1, 2, 2, 3, 0, 3, 3]
+    assert [lib.fq_planes(q) for q in (9, 16, 25, 27, 49, 125, 343)] == [4, 0, 6, 6, 6, 9, 0]
     assert lib.fq_pitch_words(0) == 0
     assert lib.fq_pitch_words(1) == 16
     assert lib.fq_pitch_words(1024) == 16
@@ -61,6 +62,12 @@ def test_argument_errors_return_before_any_launch(lib):
     assert lib.fq_matmul_ex(3, 4, 4, 4, vp(16), vp(32), vp(48), None, ctypes.byref(opt)) == fq.EINVAL
     opt = fq.Options(k=11)
     assert lib.fq_matmul_ex(3, 4, 4, 4, vp(16), vp(32), vp(48), None, ctypes.byref(opt)) == fq.EINVAL
+    # the matrix-level (Karatsuba) path exists for GF(4) and the extension fields only
+    opt = fq.Options(path=fq.PATH_KARATSUBA)
+    for q in (2, 3, 5, 7):
+        assert lib.fq_matmul_ex(q, 4, 4, 4, vp(16), vp(32), vp(48), None, ctypes.byref(opt)) == fq.EINVAL
+    assert lib.fq_matmul(16, 4, 4, 4, vp(16), vp(32), vp(48), None) == fq.EINVAL  # no F_16
+    assert lib.fq_matmul(9, 4, 4, 4, vp(16), vp(32), vp(16), None) == fq.EINVAL   # C aliases A
     # empty products are no-ops
     assert lib.fq_matmul(3, 0, 4, 4, None, None, None, None) == fq.OK
     assert lib.fq_matmul(3, 4, 4, 0, None, None, None, None) == fq.OK
@@ -74,10 +81,11 @@ def test_error_strings(lib):
 
 def test_kernel_table(lib):
     from paper_0901_1413_gb300 import fq
-    for q in (3, 4, 5, 7):
+    for q in (2, 3, 4, 5, 7):
         ks = fq.kernels(q)
         assert ks and all(6 <= k["k"] <= 10 and k["max_rows"] > 0 and k["cols"] % 512 == 0 for k in ks)
     assert lib.fq_kernel_count(6) == 0
+    assert lib.fq_kernel_count(9) == 0          # extension fields use their base field's kernels
     k = ctypes.c_int()
     assert lib.fq_kernel_info(3, 10_000, ctypes.byref(k), None, None, None) == fq.EINVAL
 
@@ -117,3 +125,7 @@ def test_autotune_cache_host_side(lib):
     # an empty product needs no device and takes the M4RM planner
     assert lib.fq_auto_choice(3, 0, 10, 10, ctypes.byref(p), ctypes.byref(k)) == fq.OK
     assert (p.value, k.value) == (fq.PATH_M4RM, 0)
+    # extension fields always take the matrix-level products
+    for q in (8, 9, 25, 27, 49, 125):
+        assert lib.fq_auto_choice(q, 100, 100, 100, ctypes.byref(p), ctypes.byref(k)) == fq.OK
+        assert (p.value, k.value) == (fq.PATH_KARATSUBA, 0)

@@ -14,7 +14,7 @@ from paper_0901_1413_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FIELDS = (3, 4, 5, 7)
+FIELDS = (2, 3, 4, 5, 7)
 
 
 def to_dev(x):
@@ -114,7 +114,7 @@ def _value(q, code):
 @pytest.mark.parametrize("q", FIELDS)
 @pytest.mark.parametrize("sub", [False, True])
 def test_add_sub_every_code_pair(fq, q, sub):
-    codes = [0, 1, 3] if q == 3 else list(range(4 if q == 4 else 8))
+    codes = {2: [0, 1], 3: [0, 1, 3], 4: list(range(4))}.get(q, list(range(8)))
     pairs = list(itertools.product(codes, repeat=2))
     assert len(pairs) <= 64
     X = fq.empty(q, 1, 64)
@@ -227,8 +227,8 @@ def test_f3_large_sampled_rows_and_freivalds(fq, n):
     assert oracle.freivalds(q, A, B, got, trials=4)
 
 
-@pytest.mark.parametrize("q,k", [(3, 6), (3, 7), (3, 9), (3, 10), (4, 6), (4, 9), (4, 10),
-                                 (5, 6), (5, 7), (7, 6), (7, 7)])
+@pytest.mark.parametrize("q,k", [(2, 6), (2, 7), (2, 9), (2, 10), (3, 6), (3, 7), (3, 9), (3, 10),
+                                 (4, 6), (4, 9), (4, 10), (5, 6), (5, 7), (7, 6), (7, 7)])
 def test_every_block_size(fq, q, k):
     """k = 6, 7, 9, 10 do not divide 64: indices straddle A's words."""
     _check_product(fq, q, 333, 777, 600, seed=k, k=k)
@@ -256,7 +256,7 @@ def test_unsupported_block_size_is_reported(fq, q, kmax):
     assert e.value.status == fq.EINVAL
 
 
-@pytest.mark.parametrize("q", [3, 4, 5, 7])
+@pytest.mark.parametrize("q", [2, 3, 4, 5, 7])
 @pytest.mark.parametrize("k", [6, 7, 9])
 def test_last_block_reaches_past_the_pitch(fq, q, k):
     """l = 1024 is a whole pitch: with k not dividing 64 the last block's index
