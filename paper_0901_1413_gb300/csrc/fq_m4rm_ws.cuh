@@ -1,4 +1,5 @@
-// Warp-specialised Four-Russians kernel for the two-plane fields (F_3, GF(4)).
+// Warp-specialised Four-Russians kernel for the two-plane fields (F_3, GF(4))
+// and F_2.
 //
 // Same product as fq_m4rm.cuh (Section 2 of Boothby & Bradshaw):
 //   C_i = sum_s sum_d alpha_d T_s[phi_d(A_i, block s)],  T_s[b] = sum_t b_t B_{sk+t},
@@ -14,8 +15,10 @@
 //  * 16 - NPW consumer warps (the other warpgroups, most registers): for every block,
 //    gather D table entries per row and add them into register accumulators.
 //
-// Tables are double- or triple-buffered by block (NBUF) and offsets
-// double-buffered by chunk: while consumers read table s mod NBUF, producers
+// Tables are double- or triple-buffered by block (NBUF), B blocks are staged
+// NSTAGE blocks ahead (enough for fast consumers: an F_2 block is short next
+// to a TMA round trip) and offsets double-buffered by chunk: while consumers
+// read table s mod NBUF, producers
 // fill the next ones, and the offsets of chunk c + 1 are written while chunk c
 // is consumed.  Hand-over is by mbarriers (tfull: 128
 // producer arrivals; tempty: 384 consumer arrivals).  Every wait is bounded;
@@ -36,18 +39,21 @@ __host__ __device__ constexpr int popc(int x) { return x == 0 ? 0 : (x & 1) + po
 __host__ __device__ constexpr int ctz(int x) { return (x & 1) ? 0 : 1 + ctz(x >> 1); }
 constexpr int round128(int x) { return (x + 127) / 128 * 128; }
 
-template <class F, int K_, int RS_, int NPW_ = 4, int NBUF_ = 2>
+template <class F, int K_, int RS_, int NPW_ = 4, int NBUF_ = 2, int NSTAGE_ = (NBUF_ == 3 ? 3 : 4)>
 struct Cfg {
   using Field = F;
-  static_assert(F::P == 2 && F::D == 2, "two planes, basis of two");
+  static_assert((F::P == 2 && F::D == 2) || (F::P == 1 && F::D == 1), "two planes and two basis elements, or F_2");
   static constexpr int K = K_;        // block size
   static constexpr int RS = RS_;      // row slots per consumer warp (even)
   static_assert(RS % 2 == 0, "slots are read in pairs");
-  static constexpr int P = 2, D = 2;
-  static constexpr int LPR = 8, GPW = 4, WPL = 2, PW = 4;  // 8-lane groups, 2 words per plane
+  static constexpr int P = F::P, D = F::D;
+  // 8-lane groups; a lane holds 16 bytes of an entry: WPL words of each plane
+  static constexpr int LPR = 8, GPW = 4, PW = 4, WPL = PW / P;
   static constexpr int NPW = NPW_, NCW = 16 - NPW;         // producer / consumer warps
-  static constexpr int NBUF = NBUF_;                        // table (and B stage) buffers
-  static_assert(NBUF == 2 || NBUF == 3, "double or triple buffering");
+  static constexpr int NBUF = NBUF_;                        // table buffers
+  static_assert(NBUF >= 2 && NBUF <= 4, "two to four table buffers");
+  static constexpr int NSTAGE = NSTAGE_;                    // B block stages
+  static_assert(NSTAGE >= NBUF && NSTAGE <= 16, "B stages");
   static_assert(NPW == 4 || NPW == 8, "one or two producer warpgroups");
   static constexpr int NT = (NPW + NCW) * 32;
   static constexpr int NPT = NPW * 32;                      // producer threads
@@ -56,7 +62,7 @@ struct Cfg {
   static_assert(NPT * PREG + NCW * 32 * CREG == 65536, "register split");
   static constexpr int ENTRY = 128;                         // bytes per table entry (idx * 128 below)
   static constexpr int ENTRIES = 1 << K;
-  static constexpr int CT = 512, CTW = 8;                   // columns (words) per tile
+  static constexpr int CT = 32 * LPR * WPL, CTW = CT / 64;  // columns (words) per tile: 512, F_2 1024
   static constexpr int ROWS_PER_SLOT = NCW * GPW;
   static constexpr int MT = RS * ROWS_PER_SLOT;             // rows per CTA
   static constexpr int NBUILD = NPW * GPW;                  // builder groups
@@ -76,9 +82,9 @@ struct Cfg {
   static constexpr int TABLE_OFF = 0;
   static constexpr int OFFS_OFF = NBUF * TABLE_BYTES;
   static constexpr int BSTAGE_OFF = OFFS_OFF + 2 * OFFS_BYTES;
-  static constexpr int ASTAGE_OFF = BSTAGE_OFF + NBUF * STAGE_STRIDE;
-  static constexpr int BAR_OFF = ASTAGE_OFF + ASTAGE_BYTES;  // bfull[NBUF], tfull[NBUF], tempty[NBUF], afull
-  static constexpr int ABORT_OFF = BAR_OFF + 8 * (3 * NBUF + 1);
+  static constexpr int ASTAGE_OFF = BSTAGE_OFF + NSTAGE * STAGE_STRIDE;
+  static constexpr int BAR_OFF = ASTAGE_OFF + ASTAGE_BYTES;  // bfull[NSTAGE], tfull[NBUF], tempty[NBUF], afull
+  static constexpr int ABORT_OFF = BAR_OFF + 8 * (NSTAGE + 2 * NBUF + 1);
   static constexpr int SMEM = ABORT_OFF + 16;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -118,9 +124,18 @@ __device__ __forceinline__ void sts128(uint32_t addr, const uint32_t (&v)[4]) {
                : "memory");
 }
 
-// Bounded wait that also gives up at once when the CTA has aborted.
+// Bounded wait that also gives up at once when the CTA has aborted.  A phase
+// that is already complete returns without reading the shared abort flag.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
 __device__ __forceinline__ void wait_or_abort(uint32_t bar, uint32_t parity, volatile int &abort_flag,
                                               unsigned *err) {
+  if (mbar_try(bar, parity)) return;
   if (abort_flag) return;
   if (!mbar_wait_bounded(bar, parity)) {
     abort_flag = 1;
@@ -165,22 +180,28 @@ __device__ __forceinline__ void build_offsets(const Params &prm, const unsigned 
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int r = (2 * j + h) * C::ROWS_PER_SLOT + rem;
-      uint64_t win[2] = {0ull, 0ull};
+      uint64_t win[C::D];
+#pragma unroll
+      for (int d = 0; d < C::D; ++d) win[d] = 0ull;
       if (r < rows_here) {
         const uint64_t *rowp = as + (r / C::ABOX_ROWS) * (C::ABOX_BYTES / 8) + (r % C::ABOX_ROWS) * C::ABOX_WORDS;
-        uint64_t f[2];
+        uint64_t f[C::P];
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
+        for (int p = 0; p < C::P; ++p) {
           const uint64_t *wp = rowp + p * (C::ABOX_ROWS * C::ABOX_WORDS);
           const uint64_t w0 = wi ? wp[1] : wp[0];
           const uint64_t w1 = wi ? wp[2] : wp[1];
           f[p] = sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;   // the chunk's 64 bits
         }
         F::phi(f, win);
-        win[0] &= keep;
-        win[1] &= keep;
+#pragma unroll
+        for (int d = 0; d < C::D; ++d) win[d] &= keep;
       }
-      if constexpr (C::K == 8) {
+      if constexpr (C::D == 1) {
+        // F_2: one offset per row and block
+#pragma unroll
+        for (int b = 0; b < C::NB; ++b) packed[h][b] = (uint32_t(win[0] >> (b * C::K)) & mask) * uint32_t(C::ENTRY);
+      } else if constexpr (C::K == 8) {
         // byte b of each map: one byte permute, then idx * 128 in both halves
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
@@ -207,6 +228,11 @@ __device__ __forceinline__ void build_offsets(const Params &prm, const unsigned 
 
 template <class C>
 __device__ __forceinline__ void load_brow(uint32_t stage, int t, int gl, uint32_t (&v)[4]) {
+  if constexpr (C::P == 1) {
+    // stage layout [row][32 x 32-bit]; lane gl's words at gl * 4
+    lds128(stage + uint32_t(t * C::CTW * 8 + gl * 16), v);
+    return;
+  }
   // stage layout [p][row][16 x 32-bit]; lane gl's words of plane p at gl * 2
   const uint32_t a0 = stage + uint32_t((0 * C::K + t) * 64 + gl * 8);
   const uint32_t a1 = stage + uint32_t((1 * C::K + t) * 64 + gl * 8);
@@ -214,15 +240,21 @@ __device__ __forceinline__ void load_brow(uint32_t stage, int t, int gl, uint32_
   asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v[2]), "=r"(v[3]) : "r"(a1));
 }
 
-// entry layout (per lane, 16 bytes): plane 0 words 0..1, plane 1 words 0..1
+// entry layout (per lane, 16 bytes): plane 0 words 0..WPL-1, then plane 1's
 template <class F>
 __device__ __forceinline__ void add_lane(uint32_t (&x)[4], const uint32_t (&y)[4]) {
+  constexpr int P = F::P, WPL = 4 / P;
 #pragma unroll
-  for (int w = 0; w < 2; ++w) {
-    uint32_t a[2] = {x[w], x[2 + w]}, b[2] = {y[w], y[2 + w]};
+  for (int w = 0; w < WPL; ++w) {
+    uint32_t a[P], b[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      a[p] = x[p * WPL + w];
+      b[p] = y[p * WPL + w];
+    }
     F::add(a, b);
-    x[w] = a[0];
-    x[2 + w] = a[1];
+#pragma unroll
+    for (int p = 0; p < P; ++p) x[p * WPL + w] = a[p];
   }
 }
 
@@ -297,20 +329,33 @@ __device__ __forceinline__ void lookup_block(uint32_t (&acc)[C::RS][4], uint32_t
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int i = 2 * j + h;
-      // off1 = o >> 16 and off0 = o - off1 * 2^16, both as IMADs
-      const uint32_t hi = __umulhi(o[h], 65536u);
-      const uint32_t a1 = imad(hi, one, tbl_lane);
-      const uint32_t a0 = imad(hi, 0xFFFF0000u, imad(o[h], one, tbl_lane));
-      uint32_t t0[4], t1[4];
-      lds128(a0, t0);
-      lds128(a1, t1);
+      if constexpr (C::D == 1) {
+        // F_2: one gather, one XOR per word
+        uint32_t t0[4];
+        lds128(imad(o[h], one, tbl_lane), t0);
 #pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        uint32_t a[2] = {acc[i][w], acc[i][2 + w]};
-        const uint32_t tt[2][2] = {{t0[w], t0[2 + w]}, {t1[w], t1[2 + w]}};
-        F::accumulate(a, tt);
-        acc[i][w] = a[0];
-        acc[i][2 + w] = a[1];
+        for (int w = 0; w < 4; ++w) {
+          uint32_t a[1] = {acc[i][w]};
+          const uint32_t tt[1][1] = {{t0[w]}};
+          F::accumulate(a, tt);
+          acc[i][w] = a[0];
+        }
+      } else {
+        // off1 = o >> 16 and off0 = o - off1 * 2^16, both as IMADs
+        const uint32_t hi = __umulhi(o[h], 65536u);
+        const uint32_t a1 = imad(hi, one, tbl_lane);
+        const uint32_t a0 = imad(hi, 0xFFFF0000u, imad(o[h], one, tbl_lane));
+        uint32_t t0[4], t1[4];
+        lds128(a0, t0);
+        lds128(a1, t1);
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+          uint32_t a[2] = {acc[i][w], acc[i][2 + w]};
+          const uint32_t tt[2][2] = {{t0[w], t0[2 + w]}, {t1[w], t1[2 + w]}};
+          F::accumulate(a, tt);
+          acc[i][w] = a[0];
+          acc[i][2 + w] = a[1];
+        }
       }
     }
   }
@@ -328,14 +373,14 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
   const int64_t w0 = int64_t(blockIdx.x) * C::CTW;
 
   const uint32_t base = smem_u32(smem);
-  const uint32_t bfull = base + C::BAR_OFF, tfull = bfull + 8 * C::NBUF, tempty = bfull + 16 * C::NBUF,
-                 afull = bfull + 24 * C::NBUF;
+  const uint32_t bfull = base + C::BAR_OFF, tfull = bfull + 8 * C::NSTAGE, tempty = tfull + 8 * C::NBUF,
+                 afull = tempty + 8 * C::NBUF;
   volatile int &abort_flag = *reinterpret_cast<int *>(smem + C::ABORT_OFF);
 
   if (tid == 0) {
     abort_flag = 0;
+    for (int i = 0; i < C::NSTAGE; ++i) mbar_init(bfull + 8 * i, 1);
     for (int i = 0; i < C::NBUF; ++i) {
-      mbar_init(bfull + 8 * i, 1);
       mbar_init(tfull + 8 * i, C::NPT);
       mbar_init(tempty + 8 * i, C::NCW * 32);
     }
@@ -351,7 +396,7 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
     const int builder = warp * C::GPW + grp;
     const uint32_t tbl_lane0 = base + C::TABLE_OFF + uint32_t(gl * 16);
     if (ptid == 0) {
-      for (int64_t s = 0; s < C::NBUF && s < prm.nblocks; ++s) {
+      for (int64_t s = 0; s < C::NSTAGE && s < prm.nblocks; ++s) {
         mbar_expect_tx(bfull + 8 * uint32_t(s), C::STAGE_BYTES);
         tma_load_3d(base + C::BSTAGE_OFF + uint32_t(s) * C::STAGE_STRIDE, &tmB, bfull + 8 * uint32_t(s), int(w0),
                     int(s * C::K), 0);
@@ -398,15 +443,16 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
         }
       }
       if (s >= C::NBUF) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
-      wait_or_abort(bfull + 8 * buf, use & 1, abort_flag, prm.err);
-      build_table<C>(tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), base + C::BSTAGE_OFF + buf * C::STAGE_STRIDE,
+      const int sb = int(s % C::NSTAGE);
+      wait_or_abort(bfull + 8 * sb, uint32_t(s / C::NSTAGE) & 1, abort_flag, prm.err);
+      build_table<C>(tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), base + C::BSTAGE_OFF + sb * C::STAGE_STRIDE,
                      builder, gl);
       producer_sync<C::NPT>();  // every producer is done with this B stage
-      if (ptid == 0 && s + C::NBUF < prm.nblocks && !abort_flag) {
+      if (ptid == 0 && s + C::NSTAGE < prm.nblocks && !abort_flag) {
         fence_proxy_async_smem();
-        mbar_expect_tx(bfull + 8 * buf, C::STAGE_BYTES);
-        tma_load_3d(base + C::BSTAGE_OFF + buf * C::STAGE_STRIDE, &tmB, bfull + 8 * buf, int(w0),
-                    int((s + C::NBUF) * C::K), 0);
+        mbar_expect_tx(bfull + 8 * sb, C::STAGE_BYTES);
+        tma_load_3d(base + C::BSTAGE_OFF + sb * C::STAGE_STRIDE, &tmB, bfull + 8 * sb, int(w0),
+                    int((s + C::NSTAGE) * C::K), 0);
       }
       mbar_arrive(tfull + 8 * buf);
     }
@@ -436,9 +482,13 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
       if (r < rows_here) {
         const int64_t row = row0 + r;
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          uint32_t *dst = reinterpret_cast<uint32_t *>(prm.C + (p * prm.m + row) * prm.pc + w0) + gl * 2;
-          *reinterpret_cast<uint2 *>(dst) = make_uint2(acc[i][2 * p + 0], acc[i][2 * p + 1]);
+        for (int p = 0; p < C::P; ++p) {
+          uint32_t *dst = reinterpret_cast<uint32_t *>(prm.C + (p * prm.m + row) * prm.pc + w0) + gl * C::WPL;
+          if constexpr (C::WPL == 4) {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+          } else {
+            *reinterpret_cast<uint2 *>(dst) = make_uint2(acc[i][2 * p + 0], acc[i][2 * p + 1]);
+          }
         }
       }
     }

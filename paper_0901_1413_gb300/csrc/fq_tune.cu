@@ -39,8 +39,8 @@ bool tuned_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel
 // The constants are fitted to GB300 measurements of the compiled kernels.
 double m4rm_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
   double fixed = 300.0, per_row = 2.9, build = 1700.0;
-  if (q == 2) {  // all-warps kernel, one 128-byte gather per row and block
-    fixed = 600.0;
+  if (q == 2) {  // warp-specialised kernels, one 128-byte gather per row and block
+    fixed = 1000.0;
     per_row = 1.0;
     build = 0.0;
   } else if (q == 5) {

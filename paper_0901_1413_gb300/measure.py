@@ -79,11 +79,30 @@ def batched_row(q, count=4096, reps=5):
     return t, count / t * 1e3, ops / t * 1e3, plan.items
 
 
+def one_case(spec, reps):
+    """--case q,m,l,n[,path[,kernel]]: one product, `reps` timed runs after a warm-up."""
+    parts = spec.split(",")
+    q, m, l, n = (int(x) for x in parts[:4])
+    path = parts[4] if len(parts) > 4 else "auto"
+    kernel = int(parts[5]) if len(parts) > 5 else 0
+    a, b, c = _operands(q, m, l, n)
+    code = {"auto": fq.PATH_AUTO, "m4rm": fq.PATH_M4RM, "mma": fq.PATH_MMA, "karatsuba": fq.PATH_KARATSUBA}[path]
+    t = _time(lambda: fq.matmul(a, b, out=c, path=code, kernel=kernel), reps)
+    if fq.status() != fq.OK:
+        raise RuntimeError("device reported an error")
+    print("| q=%d %dx%dx%d | %s | %.3f | %.3e |" % (q, m, l, n, path, t, 2.0 * m * l * n / t * 1e3))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="skip the n = 32768 product")
+    ap.add_argument("--case", help="time one product only: q,m,l,n[,path[,kernel]]")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     fq.load()
+    if args.case:
+        one_case(args.case, args.reps)
+        return
     print("| configuration | path | ms | field-ops/s |")
     print("|---|---|---:|---:|")
 
