@@ -106,7 +106,10 @@ typedef struct fq_options {
   int64_t chunk; /* MMA path: l-chunk length between mod-p reductions; 0 = largest */
   int variant;   /* M4RM rows per CTA: 0 = planner, else 1 .. the kernel's maximum */
   int kernel;    /* M4RM kernel: 0 = planner, i + 1 = compiled kernel i of field q  */
-  int reserved[4];
+  int strassen;  /* Strassen-Winograd levels over the base-field products: 0 = the
+                    time model decides, -1 = none, L > 0 = L levels (each needs
+                    m, l, n to be multiples of 2048 at that level)               */
+  int reserved[3];
 } fq_options;
 
 /* C = A B over F_q (Section 2: C_i = sum_s sum_d alpha_d T_s[phi_d(A_i, block s)]).
@@ -118,15 +121,31 @@ typedef struct fq_options {
  * MMA; k, variant and kernel refer to the base field's kernels) and one
  * elementwise combination kernel.  Their scratch (the operand sums and the
  * products beyond n, about (3 or 6 - n) x the base-field size of A, B and C)
- * is taken from and returned to the device's stream-ordered memory pool on
- * `stream` (cudaMallocAsync / cudaFreeAsync), which a CUDA graph capture
- * records as allocation nodes. */
+ * is stream-ordered on `stream` (a CUDA graph capture records it as
+ * allocation nodes) from the library's own memory pool on the device. */
 int fq_matmul(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
               const uint64_t *B, uint64_t *C, void *stream);
 
-/* fq_matmul with explicit options (path, k, l-chunk, tile variant); opt may be NULL. */
+/* fq_matmul with explicit options (path, k, l-chunk, tile variant, Strassen
+ * levels); opt may be NULL.
+ *
+ * Strassen-Winograd (the paper's remark that M4RM serves as the base case of an
+ * asymptotically faster product, Section 2): one level computes C from seven
+ * half-size products and fifteen bitsliced additions over quadrants, which are
+ * copied out of and back into the packed matrices.  Levels need m, l, n to be
+ * multiples of 2048 (halves of whole 1024-column pitches); with strassen = 0 a
+ * level is taken only where the time model expects seven half-size products
+ * and the additions to beat the direct product (on GB300, F_3 from 16384 on).
+ * Scratch (the quadrants, eight operand sums and seven products, about 3.4x
+ * the size of A, B and C together at the top level) is stream-ordered on
+ * `stream` from the library's own memory pool, see fq_release_scratch. */
 int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
                  const uint64_t *B, uint64_t *C, void *stream, const fq_options *opt);
+
+/* The number of Strassen-Winograd levels fq_matmul_ex takes for (q, m, l, n)
+ * with these options (opt may be NULL) on the current device: >= 0, or
+ * -FQ_EINVAL / -FQ_ECUDA.  Host-only apart from the device attribute query. */
+int fq_strassen_levels(int q, int64_t m, int64_t l, int64_t n, const fq_options *opt);
 
 /* ---- many products in one launch ------------------------------------------
  * A plan splits `count` products C_p = A_p B_p (shapes m[p] x l[p] times
@@ -224,6 +243,12 @@ int fq_auto_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kerne
  * Host-only; returns FQ_EINVAL for a bad q or idx. */
 int fq_kernel_count(int q);
 int fq_kernel_info(int q, int idx, int *k, int *max_rows, int *cols, int *warps);
+
+/* The library's scratch pool (one per device, created on first use) keeps the
+ * memory it has handed out for later products instead of returning it at
+ * every synchronisation.  fq_release_scratch synchronises the current device
+ * and returns the pool's unused memory to the system.  Synchronous. */
+int fq_release_scratch(void);
 
 /* Wait for `stream`, then return and clear the first error kernels recorded on
  * the current device (FQ_EVALUE, FQ_ETIMEOUT), or FQ_OK.  Synchronous. */

@@ -50,6 +50,46 @@ int status_word(unsigned **out) {
   return FQ_OK;
 }
 
+// The library's scratch pool on each device: stream-ordered allocations that
+// keep their memory between products (release threshold: unlimited), so a
+// product that needs scratch does not map fresh memory after every
+// synchronisation.  fq_release_scratch trims it.
+cudaMemPool_t g_pool[kMaxDevices];
+
+int scratch_pool(cudaMemPool_t *out) {
+  int dev = 0;
+  FQ_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return FQ_ENOTSUP;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    FQ_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = ~uint64_t(0);
+    FQ_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return FQ_OK;
+}
+
+int scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = nullptr;
+  if (int rc = scratch_pool(&pool)) return rc;
+  FQ_CUDA_TRY(cudaMallocFromPoolAsync(p, bytes, pool, s));
+  return FQ_OK;
+}
+
+int scratch_free(void *p, cudaStream_t s) {
+  FQ_CUDA_TRY(cudaFreeAsync(p, s));
+  return FQ_OK;
+}
+
 int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000 *out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_encode) {
@@ -124,6 +164,17 @@ int fq_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t 
   return FQ_OK;
 }
 
+fqk::ProdOptions prod_options(const fq_options &o) {
+  fqk::ProdOptions p;
+  p.path = o.path;
+  p.k = o.k;
+  p.variant = o.variant;
+  p.kernel = o.kernel;
+  p.chunk = o.chunk;
+  p.strassen = o.strassen;
+  return p;
+}
+
 int fq_auto_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel) {
   if (!valid_q(q) || m < 0 || l < 0 || n < 0 || !path || !kernel) return FQ_EINVAL;
   *path = base_q(q) ? FQ_PATH_M4RM : FQ_PATH_KARATSUBA;
@@ -154,24 +205,22 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, cons
   if (o.path == FQ_PATH_KARATSUBA && base_q(q) && q != 4) return FQ_EINVAL;
   if (o.k != 0 && (o.k < 6 || o.k > 10)) return FQ_EINVAL;
   if (o.chunk < 0 || o.variant < 0) return FQ_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (o.kernel < 0) return FQ_EINVAL;
-  if (!base_q(q) || o.path == FQ_PATH_KARATSUBA) {
-    // Section 4.3's matrix-level product; `path` picks the base products' path
-    fqk::ExtOptions e;
-    e.path = o.path == FQ_PATH_KARATSUBA ? FQ_PATH_AUTO : o.path;
-    if (e.path == FQ_PATH_AUTO && (o.k || o.kernel || o.variant)) e.path = FQ_PATH_M4RM;
-    e.k = o.k;
-    e.variant = o.variant;
-    e.kernel = o.kernel;
-    e.chunk = o.chunk;
-    return fqk::launch_ext(q, m, l, n, A, B, C, e, s);
-  }
-  if (o.path == FQ_PATH_AUTO && o.k == 0 && o.kernel == 0 && o.variant == 0) {
-    if (int rc = fq_auto_choice(q, m, l, n, &o.path, &o.kernel)) return rc;
-  }
-  if (o.path == FQ_PATH_MMA) return fqk::launch_mma(q, m, l, n, A, B, C, o.chunk, s);
-  return fqk::launch_m4rm(q, m, l, n, A, B, C, o.k, o.variant, o.kernel, s);
+  if (o.kernel < 0 || o.strassen < -1) return FQ_EINVAL;
+  return fqk::product(q, m, l, n, A, B, C, prod_options(o), static_cast<cudaStream_t>(stream));
+}
+
+int fq_strassen_levels(int q, int64_t m, int64_t l, int64_t n, const fq_options *opt) {
+  if (!valid_q(q) || m < 0 || l < 0 || n < 0) return -FQ_EINVAL;
+  fq_options o;
+  memset(&o, 0, sizeof(o));
+  if (opt) o = *opt;
+  if (o.path < FQ_PATH_AUTO || o.path > FQ_PATH_KARATSUBA || o.strassen < -1) return -FQ_EINVAL;
+  if (!base_q(q) || m == 0 || l == 0 || n == 0) return 0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -fqk::record_cuda_error(cudaGetLastError());
+  return fqk::strassen_levels(q, m, l, n, prod_options(o), sms);
 }
 
 int fq_matmul(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
@@ -193,6 +242,21 @@ int fq_kernel_info(int q, int idx, int *k, int *max_rows, int *cols, int *warps)
   if (max_rows) *max_rows = vs[idx].rs * vs[idx].rows_per_slot;
   if (cols) *cols = vs[idx].cols;
   if (warps) *warps = vs[idx].warps;
+  return FQ_OK;
+}
+
+int fq_release_scratch(void) {
+  int dev = 0;
+  FQ_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= fqk::kMaxDevices) return FQ_ENOTSUP;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(fqk::g_mu);
+    pool = fqk::g_pool[dev];
+  }
+  if (!pool) return FQ_OK;
+  FQ_CUDA_TRY(cudaDeviceSynchronize());
+  FQ_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
   return FQ_OK;
 }
 

@@ -16,11 +16,12 @@
 // the products, computed on the host once and applied by one bitsliced
 // elementwise kernel.
 //
-// The base-field products are ordinary fq_matmul products (Four Russians or the
-// tensor-core path); the operand sums use the base field's bitsliced add.  The
+// The base-field products are ordinary products (Four Russians or the
+// tensor-core path, with Strassen-Winograd levels where they pay); the operand
+// sums use the base field's bitsliced add.  The
 // first n products (A_j B_j) are written straight into C's coefficient slots;
-// the others, and the operand sums, live in stream-ordered scratch memory that
-// is released on the same stream.
+// the others, and the operand sums, live in stream-ordered scratch from the
+// library's pool, released on the same stream.
 #include "../../include/fq.h"
 #include "fq_fields.cuh"
 #include "fq_internal.h"
@@ -152,18 +153,8 @@ int combine(const ExtField &f, int64_t words, uint64_t *C, const uint64_t *T, co
 
 int base_planes(int p) { return p == 2 ? 1 : (p == 3 ? 2 : 3); }
 
-// One base-field product on the requested path (FQ_PATH_AUTO: the time model).
-int base_product(int p, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
-                 const ExtOptions &o, int sms, cudaStream_t s) {
-  int path = o.path;
-  if (path != FQ_PATH_M4RM && path != FQ_PATH_MMA)
-    path = mma_estimate(p, m, l, n, sms) < m4rm_estimate(p, m, l, n, sms) ? FQ_PATH_MMA : FQ_PATH_M4RM;
-  if (path == FQ_PATH_MMA) return launch_mma(p, m, l, n, A, B, C, o.chunk, s);
-  return launch_m4rm(p, m, l, n, A, B, C, o.k, o.variant, o.kernel, s);
-}
-
 int run(const ExtField &f, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
-        uint64_t *ws, const ExtOptions &o, int sms, cudaStream_t s) {
+        uint64_t *ws, const ProdOptions &o, cudaStream_t s) {
   const int N = f.n, NP = N == 2 ? 3 : 6, PP = base_planes(f.p);
   const Product *prods = N == 2 ? kQuadratic : kCubic;
   const int64_t pa = fq_pitch_words(l), pc = fq_pitch_words(n);
@@ -181,7 +172,7 @@ int run(const ExtField &f, int64_t m, int64_t l, int64_t n, const uint64_t *A, c
       b = sb;
     }
     uint64_t *dst = k < N ? C + k * c_words : T + (k - N) * c_words;
-    if (int rc = base_product(f.p, m, l, n, a, b, dst, o, sms, s)) return rc;
+    if (int rc = product(f.p, m, l, n, a, b, dst, o, s)) return rc;
   }
   return combine(f, m * pc, C, T, plan_weights(f), s);
 }
@@ -203,20 +194,17 @@ int64_t ext_workspace_words(int q, int64_t m, int64_t l, int64_t n) {
 }
 
 int launch_ext(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
-               const ExtOptions &o, cudaStream_t s) {
+               const ProdOptions &o, cudaStream_t s) {
   const ExtField *f = ext_field(q);
   if (!f) return FQ_EINVAL;
-  int dev = 0, sms = 0;
-  FQ_CUDA_TRY(cudaGetDevice(&dev));
-  FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t words = ext_workspace_words(q, m, l, n);
   void *ws = nullptr;
-  FQ_CUDA_TRY(cudaMallocAsync(&ws, size_t(words > 0 ? words : 1) * 8u, s));
-  const int rc = run(*f, m, l, n, A, B, C, static_cast<uint64_t *>(ws), o, sms, s);
-  const cudaError_t e = cudaFreeAsync(ws, s);
-  if (rc) return rc;
-  if (e != cudaSuccess) return record_cuda_error(e);
-  return FQ_OK;
+  if (int rc = scratch_alloc(&ws, size_t(words > 0 ? words : 1) * 8u, s)) return rc;
+  ProdOptions base = o;
+  if (base.path == FQ_PATH_KARATSUBA) base.path = FQ_PATH_AUTO;
+  const int rc = run(*f, m, l, n, A, B, C, static_cast<uint64_t *>(ws), base, s);
+  const int fr = scratch_free(ws, s);
+  return rc ? rc : fr;
 }
 
 }  // namespace fqk

@@ -12,6 +12,8 @@ int launch_unpack(int q, int64_t rows, int64_t cols, const uint64_t *planes, uin
                   cudaStream_t s);
 int launch_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint64_t *Y, uint64_t *Z, int sub,
                cudaStream_t s);
+// Canonical codes in place (F_5, F_7; a no-op for the other fields).
+int launch_canon(int q, int64_t rows, int64_t cols, uint64_t *Z, cudaStream_t s);
 int launch_m4rm(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                 int k, int variant, int kernel, cudaStream_t s);
 
@@ -40,14 +42,27 @@ struct ExtField {
   int r[3];
 };
 const ExtField *ext_field(int q);
-// Base-product options of an extension-field product.
-struct ExtOptions {
+// Stream-ordered scratch from the library's per-device pool (fq_api.cu).
+int scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+int scratch_free(void *p, cudaStream_t s);
+
+// Options of one product (fq_options without the ABI padding).
+struct ProdOptions {
   int path, k, variant, kernel;
   int64_t chunk;
+  int strassen;  // 0 = time model, -1 = never, L > 0 = exactly L levels where the shape allows
 };
 int64_t ext_workspace_words(int q, int64_t m, int64_t l, int64_t n);
 int launch_ext(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
-               const ExtOptions &o, cudaStream_t s);
+               const ProdOptions &o, cudaStream_t s);
+
+// C = A B over field q by the options (fq_strassen.cu): the matrix-level
+// products of an extension field, Strassen-Winograd levels over a base field,
+// then the Four-Russians or tensor-core kernels.
+int product(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+            const ProdOptions &o, cudaStream_t s);
+// Strassen-Winograd levels `product` takes for a base-field product.
+int strassen_levels(int q, int64_t m, int64_t l, int64_t n, const ProdOptions &o, int sms);
 
 // The autotuned (path, kernel) for a shape, if fq_autotune measured one.
 bool tuned_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel);

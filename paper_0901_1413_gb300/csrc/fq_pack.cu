@@ -206,6 +206,25 @@ __global__ void add_kernel(int64_t rows, int64_t pitch, const uint64_t *X, const
   }
 }
 
+template <class F>
+__global__ void canon_kernel(int64_t total, uint64_t *Z) {
+  constexpr int P = F::P;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    uint32_t lo[P], hi[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const uint64_t z = Z[p * total + i];
+      lo[p] = uint32_t(z);
+      hi[p] = uint32_t(z >> 32);
+    }
+    F::canon(lo);
+    F::canon(hi);
+#pragma unroll
+    for (int p = 0; p < P; ++p) Z[p * total + i] = uint64_t(lo[p]) | (uint64_t(hi[p]) << 32);
+  }
+}
+
 inline int grid_for(int64_t total, int threads) {
   const int64_t want = cdiv(total, threads);
   const int64_t cap = 152 * 32;
@@ -279,6 +298,19 @@ int launch_add(int q, int64_t rows, int64_t cols, const uint64_t *X, const uint6
     case 5: add_kernel<F5><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;
     case 7: add_kernel<F7><<<gr, th, 0, s>>>(rows, pitch, X, Y, Z, sub); break;
     default: return FQ_EINVAL;
+  }
+  FQ_LAUNCH_CHECK();
+  return FQ_OK;
+}
+
+int launch_canon(int q, int64_t rows, int64_t cols, uint64_t *Z, cudaStream_t s) {
+  const int64_t total = rows * fq_pitch_words(cols);
+  if (total == 0) return FQ_OK;
+  const int th = 256, gr = grid_for(total, th);
+  switch (q) {
+    case 5: canon_kernel<F5><<<gr, th, 0, s>>>(total, Z); break;
+    case 7: canon_kernel<F7><<<gr, th, 0, s>>>(total, Z); break;
+    default: return FQ_OK;  // F_2, F_3 and GF(4) codes are unique
   }
   FQ_LAUNCH_CHECK();
   return FQ_OK;

@@ -38,9 +38,10 @@ bool tuned_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel
 // part per row of the tile), plus a constant for launch and the last store.
 // The constants are fitted to GB300 measurements of the compiled kernels.
 double m4rm_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
-  double fixed = 300.0, per_row = 2.9, build = 1700.0;
+  double fixed = 300.0, per_row = 2.9, build = 1700.0, hand_off = 0.0;
   if (q == 2) {  // warp-specialised kernels, one 128-byte gather per row and block
-    fixed = 1000.0;
+    hand_off = 700.0;  // producer/consumer hand-off per block, whatever k
+    fixed = 300.0;
     per_row = 1.0;
     build = 0.0;
   } else if (q == 5) {
@@ -59,7 +60,7 @@ double m4rm_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
     const int64_t rows = int64_t(vs[i].rs) * vs[i].rows_per_slot;
     const int64_t ctas = cdiv(m, rows) * (fq_pitch_words(n) / (vs[i].cols / 64));
     const double scale = double(1 << vs[i].k) / 256.0;
-    const double lookups = fixed * scale + per_row * double(rows < m ? rows : m);
+    const double lookups = hand_off + fixed * scale + per_row * double(rows < m ? rows : m);
     const double per_block = lookups > build * scale ? lookups : build * scale;
     const double t = double(cdiv(ctas, sms)) * double(cdiv(l, vs[i].k)) * per_block;
     best = t < best ? t : best;

@@ -34,7 +34,8 @@ class FqError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("k", ctypes.c_int), ("chunk", ctypes.c_int64),
-                ("variant", ctypes.c_int), ("kernel", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("variant", ctypes.c_int), ("kernel", ctypes.c_int), ("strassen", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 def load():
@@ -54,6 +55,7 @@ def load():
             "fq_matmul": (i32, [i32, i64, i64, i64, vp, vp, vp, vp]),
             "fq_matmul_ex": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, ctypes.POINTER(Options)]),
             "fq_status": (i32, [vp]),
+            "fq_release_scratch": (i32, []),
             "fq_kernel_count": (i32, [i32]),
             "fq_kernel_info": (i32, [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(i32)]),
@@ -67,6 +69,7 @@ def load():
             "fq_autotune_lookup": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "fq_autotune_clear": (i32, []),
             "fq_auto_choice": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "fq_strassen_levels": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
             "fq_error_string": (ctypes.c_char_p, [i32]),
             "fq_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -154,13 +157,13 @@ def add(x: Packed, y: Packed, sub: bool = False, out: Packed | None = None, stre
 
 
 def matmul(a: Packed, b: Packed, out: Packed | None = None, path: int = PATH_AUTO, k: int = 0,
-           chunk: int = 0, variant: int = 0, kernel: int = 0, stream=None) -> Packed:
+           chunk: int = 0, variant: int = 0, kernel: int = 0, strassen: int = 0, stream=None) -> Packed:
     """fq_matmul_ex: C = A B over F_q."""
     if a.q != b.q or a.cols != b.rows:
         raise ValueError("shape mismatch")
     m, l, n = a.rows, a.cols, b.cols
     out = empty(a.q, m, n, a.data.device) if out is None else out
-    opt = Options(path=path, k=k, chunk=chunk, variant=variant, kernel=kernel)
+    opt = Options(path=path, k=k, chunk=chunk, variant=variant, kernel=kernel, strassen=strassen)
     _check(load().fq_matmul_ex(a.q, m, l, n, ctypes.c_void_p(a.data.data_ptr()),
                                ctypes.c_void_p(b.data.data_ptr()), ctypes.c_void_p(out.data.data_ptr()),
                                _stream(stream), ctypes.byref(opt)), "fq_matmul")
@@ -193,6 +196,15 @@ def autotune(a: Packed, b: Packed, out: Packed | None = None, stream=None) -> di
     _check(load().fq_autotune(a.q, m, l, n, ctypes.c_void_p(a.data.data_ptr()), ctypes.c_void_p(b.data.data_ptr()),
                               ctypes.c_void_p(out.data.data_ptr()), _stream(stream), ctypes.byref(r)), "fq_autotune")
     return {"path": r.path, "kernel": r.kernel, "ms": r.ms, "ms_planner": r.ms_planner, "ms_mma": r.ms_mma}
+
+
+def strassen_levels(q: int, m: int, l: int, n: int, path: int = PATH_AUTO, k: int = 0, strassen: int = 0) -> int:
+    """fq_strassen_levels: Strassen-Winograd levels a product of this shape takes."""
+    opt = Options(path=path, k=k, strassen=strassen)
+    r = load().fq_strassen_levels(q, m, l, n, ctypes.byref(opt))
+    if r < 0:
+        raise FqError(-r, "fq_strassen_levels")
+    return r
 
 
 def auto_choice(q: int, m: int, l: int, n: int) -> tuple[int, int]:

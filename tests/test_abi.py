@@ -125,6 +125,12 @@ def test_autotune_cache_host_side(lib):
     # an empty product needs no device and takes the M4RM planner
     assert lib.fq_auto_choice(3, 0, 10, 10, ctypes.byref(p), ctypes.byref(k)) == fq.OK
     assert (p.value, k.value) == (fq.PATH_M4RM, 0)
+    # Strassen level query: argument errors and device-free answers
+    opt = fq.Options(strassen=-2)
+    assert lib.fq_strassen_levels(3, 4096, 4096, 4096, ctypes.byref(opt)) == -fq.EINVAL
+    assert lib.fq_strassen_levels(6, 4096, 4096, 4096, None) == -fq.EINVAL
+    assert lib.fq_strassen_levels(3, 0, 4096, 4096, None) == 0
+    assert lib.fq_strassen_levels(9, 4096, 4096, 4096, None) == 0
     # extension fields always take the matrix-level products
     for q in (8, 9, 25, 27, 49, 125):
         assert lib.fq_auto_choice(q, 100, 100, 100, ctypes.byref(p), ctypes.byref(k)) == fq.OK
