@@ -68,9 +68,9 @@ def algorithmic_lop3(m, l, n, k=K_BLOCK):
 
 def our_launches(levels):
     """Kernels of this library one F_3 product launches: the M4RM kernel, or per
-    Strassen level fifteen bitsliced additions and seven sub-products (the
-    quadrant copies are copy-engine transfers, not kernels)."""
-    return 1 if levels == 0 else 15 + 7 * our_launches(levels - 1)
+    Strassen level twelve quadrant copies, fifteen bitsliced additions and
+    seven sub-products."""
+    return 1 if levels == 0 else 27 + 7 * our_launches(levels - 1)
 
 
 def parse():

@@ -11,8 +11,7 @@
 //   C11 = P1 + P2,  U2 = P1 + P6,  U3 = U2 + P7,  C22 = U3 + P5,
 //   C12 = U2 + P5 + P3,  C21 = U3 - P4.
 // Additions are the bitsliced elementwise formulas (fq_add); quadrants are
-// copied out of and back into the packed matrices with 2-D copies, one per
-// plane.  A level is taken where the time model says seven half-size products
+// copied out of and back into the packed matrices by a 16-byte copy kernel.  A level is taken where the time model says seven half-size products
 // plus the additions and copies beat the direct product, and only for shapes
 // whose halves are whole 1024-column pitches (m, l, n multiples of 2048).
 #include "../../include/fq.h"
@@ -71,19 +70,31 @@ double best_cycles(int q, int64_t m, int64_t l, int64_t n, const ProdOptions &o,
 
 // Quadrant (qi, qj) of a packed rows x cols matrix <-> a packed (rows/2) x
 // (cols/2) matrix; cols/2 is a multiple of 1024, so neither side has padding.
+// One thread per 16-byte piece, grid-stride over planes x rows x pieces.
+__global__ void quadrant_kernel(int P, int64_t rows, int64_t pf, int64_t pq, const uint64_t *src, uint64_t *dst,
+                                int64_t src_off, int64_t dst_off, bool out_of_full) {
+  const int64_t hr = rows / 2, pieces = pq / 2, total = int64_t(P) * hr * pieces;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t w = (i % pieces) * 2, r = (i / pieces) % hr, p = i / pieces / hr;
+    const int64_t f = (p * rows + r) * pf + w, h = (p * hr + r) * pq + w;
+    const int64_t si = out_of_full ? src_off + f : h, di = out_of_full ? h : dst_off + f;
+    *reinterpret_cast<uint4 *>(dst + di) = *reinterpret_cast<const uint4 *>(src + si);
+  }
+}
+
 int copy_quadrant(int P, int64_t rows, int64_t cols, const uint64_t *full, uint64_t *quad, int qi, int qj,
                   bool out_of_full, cudaStream_t s) {
   const int64_t pf = fq_pitch_words(cols), hr = rows / 2, pq = fq_pitch_words(cols / 2);
-  for (int p = 0; p < P; ++p) {
-    const uint64_t *f = full + (p * rows + qi * hr) * pf + qj * pq;
-    uint64_t *h = quad + p * hr * pq;
-    const cudaError_t e =
-        out_of_full ? cudaMemcpy2DAsync(h, size_t(pq) * 8, f, size_t(pf) * 8, size_t(pq) * 8, size_t(hr),
-                                        cudaMemcpyDeviceToDevice, s)
-                    : cudaMemcpy2DAsync(const_cast<uint64_t *>(f), size_t(pf) * 8, h, size_t(pq) * 8,
-                                        size_t(pq) * 8, size_t(hr), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return record_cuda_error(e);
-  }
+  const int64_t off = qi * hr * pf + qj * pq;  // the quadrant's first word within each plane
+  const int64_t total = int64_t(P) * hr * (pq / 2);
+  const int64_t want = cdiv(total, 256), cap = 152 * 16;
+  const unsigned grid = unsigned(want < cap ? want : cap);
+  if (out_of_full)
+    quadrant_kernel<<<grid, 256, 0, s>>>(P, rows, pf, pq, full, quad, off, 0, true);
+  else
+    quadrant_kernel<<<grid, 256, 0, s>>>(P, rows, pf, pq, quad, const_cast<uint64_t *>(full), 0, off, false);
+  FQ_LAUNCH_CHECK();
   return FQ_OK;
 }
 
