@@ -93,15 +93,39 @@ def one_case(spec, reps):
     print("| q=%d %dx%dx%d | %s | %.3f | %.3e |" % (q, m, l, n, path, t, 2.0 * m * l * n / t * 1e3))
 
 
+def strassen_table():
+    """Direct product against one and two Strassen-Winograd levels, and the
+    levels the time model takes (M4RM base products)."""
+    print("| field | n | model levels | direct ms | 1 level ms | 2 levels ms |")
+    print("|---|---:|---:|---:|---:|---:|")
+    for q, n in ((3, 8192), (3, 16384), (3, 32768), (2, 8192), (2, 16384), (2, 32768), (4, 8192), (4, 16384),
+                 (5, 8192), (5, 16384), (7, 8192), (7, 16384)):
+        a, b, c = _operands(q, n, n, n)
+        t = {}
+        for lv in (-1, 1, 2):
+            if lv == 2 and n < 16384:
+                continue
+            t[lv] = _time(lambda: fq.matmul(a, b, out=c, path=fq.PATH_M4RM, strassen=lv), 3)
+        model = fq.strassen_levels(q, n, n, n, path=fq.PATH_M4RM)
+        two = "%.3f" % t[2] if 2 in t else "-"
+        print("| %d | %d | %d | %.3f | %.3f | %s |" % (q, n, model, t[-1], t[1], two), flush=True)
+        del a, b, c
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="skip the n = 32768 product")
     ap.add_argument("--case", help="time one product only: q,m,l,n[,path[,kernel]]")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--strassen", action="store_true", help="direct vs Strassen-Winograd levels only")
     args = ap.parse_args()
     fq.load()
     if args.case:
         one_case(args.case, args.reps)
+        return
+    if args.strassen:
+        strassen_table()
         return
     print("| configuration | path | ms | field-ops/s |")
     print("|---|---|---:|---:|")
