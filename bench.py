@@ -39,7 +39,6 @@ sys.path.insert(0, ROOT)
 METRIC = "F_q matmul 2mln/s: bitsliced M4RM vs INT8-TC path; batched products/s"
 UNIT = "field-ops/s (2mln/t)"
 Q = 3
-K_BLOCK = 8
 # (m, l, n, A law)
 PRODUCTS = [(4096, 4096, 4096, "uniform"), (8192, 8192, 8192, "uniform"),
             (16384, 16384, 16384, "uniform"), (8192, 8192, 8192, "sparse90")]
@@ -57,7 +56,7 @@ def cdiv(a, b):
     return -(-a // b)
 
 
-def algorithmic_lop3(m, l, n, k=K_BLOCK):
+def algorithmic_lop3(m, l, n, k):
     """LOP3 lane-ops of one F_3 product by M4RM: every (row, block, basis element)
     lookup adds one table row (ceil(n/32) word pairs), and every block's table of
     2^k - 1 nonzero combinations is built once."""
@@ -278,14 +277,29 @@ def main():
 
     # ---- inputs, packed and resident -------------------------------------
     res = make_inputs(torch, inputs, prods)
-    # Strassen-Winograd levels the library takes for each product (time model)
-    levels = [fq.strassen_levels(Q, m, l, n, k=K_BLOCK) for (m, l, n, _) in prods]
     packed = []
     for (A, B), (m, l, n, _) in zip(res, prods):
         a, b = fq.pack(Q, A), fq.pack(Q, B)
         packed.append((a, b, fq.empty(Q, m, n)))
     if fq.status() != fq.OK:
         raise SystemExit("device error while packing")
+    # Untimed set-up: Strassen-Winograd levels the library takes for each
+    # product (time model), and fq_autotune on every direct product's shape
+    # (k in 6..10 over the compiled kernels, and the tensor-core path); a
+    # Strassen product's half-size leaves share a tuned shape of the workload.
+    levels = [fq.strassen_levels(Q, m, l, n) for (m, l, n, _) in prods]
+    tuned = {}
+    for lv, (a, b, c), (m, l, n, _) in zip(levels, packed, prods):
+        if lv == 0 and (m, l, n) not in tuned:
+            tuned[(m, l, n)] = fq.autotune(a, b, out=c)
+    leaves = [(m >> lv, l >> lv, n >> lv) for lv, (m, l, n, _) in zip(levels, prods)]
+    for (A, B), leaf in zip(res, leaves):
+        if leaf not in tuned:   # tune the leaf shape on the product's leading blocks
+            lm, ll, ln = leaf
+            tuned[leaf] = fq.autotune(fq.pack(Q, A[:lm, :ll]), fq.pack(Q, B[:ll, :ln]))
+        if tuned[leaf]["path"] != fq.PATH_M4RM:
+            raise SystemExit("leaf %s tuned to the tensor-core path" % (leaf,))
+    leaf_k = [fq.planned_kernel(Q, *leaf)["k"] for leaf in leaves]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -293,7 +307,7 @@ def main():
         for j, (a, b, c) in enumerate(packed):
             if evs is not None:
                 evs[j][0].record(stream)
-            fq.matmul(a, b, out=c, k=K_BLOCK)
+            fq.matmul(a, b, out=c)
             if evs is not None:
                 evs[j][1].record(stream)
 
@@ -329,8 +343,8 @@ def main():
     value = ops_step * dist.world / (mean_ms * 1e-3)
 
     kernel_ms = sum(sum(r) for r in per_launch) / args.steps
-    lop3_step = sum(7 ** lv * algorithmic_lop3(m >> lv, l >> lv, n >> lv)
-                    for lv, (m, l, n, _) in zip(levels, prods))
+    lop3_step = sum(7 ** lv * algorithmic_lop3(m >> lv, l >> lv, n >> lv, k)
+                    for lv, k, (m, l, n, _) in zip(levels, leaf_k, prods))
     achieved = lop3_step / (kernel_ms * 1e-3) / 1e12
     traffic_rec = measured_traffic()
     traffic = None
@@ -355,7 +369,7 @@ def main():
                 dB.copy_(hB, non_blocking=True)
                 fq.pack(Q, dA, out=a)
                 fq.pack(Q, dB, out=b)
-                fq.matmul(a, b, out=c, k=K_BLOCK)
+                fq.matmul(a, b, out=c)
                 fq.unpack(c, out=dC)
                 hC.copy_(dC, non_blocking=True)
 
@@ -393,7 +407,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.sizes else "F_3 square n=" + args.sizes,
-                       "q": Q, "k": K_BLOCK, "products": [list(p) for p in prods],
+                       "q": Q, "k": leaf_k, "k_choice": "fq_autotune per shape over k in 6..10",
+                       "products": [list(p) for p in prods],
                        "path": "m4rm", "strassen_levels": levels,
                        "l2": "flushed (256 MiB write) before every step",
                        "parallelism": "replicas" if dist.world > 1 else "single GPU"},

@@ -242,6 +242,14 @@ int fq_auto_choice(int q, int64_t m, int64_t l, int64_t n, int *path, int *kerne
  * block size k, the most rows one CTA holds, columns per CTA and warps per CTA.
  * Host-only; returns FQ_EINVAL for a bad q or idx. */
 int fq_kernel_count(int q);
+
+/* The compiled M4RM kernel (1-based, as fq_options.kernel) that a direct
+ * Four-Russians product of this shape runs with these options (opt may be
+ * NULL): opt->kernel when set, else the fq_autotune choice when one is
+ * remembered (AUTO path, k = 0), else the planner's.  Negative status on
+ * error (-FQ_EINVAL for a bad q or shape, -FQ_ENOTSUP if no kernel has the
+ * requested k).  Host-only apart from the device attribute query. */
+int fq_planned_kernel(int q, int64_t m, int64_t l, int64_t n, const fq_options *opt);
 int fq_kernel_info(int q, int idx, int *k, int *max_rows, int *cols, int *warps);
 
 /* The library's scratch pool (one per device, created on first use) keeps the

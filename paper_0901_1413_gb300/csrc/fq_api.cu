@@ -209,6 +209,25 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, cons
   return fqk::product(q, m, l, n, A, B, C, prod_options(o), static_cast<cudaStream_t>(stream));
 }
 
+int fq_planned_kernel(int q, int64_t m, int64_t l, int64_t n, const fq_options *opt) {
+  if (!base_q(q) || m <= 0 || l <= 0 || n <= 0) return -FQ_EINVAL;
+  fq_options o;
+  memset(&o, 0, sizeof(o));
+  if (opt) o = *opt;
+  if (o.k != 0 && (o.k < 6 || o.k > 10)) return -FQ_EINVAL;
+  if (o.kernel > 0) return o.kernel <= fq_kernel_count(q) ? o.kernel : -FQ_EINVAL;
+  if (o.path == FQ_PATH_AUTO && o.k == 0 && o.variant == 0) {
+    int path = 0, kernel = 0;
+    if (fqk::tuned_choice(q, m, l, n, &path, &kernel) && path == FQ_PATH_M4RM && kernel > 0) return kernel;
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -fqk::record_cuda_error(cudaGetLastError());
+  const int i = fqk::m4rm_planned(q, m, l, n, o.k, o.variant, sms);
+  return i < 0 ? -FQ_ENOTSUP : i + 1;
+}
+
 int fq_strassen_levels(int q, int64_t m, int64_t l, int64_t n, const fq_options *opt) {
   if (!valid_q(q) || m < 0 || l < 0 || n < 0) return -FQ_EINVAL;
   fq_options o;

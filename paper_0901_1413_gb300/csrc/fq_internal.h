@@ -29,6 +29,8 @@ struct Variant {
 };
 // The variant table of field q (nullptr and 0 for a bad q).
 const Variant *m4rm_variants(int q, int *count);
+// The variant index the M4RM planner picks for a product (-1 if none).
+int m4rm_planned(int q, int64_t m, int64_t l, int64_t n, int k, int mt, int sms);
 
 // Modelled times (SM cycles) of the two paths for a product, for the
 // FQ_PATH_AUTO choice when no measured choice exists.

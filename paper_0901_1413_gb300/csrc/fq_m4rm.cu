@@ -2,6 +2,7 @@
 // compiled kernel variants.
 #include "../../include/fq.h"
 #include "fq_internal.h"
+#include "fq_m4rm.cuh"
 
 namespace fqk {
 
@@ -39,6 +40,14 @@ const Variant *m4rm_variants(int q, int *count) {
     case 7: return m4rm_variants_f7(count);
     default: return nullptr;
   }
+}
+
+int m4rm_planned(int q, int64_t m, int64_t l, int64_t n, int k, int mt, int sms) {
+  int nv = 0;
+  const Variant *vs = m4rm_variants(q, &nv);
+  if (!vs) return -1;
+  const int d = q == 2 ? 1 : ((q == 5 || q == 7) ? 3 : 2);
+  return plan_pick(vs, nv, d, m, l, n, k, mt, sms);
 }
 
 }  // namespace fqk

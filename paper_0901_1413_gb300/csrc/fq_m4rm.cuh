@@ -473,11 +473,34 @@ int launch_cfg(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_
   return FQ_OK;
 }
 
-// Picks (k, rows per CTA) for a product.  Without a request, every compiled
-// variant is costed: one CTA per SM, waves of CTAs, and per CTA ceil(l/k)
-// blocks of (about 1.2 * 2^k table adds + D adds per row).  A requested k
-// narrows the choice; a requested height (tests) takes the tallest variant of
-// that k and runs it with `mt` rows per CTA.
+// Picks (k, rows per CTA) for a product: the index of the variant, or -1.
+// Without a request, every compiled variant is costed: one CTA per SM, waves
+// of CTAs, and per CTA ceil(l/k) blocks of (about 1.2 * 2^k table adds + D adds
+// per row).  A requested k narrows the choice; a requested height (tests) takes
+// the tallest variant of that k, to run with `mt` rows per CTA.
+inline int plan_pick(const Variant *vs, int nv, int d, int64_t m, int64_t l, int64_t n, int k, int mt, int sms) {
+  int pick = -1;
+  if (mt > 0) {
+    for (int i = 0; i < nv; ++i)
+      if ((k == 0 ? vs[i].k == 8 : vs[i].k == k) && (pick < 0 || vs[i].rs > vs[pick].rs)) pick = i;
+    return pick;
+  }
+  double best = 1e300;
+  for (int i = 0; i < nv; ++i) {
+    if (k != 0 && vs[i].k != k) continue;
+    const int64_t rows = int64_t(vs[i].rs) * vs[i].rows_per_slot;
+    const int64_t ctas = cdiv(m, rows) * (fq_pitch_words(n) / (vs[i].cols / 64));
+    const int64_t waves = cdiv(ctas, sms);
+    const double cost =
+        double(waves) * double(cdiv(l, vs[i].k)) * (1.2 * double(1 << vs[i].k) + double(rows) * d);
+    if (cost < best * 0.999) {
+      best = cost;
+      pick = i;
+    }
+  }
+  return pick;
+}
+
 inline int plan_and_launch(const Variant *vs, int nv, int d, int64_t m, int64_t l, int64_t n,
                            const uint64_t *A, const uint64_t *B, uint64_t *C, int k, int mt, int kernel,
                            cudaStream_t s) {
@@ -490,28 +513,9 @@ inline int plan_and_launch(const Variant *vs, int nv, int d, int64_t m, int64_t 
   int dev = 0, sms = 152;
   FQ_CUDA_TRY(cudaGetDevice(&dev));
   FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const Variant *pick = nullptr;
-  if (mt > 0) {
-    for (int i = 0; i < nv; ++i)
-      if ((k == 0 ? vs[i].k == 8 : vs[i].k == k) && (!pick || vs[i].rs > pick->rs)) pick = &vs[i];
-    if (!pick) return FQ_ENOTSUP;
-    return pick->launch(m, l, n, A, B, C, mt, s);
-  }
-  double best = 1e300;
-  for (int i = 0; i < nv; ++i) {
-    if (k != 0 && vs[i].k != k) continue;
-    const int64_t rows = int64_t(vs[i].rs) * vs[i].rows_per_slot;
-    const int64_t ctas = cdiv(m, rows) * (fq_pitch_words(n) / (vs[i].cols / 64));
-    const int64_t waves = cdiv(ctas, sms);
-    const double cost =
-        double(waves) * double(cdiv(l, vs[i].k)) * (1.2 * double(1 << vs[i].k) + double(rows) * d);
-    if (cost < best * 0.999) {
-      best = cost;
-      pick = &vs[i];
-    }
-  }
-  if (!pick) return FQ_ENOTSUP;
-  return pick->launch(m, l, n, A, B, C, pick->rs * pick->rows_per_slot, s);
+  const int i = plan_pick(vs, nv, d, m, l, n, k, mt, sms);
+  if (i < 0) return FQ_ENOTSUP;
+  return vs[i].launch(m, l, n, A, B, C, mt > 0 ? mt : vs[i].rs * vs[i].rows_per_slot, s);
 }
 
 }  // namespace fqk

@@ -70,6 +70,7 @@ def load():
             "fq_autotune_clear": (i32, []),
             "fq_auto_choice": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "fq_strassen_levels": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
+            "fq_planned_kernel": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
             "fq_error_string": (ctypes.c_char_p, [i32]),
             "fq_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -205,6 +206,16 @@ def strassen_levels(q: int, m: int, l: int, n: int, path: int = PATH_AUTO, k: in
     if r < 0:
         raise FqError(-r, "fq_strassen_levels")
     return r
+
+
+def planned_kernel(q: int, m: int, l: int, n: int, path: int = PATH_AUTO, k: int = 0, kernel: int = 0) -> dict:
+    """fq_planned_kernel: the compiled M4RM kernel a direct product runs (its
+    kernels() entry)."""
+    opt = Options(path=path, k=k, kernel=kernel)
+    r = load().fq_planned_kernel(q, m, l, n, ctypes.byref(opt))
+    if r <= 0:
+        raise FqError(-r, "fq_planned_kernel")
+    return kernels(q)[r - 1]
 
 
 def auto_choice(q: int, m: int, l: int, n: int) -> tuple[int, int]:

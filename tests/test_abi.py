@@ -125,6 +125,13 @@ def test_autotune_cache_host_side(lib):
     # an empty product needs no device and takes the M4RM planner
     assert lib.fq_auto_choice(3, 0, 10, 10, ctypes.byref(p), ctypes.byref(k)) == fq.OK
     assert (p.value, k.value) == (fq.PATH_M4RM, 0)
+    # planned kernel query: argument errors and device-free answers
+    assert lib.fq_planned_kernel(6, 10, 10, 10, None) == -fq.EINVAL
+    assert lib.fq_planned_kernel(9, 10, 10, 10, None) == -fq.EINVAL      # extension fields: none
+    opt = fq.Options(kernel=2)
+    assert lib.fq_planned_kernel(3, 10, 10, 10, ctypes.byref(opt)) == 2
+    opt = fq.Options(kernel=10_000)
+    assert lib.fq_planned_kernel(3, 10, 10, 10, ctypes.byref(opt)) == -fq.EINVAL
     # Strassen level query: argument errors and device-free answers
     opt = fq.Options(strassen=-2)
     assert lib.fq_strassen_levels(3, 4096, 4096, 4096, ctypes.byref(opt)) == -fq.EINVAL

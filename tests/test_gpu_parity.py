@@ -346,6 +346,8 @@ def test_autotune_picks_a_candidate_and_auto_uses_it(fq, q):
     assert (path.value, kernel.value) == (res["path"], res["kernel"])
     got = fq.unpack(fq.matmul(a, b)).cpu().numpy()                       # AUTO: the tuned choice
     assert np.array_equal(got, want)
+    if res["path"] == fq.PATH_M4RM and res["kernel"] > 0:
+        assert fq.planned_kernel(q, m, l, n)["index"] == res["kernel"] - 1
     lib.fq_autotune_clear()
     assert lib.fq_autotune_lookup(q, m, l, n, None, None) == fq.ENOTSUP
 
@@ -360,6 +362,12 @@ def test_auto_choice_by_time_model(fq):
     assert fq.auto_choice(3, 0, 512, 512) == (fq.PATH_M4RM, 0)
     for q in FIELDS:
         _check_product(fq, q, 512, 512, 512, seed=q + 40)       # AUTO, whichever path
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_planned_kernel_honours_k(fq, q):
+    for k in (6, 7, 8):
+        assert fq.planned_kernel(q, 3000, 2000, 4000, k=k)["k"] == k
 
 
 @pytest.mark.parametrize("q", FIELDS)
