@@ -363,18 +363,44 @@ def main():
                                                                                    device=dev))
               for (m, l, n, _) in prods]
 
+        # Copies in and out run on their own streams so that they overlap the
+        # products: product j's inputs go up while product j - 1 computes, its
+        # result comes down while product j + 1 computes.  Events keep each
+        # product's device buffers from being overwritten before they are read.
+        h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
+        ev = {name: [torch.cuda.Event() for _ in prods] for name in ("in", "packed", "out", "read")}
+        started = [False]
+
         def e2e_step():
-            for (hA, hB, hC), (dA, dB), (a, b, c, dC) in zip(host, dbuf, pk):
-                dA.copy_(hA, non_blocking=True)
-                dB.copy_(hB, non_blocking=True)
+            for j, ((hA, hB, hC), (dA, dB), (a, b, c, dC)) in enumerate(zip(host, dbuf, pk)):
+                with torch.cuda.stream(h2d_s):
+                    if started[0]:
+                        h2d_s.wait_event(ev["packed"][j])      # last step's pack has read dA, dB
+                    dA.copy_(hA, non_blocking=True)
+                    dB.copy_(hB, non_blocking=True)
+                    ev["in"][j].record(h2d_s)
+                stream.wait_event(ev["in"][j])
                 fq.pack(Q, dA, out=a)
                 fq.pack(Q, dB, out=b)
+                ev["packed"][j].record(stream)
                 fq.matmul(a, b, out=c)
+                if started[0]:
+                    stream.wait_event(ev["read"][j])           # last step's result has left dC
                 fq.unpack(c, out=dC)
-                hC.copy_(dC, non_blocking=True)
+                ev["out"][j].record(stream)
+                with torch.cuda.stream(d2h_s):
+                    d2h_s.wait_event(ev["out"][j])
+                    hC.copy_(dC, non_blocking=True)
+                    ev["read"][j].record(d2h_s)
+            started[0] = True
+
+        def join():
+            stream.wait_stream(h2d_s)
+            stream.wait_stream(d2h_s)
 
         for _ in range(args.warmup):
             e2e_step()
+        join()
         torch.cuda.synchronize()
         e_steps = max(3, min(args.steps, 10))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -383,8 +409,13 @@ def main():
         e0.record(stream)
         for _ in range(e_steps):
             e2e_step()
+        join()
         e1.record(stream)
         torch.cuda.synchronize()
+        # the results that reached the host equal the device-resident products
+        for (hA, hB, hC), (a, b, c) in zip(host, packed):
+            if not torch.equal(hC, fq.unpack(c).cpu()):
+                raise SystemExit("end-to-end result differs from the device-resident product")
         dist.barrier()
         if fq.status() != fq.OK:
             raise SystemExit("device error in the end-to-end region")
