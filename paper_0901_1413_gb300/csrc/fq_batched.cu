@@ -79,6 +79,7 @@ __device__ __noinline__ void run_item(const M4rmParams &prm, const uint64_t *B, 
   const uint32_t astage_s = smem_u32(smem + Cfg::ASTAGE_OFF);
   typename Cfg::Off *offs = reinterpret_cast<typename Cfg::Off *>(smem + Cfg::OFFS_OFF);
   const bool builder = warp < Cfg::NBW;
+  const int slots = (rows_here + Cfg::ROWS_PER_SLOT - 1) / Cfg::ROWS_PER_SLOT;  // slots holding rows
 
   uint32_t acc[Cfg::RS][Cfg::PW];
 #pragma unroll
@@ -107,7 +108,7 @@ __device__ __noinline__ void run_item(const M4rmParams &prm, const uint64_t *B, 
         stage_b<Cfg>(B, prm.l, prm.pc, bstage_s + (buf ^ 1) * Cfg::STAGE_STRIDE, w0, s + 1, tid);
       if (builder) build_table<Cfg>(tbl_lane, bstage_s + buf * Cfg::STAGE_STRIDE, warp * Cfg::GPW + grp, gl);
       __syncthreads();  // table complete
-      lookup_block<Cfg>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one);
+      lookup_block<Cfg, true>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one, slots);
     }
   }
   cp_async_wait_all();

@@ -279,16 +279,19 @@ __device__ __forceinline__ void build_table(uint32_t tbl_lane, uint32_t stage, i
   build_walk<Cfg, 1>(S, rows, tbl_lane, e0);
 }
 
-template <class Cfg>
+// PARTIAL = false: every slot is processed (rows past the tile have offset 0,
+// the zero entry), so the unrolled loop is one basic block the scheduler can
+// pipeline.  PARTIAL = true: slots from `slots` on hold no row of the tile and
+// are skipped (tiles much shorter than the kernel's height).
+template <class Cfg, bool PARTIAL = false>
 __device__ __forceinline__ void lookup_block(uint32_t (&acc)[Cfg::RS][Cfg::PW], uint32_t tbl_lane,
-                                             const typename Cfg::Off *offs_b, int warp, int grp, uint32_t one) {
+                                             const typename Cfg::Off *offs_b, int warp, int grp, uint32_t one,
+                                             int slots = Cfg::RS) {
   using F = typename Cfg::Field;
   constexpr int P = Cfg::P, D = Cfg::D, WPL = Cfg::WPL, PW = Cfg::PW, CH = Cfg::CH, VW = Cfg::VW;
-  // Every slot is processed: rows past the tile have offset 0 (the zero entry),
-  // so the unrolled loop is one basic block the scheduler can pipeline.
 #pragma unroll
   for (int i = 0; i < Cfg::RS; ++i) {
-    {
+    if (!PARTIAL || i < slots) {
       const int r = i * Cfg::ROWS_PER_SLOT + warp * Cfg::GPW + grp;
       const typename Cfg::Off o = offs_b[r];
       uint32_t od[D];
@@ -425,7 +428,11 @@ __global__ void __launch_bounds__(Cfg::NT, 1)
       }
       if (builder) build_table<Cfg>(tbl_lane, bstage_s + buf * Cfg::STAGE_STRIDE, warp * Cfg::GPW + grp, gl);
       __syncthreads();  // table complete
-      lookup_block<Cfg>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one);
+      if (rows_here == Cfg::MT)
+        lookup_block<Cfg>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one);
+      else
+        lookup_block<Cfg, true>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one,
+                                (rows_here + Cfg::ROWS_PER_SLOT - 1) / Cfg::ROWS_PER_SLOT);
     }
   }
   store_tile<Cfg>(acc, prm, row0, rows_here, w0, warp, grp, gl);
