@@ -3,8 +3,9 @@
 // The host plan splits every product into items (a run of rows x one column
 // tile of C) with a block size k chosen per item by the planner's cost model,
 // and orders items longest first.  The work list lives in a device workspace
-// the caller owns; each launch resets one queue counter and starts one CTA per
-// SM, and every CTA pops items with an atomic until the list is exhausted,
+// the caller owns; each launch resets one queue counter and starts as many
+// CTAs as fit on the SMs (two per SM for F_3 and GF(4)), and every CTA pops
+// items with an atomic until the list is exhausted,
 // running the Four-Russians item body of fq_m4rm.cuh on each (B blocks staged
 // with cp.async, since the operands' addresses are only known at launch).  A
 // launch allocates nothing and never waits on the host, so it can be captured
@@ -116,7 +117,7 @@ __device__ __noinline__ void run_item(const M4rmParams &prm, const uint64_t *B, 
 }
 
 template <class C6, class C7, class C8>
-__global__ void __launch_bounds__(C8::NT, 1)
+__global__ void __launch_bounds__(C8::NT, C8::P == 2 ? 2 : 1)
     batched_kernel(unsigned char *ws, const uint64_t *const *Aptr, const uint64_t *const *Bptr, uint64_t *const *Cptr,
                    unsigned *err) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -178,17 +179,19 @@ __global__ void __launch_bounds__(C8::NT, 1)
 
 template <class F>
 struct Kernels;
+// Two-plane fields: 8 warps and 512 rows per CTA, two CTAs per SM, so that one
+// CTA's table build overlaps the other's lookups.
 template <>
 struct Kernels<F3> {
-  using C6 = M4rmCfg<F3, 6, 8, 2, 16, 16>;
-  using C7 = M4rmCfg<F3, 7, 8, 2, 16, 16>;
-  using C8 = M4rmCfg<F3, 8, 8, 2, 16, 16>;
+  using C6 = M4rmCfg<F3, 6, 8, 2, 16, 8>;
+  using C7 = M4rmCfg<F3, 7, 8, 2, 16, 8>;
+  using C8 = M4rmCfg<F3, 8, 8, 2, 16, 8>;
 };
 template <>
 struct Kernels<GF4> {
-  using C6 = M4rmCfg<GF4, 6, 8, 2, 16, 16>;
-  using C7 = M4rmCfg<GF4, 7, 8, 2, 16, 16>;
-  using C8 = M4rmCfg<GF4, 8, 8, 2, 16, 16>;
+  using C6 = M4rmCfg<GF4, 6, 8, 2, 16, 8>;
+  using C7 = M4rmCfg<GF4, 7, 8, 2, 16, 8>;
+  using C8 = M4rmCfg<GF4, 8, 8, 2, 16, 8>;
 };
 template <>
 struct Kernels<F5> {
@@ -224,8 +227,11 @@ int launch_field(unsigned char *ws, const uint64_t *const *A, const uint64_t *co
   int dev = 0, sms = 152;
   FQ_CUDA_TRY(cudaGetDevice(&dev));
   FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int per_sm = 1;
+  FQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::C8::NT, smem));
+  if (per_sm < 1) per_sm = 1;
   FQ_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(uint32_t), s));
-  kern<<<sms, K::C8::NT, smem, s>>>(ws, A, B, C, err);
+  kern<<<sms * per_sm, K::C8::NT, smem, s>>>(ws, A, B, C, err);
   FQ_LAUNCH_CHECK();
   return FQ_OK;
 }
