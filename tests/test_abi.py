@@ -100,10 +100,10 @@ def test_batch_plan_host_side(lib):
     n = np.array([600, 64, 9, 1100], np.int64)
     h = ctypes.c_void_p()
     assert lib.fq_batched_plan_create(3, 4, i64p(m), i64p(l), i64p(n), ctypes.byref(h)) == fq.OK
-    # items: one per row tile x column tile of the pitch (512-column tiles;
-    # tiles of padding only are zero-fill items): 1 x 2, 2 x 2, 0, 1 x 4
-    assert lib.fq_batched_items(h) == 2 + 4 + 0 + 4
-    assert lib.fq_batched_workspace_bytes(h) == 64 + 128 + 10 * 32
+    # items: one per row tile x column tile of the pitch (512-row x 512-column
+    # tiles; tiles of padding only are zero-fill items): 1 x 2, 4 x 2, 0, 1 x 4
+    assert lib.fq_batched_items(h) == 2 + 8 + 0 + 4
+    assert lib.fq_batched_workspace_bytes(h) == 64 + 128 + 14 * 32
     assert lib.fq_batched_plan_upload(h, ctypes.c_void_p(8), None) == fq.EINVAL      # misaligned
     assert lib.fq_matmul_batched(h, None, None, None, ctypes.c_void_p(64), None) == fq.EINVAL
     assert lib.fq_batched_plan_destroy(h) == fq.OK
