@@ -34,10 +34,10 @@ def _rank_max(rank, world, port, out):
 
 
 def test_dist_max_over_two_gloo_ranks():
-    mgr = mp.Manager()
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
     out = mgr.dict()
     port = free_port()
-    ctx = mp.get_context("spawn")
     procs = [ctx.Process(target=_rank_max, args=(r, 2, port, out)) for r in range(2)]
     for p in procs:
         p.start()
