@@ -7,7 +7,9 @@ runs after one warm-up, inputs resident in device memory (seeded synthetic
 residues, uniform unless stated).  Throughput is 2 m l n / t in field
 operations per second; batched rows also give products per second.  Both
 product paths are timed where the configuration asks for them: the bitsliced
-Four-Russians path (M4RM) and the exact tensor-core path (MMA); for the
+Four-Russians path (M4RM) and the exact tensor-core path (MMA), each with its
+direct kernels and, where the time model takes them, with Strassen-Winograd
+levels ("+strassen"); for the
 extension fields these name the path of the base-field products inside
 Section 4.3's matrix-level product, and "karatsuba" is GF(4) by three F_2
 products.
@@ -43,13 +45,18 @@ def _operands(q, m, l, n, sparse=False):
 
 
 def product_rows(q, m, l, n, paths=("m4rm",), sparse=False, reps=3):
+    """Each path's direct kernels (no Strassen-Winograd level), then, where the
+    time model takes levels, the same path with them ("+strassen")."""
     a, b, c = _operands(q, m, l, n, sparse)
     ops = 2.0 * m * l * n
     out = []
     for p in paths:
         path = {"m4rm": fq.PATH_M4RM, "mma": fq.PATH_MMA, "karatsuba": fq.PATH_KARATSUBA}[p]
-        t = _time(lambda: fq.matmul(a, b, out=c, path=path), reps)
+        t = _time(lambda: fq.matmul(a, b, out=c, path=path, strassen=-1), reps)
         out.append((p, t, ops / t * 1e3))
+        if p != "karatsuba" and q in (2, 3, 4, 5, 7) and fq.strassen_levels(q, m, l, n, path=path) > 0:
+            t = _time(lambda: fq.matmul(a, b, out=c, path=path), reps)
+            out.append((p + "+strassen", t, ops / t * 1e3))
     if fq.status() != fq.OK:
         raise RuntimeError("device reported an error")
     return out
