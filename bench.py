@@ -2,19 +2,22 @@
 """Throughput of exact F_q matrix products on GB300: one JSON line on stdout.
 
 Workload (one step): the F_3 square products n = 4096, 8192 and 16384 with
-entries uniform on {0, 1, 2}, and n = 8192 with A 90% zeros (i.i.d.), by the
-bitsliced Method of Four Russians (with the Strassen-Winograd levels the
-library's time model takes: one for n = 16384).  Metric: field operations per
-second, 2 m l n / t (the paper's normalisation against the classical product's
-work, also where a faster algorithm runs on top).
+entries uniform on {0, 1, 2}, and n = 8192 with A 90% zeros (i.i.d.).
+Metric: field operations per second, 2 m l n / t (the paper's normalisation
+against the classical product's work).
 
-* ``value``: packed inputs resident in HBM, kernel time only (CUDA events on the
-  launching stream), L2 flushed before every step.
+* ``value``: packed inputs resident in HBM, device time (CUDA events on the
+  launching stream), L2 flushed before every step; each product runs in the
+  form fq_autotune picks for its shape (for these F_3 shapes the tcgen05
+  tensor-core form: operand conversion, then the product kernel).
+* ``m4rm``: the same products by the plain bitsliced Four-Russians path, with
+  ``speedup_vs_m4rm`` the factor between the two.
 * ``e2e``: the same products through the public API from pinned host residues:
   host->device copy, fq_pack, fq_matmul, fq_unpack, device->host copy.
-* ``roofline``: the M4RM kernel against the integer-logic (LOP3) issue rate:
-  the algorithmic LOP3 of every M4RM launch of a step (seven half-size
-  products where a Strassen level is taken) over the step's device time.
+* ``roofline``: the dominant kernel, the tcgen05 product, at 2 m l n flops
+  per launch over its own event time, against the measured dense bf16 peak;
+  ``m4rm.roofline``: the M4RM kernels against the integer-logic (LOP3) issue
+  rate (the algorithmic LOP3 of every M4RM launch over the products' time).
 * ``cpu_baseline``: the CPU oracle on a bounded sample of rows of the same
   products, all host cores.
 
@@ -170,31 +173,52 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_sources_digest():
-    """Digest of the sources the M4RM kernels are compiled from."""
-    import glob
+def sources_digest(names):
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_0901_1413_gb300", "csrc")
-    names = sorted(glob.glob(os.path.join(csrc, "fq_m4rm*")) +
-                   [os.path.join(csrc, n) for n in ("fq_fields.cuh", "fq_common.cuh")])
     for name in names:
         with open(name, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the M4RM kernel from the committed ncu summary,
-    if it was taken on the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "m4rm_f3_dram_traffic.json")
+def kernel_sources_digest():
+    """Digest of the sources the M4RM kernels are compiled from."""
+    import glob
+    csrc = os.path.join(ROOT, "paper_0901_1413_gb300", "csrc")
+    return sources_digest(sorted(glob.glob(os.path.join(csrc, "fq_m4rm*")) +
+                                 [os.path.join(csrc, n) for n in ("fq_fields.cuh", "fq_common.cuh")]))
+
+
+def tc_sources_digest():
+    """Digest of the sources the tcgen05 product kernel is compiled from."""
+    csrc = os.path.join(ROOT, "paper_0901_1413_gb300", "csrc")
+    return sources_digest([os.path.join(csrc, n) for n in ("fq_tc.cu", "fq_common.cuh")])
+
+
+def measured_traffic(name, digest):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_sources_sha256_16") != kernel_sources_digest():
+    if rec.get("kernel_sources_sha256_16") != digest:
         return None
     return rec
+
+
+def measured_peaks():
+    """Dense bf16 tensor peak for the roofline: the measured burst figure of
+    MEASURED_PEAKS.json when present, else 1900 TFLOP/s (an earlier GB300
+    measurement)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            rec = json.load(f)
+        return {"bf16": float(rec["bf16_tflops"]), "note": "of measured: cuBLAS bf16 burst (MEASURED_PEAKS.json)"}
+    except (OSError, ValueError, KeyError):
+        return {"bf16": 1900.0, "note": "of fallback: 1.9 PFLOP/s bf16"}
 
 
 def make_inputs(torch, inputs, prods, seed=0):
@@ -283,73 +307,107 @@ def main():
         packed.append((a, b, fq.empty(Q, m, n)))
     if fq.status() != fq.OK:
         raise SystemExit("device error while packing")
-    # Untimed set-up: Strassen-Winograd levels the library takes for each
-    # product (time model), and fq_autotune on every direct product's shape
-    # (k in 6..10 over the compiled kernels, and the tensor-core path); a
-    # Strassen product's half-size leaves share a tuned shape of the workload.
-    levels = [fq.strassen_levels(Q, m, l, n) for (m, l, n, _) in prods]
+    # Untimed set-up: fq_autotune on every shape (the compiled M4RM kernels,
+    # k in 6..10, and the tensor-core path) picks each product's form.  A
+    # tensor-core product runs as its two stages, operand conversion and the
+    # tcgen05 product, so that the product kernel can be timed on its own.
     tuned = {}
-    for lv, (a, b, c), (m, l, n, _) in zip(levels, packed, prods):
-        if lv == 0 and (m, l, n) not in tuned:
+    for (a, b, c), (m, l, n, _) in zip(packed, prods):
+        if (m, l, n) not in tuned:
             tuned[(m, l, n)] = fq.autotune(a, b, out=c)
-    leaves = [(m >> lv, l >> lv, n >> lv) for lv, (m, l, n, _) in zip(levels, prods)]
-    for (A, B), leaf in zip(res, leaves):
-        if leaf not in tuned:   # tune the leaf shape on the product's leading blocks
-            lm, ll, ln = leaf
-            tuned[leaf] = fq.autotune(fq.pack(Q, A[:lm, :ll]), fq.pack(Q, B[:ll, :ln]))
-        if tuned[leaf]["path"] != fq.PATH_M4RM:
-            raise SystemExit("leaf %s tuned to the tensor-core path" % (leaf,))
-    leaf_k = [fq.planned_kernel(Q, *leaf)["k"] for leaf in leaves]
+    forms = ["tensor" if tuned[(m, l, n)]["path"] == fq.PATH_MMA else "m4rm" for (m, l, n, _) in prods]
+    tops = [fq.TensorOperands(a, b) if f == "tensor" else None for f, (a, b, c) in zip(forms, packed)]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
     def step(evs=None):
-        for j, (a, b, c) in enumerate(packed):
+        # evs[j] = (start, operands ready, product done)
+        for j, ((a, b, c), t) in enumerate(zip(packed, tops)):
             if evs is not None:
                 evs[j][0].record(stream)
-            fq.matmul(a, b, out=c)
+            if t is not None:
+                t.prepare(a, b)
             if evs is not None:
                 evs[j][1].record(stream)
+            if t is not None:
+                t.multiply(out=c)
+            else:
+                fq.matmul(a, b, out=c)
+            if evs is not None:
+                evs[j][2].record(stream)
 
-    for w in range(args.warmup):
-        flush.fill_(w)
-        step()
-    torch.cuda.synchronize()
-    if fq.status() != fq.OK:
-        raise SystemExit("device error during warm-up")
+    def timed(step_fn, steps, warmup):
+        for w in range(warmup):
+            flush.fill_(w)
+            step_fn()
+        torch.cuda.synchronize()
+        if fq.status() != fq.OK:
+            raise SystemExit("device error during warm-up")
+        evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in packed] for _ in range(steps)]
+        dist.barrier()
+        torch.cuda.synchronize()
+        for s_ in range(steps):
+            flush.fill_(s_ + 1)
+            step_fn(evs[s_])
+        torch.cuda.synchronize()
+        dist.barrier()
+        if fq.status() != fq.OK:
+            raise SystemExit("device error in the timed region")
+        stage = [[[evs[s_][j][0].elapsed_time(evs[s_][j][1]), evs[s_][j][1].elapsed_time(evs[s_][j][2])]
+                  for j in range(len(packed))] for s_ in range(steps)]
+        step_ms = [evs[s_][0][0].elapsed_time(evs[s_][-1][2]) for s_ in range(steps)]
+        return stage, dist.max(sum(step_ms) / len(step_ms), dev)
 
     props = torch.cuda.get_device_properties(dev)
     uuid = str(getattr(props, "uuid", "")) or str(dist.local)
     clocks = ClockSampler(uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if len(uuid) > 30 else uuid))
-    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in packed]
-           for _ in range(args.steps)]
-    dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    for s in range(args.steps):
-        flush.fill_(s + 1)
-        step(evs[s])
-    torch.cuda.synchronize()
-    dist.barrier()
+    stage, mean_ms = timed(step, args.steps, args.warmup)
     clk = clocks.stop()
-    if fq.status() != fq.OK:
-        raise SystemExit("device error in the timed region")
-
-    per_launch = [[evs[s][j][0].elapsed_time(evs[s][j][1]) for j in range(len(packed))]
-                  for s in range(args.steps)]
-    step_ms = [evs[s][0][0].elapsed_time(evs[s][-1][1]) for s in range(args.steps)]
-    mean_ms = dist.max(sum(step_ms) / len(step_ms), dev)
     ops_step = sum(2.0 * m * l * n for (m, l, n, _) in prods)
     value = ops_step * dist.world / (mean_ms * 1e-3)
+    per_product = [sum(stage[s_][j][0] + stage[s_][j][1] for s_ in range(args.steps)) / args.steps
+                   for j in range(len(prods))]
+    product_ms = [sum(stage[s_][j][1] for s_ in range(args.steps)) / args.steps for j in range(len(prods))]
 
-    kernel_ms = sum(sum(r) for r in per_launch) / args.steps
+    # Roofline of the dominant kernel, the tcgen05 product: 2 m l n flops (bf16
+    # operands, fp32 sums) per launch over the product stage's event time.
+    peaks = measured_peaks()
+    t_flops = sum(2.0 * m * l * n for f, (m, l, n, _) in zip(forms, prods) if f == "tensor")
+    t_ms = sum(t for f, t in zip(forms, product_ms) if f == "tensor")
+    achieved = t_flops / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
+    traffic_rec = measured_traffic("tc_f3_dram_traffic.json", tc_sources_digest())
+    traffic = traffic_rec.get("bytes_per_launch") if traffic_rec else None
+
+    # ---- the plain bitsliced M4RM path on the same products, for the factor --
+    m_levels = [fq.strassen_levels(Q, m, l, n, path=fq.PATH_M4RM) for (m, l, n, _) in prods]
+    leaves = [(m >> lv, l >> lv, n >> lv) for lv, (m, l, n, _) in zip(m_levels, prods)]
+    leaf_k = [fq.planned_kernel(Q, *leaf, path=fq.PATH_M4RM)["k"] for leaf in leaves]
+
+    def m4rm_step(evs=None):
+        for j, (a, b, c) in enumerate(packed):
+            if evs is not None:
+                evs[j][0].record(stream)
+                evs[j][1].record(stream)
+            fq.matmul(a, b, out=c, path=fq.PATH_M4RM)
+            if evs is not None:
+                evs[j][2].record(stream)
+
+    m_steps = max(3, min(args.steps, 5))
+    m_stage, m_ms = timed(m4rm_step, m_steps, 3)
+    m_value = ops_step * dist.world / (m_ms * 1e-3)
+    m_per_product = [sum(m_stage[s_][j][1] for s_ in range(m_steps)) / m_steps for j in range(len(prods))]
     lop3_step = sum(7 ** lv * algorithmic_lop3(m >> lv, l >> lv, n >> lv, k)
-                    for lv, k, (m, l, n, _) in zip(levels, leaf_k, prods))
-    achieved = lop3_step / (kernel_ms * 1e-3) / 1e12
-    traffic_rec = measured_traffic()
-    traffic = None
-    if traffic_rec is not None:
-        traffic = traffic_rec.get("bytes_per_m4rm_launch")
+                    for lv, k, (m, l, n, _) in zip(m_levels, leaf_k, prods))
+    m_achieved = lop3_step / (sum(m_per_product) * 1e-3) / 1e12
+    m_traffic_rec = measured_traffic("m4rm_f3_dram_traffic.json", kernel_sources_digest())
+    m4rm = {"value": m_value, "unit": UNIT, "ms_per_step": m_ms, "steps": m_steps, "per_product_ms": m_per_product,
+            "strassen_levels": m_levels, "k": leaf_k,
+            "gpu_launches": m_steps * sum(our_launches(lv) for lv in m_levels),
+            "roofline": {"bound": "alu", "achieved": m_achieved, "peak": ALU_PEAK_TLOPS, "unit": "Tlop3/s",
+                         "frac": m_achieved / ALU_PEAK_TLOPS,
+                         "traffic": m_traffic_rec.get("bytes_per_m4rm_launch") if m_traffic_rec else None,
+                         "peak_note": "derived: 64 LOP3 lanes/clk/SM x 152 SMs x 2070 MHz"}}
 
     # ---- end to end through the public API, host buffers -------------------
     e2e = None
@@ -436,22 +494,25 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16 (exact integers, fp32 sums)", "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.sizes else "F_3 square n=" + args.sizes,
-                       "q": Q, "k": leaf_k, "k_choice": "fq_autotune per shape over k in 6..10",
-                       "products": [list(p) for p in prods],
-                       "path": "m4rm", "strassen_levels": levels,
+                       "q": Q, "products": [list(p) for p in prods],
+                       "path": forms, "path_choice": "fq_autotune per shape: compiled M4RM kernels "
+                                                     "(k in 6..10) and the tensor-core path",
                        "l2": "flushed (256 MiB write) before every step",
                        "parallelism": "replicas" if dist.world > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TLOPS, "unit": "Tlop3/s",
-                         "frac": achieved / ALU_PEAK_TLOPS, "traffic": traffic,
-                         "peak_note": "derived: 64 LOP3 lanes/clk/SM x 152 SMs x 2070 MHz",
-                         "kernel_ms_per_step": kernel_ms},
-            "per_product_ms": [sum(r[j] for r in per_launch) / args.steps for j in range(len(prods))],
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["bf16"], "traffic": traffic,
+                         "peak_note": peaks["note"], "kernel": "tc_gemm_kernel (tcgen05 kind::f16, 128x256 tiles)",
+                         "kernel_ms_per_step": sum(product_ms)},
+            "per_product_ms": per_product,
+            "product_stage_ms": product_ms,
+            "m4rm": m4rm,
+            "speedup_vs_m4rm": value / m_value,
             "e2e": e2e,
             "cpu_baseline": base,
             "clocks": clk,
-            "gpu_launches": args.steps * sum(our_launches(lv) for lv in levels),
+            "gpu_launches": args.steps * sum(3 if f == "tensor" else 1 for f in forms),
         }
         print(json.dumps(line), flush=True)
     dist.done()

@@ -61,7 +61,7 @@ extern "C" {
 /* ---- product paths (fq_options.path) --------------------------------------- */
 #define FQ_PATH_AUTO 0 /* planner's choice                                         */
 #define FQ_PATH_M4RM 1 /* bitsliced Method of Four Russians (Sections 2-4)         */
-#define FQ_PATH_MMA 2  /* exact integer tensor-core contraction, mod p per l-chunk */
+#define FQ_PATH_MMA 2  /* exact tensor-core contraction (tcgen05; mma.sync s8 for long l) */
 #define FQ_PATH_KARATSUBA 3 /* GF(4) only: Section 4.3's three F_2 products        */
 
 /* Number of bit-planes of a field element (1 for q = 2; 2 for q = 3, 4; 3 for
@@ -105,7 +105,8 @@ typedef struct fq_options {
   int k;         /* M4RM block size: 0 = planner, else 6..10 (Section 2's k)       */
   int64_t chunk; /* MMA path: l-chunk length between mod-p reductions; 0 = largest */
   int variant;   /* M4RM rows per CTA: 0 = planner, else 1 .. the kernel's maximum */
-  int kernel;    /* M4RM kernel: 0 = planner, i + 1 = compiled kernel i of field q  */
+  int kernel;    /* M4RM kernel: 0 = planner, i + 1 = compiled kernel i of field q;
+                    tensor-core path: 1 = the mma.sync s8 form                  */
   int strassen;  /* Strassen-Winograd levels over the base-field products: 0 = the
                     time model decides, -1 = none, L > 0 = L levels (each needs
                     m, l, n to be multiples of 2048 at that level)               */
@@ -146,6 +147,29 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
  * with these options (opt may be NULL) on the current device: >= 0, or
  * -FQ_EINVAL / -FQ_ECUDA.  Host-only apart from the device attribute query. */
 int fq_strassen_levels(int q, int64_t m, int64_t l, int64_t n, const fq_options *opt);
+
+/* ---- the tensor-core path in two stages -------------------------------------
+ * FQ_PATH_MMA runs on the tcgen05 tensor cores (kind::f16: bf16 operands,
+ * fp32 accumulation) whenever l * ((p-1)/2)^2 < 2^24 (l < 2^23 for GF(4)):
+ * the balanced residues are exact in bf16 and every partial sum is an integer
+ * below 2^24, so the fp32 sums are exact and the product is bit-exact.  Longer
+ * l, or fq_options.chunk > 0, or fq_options.kernel = 1 select the mma.sync
+ * s8 form with mod-p reduction every chunk.  fq_matmul converts the operands
+ * into stream-ordered scratch; these calls expose the two stages so that a
+ * caller can keep the converted operands:
+ *   fq_tc_workspace_bytes: device bytes of the converted operands (A as m x la
+ *     bf16 values, B transposed as 64 * fq_pitch_words(n) x la, la = l rounded
+ *     up to 64 -- twice for GF(4), whose two stacked products have depth 2l --
+ *     and B's bit-planes transposed on the way), or -1 outside the tcgen05
+ *     form (bad q, negative size, l too long);
+ *   fq_tc_prepare: A, B (planes buffers) -> workspace (16-byte aligned);
+ *   fq_tc_multiply: workspace -> C (planes buffer, written entirely).
+ * Both are asynchronous on `stream`; FQ_ENOTSUP outside the tcgen05 form. */
+int64_t fq_tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n);
+int fq_tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B,
+                  void *workspace, void *stream);
+int fq_tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *workspace, uint64_t *C,
+                   void *stream);
 
 /* ---- many products in one launch ------------------------------------------
  * A plan splits `count` products C_p = A_p B_p (shapes m[p] x l[p] times

@@ -209,6 +209,27 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, cons
   return fqk::product(q, m, l, n, A, B, C, prod_options(o), static_cast<cudaStream_t>(stream));
 }
 
+int64_t fq_tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n) {
+  if (!base_q(q) || m < 0 || l < 0 || n < 0) return -1;
+  return fqk::tc_workspace_bytes(q, m, l, n);
+}
+
+int fq_tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, void *workspace,
+                  void *stream) {
+  if (fq_tc_workspace_bytes(q, m, l, n) < 0) return base_q(q) && m >= 0 && l >= 0 && n >= 0 ? FQ_ENOTSUP : FQ_EINVAL;
+  if (m == 0 || n == 0 || l == 0) return FQ_OK;
+  if (!A || !B || !workspace || !aligned16(A) || !aligned16(B) || !aligned16(workspace)) return FQ_EINVAL;
+  return fqk::tc_prepare(q, m, l, n, A, B, workspace, static_cast<cudaStream_t>(stream));
+}
+
+int fq_tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *workspace, uint64_t *C, void *stream) {
+  if (fq_tc_workspace_bytes(q, m, l, n) < 0) return base_q(q) && m >= 0 && l >= 0 && n >= 0 ? FQ_ENOTSUP : FQ_EINVAL;
+  if (m == 0 || n == 0) return FQ_OK;
+  if (!C || !aligned16(C) || (l > 0 && (!workspace || !aligned16(workspace)))) return FQ_EINVAL;
+  if (m >= (int64_t(1) << 31) / 2 || n >= (int64_t(1) << 36)) return FQ_ENOTSUP;
+  return fqk::tc_multiply(q, m, l, n, workspace, C, static_cast<cudaStream_t>(stream));
+}
+
 int fq_planned_kernel(int q, int64_t m, int64_t l, int64_t n, const fq_options *opt) {
   if (!base_q(q) || m <= 0 || l <= 0 || n <= 0) return -FQ_EINVAL;
   fq_options o;

@@ -19,6 +19,18 @@ int launch_m4rm(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const
 
 int launch_mma(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                int64_t chunk, cudaStream_t s);
+// The tcgen05 form of the tensor-core path (fq_tc.cu): FQ_ENOTSUP when l is
+// beyond the exact fp32 range of the field (tc_max_l).
+int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+              cudaStream_t s);
+int64_t tc_max_l(int q);
+// Its two stages on a caller's workspace (bytes: tc_workspace_bytes, -1 if
+// the product is outside the tcgen05 form): operands to bf16, then the product.
+int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n);
+int tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, void *ws,
+               cudaStream_t s);
+int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t *C, cudaStream_t s);
+double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms);
 
 // One compiled M4RM kernel shape of a field (the planner's candidates).
 struct Variant {

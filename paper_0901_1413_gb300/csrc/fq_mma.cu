@@ -276,10 +276,13 @@ int launch_q(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t 
 
 }  // namespace
 
-// Modelled time (SM cycles) of the tensor-core path: waves of CTAs (one per
-// SM) times 64-column k-steps times the measured cycles of one k-step, plus a
-// constant for launch, the first loads and the epilogue (fitted on GB300).
+// Modelled time (SM cycles) of the tensor-core path: the tcgen05 form where l
+// is in its exact range (fq_tc.cu), else this mma.sync form: waves of CTAs
+// (one per SM) times 64-column k-steps times the measured cycles of one
+// k-step, plus a constant for launch, the first loads and the epilogue (fitted
+// on GB300).
 double mma_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
+  if (l <= tc_max_l(q)) return tc_estimate(q, m, l, n, sms);
   const int bn = q == 4 ? MmaSpec<4>::BN : 128;
   const double per_step = (q == 2 || q == 3) ? 4800.0 : (q == 4 ? 8670.0 : 8040.0);
   const int64_t ctas = (fq_pitch_words(n) * 64 / bn) * cdiv(m, 128);

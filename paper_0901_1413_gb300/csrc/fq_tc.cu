@@ -1,0 +1,558 @@
+// Exact F_q product on the 5th-generation tensor cores (tcgen05, TMEM).
+//
+// The same product C = A B as the Four-Russians path, as a dense contraction
+// of small integers.  The integer tcgen05 kind is not available on sm_103a, so
+// residues enter kind::f16 with bf16 operands and fp32 accumulation, which is
+// exact here: balanced residues |a|, |b| <= (p - 1) / 2 are exact in bf16,
+// every product is an exact small integer, and every partial sum of l of them
+// stays an integer below 2^24 in magnitude (the launcher checks l * B^2 <
+// 2^24 and otherwise takes the mma.sync s8 path), so no rounding ever happens.
+// The epilogue reads the fp32 accumulators from TMEM, reduces mod p and packs
+// the residues into bit-planes.
+//
+// GF(4) follows Section 4.3 at matrix level with two stacked products over
+// F_2: [A0 | A1] [B0 ; B1] = A0 B0 + A1 B1 (plane 0) and
+// [A0 + A1 | A0] [B0 + B1 ; B0] = (A0 + A1)(B0 + B1) + A0 B0 (plane 1), each
+// read mod 2.
+//
+// Layout.  The operands are first converted from planes to bf16: A as m rows
+// of la = roundup(l, 64) values, B transposed to n_pad rows of la values (K
+// contiguous for both, as the tensor core reads them), zero past l.  A CTA
+// owns a 128 x 256 tile of C: one thread issues TMA loads of 64-column slices
+// of A and B into a 4-stage ring (128-byte swizzle), one thread issues the
+// tcgen05.mma instructions (M = 128, N = 256, K = 16, accumulator in 256 TMEM
+// columns), and a warpgroup reads the accumulator back (tcgen05.ld) and
+// writes the packed codes.  Every mbarrier wait is bounded.
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "../../include/fq.h"
+#include "fq_common.cuh"
+#include "fq_internal.h"
+
+namespace fqk {
+
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BAR_OFF = STAGES * STAGE_BYTES;  // full[S], empty[S], accfull, tmem slot, abort
+constexpr int SMEM = BAR_OFF + 8 * (2 * STAGES + 1) + 16 + 1024;  // + alignment slack
+constexpr int TMEM_COLS = BN;
+constexpr int THREADS = 256;
+
+// ---------------------------------------------------------- conversions --
+
+// bf16 bit pattern of a small integer (sign, exponent, mantissa of 0, +-1,
+// +-2, +-3; exact).
+__host__ __device__ constexpr uint32_t bf16_pattern(int v) {
+  return v == 0 ? 0u
+                : ((v < 0 ? 0x8000u : 0u) |
+                   ((v == 1 || v == -1) ? 0x3F80u : ((v == 2 || v == -2) ? 0x4000u : 0x4040u)));
+}
+
+// Balanced value of a code (the bits of the element in planes 0, 1, 2).
+// F_3: unit | sign << 1 (code 2 is unused); F_5, F_7: any 3-bit code, read mod
+// p; F_2 and the GF(4) planes: the bit.
+template <int Q>
+__host__ __device__ constexpr int code_value(int code) {
+  if (Q == 3) return code == 1 ? 1 : (code == 3 ? -1 : 0);
+  if (Q == 5 || Q == 7) {
+    const int r = code % Q;
+    return r > Q / 2 ? r - Q : r;
+  }
+  return code & 1;
+}
+
+// Byte `half` (0 low, 1 high) of the patterns of codes 4 g .. 4 g + 3.
+template <int Q>
+__host__ __device__ constexpr uint32_t table_word(int half, int g) {
+  uint32_t w = 0;
+  for (int i = 0; i < 4; ++i) w |= ((bf16_pattern(code_value<Q>(4 * g + i)) >> (8 * half)) & 0xFFu) << (8 * i);
+  return w;
+}
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
+}
+
+// Bits 0..3 of b spread to bits 0, 4, 8, 12: bits 2, 3 move up by 6, then the
+// odd bits of each pair move up by 3.
+__device__ __forceinline__ uint32_t spread4(uint32_t b) {
+  const uint32_t x = (b | (b << 6)) & 0x0303u;
+  return (x | (x << 3)) & 0x1111u;
+}
+
+// Four elements e .. e + 3 of one word group (planes x) as four bf16 values
+// (two 32-bit words): the codes become a byte-permute selector into the
+// pattern tables.  `sel` picks, for GF(4), plane 0, plane 1 or their sum.
+template <int Q, int P>
+__device__ __forceinline__ void bf16x4(const uint64_t (&x)[P], int e, int sel, uint32_t &w0, uint32_t &w1) {
+  uint32_t c;
+  if constexpr (Q == 4) {
+    const uint64_t b = sel == 0 ? x[0] : (sel == 1 ? x[1] : (x[0] ^ x[1]));
+    c = spread4(uint32_t(b >> e) & 0xFu);
+  } else {
+    c = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) c |= spread4(uint32_t(x[p] >> e) & 0xFu) << p;
+  }
+  constexpr uint32_t L0 = table_word<Q>(0, 0), L1 = table_word<Q>(0, 1);
+  constexpr uint32_t H0 = table_word<Q>(1, 0), H1 = table_word<Q>(1, 1);
+  const uint32_t lo = prmt(L0, L1, c);
+  const uint32_t hi = prmt(H0, H1, c);
+  w0 = prmt(lo, hi, 0x5140u);  // elements e, e + 1
+  w1 = prmt(lo, hi, 0x7362u);  // elements e + 2, e + 3
+}
+
+// Rows of a planes matrix to bf16 values: out[r * ld + off + c] for c < cols
+// (cols may run into the planes' zero padding, which gives zeros).  One thread
+// per 8 elements (a 16-byte store), so that a warp writes 512 contiguous bytes.
+template <int Q, int P>
+__global__ void rows_to_bf16(const uint64_t *__restrict__ X, int64_t rows, int64_t cols, int64_t pitch,
+                             uint16_t *__restrict__ out, int64_t ld, int64_t off, int sel) {
+  // grid: x over the 16-byte pieces of a row, y over rows (grid-stride)
+  const int piece = int(blockIdx.x) * int(blockDim.x) + int(threadIdx.x);
+  const int w = piece >> 3, e0 = 8 * (piece & 7);
+  const int64_t c0 = int64_t(w) * 64 + e0;
+  if (c0 >= cols) return;
+  const bool vec = c0 + 8 <= cols && ((off & 7) == 0);
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+    uint64_t x[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) x[p] = __ldg(X + (p * rows + r) * pitch + w);
+    uint32_t v[4];
+    bf16x4<Q, P>(x, e0, sel, v[0], v[1]);
+    bf16x4<Q, P>(x, e0 + 4, sel, v[2], v[3]);
+    uint16_t *dst = out + r * ld + off + c0;
+    if (vec) {
+      *reinterpret_cast<uint4 *>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+    } else {
+      for (int k = 0; k < 8 && c0 + k < cols; ++k) dst[k] = uint16_t(v[k >> 1] >> (16 * (k & 1)));
+    }
+  }
+}
+
+// Launch shape of rows_to_bf16 for rows x cols.
+inline dim3 rows_grid(int64_t rows, int64_t cols) {
+  const int64_t pieces = cdiv(cols, 64) * 8;
+  return dim3(unsigned(cdiv(pieces, 256)), unsigned(rows < 65535 ? (rows > 0 ? rows : 1) : 65535));
+}
+
+// Zeros out[r * ld + c] for c in [from, ld): depth padding of the operands.
+__global__ void zero_tail(uint16_t *out, int64_t rows, int64_t ld, int64_t from) {
+  const int64_t width = ld - from, total = rows * width;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / width, c = from + (i - r * width);
+    out[r * ld + c] = 0;
+  }
+}
+
+int grid_for(int64_t total) {
+  const int64_t want = cdiv(total, 256), cap = 152 * 16;
+  return int(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+// Bit transpose of every plane: XT[p][c][r] = X[p][r][c] for r < rows and
+// every column c of X's pitch; XT has npad = 64 * pitch rows of pitch_t words
+// (rows past `rows` read as zero).  A warp turns 256 rows x 32 columns around
+// with 8 x 32 ballots and each lane stores its column's four words (32 bytes).
+template <int P>
+__global__ void transpose_planes(const uint64_t *__restrict__ X, int64_t rows, int64_t pitch, uint64_t *__restrict__ XT,
+                                 int64_t pitch_t) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  const int64_t rgroups = pitch_t / 4, cblocks = pitch * 2, total = int64_t(P) * rgroups * cblocks;
+  const int64_t npad = pitch * 64;
+  for (int64_t t = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); t < total; t += warps) {
+    const int64_t cb = t % cblocks, rg = (t / cblocks) % rgroups, p = t / cblocks / rgroups;
+    const int64_t c0 = cb * 32;
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t r = rg * 256 + 32 * k + lane;
+      v[k] = r < rows ? uint32_t(__ldg(X + (p * rows + r) * pitch + c0 / 64) >> (c0 % 64)) : 0u;
+    }
+    uint32_t mine[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      mine[k] = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const uint32_t col = __ballot_sync(0xFFFFFFFFu, (v[k] >> j) & 1u);
+        mine[k] = lane == j ? col : mine[k];
+      }
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(XT + (p * npad + c0 + lane) * pitch_t + rg * 4);
+    dst[0] = make_uint4(mine[0], mine[1], mine[2], mine[3]);
+    dst[1] = make_uint4(mine[4], mine[5], mine[6], mine[7]);
+  }
+}
+
+// ------------------------------------------------------------------ GEMM --
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major bf16 tile with 128-byte rows
+// and the 128-byte swizzle: start address, leading byte offset 16 (unused by
+// this layout), stride 1024 bytes between 8-row groups, descriptor version 1,
+// layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= uint64_t((addr >> 4) & 0x3FFFu);
+  d |= uint64_t(1) << 16;                 // leading byte offset 16 B
+  d |= uint64_t(1024 >> 4) << 32;         // stride byte offset 1024 B
+  d |= uint64_t(1) << 46;                 // version
+  d |= uint64_t(2) << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Bounded wait that gives up at once when the CTA has aborted.
+__device__ __forceinline__ void wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag, unsigned *err) {
+  if (*abort_flag) return;
+  if (!mbar_wait_bounded(bar, parity)) {
+    *abort_flag = 1;
+    record_error(err, FQ_ETIMEOUT);
+  }
+}
+
+struct GemmParams {
+  uint64_t *C;
+  int64_t m, pc;   // rows of C, pitch words of C
+  int ksteps;      // la / 64
+  int plane;       // GF(4): the plane this product writes
+  unsigned *err;
+};
+
+template <int Q, int P>
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const GemmParams prm) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned (128-byte swizzle atoms)
+  unsigned char *smem = smem_raw + (base - raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t full = base + BAR_OFF, empty = full + 8 * STAGES, accfull = empty + 8 * STAGES;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + BAR_OFF + 8 * (2 * STAGES + 1));
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + BAR_OFF + 8 * (2 * STAGES + 1) + 8);
+  const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
+
+  if (tid == 0) {
+    *abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + 8 * s, 1);
+      mbar_init(empty + 8 * s, 1);
+    }
+    mbar_init(accfull, 1);
+    fence_mbar_init();
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    for (int ks = 0; ks < prm.ksteps; ++ks) {
+      const int s = ks % STAGES;
+      if (ks >= STAGES) wait_bar(empty + 8 * s, uint32_t((ks / STAGES - 1) & 1), abort_flag, prm.err);
+      if (*abort_flag) break;
+      const uint32_t a_dst = base + uint32_t(s * STAGE_BYTES), b_dst = a_dst + A_BYTES;
+      mbar_expect_tx(full + 8 * s, STAGE_BYTES);
+      tma_load_2d(a_dst, &tmA, full + 8 * s, ks * BK, int(m0));
+      tma_load_2d(b_dst, &tmB, full + 8 * s, ks * BK, int(n0));
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    for (int ks = 0; ks < prm.ksteps; ++ks) {
+      const int s = ks % STAGES;
+      wait_bar(full + 8 * s, uint32_t((ks / STAGES) & 1), abort_flag, prm.err);
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_src = base + uint32_t(s * STAGE_BYTES), b_src = a_src + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        mma_bf16(tmem, smem_desc(a_src + 32 * kk), smem_desc(b_src + 32 * kk), (ks | kk) != 0);
+      mma_commit(empty + 8 * s);  // the stage is free once these MMAs have read it
+    }
+    mma_commit(accfull);          // the accumulator is complete
+  } else if (warp >= 4) {
+    // ---- epilogue: TMEM lanes 32 (warp - 4) .. + 31 are rows of the tile
+    const int ew = warp - 4;
+    wait_bar(accfull, 0u, abort_flag, prm.err);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int64_t row = m0 + ew * 32 + lane;
+    uint64_t words[P][BN / 64];
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int w = 0; w < BN / 64; ++w) words[p][w] = 0ull;
+#pragma unroll
+    for (int c = 0; c < BN / 32; ++c) {
+      uint32_t v[32];
+      tmem_ld32(tmem + (uint32_t(ew * 32) << 16) + uint32_t(c * 32), v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int x = int(__uint_as_float(v[i]));  // an exact integer
+        const int mod = Q == 4 ? 2 : Q;
+        int r = x % mod;
+        r += r < 0 ? mod : 0;
+        const int col = c * 32 + i, w = col / 64, b = col % 64;
+        if constexpr (Q == 3) {
+          words[0][w] |= uint64_t(r != 0) << b;
+          words[1][w] |= uint64_t(r == 2) << b;
+        } else if constexpr (Q == 4) {
+          words[0][w] |= uint64_t(r) << b;
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p) words[p][w] |= uint64_t((r >> p) & 1) << b;
+        }
+      }
+    }
+    if (row < prm.m && !*abort_flag) {
+      if constexpr (Q == 4) {
+        uint64_t *dst = prm.C + (int64_t(prm.plane) * prm.m + row) * prm.pc + n0 / 64;
+#pragma unroll
+        for (int w = 0; w < BN / 64; ++w) dst[w] = words[0][w];
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + n0 / 64;
+#pragma unroll
+          for (int w = 0; w < BN / 64; ++w) dst[w] = words[p][w];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host --
+
+int make_map(CUtensorMap *map, const uint16_t *ptr, int64_t inner, int64_t rows, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (int rc = tensor_map_encoder(&encode)) return rc;
+  memset(map, 0, sizeof(*map));
+  const cuuint64_t dims[2] = {cuuint64_t(inner), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(inner) * 2u};
+  const cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult cr = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(ptr), dims, strides,
+                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return cr == CUDA_SUCCESS ? FQ_OK : FQ_EINVAL;
+}
+
+
+template <int Q, int P>
+int gemm(const uint16_t *Ab, const uint16_t *Bt, uint64_t *C, int64_t m, int64_t la, int64_t npad, int64_t pc,
+         int plane, cudaStream_t s) {
+  unsigned *err = nullptr;
+  if (int rc = status_word(&err)) return rc;
+  CUtensorMap ma, mb;
+  if (int rc = make_map(&ma, Ab, la, m, BM)) return rc;
+  if (int rc = make_map(&mb, Bt, la, npad, BN)) return rc;
+  GemmParams prm;
+  prm.C = C;
+  prm.m = m;
+  prm.pc = pc;
+  prm.ksteps = int(la / BK);
+  prm.plane = plane;
+  prm.err = err;
+  FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+  const dim3 grid(unsigned(npad / BN), unsigned(cdiv(m, BM)));
+  if (grid.y > 65535u) return FQ_ENOTSUP;
+  tc_gemm_kernel<Q, P><<<grid, THREADS, SMEM, s>>>(ma, mb, prm);
+  FQ_LAUNCH_CHECK();
+  return FQ_OK;
+}
+
+// Prepared operands in a workspace: per round (GF(4) has two, the other
+// fields one) A as m x la bf16, then B transposed as npad x la bf16; after
+// the rounds, B's planes bit-transposed (P planes of npad rows of pt words).
+struct Layout {
+  int rounds;
+  int64_t la, npad, pc, pt, a_elems, b_elems;
+};
+
+inline Layout layout_for(int q, int64_t m, int64_t l, int64_t n) {
+  Layout lo;
+  lo.rounds = q == 4 ? 2 : 1;
+  lo.la = cdiv(q == 4 ? 2 * l : l, BK) * BK;
+  lo.pc = fq_pitch_words(n);
+  lo.npad = lo.pc * 64;
+  lo.pt = fq_pitch_words(l);
+  lo.a_elems = m * lo.la;
+  lo.b_elems = lo.npad * lo.la;
+  return lo;
+}
+
+inline int64_t transposed_words(int q, const Layout &lo) {
+  return int64_t(q == 2 ? 1 : ((q == 5 || q == 7) ? 3 : 2)) * lo.npad * lo.pt;
+}
+
+template <int Q, int P>
+int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint16_t *ws, cudaStream_t s) {
+  const Layout lo = layout_for(Q, m, l, n);
+  const int64_t pa = fq_pitch_words(l);
+  uint64_t *BT = reinterpret_cast<uint64_t *>(ws + lo.rounds * (lo.a_elems + lo.b_elems));
+  const int64_t blocks = int64_t(P) * (lo.pt / 4) * lo.pc * 2;  // 256 x 32 bit blocks, 8 per CTA
+  transpose_planes<P><<<unsigned(cdiv(blocks, 8) < 152 * 32 ? cdiv(blocks, 8) : 152 * 32), 256, 0, s>>>(
+      B, l, lo.pc, BT, lo.pt);
+  const dim3 ga = rows_grid(m, lo.la), gb = rows_grid(lo.npad, lo.la);
+  if (Q == 4) {
+    // round 0: [A0 | A1] [B0 ; B1];  round 1: [A0 + A1 | A0] [B0 + B1 ; B0]
+    const int sa[2][2] = {{0, 1}, {2, 0}};
+    const dim3 ha = rows_grid(m, l), hb = rows_grid(lo.npad, l);
+    for (int r = 0; r < 2; ++r) {
+      uint16_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
+      rows_to_bf16<Q, P><<<ha, 256, 0, s>>>(A, m, l, pa, a, lo.la, 0, sa[r][0]);
+      rows_to_bf16<Q, P><<<ha, 256, 0, s>>>(A, m, l, pa, a, lo.la, l, sa[r][1]);
+      rows_to_bf16<Q, P><<<hb, 256, 0, s>>>(BT, lo.npad, l, lo.pt, b, lo.la, 0, sa[r][0]);
+      rows_to_bf16<Q, P><<<hb, 256, 0, s>>>(BT, lo.npad, l, lo.pt, b, lo.la, l, sa[r][1]);
+      if (2 * l < lo.la) {  // depth padding past the two stacked segments
+        zero_tail<<<grid_for(m * (lo.la - 2 * l)), 256, 0, s>>>(a, m, lo.la, 2 * l);
+        zero_tail<<<grid_for(lo.npad * (lo.la - 2 * l)), 256, 0, s>>>(b, lo.npad, lo.la, 2 * l);
+      }
+    }
+  } else {
+    rows_to_bf16<Q, P><<<ga, 256, 0, s>>>(A, m, lo.la, pa, ws, lo.la, 0, 0);
+    rows_to_bf16<Q, P><<<gb, 256, 0, s>>>(BT, lo.npad, lo.la, lo.pt, ws + lo.a_elems, lo.la, 0, 0);
+  }
+  FQ_LAUNCH_CHECK();
+  return FQ_OK;
+}
+
+template <int Q, int P>
+int multiply(int64_t m, int64_t l, int64_t n, const uint16_t *ws, uint64_t *C, cudaStream_t s) {
+  const Layout lo = layout_for(Q, m, l, n);
+  for (int r = 0; r < lo.rounds; ++r) {
+    const uint16_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
+    if (int rc = gemm<Q, P>(a, b, C, m, lo.la, lo.npad, lo.pc, r, s)) return rc;
+  }
+  return FQ_OK;
+}
+
+}  // namespace tc
+
+// Largest l for which every partial sum stays below 2^24 in magnitude.
+int64_t tc_max_l(int q) {
+  const int64_t b = q == 2 || q == 4 ? 1 : (q - 1) / 2;
+  const int64_t lim = ((int64_t(1) << 24) - 1) / (b * b);
+  return q == 4 ? lim / 2 : lim;
+}
+
+// Modelled time (SM cycles): waves of 128 x 256 tiles (one CTA per SM) times
+// 64-column k-steps at the measured ~1100 cycles each, the operand conversion
+// at about 5 TB/s, and a constant for the launches (fitted on GB300).  GF(4)
+// runs two products of twice the depth.
+double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
+  const int64_t la = cdiv(q == 4 ? 2 * l : l, tc::BK) * tc::BK;
+  const int64_t npad = fq_pitch_words(n) * 64;
+  const int64_t ctas = (npad / tc::BN) * cdiv(m, tc::BM);
+  const double products = q == 4 ? 2.0 : 1.0;
+  const double gemm = double(cdiv(ctas, sms)) * double(la / tc::BK) * 1100.0;
+  const double convert = double(m + npad) * double(la) * 2.0 * 2.07e9 / 5.0e12;
+  return products * (gemm + convert) + 30000.0;
+}
+
+int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n) {
+  if (!(q == 2 || q == 3 || q == 4 || q == 5 || q == 7) || m < 0 || l < 0 || n < 0 || l > tc_max_l(q)) return -1;
+  const tc::Layout lo = tc::layout_for(q, m, l, n);
+  return int64_t(lo.rounds) * (lo.a_elems + lo.b_elems) * 2 + tc::transposed_words(q, lo) * 8;
+}
+
+int tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, void *ws,
+               cudaStream_t s) {
+  if (l == 0 || m == 0 || n == 0) return FQ_OK;
+  uint16_t *w = static_cast<uint16_t *>(ws);
+  switch (q) {
+    case 2: return tc::prepare<2, 1>(m, l, n, A, B, w, s);
+    case 3: return tc::prepare<3, 2>(m, l, n, A, B, w, s);
+    case 4: return tc::prepare<4, 2>(m, l, n, A, B, w, s);
+    case 5: return tc::prepare<5, 3>(m, l, n, A, B, w, s);
+    case 7: return tc::prepare<7, 3>(m, l, n, A, B, w, s);
+    default: return FQ_EINVAL;
+  }
+}
+
+int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t *C, cudaStream_t s) {
+  if (m == 0 || n == 0) return FQ_OK;
+  if (l == 0) {
+    FQ_CUDA_TRY(cudaMemsetAsync(C, 0, size_t(fq_planes(q)) * size_t(m) * size_t(fq_pitch_words(n)) * 8u, s));
+    return FQ_OK;
+  }
+  const uint16_t *w = static_cast<const uint16_t *>(ws);
+  switch (q) {
+    case 2: return tc::multiply<2, 1>(m, l, n, w, C, s);
+    case 3: return tc::multiply<3, 2>(m, l, n, w, C, s);
+    case 4: return tc::multiply<4, 2>(m, l, n, w, C, s);
+    case 5: return tc::multiply<5, 3>(m, l, n, w, C, s);
+    case 7: return tc::multiply<7, 3>(m, l, n, w, C, s);
+    default: return FQ_EINVAL;
+  }
+}
+
+int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
+              cudaStream_t s) {
+  const int64_t bytes = tc_workspace_bytes(q, m, l, n);
+  if (bytes < 0) return FQ_ENOTSUP;
+  if (l == 0) return tc_multiply(q, m, l, n, nullptr, C, s);
+  void *mem = nullptr;
+  if (int rc = scratch_alloc(&mem, size_t(bytes), s)) return rc;
+  int rc = tc_prepare(q, m, l, n, A, B, mem, s);
+  if (rc == FQ_OK) rc = tc_multiply(q, m, l, n, mem, C, s);
+  const int fr = scratch_free(mem, s);
+  return rc ? rc : fr;
+}
+
+}  // namespace fqk

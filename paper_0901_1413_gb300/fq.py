@@ -71,6 +71,9 @@ def load():
             "fq_auto_choice": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "fq_strassen_levels": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
             "fq_planned_kernel": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
+            "fq_tc_workspace_bytes": (i64, [i32, i64, i64, i64]),
+            "fq_tc_prepare": (i32, [i32, i64, i64, i64, vp, vp, vp, vp]),
+            "fq_tc_multiply": (i32, [i32, i64, i64, i64, vp, vp, vp]),
             "fq_error_string": (ctypes.c_char_p, [i32]),
             "fq_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -223,6 +226,32 @@ def auto_choice(q: int, m: int, l: int, n: int) -> tuple[int, int]:
     path, kernel = ctypes.c_int(), ctypes.c_int()
     _check(load().fq_auto_choice(q, m, l, n, ctypes.byref(path), ctypes.byref(kernel)), "fq_auto_choice")
     return path.value, kernel.value
+
+
+class TensorOperands:
+    """fq_tc_prepare / fq_tc_multiply: the tensor-core path's converted operands
+    of A and B, kept in a device workspace (a torch buffer) for reuse."""
+
+    def __init__(self, a: Packed, b: Packed, stream=None):
+        if a.q != b.q or a.cols != b.rows:
+            raise ValueError("shape mismatch")
+        self.q, self.m, self.l, self.n = a.q, a.rows, a.cols, b.cols
+        nbytes = load().fq_tc_workspace_bytes(self.q, self.m, self.l, self.n)
+        if nbytes < 0:
+            raise FqError(ENOTSUP, "fq_tc_workspace_bytes")
+        self.workspace = torch.empty(max(2, (nbytes + 7) // 8), dtype=torch.int64, device=a.data.device)
+        self.prepare(a, b, stream)
+
+    def prepare(self, a: Packed, b: Packed, stream=None):
+        _check(load().fq_tc_prepare(self.q, self.m, self.l, self.n, ctypes.c_void_p(a.data.data_ptr()),
+                                    ctypes.c_void_p(b.data.data_ptr()), ctypes.c_void_p(self.workspace.data_ptr()),
+                                    _stream(stream)), "fq_tc_prepare")
+
+    def multiply(self, out: Packed | None = None, stream=None) -> Packed:
+        out = empty(self.q, self.m, self.n, self.workspace.device) if out is None else out
+        _check(load().fq_tc_multiply(self.q, self.m, self.l, self.n, ctypes.c_void_p(self.workspace.data_ptr()),
+                                     ctypes.c_void_p(out.data.data_ptr()), _stream(stream)), "fq_tc_multiply")
+        return out
 
 
 class BatchPlan:

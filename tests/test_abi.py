@@ -125,6 +125,17 @@ def test_autotune_cache_host_side(lib):
     # an empty product needs no device and takes the M4RM planner
     assert lib.fq_auto_choice(3, 0, 10, 10, ctypes.byref(p), ctypes.byref(k)) == fq.OK
     assert (p.value, k.value) == (fq.PATH_M4RM, 0)
+    # tensor-core workspace sizes (host-only)
+    # bf16 operands (A: m x la, B transposed: 64 pitch(n) x la), then B's planes
+    # bit-transposed (planes x 64 pitch(n) rows x pitch(l) words)
+    assert lib.fq_tc_workspace_bytes(3, 100, 200, 300) == 2 * (100 + 1024) * 256 + 2 * 1024 * 16 * 8
+    assert lib.fq_tc_workspace_bytes(4, 100, 200, 300) == 2 * 2 * (100 + 1024) * 448 + 2 * 1024 * 16 * 8
+    assert lib.fq_tc_workspace_bytes(6, 100, 200, 300) == -1
+    assert lib.fq_tc_workspace_bytes(9, 100, 200, 300) == -1
+    assert lib.fq_tc_workspace_bytes(7, 10, 2_000_000, 10) == -1                 # beyond exact fp32 sums
+    vp = ctypes.c_void_p
+    assert lib.fq_tc_prepare(7, 10, 2_000_000, 10, vp(16), vp(16), vp(16), None) == fq.ENOTSUP
+    assert lib.fq_tc_multiply(6, 10, 10, 10, vp(16), vp(16), None) == fq.EINVAL
     # planned kernel query: argument errors and device-free answers
     assert lib.fq_planned_kernel(6, 10, 10, 10, None) == -fq.EINVAL
     assert lib.fq_planned_kernel(9, 10, 10, 10, None) == -fq.EINVAL      # extension fields: none

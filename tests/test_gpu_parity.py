@@ -291,6 +291,40 @@ def test_mma_path_matches_oracle(fq, q, mln):
 
 
 @pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("mln", [(1, 1, 1), (37, 100, 70), (300, 500, 260), (513, 257, 1025)])
+def test_mma_sync_form_matches_oracle(fq, q, mln):
+    """The mma.sync s8 form (fq_options.kernel = 1), kept for l beyond the
+    tcgen05 form's exact range."""
+    _check_product(fq, q, *mln, seed=sum(mln) + 11 * q, path=fq.PATH_MMA, kernel=1)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+def test_tensor_operands_prepared_once(fq, q):
+    """fq_tc_prepare once, fq_tc_multiply twice: both results equal the oracle."""
+    m, l, n = 300, 520, 700
+    A = inputs.uniform(q, m, l, seed=q + 60, stream=inputs.STREAM_A)
+    B = inputs.uniform(q, l, n, seed=q + 60, stream=inputs.STREAM_B)
+    ops = fq.TensorOperands(gpu_pack(fq, q, A), gpu_pack(fq, q, B))
+    want = oracle.matmul(q, A, B)
+    c1 = ops.multiply()
+    c2 = ops.multiply()
+    assert np.array_equal(fq.unpack(c1).cpu().numpy(), want)
+    assert torch.equal(c1.data, c2.data)
+    assert fq.status() == fq.OK
+
+
+@pytest.mark.slow
+def test_tcgen05_exact_near_its_range(fq):
+    """F_7 with every entry 3: each entry of C is 9 l before the reduction,
+    9.4e6 for l = 2^20 (the fp32 sums must stay exact up to 2^24)."""
+    m, l, n = 3, 1 << 20, 70
+    A = np.full((m, l), 3, np.uint8)
+    B = np.full((l, n), 3, np.uint8)
+    got, _ = gpu_product(fq, 7, A, B, path=fq.PATH_MMA)
+    assert (got == (9 * l) % 7).all()
+
+
+@pytest.mark.parametrize("q", FIELDS)
 @pytest.mark.parametrize("chunk", [64, 128, 1000])
 def test_mma_path_reduces_between_chunks(fq, q, chunk):
     """A forced short l-chunk runs the mod-p reduction between chunks many times."""
@@ -353,12 +387,15 @@ def test_autotune_picks_a_candidate_and_auto_uses_it(fq, q):
 
 
 def test_auto_choice_by_time_model(fq):
-    """Without a measurement, AUTO takes the tensor-core path for a small F_3
-    product and Four-Russians for a large one; both give the oracle's result."""
+    """Without a measurement, AUTO takes the tcgen05 tensor-core path for F_3,
+    F_5 and F_7 and Four Russians for GF(4) and F_2 (one 2-plane table serves
+    both GF(4) lookups; F_2 is one XOR per lookup); all give the oracle's result."""
     fq.load().fq_autotune_clear()
     assert fq.auto_choice(3, 512, 512, 512) == (fq.PATH_MMA, 0)
-    assert fq.auto_choice(3, 8192, 8192, 8192) == (fq.PATH_M4RM, 0)
+    assert fq.auto_choice(3, 8192, 8192, 8192) == (fq.PATH_MMA, 0)
+    assert fq.auto_choice(5, 8192, 8192, 8192) == (fq.PATH_MMA, 0)
     assert fq.auto_choice(4, 8192, 8192, 8192) == (fq.PATH_M4RM, 0)
+    assert fq.auto_choice(2, 8192, 8192, 8192) == (fq.PATH_M4RM, 0)
     assert fq.auto_choice(3, 0, 512, 512) == (fq.PATH_M4RM, 0)
     for q in FIELDS:
         _check_product(fq, q, 512, 512, 512, seed=q + 40)       # AUTO, whichever path

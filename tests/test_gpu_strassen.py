@@ -85,10 +85,13 @@ def test_shapes_that_do_not_split(fq):
 
 
 def test_time_model_levels(fq):
-    """On GB300 the model takes one level for F_3 at 16384 and none at 8192."""
-    assert fq.strassen_levels(3, 8192, 8192, 8192) == 0
-    assert fq.strassen_levels(3, 16384, 16384, 16384) >= 1
-    assert fq.strassen_levels(3, 16384, 16384, 16384, strassen=-1) == 0
+    """On GB300 the model takes one level for F_3 M4RM products at 16384 and
+    none at 8192; the tcgen05 products stay direct."""
+    M = fq.PATH_M4RM
+    assert fq.strassen_levels(3, 8192, 8192, 8192, path=M) == 0
+    assert fq.strassen_levels(3, 16384, 16384, 16384, path=M) >= 1
+    assert fq.strassen_levels(3, 16384, 16384, 16384, path=M, strassen=-1) == 0
+    assert fq.strassen_levels(3, 16384, 16384, 16384, path=fq.PATH_MMA) == 0
     assert fq.strassen_levels(9, 16384, 16384, 16384) == 0    # extension fields: per base product
 
 
@@ -124,5 +127,5 @@ def test_f3_16384_auto_level_matches_direct(fq):
     A, B, a, b = operands(fq, 3, 16384, 16384, 16384, seed=80)
     assert fq.strassen_levels(3, 16384, 16384, 16384, k=8) >= 1
     c1 = fq.matmul(a, b, k=8)
-    c0 = fq.matmul(a, b, k=8, strassen=-1)
+    c0 = fq.matmul(a, b, path=fq.PATH_MMA, strassen=-1)     # the tcgen05 form
     assert torch.equal(c1.data, c0.data)
