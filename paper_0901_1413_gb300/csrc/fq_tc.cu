@@ -17,12 +17,14 @@
 //
 // Layout.  The operands are first converted from planes to bf16: A as m rows
 // of la = roundup(l, 64) values, B transposed to n_pad rows of la values (K
-// contiguous for both, as the tensor core reads them), zero past l.  A CTA
-// owns a 128 x 256 tile of C: one thread issues TMA loads of 64-column slices
-// of A and B into a 4-stage ring (128-byte swizzle), one thread issues the
-// tcgen05.mma instructions (M = 128, N = 256, K = 16, accumulator in 256 TMEM
-// columns), and a warpgroup reads the accumulator back (tcgen05.ld) and
-// writes the packed codes.  Every mbarrier wait is bounded.
+// contiguous for both, as the tensor core reads them), zero past l.  One
+// persistent CTA per SM walks 128 x 256 tiles of C in groups of 8 row blocks:
+// one thread issues TMA loads of 64-column slices of A and B into a 4-stage
+// ring (128-byte swizzle), one thread issues the tcgen05.mma instructions
+// (M = 128, N = 256, K = 16) into one of two 256-column TMEM accumulators,
+// and a warpgroup reads the other accumulator back (tcgen05.ld) and writes
+// the packed codes, so a tile's epilogue overlaps the next tile's products.
+// Every mbarrier wait is bounded.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -37,10 +39,13 @@ namespace tc {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int BAR_OFF = STAGES * STAGE_BYTES;  // full[S], empty[S], accfull, tmem slot, abort
-constexpr int SMEM = BAR_OFF + 8 * (2 * STAGES + 1) + 16 + 1024;  // + alignment slack
-constexpr int TMEM_COLS = BN;
+constexpr int ACC = 2;                         // TMEM accumulators (epilogue overlaps the next tile)
+constexpr int BAR_OFF = STAGES * STAGE_BYTES;  // full[S], empty[S], accfull[ACC], accempty[ACC], tmem slot, abort
+constexpr int NBARS = 2 * STAGES + 2 * ACC;
+constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;  // + alignment slack
+constexpr int TMEM_COLS = ACC * BN;
 constexpr int THREADS = 256;
+constexpr int GROUP_M = 8;                     // tile order: groups of 8 row blocks (L2 reuse)
 
 // ---------------------------------------------------------- conversions --
 
@@ -244,6 +249,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive_cta(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // Bounded wait that gives up at once when the CTA has aborted.
 __device__ __forceinline__ void wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag, unsigned *err) {
   if (*abort_flag) return;
@@ -257,10 +266,27 @@ struct GemmParams {
   uint64_t *C;
   int64_t m, pc;   // rows of C, pitch words of C
   int ksteps;      // la / 64
+  int mblocks, nblocks, tiles;
   int plane;       // GF(4): the plane this product writes
   unsigned *err;
 };
 
+// Tile t in grouped order: GROUP_M row blocks at a time, all column blocks
+// of the group, so that a wave of tiles reuses a few rows of A and columns
+// of B from L2.
+__device__ __forceinline__ void tile_coords(const GemmParams &prm, int t, int &mb, int &nb) {
+  const int per_group = GROUP_M * prm.nblocks;
+  const int g = t / per_group, first = g * GROUP_M;
+  const int rows = prm.mblocks - first < GROUP_M ? prm.mblocks - first : GROUP_M;
+  const int in = t - g * per_group;
+  mb = first + in % rows;
+  nb = in / rows;
+}
+
+// Persistent: CTA b takes tiles b, b + grid, ...  Warp 0 streams A and B
+// slices through the stage ring, warp 1 issues the MMAs of each tile into one
+// of two TMEM accumulators, warps 4..7 drain the other accumulator (TMEM
+// lanes 32 (warp - 4) .. + 31 are rows of the tile) and store the codes.
 template <int Q, int P>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -270,10 +296,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned (128-byte swizzle atoms)
   unsigned char *smem = smem_raw + (base - raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t full = base + BAR_OFF, empty = full + 8 * STAGES, accfull = empty + 8 * STAGES;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + BAR_OFF + 8 * (2 * STAGES + 1));
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + BAR_OFF + 8 * (2 * STAGES + 1) + 8);
-  const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
+  const uint32_t full = base + BAR_OFF, empty = full + 8 * STAGES, accfull = empty + 8 * STAGES,
+                 accempty = accfull + 8 * ACC;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + BAR_OFF + 8 * NBARS);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + BAR_OFF + 8 * NBARS + 8);
 
   if (tid == 0) {
     *abort_flag = 0;
@@ -281,7 +307,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(full + 8 * s, 1);
       mbar_init(empty + 8 * s, 1);
     }
-    mbar_init(accfull, 1);
+    for (int b = 0; b < ACC; ++b) {
+      mbar_init(accfull + 8 * b, 1);
+      mbar_init(accempty + 8 * b, 4);  // one arrival per epilogue warp
+    }
     fence_mbar_init();
   }
   if (warp == 2) {
@@ -297,73 +326,97 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer
-    for (int ks = 0; ks < prm.ksteps; ++ks) {
-      const int s = ks % STAGES;
-      if (ks >= STAGES) wait_bar(empty + 8 * s, uint32_t((ks / STAGES - 1) & 1), abort_flag, prm.err);
-      if (*abort_flag) break;
-      const uint32_t a_dst = base + uint32_t(s * STAGE_BYTES), b_dst = a_dst + A_BYTES;
-      mbar_expect_tx(full + 8 * s, STAGE_BYTES);
-      tma_load_2d(a_dst, &tmA, full + 8 * s, ks * BK, int(m0));
-      tma_load_2d(b_dst, &tmB, full + 8 * s, ks * BK, int(n0));
+    int it = 0;
+    for (int t = blockIdx.x; t < prm.tiles && !*abort_flag; t += gridDim.x) {
+      int mb, nb;
+      tile_coords(prm, t, mb, nb);
+      for (int ks = 0; ks < prm.ksteps; ++ks, ++it) {
+        const int s = it % STAGES;
+        if (it >= STAGES) wait_bar(empty + 8 * s, uint32_t((it / STAGES - 1) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+        const uint32_t a_dst = base + uint32_t(s * STAGE_BYTES), b_dst = a_dst + A_BYTES;
+        mbar_expect_tx(full + 8 * s, STAGE_BYTES);
+        tma_load_2d(a_dst, &tmA, full + 8 * s, ks * BK, mb * BM);
+        tma_load_2d(b_dst, &tmB, full + 8 * s, ks * BK, nb * BN);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
-    for (int ks = 0; ks < prm.ksteps; ++ks) {
-      const int s = ks % STAGES;
-      wait_bar(full + 8 * s, uint32_t((ks / STAGES) & 1), abort_flag, prm.err);
+    int it = 0, li = 0;
+    for (int t = blockIdx.x; t < prm.tiles && !*abort_flag; t += gridDim.x, ++li) {
+      const int b = li % ACC;
+      if (li >= ACC) wait_bar(accempty + 8 * b, uint32_t((li / ACC - 1) & 1), abort_flag, prm.err);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t d = tmem + uint32_t(b * BN);
+      for (int ks = 0; ks < prm.ksteps; ++ks, ++it) {
+        const int s = it % STAGES;
+        wait_bar(full + 8 * s, uint32_t((it / STAGES) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_src = base + uint32_t(s * STAGE_BYTES), b_src = a_src + A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk)
+          mma_bf16(d, smem_desc(a_src + 32 * kk), smem_desc(b_src + 32 * kk), (ks | kk) != 0);
+        mma_commit(empty + 8 * s);  // the stage is free once these MMAs have read it
+      }
+      mma_commit(accfull + 8 * b);  // this tile's accumulator is complete
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue
+    const int ew = warp - 4;
+    int li = 0;
+    for (int t = blockIdx.x; t < prm.tiles; t += gridDim.x, ++li) {
+      const int b = li % ACC;
+      wait_bar(accfull + 8 * b, uint32_t((li / ACC) & 1), abort_flag, prm.err);
       if (*abort_flag) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_src = base + uint32_t(s * STAGE_BYTES), b_src = a_src + A_BYTES;
+      int mb, nb;
+      tile_coords(prm, t, mb, nb);
+      const int64_t row = int64_t(mb) * BM + ew * 32 + lane;
+      const int64_t w0 = int64_t(nb) * (BN / 64);
+      uint64_t words[P][BN / 64];
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
-        mma_bf16(tmem, smem_desc(a_src + 32 * kk), smem_desc(b_src + 32 * kk), (ks | kk) != 0);
-      mma_commit(empty + 8 * s);  // the stage is free once these MMAs have read it
-    }
-    mma_commit(accfull);          // the accumulator is complete
-  } else if (warp >= 4) {
-    // ---- epilogue: TMEM lanes 32 (warp - 4) .. + 31 are rows of the tile
-    const int ew = warp - 4;
-    wait_bar(accfull, 0u, abort_flag, prm.err);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int64_t row = m0 + ew * 32 + lane;
-    uint64_t words[P][BN / 64];
+      for (int p = 0; p < P; ++p)
 #pragma unroll
-    for (int p = 0; p < P; ++p)
+        for (int w = 0; w < BN / 64; ++w) words[p][w] = 0ull;
 #pragma unroll
-      for (int w = 0; w < BN / 64; ++w) words[p][w] = 0ull;
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN + c * 32), v);
 #pragma unroll
-    for (int c = 0; c < BN / 32; ++c) {
-      uint32_t v[32];
-      tmem_ld32(tmem + (uint32_t(ew * 32) << 16) + uint32_t(c * 32), v);
+        for (int i = 0; i < 32; ++i) {
+          const int x = int(__uint_as_float(v[i]));  // an exact integer
+          const int mod = Q == 4 ? 2 : Q;
+          int r = x % mod;
+          r += r < 0 ? mod : 0;
+          const int col = c * 32 + i, w = col / 64, bit = col % 64;
+          if constexpr (Q == 3) {
+            words[0][w] |= uint64_t(r != 0) << bit;
+            words[1][w] |= uint64_t(r == 2) << bit;
+          } else if constexpr (Q == 4) {
+            words[0][w] |= uint64_t(r) << bit;
+          } else {
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int x = int(__uint_as_float(v[i]));  // an exact integer
-        const int mod = Q == 4 ? 2 : Q;
-        int r = x % mod;
-        r += r < 0 ? mod : 0;
-        const int col = c * 32 + i, w = col / 64, b = col % 64;
-        if constexpr (Q == 3) {
-          words[0][w] |= uint64_t(r != 0) << b;
-          words[1][w] |= uint64_t(r == 2) << b;
-        } else if constexpr (Q == 4) {
-          words[0][w] |= uint64_t(r) << b;
-        } else {
-#pragma unroll
-          for (int p = 0; p < P; ++p) words[p][w] |= uint64_t((r >> p) & 1) << b;
+            for (int p = 0; p < P; ++p) words[p][w] |= uint64_t((r >> p) & 1) << bit;
+          }
         }
       }
-    }
-    if (row < prm.m && !*abort_flag) {
-      if constexpr (Q == 4) {
-        uint64_t *dst = prm.C + (int64_t(prm.plane) * prm.m + row) * prm.pc + n0 / 64;
+      // the accumulator has been read: hand it back to the MMA warp
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(accempty + 8 * b);
+      if (row < prm.m) {
+        if constexpr (Q == 4) {
+          uint64_t *dst = prm.C + (int64_t(prm.plane) * prm.m + row) * prm.pc + w0;
 #pragma unroll
-        for (int w = 0; w < BN / 64; ++w) dst[w] = words[0][w];
-      } else {
+          for (int w = 0; w < BN / 64; ++w) dst[w] = words[0][w];
+        } else {
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-          uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + n0 / 64;
+          for (int p = 0; p < P; ++p) {
+            uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + w0;
 #pragma unroll
-          for (int w = 0; w < BN / 64; ++w) dst[w] = words[p][w];
+            for (int w = 0; w < BN / 64; ++w) dst[w] = words[p][w];
+          }
         }
       }
     }
@@ -406,11 +459,18 @@ int gemm(const uint16_t *Ab, const uint16_t *Bt, uint64_t *C, int64_t m, int64_t
   prm.m = m;
   prm.pc = pc;
   prm.ksteps = int(la / BK);
+  prm.mblocks = int(cdiv(m, BM));
+  prm.nblocks = int(npad / BN);
+  const int64_t tiles = int64_t(prm.mblocks) * prm.nblocks;
+  if (tiles >= (int64_t(1) << 31)) return FQ_ENOTSUP;
+  prm.tiles = int(tiles);
   prm.plane = plane;
   prm.err = err;
+  int dev = 0, sms = 0;
+  FQ_CUDA_TRY(cudaGetDevice(&dev));
+  FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-  const dim3 grid(unsigned(npad / BN), unsigned(cdiv(m, BM)));
-  if (grid.y > 65535u) return FQ_ENOTSUP;
+  const int grid = int(tiles < sms ? tiles : sms);
   tc_gemm_kernel<Q, P><<<grid, THREADS, SMEM, s>>>(ma, mb, prm);
   FQ_LAUNCH_CHECK();
   return FQ_OK;
