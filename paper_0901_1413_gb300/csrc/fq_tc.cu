@@ -2,31 +2,30 @@
 //
 // The same product C = A B as the Four-Russians path, as a dense contraction
 // of small integers.  The integer tcgen05 kind is not available on sm_103a, so
-// residues enter kind::f16 with bf16 operands and fp32 accumulation, which is
-// exact here: balanced residues |a|, |b| <= (p - 1) / 2 are exact in bf16,
-// every product is an exact small integer, and every partial sum of l of them
-// stays an integer below 2^24 in magnitude (the launcher checks l * B^2 <
-// 2^24 and otherwise takes the mma.sync s8 path), so no rounding ever happens.
-// The epilogue reads the fp32 accumulators from TMEM, reduces mod p and packs
-// the residues into bit-planes.
+// residues enter kind::f8f6f4 with e4m3 operands and fp32 accumulation, which
+// is exact here: balanced residues |a|, |b| <= (p - 1) / 2 <= 3 are exact in
+// e4m3 (1, 2, 3 = 1.000, 1.000 x 2, 1.100 x 2 in binary), every product is an
+// exact small integer, and every partial sum of l of them stays an integer
+// below 2^24 in magnitude (the launcher checks l * B^2 < 2^24 and otherwise
+// takes the mma.sync s8 path), so no rounding ever happens.  The epilogue
+// reads the fp32 accumulators from TMEM, reduces mod p and packs the residues
+// into bit-planes.
 //
 // GF(4) follows Section 4.3 at matrix level with two stacked products over
 // F_2: [A0 | A1] [B0 ; B1] = A0 B0 + A1 B1 (plane 0) and
 // [A0 + A1 | A0] [B0 + B1 ; B0] = (A0 + A1)(B0 + B1) + A0 B0 (plane 1), each
 // read mod 2.
 //
-// Layout.  The operands are first converted from planes to bf16: A as m rows
-// of la = roundup(l, 64) values, B transposed to n_pad rows of la values (K
-// contiguous for both, as the tensor core reads them), zero past l.  One
+// Layout.  The operands are first converted from planes to e4m3 bytes: A as m
+// rows of la = roundup(l, 128) values, B transposed to n_pad rows of la values
+// (K contiguous for both, as the tensor core reads them), zero past l.  One
 // persistent CTA per SM walks 128 x 256 tiles of C in groups of 8 row blocks:
-// one thread issues TMA loads of 64-column slices of A and B into a 4-stage
+// one thread issues TMA loads of 128-byte slices of A and B into a 4-stage
 // ring (128-byte swizzle), one thread issues the tcgen05.mma instructions
-// (M = 128, N = 256, K = 16) into one of two 256-column TMEM accumulators,
+// (M = 128, N = 256, K = 32) into one of two 256-column TMEM accumulators,
 // and a warpgroup reads the other accumulator back (tcgen05.ld) and writes
 // the packed codes, so a tile's epilogue overlaps the next tile's products.
 // Every mbarrier wait is bounded.
-#include <cuda_bf16.h>
-
 #include <cstring>
 
 #include "../../include/fq.h"
@@ -37,8 +36,8 @@ namespace fqk {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BM = 128, BN = 256, BK = 128, UK = 32, STAGES = 4;  // BK, UK: k per stage, per MMA (bytes)
+constexpr int A_BYTES = BM * BK, B_BYTES = BN * BK, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int ACC = 2;                         // TMEM accumulators (epilogue overlaps the next tile)
 constexpr int BAR_OFF = STAGES * STAGE_BYTES;  // full[S], empty[S], accfull[ACC], accempty[ACC], tmem slot, abort
 constexpr int NBARS = 2 * STAGES + 2 * ACC;
@@ -49,12 +48,11 @@ constexpr int GROUP_M = 8;                     // tile order: groups of 8 row bl
 
 // ---------------------------------------------------------- conversions --
 
-// bf16 bit pattern of a small integer (sign, exponent, mantissa of 0, +-1,
-// +-2, +-3; exact).
-__host__ __device__ constexpr uint32_t bf16_pattern(int v) {
+// e4m3 byte of a small integer (sign, 4 exponent bits biased by 7, 3 mantissa
+// bits): 0, +-1, +-2, +-3 are exact.
+__host__ __device__ constexpr uint32_t e4m3_byte(int v) {
   return v == 0 ? 0u
-                : ((v < 0 ? 0x8000u : 0u) |
-                   ((v == 1 || v == -1) ? 0x3F80u : ((v == 2 || v == -2) ? 0x4000u : 0x4040u)));
+                : ((v < 0 ? 0x80u : 0u) | ((v == 1 || v == -1) ? 0x38u : ((v == 2 || v == -2) ? 0x40u : 0x44u)));
 }
 
 // Balanced value of a code (the bits of the element in planes 0, 1, 2).
@@ -70,11 +68,11 @@ __host__ __device__ constexpr int code_value(int code) {
   return code & 1;
 }
 
-// Byte `half` (0 low, 1 high) of the patterns of codes 4 g .. 4 g + 3.
+// The e4m3 bytes of codes 4 g .. 4 g + 3, one per byte.
 template <int Q>
-__host__ __device__ constexpr uint32_t table_word(int half, int g) {
+__host__ __device__ constexpr uint32_t table_word(int g) {
   uint32_t w = 0;
-  for (int i = 0; i < 4; ++i) w |= ((bf16_pattern(code_value<Q>(4 * g + i)) >> (8 * half)) & 0xFFu) << (8 * i);
+  for (int i = 0; i < 4; ++i) w |= e4m3_byte(code_value<Q>(4 * g + i)) << (8 * i);
   return w;
 }
 
@@ -91,11 +89,12 @@ __device__ __forceinline__ uint32_t spread4(uint32_t b) {
   return (x | (x << 3)) & 0x1111u;
 }
 
-// Four elements e .. e + 3 of one word group (planes x) as four bf16 values
-// (two 32-bit words): the codes become a byte-permute selector into the
-// pattern tables.  `sel` picks, for GF(4), plane 0, plane 1 or their sum.
+// Elements e .. e + 3 of one word group (planes x) as four e4m3 bytes: the
+// codes become a byte-permute selector into the table (selector nibbles stay
+// below 8, so no sign replication).  `sel` picks, for GF(4), plane 0, plane 1
+// or their sum.
 template <int Q, int P>
-__device__ __forceinline__ void bf16x4(const uint64_t (&x)[P], int e, int sel, uint32_t &w0, uint32_t &w1) {
+__device__ __forceinline__ uint32_t e4m3x4(const uint64_t (&x)[P], int e, int sel) {
   uint32_t c;
   if constexpr (Q == 4) {
     const uint64_t b = sel == 0 ? x[0] : (sel == 1 ? x[1] : (x[0] ^ x[1]));
@@ -105,50 +104,45 @@ __device__ __forceinline__ void bf16x4(const uint64_t (&x)[P], int e, int sel, u
 #pragma unroll
     for (int p = 0; p < P; ++p) c |= spread4(uint32_t(x[p] >> e) & 0xFu) << p;
   }
-  constexpr uint32_t L0 = table_word<Q>(0, 0), L1 = table_word<Q>(0, 1);
-  constexpr uint32_t H0 = table_word<Q>(1, 0), H1 = table_word<Q>(1, 1);
-  const uint32_t lo = prmt(L0, L1, c);
-  const uint32_t hi = prmt(H0, H1, c);
-  w0 = prmt(lo, hi, 0x5140u);  // elements e, e + 1
-  w1 = prmt(lo, hi, 0x7362u);  // elements e + 2, e + 3
+  constexpr uint32_t T0 = table_word<Q>(0), T1 = table_word<Q>(1);
+  return prmt(T0, T1, c);
 }
 
-// Rows of a planes matrix to bf16 values: out[r * ld + off + c] for c < cols
-// (cols may run into the planes' zero padding, which gives zeros).  One thread
-// per 8 elements (a 16-byte store), so that a warp writes 512 contiguous bytes.
+// Rows of a planes matrix to e4m3 bytes: out[r * ld + off + c] for c < cols,
+// cols and off multiples of 16 (cols may run into the planes' zero padding,
+// which gives zeros).  One thread per 16 elements (a 16-byte store), so that
+// a warp writes 512 contiguous bytes; a thread walks RPT rows.
+constexpr int RPT = 4;
 template <int Q, int P>
-__global__ void rows_to_bf16(const uint64_t *__restrict__ X, int64_t rows, int64_t cols, int64_t pitch,
-                             uint16_t *__restrict__ out, int64_t ld, int64_t off, int sel) {
-  // grid: x over the 16-byte pieces of a row, y over rows (grid-stride)
-  const int piece = int(blockIdx.x) * int(blockDim.x) + int(threadIdx.x);
-  const int w = piece >> 3, e0 = 8 * (piece & 7);
-  const int64_t c0 = int64_t(w) * 64 + e0;
+__global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64_t cols, int64_t pitch,
+                             uint8_t *__restrict__ out, int64_t ld, int64_t off, int sel) {
+  // grid: x over the 16-byte pieces of a row, y over groups of rows (grid-stride)
+  const int64_t piece = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t w = piece >> 2;
+  const int e0 = 16 * int(piece & 3);
+  const int64_t c0 = w * 64 + e0;
   if (c0 >= cols) return;
-  const bool vec = c0 + 8 <= cols && ((off & 7) == 0);
   for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
     uint64_t x[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) x[p] = __ldg(X + (p * rows + r) * pitch + w);
-    uint32_t v[4];
-    bf16x4<Q, P>(x, e0, sel, v[0], v[1]);
-    bf16x4<Q, P>(x, e0 + 4, sel, v[2], v[3]);
-    uint16_t *dst = out + r * ld + off + c0;
-    if (vec) {
-      *reinterpret_cast<uint4 *>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
-    } else {
-      for (int k = 0; k < 8 && c0 + k < cols; ++k) dst[k] = uint16_t(v[k >> 1] >> (16 * (k & 1)));
-    }
+    uint4 v;
+    v.x = e4m3x4<Q, P>(x, e0, sel);
+    v.y = e4m3x4<Q, P>(x, e0 + 4, sel);
+    v.z = e4m3x4<Q, P>(x, e0 + 8, sel);
+    v.w = e4m3x4<Q, P>(x, e0 + 12, sel);
+    *reinterpret_cast<uint4 *>(out + r * ld + off + c0) = v;
   }
 }
 
-// Launch shape of rows_to_bf16 for rows x cols.
+// Launch shape of rows_to_e4m3 for rows x cols (cols a multiple of 16).
 inline dim3 rows_grid(int64_t rows, int64_t cols) {
-  const int64_t pieces = cdiv(cols, 64) * 8;
-  return dim3(unsigned(cdiv(pieces, 256)), unsigned(rows < 65535 ? (rows > 0 ? rows : 1) : 65535));
+  const int64_t pieces = cols / 16, ys = cdiv(rows, RPT);
+  return dim3(unsigned(cdiv(pieces, 256)), unsigned(ys < 65535 ? (ys > 0 ? ys : 1) : 65535));
 }
 
 // Zeros out[r * ld + c] for c in [from, ld): depth padding of the operands.
-__global__ void zero_tail(uint16_t *out, int64_t rows, int64_t ld, int64_t from) {
+__global__ void zero_tail(uint8_t *out, int64_t rows, int64_t ld, int64_t from) {
   const int64_t width = ld - from, total = rows * width;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
        i += int64_t(gridDim.x) * blockDim.x) {
@@ -207,7 +201,7 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-// Shared-memory matrix descriptor of a K-major bf16 tile with 128-byte rows
+// Shared-memory matrix descriptor of a K-major tile with 128-byte rows
 // and the 128-byte swizzle: start address, leading byte offset 16 (unused by
 // this layout), stride 1024 bytes between 8-row groups, descriptor version 1,
 // layout type 2 (128-byte swizzle).
@@ -221,14 +215,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
-// K-major, N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+// Instruction descriptor, kind::f8f6f4: fp32 accumulator (bits 4-5 = 1), e4m3
+// A and B (bits 7-9, 10-12 = 0), both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
       : "memory");
 }
@@ -265,7 +259,7 @@ __device__ __forceinline__ void wait_bar(uint32_t bar, uint32_t parity, volatile
 struct GemmParams {
   uint64_t *C;
   int64_t m, pc;   // rows of C, pitch words of C
-  int ksteps;      // la / 64
+  int ksteps;      // la / 128
   int mblocks, nblocks, tiles;
   int plane;       // GF(4): the plane this product writes
   unsigned *err;
@@ -355,8 +349,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a_src = base + uint32_t(s * STAGE_BYTES), b_src = a_src + A_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk)
-          mma_bf16(d, smem_desc(a_src + 32 * kk), smem_desc(b_src + 32 * kk), (ks | kk) != 0);
+        for (int kk = 0; kk < BK / UK; ++kk)
+          mma_e4m3(d, smem_desc(a_src + UK * kk), smem_desc(b_src + UK * kk), (ks | kk) != 0);
         mma_commit(empty + 8 * s);  // the stage is free once these MMAs have read it
       }
       mma_commit(accfull + 8 * b);  // this tile's accumulator is complete
@@ -431,15 +425,15 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // ------------------------------------------------------------------ host --
 
-int make_map(CUtensorMap *map, const uint16_t *ptr, int64_t inner, int64_t rows, int box_rows) {
+int make_map(CUtensorMap *map, const uint8_t *ptr, int64_t inner, int64_t rows, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (int rc = tensor_map_encoder(&encode)) return rc;
   memset(map, 0, sizeof(*map));
   const cuuint64_t dims[2] = {cuuint64_t(inner), cuuint64_t(rows)};
-  const cuuint64_t strides[1] = {cuuint64_t(inner) * 2u};
+  const cuuint64_t strides[1] = {cuuint64_t(inner)};
   const cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult cr = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(ptr), dims, strides,
+  const CUresult cr = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(ptr), dims, strides,
                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return cr == CUDA_SUCCESS ? FQ_OK : FQ_EINVAL;
@@ -447,7 +441,7 @@ int make_map(CUtensorMap *map, const uint16_t *ptr, int64_t inner, int64_t rows,
 
 
 template <int Q, int P>
-int gemm(const uint16_t *Ab, const uint16_t *Bt, uint64_t *C, int64_t m, int64_t la, int64_t npad, int64_t pc,
+int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t la, int64_t npad, int64_t pc,
          int plane, cudaStream_t s) {
   unsigned *err = nullptr;
   if (int rc = status_word(&err)) return rc;
@@ -477,17 +471,19 @@ int gemm(const uint16_t *Ab, const uint16_t *Bt, uint64_t *C, int64_t m, int64_t
 }
 
 // Prepared operands in a workspace: per round (GF(4) has two, the other
-// fields one) A as m x la bf16, then B transposed as npad x la bf16; after
-// the rounds, B's planes bit-transposed (P planes of npad rows of pt words).
+// fields one) A as m x la e4m3 bytes, then B transposed as npad x la bytes;
+// after the rounds, B's planes bit-transposed (P planes of npad rows of pt
+// words).  GF(4) stacks two segments of seg = roundup(l, 16) columns.
 struct Layout {
   int rounds;
-  int64_t la, npad, pc, pt, a_elems, b_elems;
+  int64_t seg, la, npad, pc, pt, a_elems, b_elems;
 };
 
 inline Layout layout_for(int q, int64_t m, int64_t l, int64_t n) {
   Layout lo;
   lo.rounds = q == 4 ? 2 : 1;
-  lo.la = cdiv(q == 4 ? 2 * l : l, BK) * BK;
+  lo.seg = cdiv(l, 16) * 16;
+  lo.la = cdiv(q == 4 ? 2 * lo.seg : l, BK) * BK;
   lo.pc = fq_pitch_words(n);
   lo.npad = lo.pc * 64;
   lo.pt = fq_pitch_words(l);
@@ -501,42 +497,44 @@ inline int64_t transposed_words(int q, const Layout &lo) {
 }
 
 template <int Q, int P>
-int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint16_t *ws, cudaStream_t s) {
+int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint8_t *ws, cudaStream_t s) {
   const Layout lo = layout_for(Q, m, l, n);
   const int64_t pa = fq_pitch_words(l);
-  uint64_t *BT = reinterpret_cast<uint64_t *>(ws + lo.rounds * (lo.a_elems + lo.b_elems));
+  uint64_t *BT = reinterpret_cast<uint64_t *>(ws + lo.rounds * (lo.a_elems + lo.b_elems));  // 8-byte aligned: la % 128 == 0
   const int64_t blocks = int64_t(P) * (lo.pt / 4) * lo.pc * 2;  // 256 x 32 bit blocks, 8 per CTA
   transpose_planes<P><<<unsigned(cdiv(blocks, 8) < 152 * 32 ? cdiv(blocks, 8) : 152 * 32), 256, 0, s>>>(
       B, l, lo.pc, BT, lo.pt);
   const dim3 ga = rows_grid(m, lo.la), gb = rows_grid(lo.npad, lo.la);
   if (Q == 4) {
-    // round 0: [A0 | A1] [B0 ; B1];  round 1: [A0 + A1 | A0] [B0 + B1 ; B0]
+    // round 0: [A0 | A1] [B0 ; B1];  round 1: [A0 + A1 | A0] [B0 + B1 ; B0].
+    // A segment's columns l .. seg - 1 come from the planes' zero padding.
     const int sa[2][2] = {{0, 1}, {2, 0}};
-    const dim3 ha = rows_grid(m, l), hb = rows_grid(lo.npad, l);
+    const int64_t seg = lo.seg;
+    const dim3 ha = rows_grid(m, seg), hb = rows_grid(lo.npad, seg);
     for (int r = 0; r < 2; ++r) {
-      uint16_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
-      rows_to_bf16<Q, P><<<ha, 256, 0, s>>>(A, m, l, pa, a, lo.la, 0, sa[r][0]);
-      rows_to_bf16<Q, P><<<ha, 256, 0, s>>>(A, m, l, pa, a, lo.la, l, sa[r][1]);
-      rows_to_bf16<Q, P><<<hb, 256, 0, s>>>(BT, lo.npad, l, lo.pt, b, lo.la, 0, sa[r][0]);
-      rows_to_bf16<Q, P><<<hb, 256, 0, s>>>(BT, lo.npad, l, lo.pt, b, lo.la, l, sa[r][1]);
-      if (2 * l < lo.la) {  // depth padding past the two stacked segments
-        zero_tail<<<grid_for(m * (lo.la - 2 * l)), 256, 0, s>>>(a, m, lo.la, 2 * l);
-        zero_tail<<<grid_for(lo.npad * (lo.la - 2 * l)), 256, 0, s>>>(b, lo.npad, lo.la, 2 * l);
+      uint8_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
+      rows_to_e4m3<Q, P><<<ha, 256, 0, s>>>(A, m, seg, pa, a, lo.la, 0, sa[r][0]);
+      rows_to_e4m3<Q, P><<<ha, 256, 0, s>>>(A, m, seg, pa, a, lo.la, seg, sa[r][1]);
+      rows_to_e4m3<Q, P><<<hb, 256, 0, s>>>(BT, lo.npad, seg, lo.pt, b, lo.la, 0, sa[r][0]);
+      rows_to_e4m3<Q, P><<<hb, 256, 0, s>>>(BT, lo.npad, seg, lo.pt, b, lo.la, seg, sa[r][1]);
+      if (2 * seg < lo.la) {  // depth padding past the two stacked segments
+        zero_tail<<<grid_for(m * (lo.la - 2 * seg)), 256, 0, s>>>(a, m, lo.la, 2 * seg);
+        zero_tail<<<grid_for(lo.npad * (lo.la - 2 * seg)), 256, 0, s>>>(b, lo.npad, lo.la, 2 * seg);
       }
     }
   } else {
-    rows_to_bf16<Q, P><<<ga, 256, 0, s>>>(A, m, lo.la, pa, ws, lo.la, 0, 0);
-    rows_to_bf16<Q, P><<<gb, 256, 0, s>>>(BT, lo.npad, lo.la, lo.pt, ws + lo.a_elems, lo.la, 0, 0);
+    rows_to_e4m3<Q, P><<<ga, 256, 0, s>>>(A, m, lo.la, pa, ws, lo.la, 0, 0);
+    rows_to_e4m3<Q, P><<<gb, 256, 0, s>>>(BT, lo.npad, lo.la, lo.pt, ws + lo.a_elems, lo.la, 0, 0);
   }
   FQ_LAUNCH_CHECK();
   return FQ_OK;
 }
 
 template <int Q, int P>
-int multiply(int64_t m, int64_t l, int64_t n, const uint16_t *ws, uint64_t *C, cudaStream_t s) {
+int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, cudaStream_t s) {
   const Layout lo = layout_for(Q, m, l, n);
   for (int r = 0; r < lo.rounds; ++r) {
-    const uint16_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
+    const uint8_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
     if (int rc = gemm<Q, P>(a, b, C, m, lo.la, lo.npad, lo.pc, r, s)) return rc;
   }
   return FQ_OK;
@@ -551,30 +549,30 @@ int64_t tc_max_l(int q) {
   return q == 4 ? lim / 2 : lim;
 }
 
-// Modelled time (SM cycles): waves of 128 x 256 tiles (one CTA per SM) times
-// 64-column k-steps at the measured ~1100 cycles each, the operand conversion
-// at about 5 TB/s, and a constant for the launches (fitted on GB300).  GF(4)
-// runs two products of twice the depth.
+// Modelled time (SM cycles): waves of 128 x 256 tiles (one persistent CTA per
+// SM) times 128-deep k-steps at the measured ~1100 cycles each, the operand
+// conversion at about 5 TB/s, and a constant for the launches (fitted on
+// GB300).  GF(4) runs two products of twice the depth.
 double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
-  const int64_t la = cdiv(q == 4 ? 2 * l : l, tc::BK) * tc::BK;
+  const int64_t la = cdiv(q == 4 ? 2 * cdiv(l, 16) * 16 : l, tc::BK) * tc::BK;
   const int64_t npad = fq_pitch_words(n) * 64;
   const int64_t ctas = (npad / tc::BN) * cdiv(m, tc::BM);
   const double products = q == 4 ? 2.0 : 1.0;
   const double gemm = double(cdiv(ctas, sms)) * double(la / tc::BK) * 1100.0;
-  const double convert = double(m + npad) * double(la) * 2.0 * 2.07e9 / 5.0e12;
+  const double convert = double(m + npad) * double(la) * 2.07e9 / 5.0e12;
   return products * (gemm + convert) + 30000.0;
 }
 
 int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n) {
   if (!(q == 2 || q == 3 || q == 4 || q == 5 || q == 7) || m < 0 || l < 0 || n < 0 || l > tc_max_l(q)) return -1;
   const tc::Layout lo = tc::layout_for(q, m, l, n);
-  return int64_t(lo.rounds) * (lo.a_elems + lo.b_elems) * 2 + tc::transposed_words(q, lo) * 8;
+  return int64_t(lo.rounds) * (lo.a_elems + lo.b_elems) + tc::transposed_words(q, lo) * 8;
 }
 
 int tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, void *ws,
                cudaStream_t s) {
   if (l == 0 || m == 0 || n == 0) return FQ_OK;
-  uint16_t *w = static_cast<uint16_t *>(ws);
+  uint8_t *w = static_cast<uint8_t *>(ws);
   switch (q) {
     case 2: return tc::prepare<2, 1>(m, l, n, A, B, w, s);
     case 3: return tc::prepare<3, 2>(m, l, n, A, B, w, s);
@@ -591,7 +589,7 @@ int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t
     FQ_CUDA_TRY(cudaMemsetAsync(C, 0, size_t(fq_planes(q)) * size_t(m) * size_t(fq_pitch_words(n)) * 8u, s));
     return FQ_OK;
   }
-  const uint16_t *w = static_cast<const uint16_t *>(ws);
+  const uint8_t *w = static_cast<const uint8_t *>(ws);
   switch (q) {
     case 2: return tc::multiply<2, 1>(m, l, n, w, C, s);
     case 3: return tc::multiply<3, 2>(m, l, n, w, C, s);

@@ -126,10 +126,13 @@ def test_autotune_cache_host_side(lib):
     assert lib.fq_auto_choice(3, 0, 10, 10, ctypes.byref(p), ctypes.byref(k)) == fq.OK
     assert (p.value, k.value) == (fq.PATH_M4RM, 0)
     # tensor-core workspace sizes (host-only)
-    # bf16 operands (A: m x la, B transposed: 64 pitch(n) x la), then B's planes
-    # bit-transposed (planes x 64 pitch(n) rows x pitch(l) words)
-    assert lib.fq_tc_workspace_bytes(3, 100, 200, 300) == 2 * (100 + 1024) * 256 + 2 * 1024 * 16 * 8
-    assert lib.fq_tc_workspace_bytes(4, 100, 200, 300) == 2 * 2 * (100 + 1024) * 448 + 2 * 1024 * 16 * 8
+    # e4m3 operand bytes (A: m x la, B transposed: 64 pitch(n) x la, la = l up
+    # to a multiple of 128), then B's planes bit-transposed (planes x 64 pitch(n)
+    # rows x pitch(l) words); GF(4): two rounds of two segments of l up to 16
+    assert lib.fq_tc_workspace_bytes(3, 100, 200, 300) == (100 + 1024) * 256 + 2 * 1024 * 16 * 8
+    assert lib.fq_tc_workspace_bytes(4, 100, 200, 300) == 2 * (100 + 1024) * 512 + 2 * 1024 * 16 * 8
+    assert lib.fq_tc_workspace_bytes(4, 1, 64, 1) == 2 * (1 + 1024) * 128 + 2 * 1024 * 16 * 8
+    assert lib.fq_tc_workspace_bytes(4, 1, 65, 1) == 2 * (1 + 1024) * 256 + 2 * 1024 * 16 * 8
     assert lib.fq_tc_workspace_bytes(6, 100, 200, 300) == -1
     assert lib.fq_tc_workspace_bytes(9, 100, 200, 300) == -1
     assert lib.fq_tc_workspace_bytes(7, 10, 2_000_000, 10) == -1                 # beyond exact fp32 sums

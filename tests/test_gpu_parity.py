@@ -324,6 +324,36 @@ def test_tcgen05_exact_near_its_range(fq):
     assert (got == (9 * l) % 7).all()
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("q, l, codes", [(7, None, (1, 2, 3)), (3, 1 << 22, (0, 1))])
+def test_tcgen05_exact_with_random_low_bits(fq, q, l, codes):
+    """Rows of A all +3 (F_7) or all +1 (F_3) against random positive B: every
+    step of the tensor-core sum adds a random amount, so an accumulation that
+    dropped low bits anywhere on the way to 2^24 (F_7 at its longest exact l)
+    or 2^22 (F_3) would change the residues.  C = A B is a column sum of B."""
+    l = l or _tc_max_l(fq, q)
+    m, n = 3, 70
+    a = 3 if q == 7 else 1
+    A = np.full((m, l), a, np.uint8)
+    B = np.random.default_rng(q).choice(np.array(codes, np.uint8), size=(l, n))
+    got, _ = gpu_product(fq, q, A, B, path=fq.PATH_MMA)
+    want = (a * B.sum(axis=0, dtype=np.int64)) % q
+    assert (got == want[None, :]).all()
+
+
+def _tc_max_l(fq, q):
+    """Longest l the tcgen05 form takes for q (found through the workspace query)."""
+    lib = fq.load()
+    lo, hi = 1, 1 << 26
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if lib.fq_tc_workspace_bytes(q, 1, mid, 1) >= 0:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
 @pytest.mark.parametrize("q", FIELDS)
 @pytest.mark.parametrize("chunk", [64, 128, 1000])
 def test_mma_path_reduces_between_chunks(fq, q, chunk):
