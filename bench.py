@@ -14,8 +14,11 @@ against the classical product's work).
   ``speedup_vs_m4rm`` the factor between the two.
 * ``e2e``: the same products through the public API from pinned host residues:
   host->device copy, fq_pack, fq_matmul, fq_unpack, device->host copy.
-* ``roofline``: the dominant kernel, the tcgen05 product, at 2 m l n flops
-  per launch over its own event time, against the measured dense bf16 peak;
+* ``roofline``: the dominant kernel, the tcgen05 product (e4m3 operands), at
+  2 m l n flops per launch over its own event time, against the dense fp8
+  peak (the measured cuBLAS bf16 burst times the nominal fp8/bf16 ratio 2);
+  ``prepare``: the operand conversion's bytes over its time, against the
+  measured HBM copy bandwidth;
   ``m4rm.roofline``: the M4RM kernels against the integer-logic (LOP3) issue
   rate (the algorithmic LOP3 of every M4RM launch over the products' time).
 * ``cpu_baseline``: the CPU oracle on a bounded sample of rows of the same
@@ -59,6 +62,22 @@ def cdiv(a, b):
     return -(-a // b)
 
 
+# Launches of one F_3 tensor-core product: A to e4m3, B's planes to e4m3 B^T,
+# the tcgen05 product.
+TC_LAUNCHES = 3
+
+
+def pitch_words(cols):
+    return cdiv(max(cols, 1), 1024) * 16
+
+
+def prepare_bytes(m, l, n, planes=2):
+    """Algorithmic DRAM bytes of the F_3 operand conversion: both planes of A
+    and of B read, e4m3 A and B^T written."""
+    la, npad = cdiv(l, 128) * 128, pitch_words(n) * 64
+    return planes * (m * pitch_words(l) + l * pitch_words(n)) * 8 + (m + npad) * la
+
+
 def algorithmic_lop3(m, l, n, k):
     """LOP3 lane-ops of one F_3 product by M4RM: every (row, block, basis element)
     lookup adds one table row (ceil(n/32) word pairs), and every block's table of
@@ -78,7 +97,7 @@ def our_launches(levels):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sizes", type=str, default="",
@@ -126,9 +145,10 @@ class Dist:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms; only the
+    samples stamped inside the timed window (mark_start .. mark_stop) count."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
@@ -136,17 +156,39 @@ class ClockSampler:
         self.gpu_id = gpu_id
         self.proc = None
         self.path = None
+        self.window = [None, None]
 
     def start(self):
+        """Start sampling and wait (up to 5 s) for the first sample."""
         import tempfile
         fd, self.path = tempfile.mkstemp(prefix="fq_clocks_", suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+
+    def mark_start(self):
+        self.window[0] = time.time()
+
+    def mark_stop(self):
+        self.window[1] = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
 
     def stop(self):
         if self.proc is None:
@@ -160,17 +202,22 @@ class ClockSampler:
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) == 7:
+                if len(parts) == 8:
                     rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        lo, hi = self.window
+        inside = [r for r in rows if lo is not None and hi is not None and
+                  (self._stamp(r[0]) or 0.0) >= lo - 0.025 and (self._stamp(r[0]) or 0.0) <= hi + 0.025]
+        use = inside or rows
+        sm = [float(r[1]) for r in use if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in use if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in use for i in range(4) if r[4 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(use),
+                "window": "timed region" if inside else "whole run (no sample stamped inside the timed region)"}
 
 
 def sources_digest(names):
@@ -210,15 +257,20 @@ def measured_traffic(name, digest):
 
 
 def measured_peaks():
-    """Dense bf16 tensor peak for the roofline: the measured burst figure of
-    MEASURED_PEAKS.json when present, else 1900 TFLOP/s (an earlier GB300
-    measurement)."""
+    """Peaks for the rooflines: the measured dense bf16 burst of
+    MEASURED_PEAKS.json (else 1900 TFLOP/s, an earlier GB300 measurement); the
+    dense fp8 (e4m3) peak as twice that, the nominal ratio of the two (4.5 and
+    2.25 PFLOP/s); the measured HBM copy bandwidth (else 6800 GB/s)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             rec = json.load(f)
-        return {"bf16": float(rec["bf16_tflops"]), "note": "of measured: cuBLAS bf16 burst (MEASURED_PEAKS.json)"}
+        bf16, hbm = float(rec["bf16_tflops"]), float(rec["hbm_gbs"])
+        note = "of measured: cuBLAS bf16 burst x 2 (nominal fp8/bf16 ratio), MEASURED_PEAKS.json"
+        hbm_note = "of measured: HBM copy (MEASURED_PEAKS.json)"
     except (OSError, ValueError, KeyError):
-        return {"bf16": 1900.0, "note": "of fallback: 1.9 PFLOP/s bf16"}
+        bf16, hbm = 1900.0, 6800.0
+        note, hbm_note = "of fallback: 1.9 PFLOP/s bf16 x 2", "of fallback: 6.8 TB/s"
+    return {"bf16": bf16, "fp8": 2.0 * bf16, "note": note, "hbm": hbm, "hbm_note": hbm_note}
 
 
 def make_inputs(torch, inputs, prods, seed=0):
@@ -336,7 +388,7 @@ def main():
             if evs is not None:
                 evs[j][2].record(stream)
 
-    def timed(step_fn, steps, warmup):
+    def timed(step_fn, steps, warmup, sampler=None):
         for w in range(warmup):
             flush.fill_(w)
             step_fn()
@@ -346,10 +398,14 @@ def main():
         evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in packed] for _ in range(steps)]
         dist.barrier()
         torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.mark_start()
         for s_ in range(steps):
             flush.fill_(s_ + 1)
             step_fn(evs[s_])
         torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.mark_stop()
         dist.barrier()
         if fq.status() != fq.OK:
             raise SystemExit("device error in the timed region")
@@ -362,7 +418,7 @@ def main():
     uuid = str(getattr(props, "uuid", "")) or str(dist.local)
     clocks = ClockSampler(uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if len(uuid) > 30 else uuid))
     clocks.start()
-    stage, mean_ms = timed(step, args.steps, args.warmup)
+    stage, mean_ms = timed(step, args.steps, args.warmup, clocks)
     clk = clocks.stop()
     ops_step = sum(2.0 * m * l * n for (m, l, n, _) in prods)
     value = ops_step * dist.world / (mean_ms * 1e-3)
@@ -370,12 +426,18 @@ def main():
                    for j in range(len(prods))]
     product_ms = [sum(stage[s_][j][1] for s_ in range(args.steps)) / args.steps for j in range(len(prods))]
 
-    # Roofline of the dominant kernel, the tcgen05 product: 2 m l n flops (bf16
+    # Roofline of the dominant kernel, the tcgen05 product: 2 m l n flops (e4m3
     # operands, fp32 sums) per launch over the product stage's event time.
     peaks = measured_peaks()
     t_flops = sum(2.0 * m * l * n for f, (m, l, n, _) in zip(forms, prods) if f == "tensor")
     t_ms = sum(t for f, t in zip(forms, product_ms) if f == "tensor")
     achieved = t_flops / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
+    # The conversion stage: e4m3 bytes written (A: m x la, B^T: 64 pitch(n) x
+    # la) plus the planes read (A; B, then B^T's planes written and read).
+    prep_ms = sum(sum(stage[s_][j][0] for s_ in range(args.steps)) / args.steps
+                  for j, f in enumerate(forms) if f == "tensor")
+    prep_bytes = sum(prepare_bytes(m, l, n) for f, (m, l, n, _) in zip(forms, prods) if f == "tensor")
+    prep_gbs = prep_bytes / (prep_ms * 1e-3) / 1e9 if prep_ms > 0 else 0.0
     traffic_rec = measured_traffic("tc_f3_dram_traffic.json", tc_sources_digest())
     traffic = traffic_rec.get("bytes_per_launch") if traffic_rec else None
 
@@ -494,17 +556,21 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16 (exact integers, fp32 sums)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "e4m3 (exact integers, fp32 sums)", "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.sizes else "F_3 square n=" + args.sizes,
                        "q": Q, "products": [list(p) for p in prods],
                        "path": forms, "path_choice": "fq_autotune per shape: compiled M4RM kernels "
                                                      "(k in 6..10) and the tensor-core path",
                        "l2": "flushed (256 MiB write) before every step",
                        "parallelism": "replicas" if dist.world > 1 else "single GPU"},
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16"], "unit": "TFLOP/s",
-                         "frac": achieved / peaks["bf16"], "traffic": traffic,
-                         "peak_note": peaks["note"], "kernel": "tc_gemm_kernel (tcgen05 kind::f16, 128x256 tiles)",
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["fp8"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp8"], "traffic": traffic,
+                         "peak_note": peaks["note"],
+                         "kernel": "tc_gemm_kernel (tcgen05 kind::f8f6f4 e4m3, 128x256 tiles, persistent)",
                          "kernel_ms_per_step": sum(product_ms)},
+            "prepare": {"bound": "hbm", "ms_per_step": prep_ms, "bytes": prep_bytes, "achieved": prep_gbs,
+                        "peak": peaks["hbm"], "unit": "GB/s", "frac": prep_gbs / peaks["hbm"],
+                        "peak_note": peaks["hbm_note"]},
             "per_product_ms": per_product,
             "product_stage_ms": product_ms,
             "m4rm": m4rm,
@@ -512,7 +578,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": base,
             "clocks": clk,
-            "gpu_launches": args.steps * sum(3 if f == "tensor" else 1 for f in forms),
+            "gpu_launches": args.steps * sum(TC_LAUNCHES if f == "tensor" else 1 for f in forms),
         }
         print(json.dumps(line), flush=True)
     dist.done()

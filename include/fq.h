@@ -160,9 +160,8 @@ int fq_strassen_levels(int q, int64_t m, int64_t l, int64_t n, const fq_options 
  *   fq_tc_workspace_bytes: device bytes of the converted operands (A as m x la
  *     e4m3 bytes, B transposed as 64 * fq_pitch_words(n) x la, la = l rounded
  *     up to 128; GF(4) holds two such pairs, each of depth la = 2 s rounded up
- *     to 128 with s = l rounded up to 16, for its two stacked products) and
- *     B's bit-planes transposed on the way, or -1 outside the tcgen05 form
- *     (bad q, negative size, l too long);
+ *     to 128 with s = l rounded up to 16, for its two stacked products), or
+ *     -1 outside the tcgen05 form (bad q, negative size, l too long);
  *   fq_tc_prepare: A, B (planes buffers) -> workspace (16-byte aligned);
  *   fq_tc_multiply: workspace -> C (planes buffer, written entirely).
  * Both are asynchronous on `stream`; FQ_ENOTSUP outside the tcgen05 form. */

@@ -89,49 +89,88 @@ __device__ __forceinline__ uint32_t spread4(uint32_t b) {
   return (x | (x << 3)) & 0x1111u;
 }
 
-// Elements e .. e + 3 of one word group (planes x) as four e4m3 bytes: the
-// codes become a byte-permute selector into the table (selector nibbles stay
-// below 8, so no sign replication).  `sel` picks, for GF(4), plane 0, plane 1
-// or their sum.
+// Bits 0..3 of b to the low bit of bytes 0..3: b times 1 + 2^7 + 2^14 + 2^21
+// puts bit i at bit 8 i, and the four shifted copies of b do not overlap.
+__device__ __forceinline__ uint32_t bytes_of_bits(uint32_t b) { return (b * 0x204081u) & 0x01010101u; }
+
+// Elements e .. e + 3 as four e4m3 bytes, from 32-bit plane words t (element
+// i at bit i).  Q = 2 takes one plane (F_2, and a selected GF(4) plane): 1 ->
+// 0x38.  Q = 3: unit u, sign s -> u 0x38 | s 0x80 (u = 0, s = 1 gives -0,
+// which adds nothing, as code 2 stands for 0).  F_5, F_7: the 3-bit codes
+// become a byte-permute selector into the table (nibbles below 8, so no sign
+// replication).
 template <int Q, int P>
-__device__ __forceinline__ uint32_t e4m3x4(const uint64_t (&x)[P], int e, int sel) {
-  uint32_t c;
-  if constexpr (Q == 4) {
-    const uint64_t b = sel == 0 ? x[0] : (sel == 1 ? x[1] : (x[0] ^ x[1]));
-    c = spread4(uint32_t(b >> e) & 0xFu);
+__device__ __forceinline__ uint32_t e4m3x4(const uint32_t (&t)[P], int e) {
+  if constexpr (Q == 2) {
+    return bytes_of_bits((t[0] >> e) & 0xFu) * 0x38u;
+  } else if constexpr (Q == 3) {
+    const uint32_t u = (t[0] >> e) & 0xFu, sg = (t[1] >> e) & 0xFu;
+    return (bytes_of_bits(u) * 0x38u) | ((sg * 0x10204080u) & 0x80808080u);
   } else {
-    c = 0;
+    uint32_t c = 0;
 #pragma unroll
-    for (int p = 0; p < P; ++p) c |= spread4(uint32_t(x[p] >> e) & 0xFu) << p;
+    for (int p = 0; p < P; ++p) c |= spread4((t[p] >> e) & 0xFu) << p;
+    constexpr uint32_t T0 = table_word<Q>(0), T1 = table_word<Q>(1);
+    return prmt(T0, T1, c);
   }
-  constexpr uint32_t T0 = table_word<Q>(0), T1 = table_word<Q>(1);
-  return prmt(T0, T1, c);
+}
+
+// The planes a conversion reads: GF(4) becomes one F_2 plane, `sel` 0, 1 or
+// 2 picking plane 0, plane 1 or their sum; other fields pass through.
+template <int Q>
+struct ConvField {
+  static constexpr int Q2 = Q == 4 ? 2 : Q;
+  static constexpr int P2 = Q == 2 || Q == 4 ? 1 : (Q == 3 ? 2 : 3);
+};
+template <int Q, int P>
+__device__ __forceinline__ void select_planes(const uint32_t (&t)[P], int sel, uint32_t (&o)[ConvField<Q>::P2]) {
+  if constexpr (Q == 4) {
+    o[0] = sel == 0 ? t[0] : (sel == 1 ? t[1] : (t[0] ^ t[1]));
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) o[p] = t[p];
+  }
+}
+
+// Sixteen elements b0 .. b0 + 15 of the plane words as a 16-byte vector.
+template <int Q, int P>
+__device__ __forceinline__ uint4 e4m3x16(const uint32_t (&t)[P], int b0) {
+  using CF = ConvField<Q>;
+  return make_uint4(e4m3x4<CF::Q2, P>(t, b0), e4m3x4<CF::Q2, P>(t, b0 + 4), e4m3x4<CF::Q2, P>(t, b0 + 8),
+                    e4m3x4<CF::Q2, P>(t, b0 + 12));
 }
 
 // Rows of a planes matrix to e4m3 bytes: out[r * ld + off + c] for c < cols,
 // cols and off multiples of 16 (cols may run into the planes' zero padding,
-// which gives zeros).  One thread per 16 elements (a 16-byte store), so that
-// a warp writes 512 contiguous bytes; a thread walks RPT rows.
+// which gives zeros).  One thread per 16 elements (a 16-byte store), so that a
+// warp writes 512 contiguous bytes; a thread loads RPT rows' words before it
+// converts any of them.
 constexpr int RPT = 4;
 template <int Q, int P>
 __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64_t cols, int64_t pitch,
                              uint8_t *__restrict__ out, int64_t ld, int64_t off, int sel) {
-  // grid: x over the 16-byte pieces of a row, y over groups of rows (grid-stride)
+  using CF = ConvField<Q>;
+  // grid: x over the 16-byte pieces of a row, y over groups of RPT rows (grid-stride)
   const int64_t piece = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t w = piece >> 2;
-  const int e0 = 16 * int(piece & 3);
-  const int64_t c0 = w * 64 + e0;
+  const int64_t c0 = piece * 16;
   if (c0 >= cols) return;
-  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
-    uint64_t x[P];
+  const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
+  const int64_t half = piece >> 1;    // the 32-bit half word holding the 16 elements
+  const int b0 = 16 * int(piece & 1);
+  for (int64_t r0 = int64_t(blockIdx.y) * RPT; r0 < rows; r0 += int64_t(gridDim.y) * RPT) {
+    uint32_t t[RPT][P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) x[p] = __ldg(X + (p * rows + r) * pitch + w);
-    uint4 v;
-    v.x = e4m3x4<Q, P>(x, e0, sel);
-    v.y = e4m3x4<Q, P>(x, e0 + 4, sel);
-    v.z = e4m3x4<Q, P>(x, e0 + 8, sel);
-    v.w = e4m3x4<Q, P>(x, e0 + 12, sel);
-    *reinterpret_cast<uint4 *>(out + r * ld + off + c0) = v;
+    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        t[i][p] = r0 + i < rows ? __ldg(X32 + (p * rows + r0 + i) * pitch * 2 + half) : 0u;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      if (r0 + i >= rows) break;
+      uint32_t o[CF::P2];
+      select_planes<Q, P>(t[i], sel, o);
+      *reinterpret_cast<uint4 *>(out + (r0 + i) * ld + off + c0) = e4m3x16<Q, CF::P2>(o, b0);
+    }
   }
 }
 
@@ -139,6 +178,65 @@ __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64
 inline dim3 rows_grid(int64_t rows, int64_t cols) {
   const int64_t pieces = cols / 16, ys = cdiv(rows, RPT);
   return dim3(unsigned(cdiv(pieces, 256)), unsigned(ys < 65535 ? (ys > 0 ? ys : 1) : 65535));
+}
+
+// 32 x 32 bit transpose across a warp: afterwards bit i of lane j's word is
+// bit j of lane i's word before.  Five stages swap the off-diagonal s x s
+// blocks between lanes l and l ^ s (s = 16, 8, 4, 2, 1).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const uint32_t m = s == 16 ? 0x0000FFFFu : (s == 8 ? 0x00FF00FFu : (s == 4 ? 0x0F0F0F0Fu : (s == 2 ? 0x33333333u : 0x55555555u)));
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+  }
+  return x;
+}
+
+// B^T as e4m3 bytes straight from B's planes: out[j * ld + off + k] = the byte
+// of B[k][j] for every column j of the planes' pitch (n_pad = 64 pitch) and
+// k < kcols (a multiple of 16; rows k >= rows read as zero).  A CTA of eight
+// warps turns a 128 (k) x 256 (j) block around: warp w loads rows k0 + 32 (w %
+// 4) + lane, 128 columns from j0 + 128 (w / 4), transposes each 32 x 32 bit
+// block across the warp, converts lane j's 32 bits into 32 bytes and puts
+// them in a shared 256 x 128-byte tile (16-byte chunks XOR-swizzled by row, so
+// that eight lanes hit eight bank groups); the tile leaves in 128-byte rows.
+constexpr int TK = 128, TJ = 256;
+template <int Q, int P>
+__global__ void __launch_bounds__(256) planes_to_e4m3_t(const uint64_t *__restrict__ X, int64_t rows, int64_t pitch,
+                                                        uint8_t *__restrict__ out, int64_t ld, int64_t off,
+                                                        int64_t kcols, int sel) {
+  using CF = ConvField<Q>;
+  __shared__ uint4 tile[TJ * TK / 16];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k0 = int64_t(blockIdx.x) * TK, j0 = int64_t(blockIdx.y) * TJ;
+  const int kq = warp & 3, jh = warp >> 2;
+  const int64_t k = k0 + 32 * kq + lane;
+  const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
+  const int64_t h0 = (j0 + 128 * jh) / 32;  // first 32-bit half word of the warp's columns
+  uint32_t t[4][P];
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int p = 0; p < P; ++p) t[g][p] = k < rows ? __ldg(X32 + (p * rows + k) * pitch * 2 + h0 + g) : 0u;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    uint32_t o[CF::P2];
+    select_planes<Q, P>(t[g], sel, o);
+#pragma unroll
+    for (int p = 0; p < CF::P2; ++p) o[p] = transpose32(o[p], lane);
+    // lane: column jl of the tile, bit i = row k0 + 32 kq + i
+    const int jl = 128 * jh + 32 * g + lane, c0 = 2 * kq;
+    tile[jl * 8 + (c0 ^ (jl & 7))] = e4m3x16<Q, CF::P2>(o, 0);
+    tile[jl * 8 + ((c0 + 1) ^ (jl & 7))] = e4m3x16<Q, CF::P2>(o, 16);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = threadIdx.x; i < TJ * 8; i += 256) {
+    const int jl = i >> 3, c = i & 7;
+    const int64_t kk = k0 + 16 * c;
+    if (kk < kcols) *reinterpret_cast<uint4 *>(out + (j0 + jl) * ld + off + kk) = tile[jl * 8 + (c ^ (jl & 7))];
+  }
 }
 
 // Zeros out[r * ld + c] for c in [from, ld): depth padding of the operands.
@@ -154,42 +252,6 @@ __global__ void zero_tail(uint8_t *out, int64_t rows, int64_t ld, int64_t from) 
 int grid_for(int64_t total) {
   const int64_t want = cdiv(total, 256), cap = 152 * 16;
   return int(want < cap ? (want > 0 ? want : 1) : cap);
-}
-
-// Bit transpose of every plane: XT[p][c][r] = X[p][r][c] for r < rows and
-// every column c of X's pitch; XT has npad = 64 * pitch rows of pitch_t words
-// (rows past `rows` read as zero).  A warp turns 256 rows x 32 columns around
-// with 8 x 32 ballots and each lane stores its column's four words (32 bytes).
-template <int P>
-__global__ void transpose_planes(const uint64_t *__restrict__ X, int64_t rows, int64_t pitch, uint64_t *__restrict__ XT,
-                                 int64_t pitch_t) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
-  const int64_t rgroups = pitch_t / 4, cblocks = pitch * 2, total = int64_t(P) * rgroups * cblocks;
-  const int64_t npad = pitch * 64;
-  for (int64_t t = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); t < total; t += warps) {
-    const int64_t cb = t % cblocks, rg = (t / cblocks) % rgroups, p = t / cblocks / rgroups;
-    const int64_t c0 = cb * 32;
-    uint32_t v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int64_t r = rg * 256 + 32 * k + lane;
-      v[k] = r < rows ? uint32_t(__ldg(X + (p * rows + r) * pitch + c0 / 64) >> (c0 % 64)) : 0u;
-    }
-    uint32_t mine[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      mine[k] = 0;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const uint32_t col = __ballot_sync(0xFFFFFFFFu, (v[k] >> j) & 1u);
-        mine[k] = lane == j ? col : mine[k];
-      }
-    }
-    uint4 *dst = reinterpret_cast<uint4 *>(XT + (p * npad + c0 + lane) * pitch_t + rg * 4);
-    dst[0] = make_uint4(mine[0], mine[1], mine[2], mine[3]);
-    dst[1] = make_uint4(mine[4], mine[5], mine[6], mine[7]);
-  }
 }
 
 // ------------------------------------------------------------------ GEMM --
@@ -471,12 +533,11 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
 }
 
 // Prepared operands in a workspace: per round (GF(4) has two, the other
-// fields one) A as m x la e4m3 bytes, then B transposed as npad x la bytes;
-// after the rounds, B's planes bit-transposed (P planes of npad rows of pt
-// words).  GF(4) stacks two segments of seg = roundup(l, 16) columns.
+// fields one) A as m x la e4m3 bytes, then B transposed as npad x la bytes.
+// GF(4) stacks two segments of seg = roundup(l, 16) columns.
 struct Layout {
   int rounds;
-  int64_t seg, la, npad, pc, pt, a_elems, b_elems;
+  int64_t seg, la, npad, pc, a_elems, b_elems;
 };
 
 inline Layout layout_for(int q, int64_t m, int64_t l, int64_t n) {
@@ -486,45 +547,44 @@ inline Layout layout_for(int q, int64_t m, int64_t l, int64_t n) {
   lo.la = cdiv(q == 4 ? 2 * lo.seg : l, BK) * BK;
   lo.pc = fq_pitch_words(n);
   lo.npad = lo.pc * 64;
-  lo.pt = fq_pitch_words(l);
   lo.a_elems = m * lo.la;
   lo.b_elems = lo.npad * lo.la;
   return lo;
 }
 
-inline int64_t transposed_words(int q, const Layout &lo) {
-  return int64_t(q == 2 ? 1 : ((q == 5 || q == 7) ? 3 : 2)) * lo.npad * lo.pt;
+// B^T (npad x ld bytes from offset off) from B's planes, k < kcols.
+template <int Q, int P>
+void transpose_to(const uint64_t *B, int64_t l, int64_t pitch, int64_t npad, uint8_t *out, int64_t ld, int64_t off,
+                  int64_t kcols, int sel, cudaStream_t s) {
+  const dim3 grid(unsigned(cdiv(kcols, TK)), unsigned(npad / TJ));
+  planes_to_e4m3_t<Q, P><<<grid, 256, 0, s>>>(B, l, pitch, out, ld, off, kcols, sel);
 }
 
 template <int Q, int P>
 int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint8_t *ws, cudaStream_t s) {
   const Layout lo = layout_for(Q, m, l, n);
+  if (lo.npad / TJ > 65535) return FQ_ENOTSUP;
   const int64_t pa = fq_pitch_words(l);
-  uint64_t *BT = reinterpret_cast<uint64_t *>(ws + lo.rounds * (lo.a_elems + lo.b_elems));  // 8-byte aligned: la % 128 == 0
-  const int64_t blocks = int64_t(P) * (lo.pt / 4) * lo.pc * 2;  // 256 x 32 bit blocks, 8 per CTA
-  transpose_planes<P><<<unsigned(cdiv(blocks, 8) < 152 * 32 ? cdiv(blocks, 8) : 152 * 32), 256, 0, s>>>(
-      B, l, lo.pc, BT, lo.pt);
-  const dim3 ga = rows_grid(m, lo.la), gb = rows_grid(lo.npad, lo.la);
   if (Q == 4) {
     // round 0: [A0 | A1] [B0 ; B1];  round 1: [A0 + A1 | A0] [B0 + B1 ; B0].
     // A segment's columns l .. seg - 1 come from the planes' zero padding.
     const int sa[2][2] = {{0, 1}, {2, 0}};
     const int64_t seg = lo.seg;
-    const dim3 ha = rows_grid(m, seg), hb = rows_grid(lo.npad, seg);
+    const dim3 ha = rows_grid(m, seg);
     for (int r = 0; r < 2; ++r) {
       uint8_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
       rows_to_e4m3<Q, P><<<ha, 256, 0, s>>>(A, m, seg, pa, a, lo.la, 0, sa[r][0]);
       rows_to_e4m3<Q, P><<<ha, 256, 0, s>>>(A, m, seg, pa, a, lo.la, seg, sa[r][1]);
-      rows_to_e4m3<Q, P><<<hb, 256, 0, s>>>(BT, lo.npad, seg, lo.pt, b, lo.la, 0, sa[r][0]);
-      rows_to_e4m3<Q, P><<<hb, 256, 0, s>>>(BT, lo.npad, seg, lo.pt, b, lo.la, seg, sa[r][1]);
+      transpose_to<Q, P>(B, l, lo.pc, lo.npad, b, lo.la, 0, seg, sa[r][0], s);
+      transpose_to<Q, P>(B, l, lo.pc, lo.npad, b, lo.la, seg, seg, sa[r][1], s);
       if (2 * seg < lo.la) {  // depth padding past the two stacked segments
         zero_tail<<<grid_for(m * (lo.la - 2 * seg)), 256, 0, s>>>(a, m, lo.la, 2 * seg);
         zero_tail<<<grid_for(lo.npad * (lo.la - 2 * seg)), 256, 0, s>>>(b, lo.npad, lo.la, 2 * seg);
       }
     }
   } else {
-    rows_to_e4m3<Q, P><<<ga, 256, 0, s>>>(A, m, lo.la, pa, ws, lo.la, 0, 0);
-    rows_to_e4m3<Q, P><<<gb, 256, 0, s>>>(BT, lo.npad, lo.la, lo.pt, ws + lo.a_elems, lo.la, 0, 0);
+    rows_to_e4m3<Q, P><<<rows_grid(m, lo.la), 256, 0, s>>>(A, m, lo.la, pa, ws, lo.la, 0, 0);
+    transpose_to<Q, P>(B, l, lo.pc, lo.npad, ws + lo.a_elems, lo.la, 0, lo.la, 0, s);
   }
   FQ_LAUNCH_CHECK();
   return FQ_OK;
@@ -566,7 +626,7 @@ double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
 int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n) {
   if (!(q == 2 || q == 3 || q == 4 || q == 5 || q == 7) || m < 0 || l < 0 || n < 0 || l > tc_max_l(q)) return -1;
   const tc::Layout lo = tc::layout_for(q, m, l, n);
-  return int64_t(lo.rounds) * (lo.a_elems + lo.b_elems) + tc::transposed_words(q, lo) * 8;
+  return int64_t(lo.rounds) * (lo.a_elems + lo.b_elems);
 }
 
 int tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, void *ws,
