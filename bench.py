@@ -8,7 +8,7 @@ against the classical product's work).
 
 * ``value``: packed inputs resident in HBM, device time (CUDA events on the
   launching stream), L2 flushed before every step; each product runs in the
-  form fq_autotune picks for its shape (for these F_3 shapes the tcgen05
+  form FQ_PATH_AUTO takes for its shape (for these F_3 shapes the tcgen05
   tensor-core form: operand conversion, then the product kernel).
 * ``m4rm``: the same products by the plain bitsliced Four-Russians path, with
   ``speedup_vs_m4rm`` the factor between the two.
@@ -359,15 +359,11 @@ def main():
         packed.append((a, b, fq.empty(Q, m, n)))
     if fq.status() != fq.OK:
         raise SystemExit("device error while packing")
-    # Untimed set-up: fq_autotune on every shape (the compiled M4RM kernels,
-    # k in 6..10, and the tensor-core path) picks each product's form.  A
+    # Each product runs in the form FQ_PATH_AUTO takes for its shape (the
+    # library's time model, the same with or without a profiler attached).  A
     # tensor-core product runs as its two stages, operand conversion and the
     # tcgen05 product, so that the product kernel can be timed on its own.
-    tuned = {}
-    for (a, b, c), (m, l, n, _) in zip(packed, prods):
-        if (m, l, n) not in tuned:
-            tuned[(m, l, n)] = fq.autotune(a, b, out=c)
-    forms = ["tensor" if tuned[(m, l, n)]["path"] == fq.PATH_MMA else "m4rm" for (m, l, n, _) in prods]
+    forms = ["tensor" if fq.auto_choice(Q, m, l, n)[0] == fq.PATH_MMA else "m4rm" for (m, l, n, _) in prods]
     tops = [fq.TensorOperands(a, b) if f == "tensor" else None for f, (a, b, c) in zip(forms, packed)]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -559,8 +555,8 @@ def main():
             "vs_baseline": None, "dtype": "e4m3 (exact integers, fp32 sums)", "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.sizes else "F_3 square n=" + args.sizes,
                        "q": Q, "products": [list(p) for p in prods],
-                       "path": forms, "path_choice": "fq_autotune per shape: compiled M4RM kernels "
-                                                     "(k in 6..10) and the tensor-core path",
+                       "path": forms, "path_choice": "FQ_PATH_AUTO per shape (fq_auto_choice: the library's "
+                                                     "time model of M4RM and the tensor-core path)",
                        "l2": "flushed (256 MiB write) before every step",
                        "parallelism": "replicas" if dist.world > 1 else "single GPU"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["fp8"], "unit": "TFLOP/s",

@@ -150,7 +150,7 @@ int fq_strassen_levels(int q, int64_t m, int64_t l, int64_t n, const fq_options 
 
 /* ---- the tensor-core path in two stages -------------------------------------
  * FQ_PATH_MMA runs on the tcgen05 tensor cores (kind::f8f6f4: e4m3 operands,
- * fp32 accumulation) whenever l * ((p-1)/2)^2 < 2^24 (l < 2^23 for GF(4)):
+ * fp32 accumulation) whenever l * ((p-1)/2)^2 < 2^24 (l < 2^24 for GF(4)):
  * the balanced residues 0, +-1, +-2, +-3 are exact in e4m3 and every partial
  * sum is an integer below 2^24, so the fp32 sums are exact and the product is
  * bit-exact.  Longer l, or fq_options.chunk > 0, or fq_options.kernel = 1
@@ -159,9 +159,9 @@ int fq_strassen_levels(int q, int64_t m, int64_t l, int64_t n, const fq_options 
  * two stages so that a caller can keep the converted operands:
  *   fq_tc_workspace_bytes: device bytes of the converted operands (A as m x la
  *     e4m3 bytes, B transposed as 64 * fq_pitch_words(n) x la, la = l rounded
- *     up to 128; GF(4) holds two such pairs, each of depth la = 2 s rounded up
- *     to 128 with s = l rounded up to 16, for its two stacked products), or
- *     -1 outside the tcgen05 form (bad q, negative size, l too long);
+ *     up to 128; three such pairs for GF(4), whose product is three F_2
+ *     products by Section 4.3's Karatsuba form), or -1 outside the tcgen05
+ *     form (bad q, negative size, l too long);
  *   fq_tc_prepare: A, B (planes buffers) -> workspace (16-byte aligned);
  *   fq_tc_multiply: workspace -> C (planes buffer, written entirely).
  * Both are asynchronous on `stream`; FQ_ENOTSUP outside the tcgen05 form. */

@@ -11,10 +11,11 @@
 // reads the fp32 accumulators from TMEM, reduces mod p and packs the residues
 // into bit-planes.
 //
-// GF(4) follows Section 4.3 at matrix level with two stacked products over
-// F_2: [A0 | A1] [B0 ; B1] = A0 B0 + A1 B1 (plane 0) and
-// [A0 + A1 | A0] [B0 + B1 ; B0] = (A0 + A1)(B0 + B1) + A0 B0 (plane 1), each
-// read mod 2.
+// GF(4) follows Section 4.3 at matrix level with three F_2 products (the
+// Karatsuba form): X = A0 B0, Y = A1 B1, Z = (A0 + A1)(B0 + B1), each read mod
+// 2; then C's plane 0 = X + Y and plane 1 = Z + X (= A0 B1 + A1 B0 + A1 B1,
+// the coefficient of alpha once alpha^2 = alpha + 1 is folded in).  The first
+// product writes X into both planes, the other two add theirs in (XOR).
 //
 // Layout.  The operands are first converted from planes to e4m3 bytes: A as m
 // rows of la = roundup(l, 128) values, B transposed to n_pad rows of la values
@@ -239,21 +240,6 @@ __global__ void __launch_bounds__(256) planes_to_e4m3_t(const uint64_t *__restri
   }
 }
 
-// Zeros out[r * ld + c] for c in [from, ld): depth padding of the operands.
-__global__ void zero_tail(uint8_t *out, int64_t rows, int64_t ld, int64_t from) {
-  const int64_t width = ld - from, total = rows * width;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = i / width, c = from + (i - r * width);
-    out[r * ld + c] = 0;
-  }
-}
-
-int grid_for(int64_t total) {
-  const int64_t want = cdiv(total, 256), cap = 152 * 16;
-  return int(want < cap ? (want > 0 ? want : 1) : cap);
-}
-
 // ------------------------------------------------------------------ GEMM --
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
@@ -323,7 +309,7 @@ struct GemmParams {
   int64_t m, pc;   // rows of C, pitch words of C
   int ksteps;      // la / 128
   int mblocks, nblocks, tiles;
-  int plane;       // GF(4): the plane this product writes
+  int plane;       // GF(4): -1 writes both planes, 0 or 1 adds into that plane
   unsigned *err;
 };
 
@@ -463,9 +449,18 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (lane == 0) mbar_arrive_cta(accempty + 8 * b);
       if (row < prm.m) {
         if constexpr (Q == 4) {
-          uint64_t *dst = prm.C + (int64_t(prm.plane) * prm.m + row) * prm.pc + w0;
+          if (prm.plane < 0) {
 #pragma unroll
-          for (int w = 0; w < BN / 64; ++w) dst[w] = words[0][w];
+            for (int p = 0; p < 2; ++p) {
+              uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + w0;
+#pragma unroll
+              for (int w = 0; w < BN / 64; ++w) dst[w] = words[0][w];
+            }
+          } else {
+            uint64_t *dst = prm.C + (int64_t(prm.plane) * prm.m + row) * prm.pc + w0;
+#pragma unroll
+            for (int w = 0; w < BN / 64; ++w) dst[w] ^= words[0][w];
+          }
         } else {
 #pragma unroll
           for (int p = 0; p < P; ++p) {
@@ -532,19 +527,17 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
   return FQ_OK;
 }
 
-// Prepared operands in a workspace: per round (GF(4) has two, the other
+// Prepared operands in a workspace: per product (GF(4) has three, the other
 // fields one) A as m x la e4m3 bytes, then B transposed as npad x la bytes.
-// GF(4) stacks two segments of seg = roundup(l, 16) columns.
 struct Layout {
   int rounds;
-  int64_t seg, la, npad, pc, a_elems, b_elems;
+  int64_t la, npad, pc, a_elems, b_elems;
 };
 
 inline Layout layout_for(int q, int64_t m, int64_t l, int64_t n) {
   Layout lo;
-  lo.rounds = q == 4 ? 2 : 1;
-  lo.seg = cdiv(l, 16) * 16;
-  lo.la = cdiv(q == 4 ? 2 * lo.seg : l, BK) * BK;
+  lo.rounds = q == 4 ? 3 : 1;
+  lo.la = cdiv(l, BK) * BK;
   lo.pc = fq_pitch_words(n);
   lo.npad = lo.pc * 64;
   lo.a_elems = m * lo.la;
@@ -566,21 +559,11 @@ int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *
   if (lo.npad / TJ > 65535) return FQ_ENOTSUP;
   const int64_t pa = fq_pitch_words(l);
   if (Q == 4) {
-    // round 0: [A0 | A1] [B0 ; B1];  round 1: [A0 + A1 | A0] [B0 + B1 ; B0].
-    // A segment's columns l .. seg - 1 come from the planes' zero padding.
-    const int sa[2][2] = {{0, 1}, {2, 0}};
-    const int64_t seg = lo.seg;
-    const dim3 ha = rows_grid(m, seg);
-    for (int r = 0; r < 2; ++r) {
+    // the operands of X, Y, Z: A0, A1, A0 + A1 and B0, B1, B0 + B1 (sel 0, 1, 2)
+    for (int r = 0; r < 3; ++r) {
       uint8_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
-      rows_to_e4m3<Q, P><<<ha, 256, 0, s>>>(A, m, seg, pa, a, lo.la, 0, sa[r][0]);
-      rows_to_e4m3<Q, P><<<ha, 256, 0, s>>>(A, m, seg, pa, a, lo.la, seg, sa[r][1]);
-      transpose_to<Q, P>(B, l, lo.pc, lo.npad, b, lo.la, 0, seg, sa[r][0], s);
-      transpose_to<Q, P>(B, l, lo.pc, lo.npad, b, lo.la, seg, seg, sa[r][1], s);
-      if (2 * seg < lo.la) {  // depth padding past the two stacked segments
-        zero_tail<<<grid_for(m * (lo.la - 2 * seg)), 256, 0, s>>>(a, m, lo.la, 2 * seg);
-        zero_tail<<<grid_for(lo.npad * (lo.la - 2 * seg)), 256, 0, s>>>(b, lo.npad, lo.la, 2 * seg);
-      }
+      rows_to_e4m3<Q, P><<<rows_grid(m, lo.la), 256, 0, s>>>(A, m, lo.la, pa, a, lo.la, 0, r);
+      transpose_to<Q, P>(B, l, lo.pc, lo.npad, b, lo.la, 0, lo.la, r, s);
     }
   } else {
     rows_to_e4m3<Q, P><<<rows_grid(m, lo.la), 256, 0, s>>>(A, m, lo.la, pa, ws, lo.la, 0, 0);
@@ -593,9 +576,11 @@ int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *
 template <int Q, int P>
 int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, cudaStream_t s) {
   const Layout lo = layout_for(Q, m, l, n);
+  // GF(4): X into both planes, then Y added into plane 0 and Z into plane 1
+  const int plane[3] = {-1, 0, 1};
   for (int r = 0; r < lo.rounds; ++r) {
     const uint8_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
-    if (int rc = gemm<Q, P>(a, b, C, m, lo.la, lo.npad, lo.pc, r, s)) return rc;
+    if (int rc = gemm<Q, P>(a, b, C, m, lo.la, lo.npad, lo.pc, plane[r], s)) return rc;
   }
   return FQ_OK;
 }
@@ -605,22 +590,21 @@ int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, cu
 // Largest l for which every partial sum stays below 2^24 in magnitude.
 int64_t tc_max_l(int q) {
   const int64_t b = q == 2 || q == 4 ? 1 : (q - 1) / 2;
-  const int64_t lim = ((int64_t(1) << 24) - 1) / (b * b);
-  return q == 4 ? lim / 2 : lim;
+  return ((int64_t(1) << 24) - 1) / (b * b);
 }
 
-// Modelled time (SM cycles): waves of 128 x 256 tiles (one persistent CTA per
-// SM) times 128-deep k-steps at the measured ~1100 cycles each, the operand
-// conversion at about 5 TB/s, and a constant for the launches (fitted on
-// GB300).  GF(4) runs two products of twice the depth.
+// Modelled time (SM cycles), fitted on GB300: the busiest CTA's tiles
+// (ceil(tiles / SMs), one persistent CTA per SM) times 128-deep k-steps at
+// about 760 cycles each, per product (GF(4) runs three); the operand
+// conversion's bytes at about 2.8 TB/s (1.7 TB/s for the three-plane fields);
+// and about 30 us of launches and set-up.
 double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
-  const int64_t la = cdiv(q == 4 ? 2 * cdiv(l, 16) * 16 : l, tc::BK) * tc::BK;
-  const int64_t npad = fq_pitch_words(n) * 64;
-  const int64_t ctas = (npad / tc::BN) * cdiv(m, tc::BM);
-  const double products = q == 4 ? 2.0 : 1.0;
-  const double gemm = double(cdiv(ctas, sms)) * double(la / tc::BK) * 1100.0;
-  const double convert = double(m + npad) * double(la) * 2.07e9 / 5.0e12;
-  return products * (gemm + convert) + 30000.0;
+  const tc::Layout lo = tc::layout_for(q, m, l, n);
+  const int64_t tiles = (lo.npad / tc::BN) * cdiv(m, tc::BM);
+  const double gemm = double(lo.rounds) * double(cdiv(tiles, sms > 0 ? sms : 1)) * double(lo.la / tc::BK) * 760.0;
+  const double bytes = double(lo.rounds) * double(lo.a_elems + lo.b_elems);
+  const double rate = (q == 5 || q == 7) ? 1.7e12 : 2.8e12;
+  return gemm + bytes * 2.07e9 / rate + 62000.0;
 }
 
 int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n) {

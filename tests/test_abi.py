@@ -127,12 +127,14 @@ def test_autotune_cache_host_side(lib):
     assert (p.value, k.value) == (fq.PATH_M4RM, 0)
     # tensor-core workspace sizes (host-only)
     # e4m3 operand bytes (A: m x la, B transposed: 64 pitch(n) x la, la = l up
-    # to a multiple of 128); GF(4): two rounds of two segments of l up to 16
+    # to a multiple of 128); GF(4): three such pairs (A0 B0, A1 B1, (A0+A1)(B0+B1))
     assert lib.fq_tc_workspace_bytes(3, 100, 200, 300) == (100 + 1024) * 256
     assert lib.fq_tc_workspace_bytes(5, 100, 200, 3000) == (100 + 3072) * 256
-    assert lib.fq_tc_workspace_bytes(4, 100, 200, 300) == 2 * (100 + 1024) * 512
-    assert lib.fq_tc_workspace_bytes(4, 1, 64, 1) == 2 * (1 + 1024) * 128
-    assert lib.fq_tc_workspace_bytes(4, 1, 65, 1) == 2 * (1 + 1024) * 256
+    assert lib.fq_tc_workspace_bytes(4, 100, 200, 300) == 3 * (100 + 1024) * 256
+    assert lib.fq_tc_workspace_bytes(4, 1, 128, 1) == 3 * (1 + 1024) * 128
+    assert lib.fq_tc_workspace_bytes(4, 1, 129, 1) == 3 * (1 + 1024) * 256
+    assert lib.fq_tc_workspace_bytes(4, 1, (1 << 24) - 1, 1) > 0
+    assert lib.fq_tc_workspace_bytes(4, 1, 1 << 24, 1) == -1
     assert lib.fq_tc_workspace_bytes(6, 100, 200, 300) == -1
     assert lib.fq_tc_workspace_bytes(9, 100, 200, 300) == -1
     assert lib.fq_tc_workspace_bytes(7, 10, 2_000_000, 10) == -1                 # beyond exact fp32 sums
