@@ -106,7 +106,8 @@ typedef struct fq_options {
   int64_t chunk; /* MMA path: l-chunk length between mod-p reductions; 0 = largest */
   int variant;   /* M4RM rows per CTA: 0 = planner, else 1 .. the kernel's maximum */
   int kernel;    /* M4RM kernel: 0 = planner, i + 1 = compiled kernel i of field q;
-                    tensor-core path: 1 = the mma.sync s8 form                  */
+                    tensor-core path: 0 = tcgen05 (SM pairs when m > 128),
+                    1 = the mma.sync s8 form, 2 = tcgen05 on single SMs       */
   int strassen;  /* Strassen-Winograd levels over the base-field products: 0 = the
                     time model decides, -1 = none, L > 0 = L levels (each needs
                     m, l, n to be multiples of 2048 at that level)               */

@@ -325,6 +325,66 @@ __device__ __forceinline__ void tile_coords(const GemmParams &prm, int t, int &m
   nb = in / rows;
 }
 
+// One row of a 256-column accumulator (this lane's TMEM lane, from column
+// address taddr) reduced mod p and packed into plane words.
+template <int Q, int P>
+__device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&words)[P][BN / 64]) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int w = 0; w < BN / 64; ++w) words[p][w] = 0ull;
+#pragma unroll
+  for (int c = 0; c < BN / 32; ++c) {
+    uint32_t v[32];
+    tmem_ld32(taddr + uint32_t(c * 32), v);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int x = int(__uint_as_float(v[i]));  // an exact integer
+      const int mod = Q == 4 ? 2 : Q;
+      int r = x % mod;
+      r += r < 0 ? mod : 0;
+      const int col = c * 32 + i, w = col / 64, bit = col % 64;
+      if constexpr (Q == 3) {
+        words[0][w] |= uint64_t(r != 0) << bit;
+        words[1][w] |= uint64_t(r == 2) << bit;
+      } else if constexpr (Q == 4) {
+        words[0][w] |= uint64_t(r) << bit;
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) words[p][w] |= uint64_t((r >> p) & 1) << bit;
+      }
+    }
+  }
+}
+
+// Store one row's packed words at word w0 of C's row.  GF(4): plane < 0
+// writes the F_2 result into both planes, else XORs it into that plane.
+template <int Q, int P>
+__device__ __forceinline__ void store_words(const GemmParams &prm, int64_t row, int64_t w0,
+                                            const uint64_t (&words)[P][BN / 64]) {
+  if constexpr (Q == 4) {
+    if (prm.plane < 0) {
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + w0;
+#pragma unroll
+        for (int w = 0; w < BN / 64; ++w) dst[w] = words[0][w];
+      }
+    } else {
+      uint64_t *dst = prm.C + (int64_t(prm.plane) * prm.m + row) * prm.pc + w0;
+#pragma unroll
+      for (int w = 0; w < BN / 64; ++w) dst[w] ^= words[0][w];
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + w0;
+#pragma unroll
+      for (int w = 0; w < BN / 64; ++w) dst[w] = words[p][w];
+    }
+  }
+}
+
 // Persistent: CTA b takes tiles b, b + grid, ...  Warp 0 streams A and B
 // slices through the stage ring, warp 1 issues the MMAs of each tile into one
 // of two TMEM accumulators, warps 4..7 drain the other accumulator (TMEM
@@ -415,61 +475,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       int mb, nb;
       tile_coords(prm, t, mb, nb);
       const int64_t row = int64_t(mb) * BM + ew * 32 + lane;
-      const int64_t w0 = int64_t(nb) * (BN / 64);
       uint64_t words[P][BN / 64];
-#pragma unroll
-      for (int p = 0; p < P; ++p)
-#pragma unroll
-        for (int w = 0; w < BN / 64; ++w) words[p][w] = 0ull;
-#pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t v[32];
-        tmem_ld32(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN + c * 32), v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int x = int(__uint_as_float(v[i]));  // an exact integer
-          const int mod = Q == 4 ? 2 : Q;
-          int r = x % mod;
-          r += r < 0 ? mod : 0;
-          const int col = c * 32 + i, w = col / 64, bit = col % 64;
-          if constexpr (Q == 3) {
-            words[0][w] |= uint64_t(r != 0) << bit;
-            words[1][w] |= uint64_t(r == 2) << bit;
-          } else if constexpr (Q == 4) {
-            words[0][w] |= uint64_t(r) << bit;
-          } else {
-#pragma unroll
-            for (int p = 0; p < P; ++p) words[p][w] |= uint64_t((r >> p) & 1) << bit;
-          }
-        }
-      }
+      drain_accumulator<Q, P>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN), words);
       // the accumulator has been read: hand it back to the MMA warp
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_cta(accempty + 8 * b);
-      if (row < prm.m) {
-        if constexpr (Q == 4) {
-          if (prm.plane < 0) {
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-              uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + w0;
-#pragma unroll
-              for (int w = 0; w < BN / 64; ++w) dst[w] = words[0][w];
-            }
-          } else {
-            uint64_t *dst = prm.C + (int64_t(prm.plane) * prm.m + row) * prm.pc + w0;
-#pragma unroll
-            for (int w = 0; w < BN / 64; ++w) dst[w] ^= words[0][w];
-          }
-        } else {
-#pragma unroll
-          for (int p = 0; p < P; ++p) {
-            uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + w0;
-#pragma unroll
-            for (int w = 0; w < BN / 64; ++w) dst[w] = words[p][w];
-          }
-        }
-      }
+      if (row < prm.m) store_words<Q, P>(prm, row, int64_t(nb) * (BN / 64), words);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -477,6 +489,213 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 2) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------- CTA-pair product --
+//
+// The same product on SM pairs (cta_group::2): a cluster of two CTAs owns a
+// 256 x 256 tile of C.  Each CTA stages its own 128 rows of A and its own 128
+// rows of B^T (a 6-stage ring of 32 KB stages), and the TMA loads of both
+// count on the leader CTA's full barrier.  The leader's MMA thread issues
+// tcgen05.mma.cta_group::2 (M = 256, N = 256, K = 32), which reads A and B^T
+// from both CTAs' shared memory and writes rows 128 r .. 128 r + 127 of the
+// tile into CTA r's TMEM; its commits arrive on the stage and accumulator
+// barriers of both CTAs.  Both epilogues hand an accumulator back on the
+// leader's barrier.  Per flop, each SM moves two thirds of the operand bytes
+// of the single-CTA kernel.
+
+constexpr int STAGES2 = 6;
+constexpr int A2_BYTES = 128 * BK, B2_BYTES = 128 * BK, STAGE2_BYTES = A2_BYTES + B2_BYTES;
+constexpr int BAR2_OFF = STAGES2 * STAGE2_BYTES;
+constexpr int NBARS2 = 2 * STAGES2 + 2 * ACC;
+constexpr int SMEM2 = BAR2_OFF + 8 * NBARS2 + 16 + 1024;
+// kind::f8f6f4, fp32 accumulator, e4m3 A and B, K-major, N = 256, M = 256
+constexpr uint32_t kIdesc2 = (1u << 4) | (uint32_t(BN >> 3) << 17) | (uint32_t(256 >> 4) << 24);
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// The shared::cluster address of the same variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// TMA load into this CTA's shared memory whose bytes count on an mbarrier of
+// either CTA of the pair (a shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_e4m3_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc2), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on the mbarrier at this offset in both CTAs once the pair's issued
+// MMAs have completed.
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(static_cast<uint16_t>(3))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+// Bounded wait with cluster-scope acquire (arrivals from the peer CTA).
+__device__ __forceinline__ void wait_bar_cluster(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                                 unsigned *err) {
+  if (*abort_flag) return;
+  uint32_t done = 0;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return;
+    if (globaltimer_ns() - t0 > 2000000000ull) {
+      *abort_flag = 1;
+      record_error(err, FQ_ETIMEOUT);
+      return;
+    }
+  }
+}
+
+template <int Q, int P>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+    tc_gemm2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const GemmParams prm) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned (128-byte swizzle atoms)
+  unsigned char *smem = smem_raw + (base - raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const uint32_t full = base + BAR2_OFF, empty = full + 8 * STAGES2, accfull = empty + 8 * STAGES2,
+                 accempty = accfull + 8 * ACC;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + BAR2_OFF + 8 * NBARS2);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + BAR2_OFF + 8 * NBARS2 + 8);
+
+  if (tid == 0) {
+    *abort_flag = 0;
+    for (int s = 0; s < STAGES2; ++s) {
+      mbar_init(full + 8 * s, 1);   // the leader's producer arrives; both CTAs' bytes complete it
+      mbar_init(empty + 8 * s, 1);  // one multicast commit
+    }
+    for (int b = 0; b < ACC; ++b) {
+      mbar_init(accfull + 8 * b, 1);
+      mbar_init(accempty + 8 * b, 8);  // four epilogue warps in each CTA (the leader's barrier)
+    }
+    fence_mbar_init();
+  }
+  if (warp == 2) {  // one warp of each CTA allocates the pair's columns together
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  cluster_sync();  // both CTAs' barriers initialised, the columns allocated
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int cl = int(blockIdx.x >> 1), ncl = int(gridDim.x >> 1);
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer (both CTAs): this CTA's halves of A and B^T
+    int it = 0;
+    for (int t = cl; t < prm.tiles && !*abort_flag; t += ncl) {
+      int mb, nb;
+      tile_coords(prm, t, mb, nb);
+      for (int ks = 0; ks < prm.ksteps; ++ks, ++it) {
+        const int s = it % STAGES2;
+        if (it >= STAGES2) wait_bar(empty + 8 * s, uint32_t((it / STAGES2 - 1) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+        if (leader) mbar_expect_tx(full + 8 * s, 2 * STAGE2_BYTES);
+        const uint32_t bar = map_to_rank(full + 8 * s, 0);
+        const uint32_t a_dst = base + uint32_t(s * STAGE2_BYTES), b_dst = a_dst + A2_BYTES;
+        tma_load_2d_pair(a_dst, &tmA, bar, ks * BK, mb * 256 + 128 * int(rank));
+        tma_load_2d_pair(b_dst, &tmB, bar, ks * BK, nb * 256 + 128 * int(rank));
+      }
+    }
+    // the last commits to this CTA's stage barriers have landed before it exits
+    for (int j = it > STAGES2 ? it - STAGES2 : 0; j < it; ++j)
+      wait_bar(empty + 8 * (j % STAGES2), uint32_t((j / STAGES2) & 1), abort_flag, prm.err);
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---- MMA issuer (the leader CTA only)
+    int it = 0, li = 0;
+    for (int t = cl; t < prm.tiles && !*abort_flag; t += ncl, ++li) {
+      const int b = li % ACC;
+      if (li >= ACC) wait_bar_cluster(accempty + 8 * b, uint32_t((li / ACC - 1) & 1), abort_flag, prm.err);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t d = tmem + uint32_t(b * BN);
+      for (int ks = 0; ks < prm.ksteps; ++ks, ++it) {
+        const int s = it % STAGES2;
+        wait_bar(full + 8 * s, uint32_t((it / STAGES2) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_src = base + uint32_t(s * STAGE2_BYTES), b_src = a_src + A2_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / UK; ++kk)
+          mma_e4m3_pair(d, smem_desc(a_src + UK * kk), smem_desc(b_src + UK * kk), (ks | kk) != 0);
+        mma_commit_pair(empty + 8 * s);  // both CTAs' stage s is free once these MMAs have read it
+      }
+      mma_commit_pair(accfull + 8 * b);  // this tile's accumulators are complete in both CTAs
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue (both CTAs): rows 128 rank + 32 (warp - 4) + lane of the tile
+    const int ew = warp - 4;
+    const uint32_t back = leader ? accempty : map_to_rank(accempty, 0);
+    int li = 0;
+    for (int t = cl; t < prm.tiles; t += ncl, ++li) {
+      const int b = li % ACC;
+      wait_bar(accfull + 8 * b, uint32_t((li / ACC) & 1), abort_flag, prm.err);
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int mb, nb;
+      tile_coords(prm, t, mb, nb);
+      const int64_t row = int64_t(mb) * 256 + 128 * int(rank) + ew * 32 + lane;
+      uint64_t words[P][BN / 64];
+      drain_accumulator<Q, P>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN), words);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        if (leader)
+          mbar_arrive_cta(accempty + 8 * b);
+        else
+          mbar_arrive_cluster(back + 8 * b);
+      }
+      if (row < prm.m) store_words<Q, P>(prm, row, int64_t(nb) * (BN / 64), words);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync();  // neither CTA touches the other's memory any more
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
@@ -499,18 +718,22 @@ int make_map(CUtensorMap *map, const uint8_t *ptr, int64_t inner, int64_t rows, 
 
 template <int Q, int P>
 int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t la, int64_t npad, int64_t pc,
-         int plane, cudaStream_t s) {
+         int plane, bool single_sm, cudaStream_t s) {
   unsigned *err = nullptr;
   if (int rc = status_word(&err)) return rc;
+  // SM pairs take 256 x 256 tiles; a product of at most 128 rows would leave
+  // half of every pair idle, so it runs on single SMs (128 x 256 tiles).
+  const bool pair = !single_sm && m > BM;
+  const int rows = pair ? 2 * BM : BM;
   CUtensorMap ma, mb;
   if (int rc = make_map(&ma, Ab, la, m, BM)) return rc;
-  if (int rc = make_map(&mb, Bt, la, npad, BN)) return rc;
+  if (int rc = make_map(&mb, Bt, la, npad, pair ? BM : BN)) return rc;
   GemmParams prm;
   prm.C = C;
   prm.m = m;
   prm.pc = pc;
   prm.ksteps = int(la / BK);
-  prm.mblocks = int(cdiv(m, BM));
+  prm.mblocks = int(cdiv(m, rows));
   prm.nblocks = int(npad / BN);
   const int64_t tiles = int64_t(prm.mblocks) * prm.nblocks;
   if (tiles >= (int64_t(1) << 31)) return FQ_ENOTSUP;
@@ -520,9 +743,16 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
   int dev = 0, sms = 0;
   FQ_CUDA_TRY(cudaGetDevice(&dev));
   FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-  const int grid = int(tiles < sms ? tiles : sms);
-  tc_gemm_kernel<Q, P><<<grid, THREADS, SMEM, s>>>(ma, mb, prm);
+  if (pair) {
+    FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm2_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2));
+    const int64_t pairs = sms / 2 > 0 ? sms / 2 : 1;
+    const int grid = 2 * int(tiles < pairs ? tiles : pairs);
+    tc_gemm2_kernel<Q, P><<<grid, THREADS, SMEM2, s>>>(ma, mb, prm);
+  } else {
+    FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+    const int grid = int(tiles < sms ? tiles : sms);
+    tc_gemm_kernel<Q, P><<<grid, THREADS, SMEM, s>>>(ma, mb, prm);
+  }
   FQ_LAUNCH_CHECK();
   return FQ_OK;
 }
@@ -574,13 +804,13 @@ int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *
 }
 
 template <int Q, int P>
-int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, cudaStream_t s) {
+int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, bool single_sm, cudaStream_t s) {
   const Layout lo = layout_for(Q, m, l, n);
   // GF(4): X into both planes, then Y added into plane 0 and Z into plane 1
   const int plane[3] = {-1, 0, 1};
   for (int r = 0; r < lo.rounds; ++r) {
     const uint8_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
-    if (int rc = gemm<Q, P>(a, b, C, m, lo.la, lo.npad, lo.pc, plane[r], s)) return rc;
+    if (int rc = gemm<Q, P>(a, b, C, m, lo.la, lo.npad, lo.pc, plane[r], single_sm, s)) return rc;
   }
   return FQ_OK;
 }
@@ -627,7 +857,8 @@ int tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const 
   }
 }
 
-int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t *C, cudaStream_t s) {
+int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t *C, cudaStream_t s,
+                bool single_sm) {
   if (m == 0 || n == 0) return FQ_OK;
   if (l == 0) {
     FQ_CUDA_TRY(cudaMemsetAsync(C, 0, size_t(fq_planes(q)) * size_t(m) * size_t(fq_pitch_words(n)) * 8u, s));
@@ -635,24 +866,24 @@ int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t
   }
   const uint8_t *w = static_cast<const uint8_t *>(ws);
   switch (q) {
-    case 2: return tc::multiply<2, 1>(m, l, n, w, C, s);
-    case 3: return tc::multiply<3, 2>(m, l, n, w, C, s);
-    case 4: return tc::multiply<4, 2>(m, l, n, w, C, s);
-    case 5: return tc::multiply<5, 3>(m, l, n, w, C, s);
-    case 7: return tc::multiply<7, 3>(m, l, n, w, C, s);
+    case 2: return tc::multiply<2, 1>(m, l, n, w, C, single_sm, s);
+    case 3: return tc::multiply<3, 2>(m, l, n, w, C, single_sm, s);
+    case 4: return tc::multiply<4, 2>(m, l, n, w, C, single_sm, s);
+    case 5: return tc::multiply<5, 3>(m, l, n, w, C, single_sm, s);
+    case 7: return tc::multiply<7, 3>(m, l, n, w, C, single_sm, s);
     default: return FQ_EINVAL;
   }
 }
 
 int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
-              cudaStream_t s) {
+              cudaStream_t s, bool single_sm) {
   const int64_t bytes = tc_workspace_bytes(q, m, l, n);
   if (bytes < 0) return FQ_ENOTSUP;
   if (l == 0) return tc_multiply(q, m, l, n, nullptr, C, s);
   void *mem = nullptr;
   if (int rc = scratch_alloc(&mem, size_t(bytes), s)) return rc;
   int rc = tc_prepare(q, m, l, n, A, B, mem, s);
-  if (rc == FQ_OK) rc = tc_multiply(q, m, l, n, mem, C, s);
+  if (rc == FQ_OK) rc = tc_multiply(q, m, l, n, mem, C, s, single_sm);
   const int fr = scratch_free(mem, s);
   return rc ? rc : fr;
 }

@@ -147,6 +147,7 @@ def _check_product(fq, q, m, l, n, seed, sparse=False, **kw):
     words, pad = packed_words(c)
     assert np.array_equal(words, encoding.pack(q, want))
     assert not pad.any()
+    return got, c
 
 
 def test_config1_f3_512(fq):
@@ -296,6 +297,20 @@ def test_mma_sync_form_matches_oracle(fq, q, mln):
     """The mma.sync s8 form (fq_options.kernel = 1), kept for l beyond the
     tcgen05 form's exact range."""
     _check_product(fq, q, *mln, seed=sum(mln) + 11 * q, path=fq.PATH_MMA, kernel=1)
+
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("mln", [(1, 1, 1), (128, 300, 257), (129, 300, 257), (300, 500, 260), (513, 257, 1025)])
+def test_tcgen05_single_sm_form_matches_oracle(fq, q, mln):
+    """fq_options.kernel = 2: the single-SM tcgen05 kernel (128 x 256 tiles)
+    where SM pairs would otherwise run; equal to the oracle and to the pair
+    kernel's result."""
+    got, c1 = _check_product(fq, q, *mln, seed=sum(mln) + 13 * q, path=fq.PATH_MMA, kernel=2)
+    m, l, n = mln
+    A = inputs.uniform(q, m, l, seed=sum(mln) + 13 * q, stream=inputs.STREAM_A)
+    B = inputs.uniform(q, l, n, seed=sum(mln) + 13 * q, stream=inputs.STREAM_B)
+    c0 = fq.matmul(gpu_pack(fq, q, A), gpu_pack(fq, q, B), path=fq.PATH_MMA)
+    assert torch.equal(c0.data, c1.data)
 
 
 @pytest.mark.parametrize("q", FIELDS)
