@@ -13,7 +13,10 @@ against the classical product's work).
 * ``m4rm``: the same products by the plain bitsliced Four-Russians path, with
   ``speedup_vs_m4rm`` the factor between the two.
 * ``e2e``: the same products through the public API from pinned host residues:
-  host->device copy, fq_pack, fq_matmul, fq_unpack, device->host copy.
+  host->device copy, fq_pack, fq_matmul, fq_unpack, device->host copy (bound
+  by the host link: 1 byte per element up, about 210 GB/s on GB300).
+* ``e2e_packed``: the same with the host holding the library's bit-planes
+  (the paper's representation): planes up, fq_matmul, C's planes down.
 * ``roofline``: the dominant kernel, the tcgen05 product (e4m3 operands), at
   2 m l n flops per launch over its own event time, against the dense fp8
   peak (the measured cuBLAS bf16 burst times the nominal fp8/bf16 ratio 2);
@@ -468,7 +471,7 @@ def main():
                          "peak_note": "derived: 64 LOP3 lanes/clk/SM x 152 SMs x 2070 MHz"}}
 
     # ---- end to end through the public API, host buffers -------------------
-    e2e = None
+    e2e = e2e_packed = None
     if not args.no_e2e:
         host = []
         for (A, B), (m, l, n, _) in zip(res, prods):
@@ -539,7 +542,63 @@ def main():
         e2e = {"value": ops_step * dist.world / (e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": sum(m * l + l * n for (m, l, n, _) in prods),
                "d2h_bytes_per_step": sum(m * n for (m, l, n, _) in prods),
-               "ms_per_step": e_ms, "steps": e_steps}
+               "ms_per_step": e_ms, "steps": e_steps,
+               "inputs": "uint8 residues in pinned host memory; fq_pack, fq_matmul, fq_unpack on the device"}
+
+        # The same with the host holding matrices in the library's own format
+        # (the paper's bit-planes, 2 bits per F_3 element): planes up, fq_matmul,
+        # C's planes down, copies overlapped as above.
+        del dbuf
+        hp = [(a.data.cpu().pin_memory(), b.data.cpu().pin_memory(), torch.empty_like(c.data, device="cpu").pin_memory())
+              for (a, b, c) in packed]
+        dp = [(fq.empty(Q, m, l), fq.empty(Q, l, n), fq.empty(Q, m, n)) for (m, l, n, _) in prods]
+        evp = {name: [torch.cuda.Event() for _ in prods] for name in ("in", "used", "out", "read")}
+        startedp = [False]
+
+        def e2e_packed_step():
+            for j, ((hA, hB, hC), (a, b, c)) in enumerate(zip(hp, dp)):
+                with torch.cuda.stream(h2d_s):
+                    if startedp[0]:
+                        h2d_s.wait_event(evp["used"][j])       # last step's product has read a, b
+                    a.data.copy_(hA, non_blocking=True)
+                    b.data.copy_(hB, non_blocking=True)
+                    evp["in"][j].record(h2d_s)
+                stream.wait_event(evp["in"][j])
+                if startedp[0]:
+                    stream.wait_event(evp["read"][j])          # last step's C has left the device
+                fq.matmul(a, b, out=c)
+                evp["used"][j].record(stream)
+                evp["out"][j].record(stream)
+                with torch.cuda.stream(d2h_s):
+                    d2h_s.wait_event(evp["out"][j])
+                    hC.copy_(c.data, non_blocking=True)
+                    evp["read"][j].record(d2h_s)
+            startedp[0] = True
+
+        for _ in range(args.warmup):
+            e2e_packed_step()
+        join()
+        torch.cuda.synchronize()
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(e_steps):
+            e2e_packed_step()
+        join()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for (hA, hB, hC), (a, b, c) in zip(hp, packed):
+            if not torch.equal(hC, c.data.cpu()):
+                raise SystemExit("end-to-end (packed) result differs from the device-resident product")
+        dist.barrier()
+        if fq.status() != fq.OK:
+            raise SystemExit("device error in the end-to-end (packed) region")
+        p_ms = dist.max(e0.elapsed_time(e1) / e_steps, dev)
+        e2e_packed = {"value": ops_step * dist.world / (p_ms * 1e-3), "unit": UNIT,
+                      "h2d_bytes_per_step": sum(a.data.numel() * 8 + b.data.numel() * 8 for (a, b, c) in packed),
+                      "d2h_bytes_per_step": sum(c.data.numel() * 8 for (a, b, c) in packed),
+                      "ms_per_step": p_ms, "steps": e_steps,
+                      "inputs": "bit-planes (fq_pack's format) in pinned host memory; fq_matmul on the device"}
 
     base = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -562,7 +621,8 @@ def main():
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["fp8"], "unit": "TFLOP/s",
                          "frac": achieved / peaks["fp8"], "traffic": traffic,
                          "peak_note": peaks["note"],
-                         "kernel": "tc_gemm_kernel (tcgen05 kind::f8f6f4 e4m3, 128x256 tiles, persistent)",
+                         "kernel": "tc_gemm2_kernel (tcgen05.mma.cta_group::2 kind::f8f6f4 e4m3, 256x256 tiles "
+                                   "on SM pairs, persistent)",
                          "kernel_ms_per_step": sum(product_ms)},
             "prepare": {"bound": "hbm", "ms_per_step": prep_ms, "bytes": prep_bytes, "achieved": prep_gbs,
                         "peak": peaks["hbm"], "unit": "GB/s", "frac": prep_gbs / peaks["hbm"],
@@ -572,6 +632,7 @@ def main():
             "m4rm": m4rm,
             "speedup_vs_m4rm": value / m_value,
             "e2e": e2e,
+            "e2e_packed": e2e_packed,
             "cpu_baseline": base,
             "clocks": clk,
             "gpu_launches": args.steps * sum(TC_LAUNCHES if f == "tensor" else 1 for f in forms),
