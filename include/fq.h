@@ -104,7 +104,8 @@ typedef struct fq_options {
   int path;      /* FQ_PATH_*; for q = 8 .. 125 the base-field products' path      */
   int k;         /* M4RM block size: 0 = planner, else 6..10 (Section 2's k)       */
   int64_t chunk; /* MMA path: l-chunk length between mod-p reductions; 0 = largest */
-  int variant;   /* M4RM rows per CTA: 0 = planner, else 1 .. the kernel's maximum */
+  int variant;   /* M4RM rows per CTA: 0 = planner, else 1 .. the kernel's maximum;
+                    tcgen05 path: row blocks per group of the tile order (0 = 8) */
   int kernel;    /* M4RM kernel: 0 = planner, i + 1 = compiled kernel i of field q;
                     tensor-core path: 0 = tcgen05 (SM pairs when m > 128),
                     1 = the mma.sync s8 form, 2 = tcgen05 on single SMs       */

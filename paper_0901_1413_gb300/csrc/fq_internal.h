@@ -20,10 +20,13 @@ int launch_m4rm(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const
 int launch_mma(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                int64_t chunk, cudaStream_t s);
 // The tcgen05 form of the tensor-core path (fq_tc.cu): FQ_ENOTSUP when l is
-// beyond the exact fp32 range of the field (tc_max_l).  single_sm: the
-// single-SM kernel even where SM pairs would run.
+// beyond the exact fp32 range of the field (tc_max_l).
+struct TcOptions {
+  bool single_sm = false;  // the single-SM kernel even where SM pairs would run
+  int group = 0;           // row blocks per group of the tile order (0: 8)
+};
 int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
-              cudaStream_t s, bool single_sm = false);
+              cudaStream_t s, const TcOptions &to = TcOptions());
 int64_t tc_max_l(int q);
 // Its two stages on a caller's workspace (bytes: tc_workspace_bytes, -1 if
 // the product is outside the tcgen05 form): operands to e4m3, then the product.
@@ -31,7 +34,7 @@ int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n);
 int tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, void *ws,
                cudaStream_t s);
 int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t *C, cudaStream_t s,
-                bool single_sm = false);
+                const TcOptions &to = TcOptions());
 double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms);
 
 // One compiled M4RM kernel shape of a field (the planner's candidates).

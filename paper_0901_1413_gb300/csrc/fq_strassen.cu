@@ -115,7 +115,12 @@ int direct(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint
     // tcgen05 (e4m3, exact fp32 sums) unless a reduction chunk or the
     // mma.sync s8 form (kernel = 1) is requested, or l is beyond its exact
     // range; kernel = 2 keeps it on single SMs
-    if (o.chunk == 0 && o.kernel != 1 && l <= tc_max_l(q)) return launch_tc(q, m, l, n, A, B, C, s, o.kernel == 2);
+    if (o.chunk == 0 && o.kernel != 1 && l <= tc_max_l(q)) {
+      TcOptions to;
+      to.single_sm = o.kernel == 2;
+      to.group = o.variant;
+      return launch_tc(q, m, l, n, A, B, C, s, to);
+    }
     return launch_mma(q, m, l, n, A, B, C, o.chunk, s);
   }
   return launch_m4rm(q, m, l, n, A, B, C, o.k, o.variant, kernel, s);

@@ -45,7 +45,7 @@ constexpr int NBARS = 2 * STAGES + 2 * ACC;
 constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;  // + alignment slack
 constexpr int TMEM_COLS = ACC * BN;
 constexpr int THREADS = 256;
-constexpr int GROUP_M = 8;                     // tile order: groups of 8 row blocks (L2 reuse)
+constexpr int GROUP_M = 8;                     // tile order: default row blocks per group (L2 reuse)
 
 // ---------------------------------------------------------- conversions --
 
@@ -309,17 +309,18 @@ struct GemmParams {
   int64_t m, pc;   // rows of C, pitch words of C
   int ksteps;      // la / 128
   int mblocks, nblocks, tiles;
+  int group;       // row blocks per group of the tile order
   int plane;       // GF(4): -1 writes both planes, 0 or 1 adds into that plane
   unsigned *err;
 };
 
-// Tile t in grouped order: GROUP_M row blocks at a time, all column blocks
+// Tile t in grouped order: prm.group row blocks at a time, all column blocks
 // of the group, so that a wave of tiles reuses a few rows of A and columns
 // of B from L2.
 __device__ __forceinline__ void tile_coords(const GemmParams &prm, int t, int &mb, int &nb) {
-  const int per_group = GROUP_M * prm.nblocks;
-  const int g = t / per_group, first = g * GROUP_M;
-  const int rows = prm.mblocks - first < GROUP_M ? prm.mblocks - first : GROUP_M;
+  const int per_group = prm.group * prm.nblocks;
+  const int g = t / per_group, first = g * prm.group;
+  const int rows = prm.mblocks - first < prm.group ? prm.mblocks - first : prm.group;
   const int in = t - g * per_group;
   mb = first + in % rows;
   nb = in / rows;
@@ -718,12 +719,12 @@ int make_map(CUtensorMap *map, const uint8_t *ptr, int64_t inner, int64_t rows, 
 
 template <int Q, int P>
 int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t la, int64_t npad, int64_t pc,
-         int plane, bool single_sm, cudaStream_t s) {
+         int plane, const TcOptions &to, cudaStream_t s) {
   unsigned *err = nullptr;
   if (int rc = status_word(&err)) return rc;
   // SM pairs take 256 x 256 tiles; a product of at most 128 rows would leave
   // half of every pair idle, so it runs on single SMs (128 x 256 tiles).
-  const bool pair = !single_sm && m > BM;
+  const bool pair = !to.single_sm && m > BM;
   const int rows = pair ? 2 * BM : BM;
   CUtensorMap ma, mb;
   if (int rc = make_map(&ma, Ab, la, m, BM)) return rc;
@@ -740,6 +741,7 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
   prm.tiles = int(tiles);
   prm.plane = plane;
   prm.err = err;
+  prm.group = to.group > 0 ? to.group : GROUP_M;
   int dev = 0, sms = 0;
   FQ_CUDA_TRY(cudaGetDevice(&dev));
   FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -804,13 +806,13 @@ int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *
 }
 
 template <int Q, int P>
-int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, bool single_sm, cudaStream_t s) {
+int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, const TcOptions &to, cudaStream_t s) {
   const Layout lo = layout_for(Q, m, l, n);
   // GF(4): X into both planes, then Y added into plane 0 and Z into plane 1
   const int plane[3] = {-1, 0, 1};
   for (int r = 0; r < lo.rounds; ++r) {
     const uint8_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
-    if (int rc = gemm<Q, P>(a, b, C, m, lo.la, lo.npad, lo.pc, plane[r], single_sm, s)) return rc;
+    if (int rc = gemm<Q, P>(a, b, C, m, lo.la, lo.npad, lo.pc, plane[r], to, s)) return rc;
   }
   return FQ_OK;
 }
@@ -858,7 +860,7 @@ int tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const 
 }
 
 int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t *C, cudaStream_t s,
-                bool single_sm) {
+                const TcOptions &to) {
   if (m == 0 || n == 0) return FQ_OK;
   if (l == 0) {
     FQ_CUDA_TRY(cudaMemsetAsync(C, 0, size_t(fq_planes(q)) * size_t(m) * size_t(fq_pitch_words(n)) * 8u, s));
@@ -866,24 +868,24 @@ int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t
   }
   const uint8_t *w = static_cast<const uint8_t *>(ws);
   switch (q) {
-    case 2: return tc::multiply<2, 1>(m, l, n, w, C, single_sm, s);
-    case 3: return tc::multiply<3, 2>(m, l, n, w, C, single_sm, s);
-    case 4: return tc::multiply<4, 2>(m, l, n, w, C, single_sm, s);
-    case 5: return tc::multiply<5, 3>(m, l, n, w, C, single_sm, s);
-    case 7: return tc::multiply<7, 3>(m, l, n, w, C, single_sm, s);
+    case 2: return tc::multiply<2, 1>(m, l, n, w, C, to, s);
+    case 3: return tc::multiply<3, 2>(m, l, n, w, C, to, s);
+    case 4: return tc::multiply<4, 2>(m, l, n, w, C, to, s);
+    case 5: return tc::multiply<5, 3>(m, l, n, w, C, to, s);
+    case 7: return tc::multiply<7, 3>(m, l, n, w, C, to, s);
     default: return FQ_EINVAL;
   }
 }
 
 int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
-              cudaStream_t s, bool single_sm) {
+              cudaStream_t s, const TcOptions &to) {
   const int64_t bytes = tc_workspace_bytes(q, m, l, n);
   if (bytes < 0) return FQ_ENOTSUP;
   if (l == 0) return tc_multiply(q, m, l, n, nullptr, C, s);
   void *mem = nullptr;
   if (int rc = scratch_alloc(&mem, size_t(bytes), s)) return rc;
   int rc = tc_prepare(q, m, l, n, A, B, mem, s);
-  if (rc == FQ_OK) rc = tc_multiply(q, m, l, n, mem, C, s, single_sm);
+  if (rc == FQ_OK) rc = tc_multiply(q, m, l, n, mem, C, s, to);
   const int fr = scratch_free(mem, s);
   return rc ? rc : fr;
 }

@@ -313,6 +313,14 @@ def test_tcgen05_single_sm_form_matches_oracle(fq, q, mln):
     assert torch.equal(c0.data, c1.data)
 
 
+@pytest.mark.parametrize("group", [1, 3, 64])
+def test_tcgen05_tile_order_groups(fq, group):
+    """fq_options.variant on the tcgen05 path sets the tile order's row-block
+    group; every order gives the same, exact product (ragged m and n)."""
+    _check_product(fq, 3, 1100, 300, 2100, seed=group, path=fq.PATH_MMA, variant=group)
+    _check_product(fq, 5, 700, 200, 1500, seed=group, path=fq.PATH_MMA, variant=group, kernel=2)
+
+
 @pytest.mark.parametrize("q", FIELDS)
 def test_tensor_operands_prepared_once(fq, q):
     """fq_tc_prepare once, fq_tc_multiply twice: both results equal the oracle."""
