@@ -174,32 +174,49 @@ int fq_tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *workspace
                    void *stream);
 
 /* ---- many products in one launch ------------------------------------------
- * A plan splits `count` products C_p = A_p B_p (shapes m[p] x l[p] times
- * l[p] x n[p], all over the same field q) into work items (rows x a column
- * tile of one product) with a block size k chosen per item by the planner's
- * cost model, longest first.  The plan is host memory owned by the library. */
+ * A plan assigns each of `count` products C_p = A_p B_p (shapes m[p] x l[p]
+ * times l[p] x n[p], all over the same field q) to one of the two paths by
+ * their time models (or as the caller asks):
+ *   - Four Russians: work items (rows x a column tile of one product) with a
+ *     block size k chosen per item by the planner's cost model, longest first;
+ *   - tcgen05 (F_3, F_5, F_7 with 0 < l within the exact range): the
+ *     product's A and B^T in e4m3 in two arenas of the workspace, and its
+ *     128 x 256 tiles in one list, deepest first.
+ * The plan is host memory owned by the library. */
 typedef struct fq_batch_plan fq_batch_plan;
 
 /* Build a plan (host only).  q = 3, 4, 5 or 7.  m, l, n: host arrays of `count`
- * sizes (each >= 0; l, m < 2^31).  Returns FQ_EINVAL on a bad q or bad sizes,
- * FQ_ENOMEM on allocation failure. */
+ * sizes (each >= 0 and < 2^31).  path: FQ_PATH_AUTO (per-product choice by the
+ * models), FQ_PATH_M4RM (every product by Four Russians) or FQ_PATH_MMA (every
+ * product the tcgen05 form can take; GF(4) and the rest by Four Russians);
+ * fq_batched_plan_create is path FQ_PATH_AUTO.  Returns FQ_EINVAL on a bad q,
+ * path or sizes, FQ_ENOMEM on allocation failure. */
 int fq_batched_plan_create(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n,
                            fq_batch_plan **plan);
+int fq_batched_plan_create_ex(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n, int path,
+                              fq_batch_plan **plan);
 
-/* Bytes of device workspace the plan needs (64-byte aligned, caller-owned),
- * and the number of work items it holds; -1 for a NULL plan. */
+/* Bytes of device workspace the plan needs (64-byte aligned, caller-owned:
+ * the work lists, and for tcgen05 products the e4m3 arenas, (m rounded up to
+ * 128 + n rounded up to 256) x (l rounded up to 128) bytes per product), the
+ * number of Four-Russians work items, of products on the tcgen05 path and of
+ * their tiles; -1 for a NULL plan. */
 int64_t fq_batched_workspace_bytes(const fq_batch_plan *plan);
 int64_t fq_batched_items(const fq_batch_plan *plan);
+int64_t fq_batched_tc_products(const fq_batch_plan *plan);
+int64_t fq_batched_tc_tiles(const fq_batch_plan *plan);
 
-/* Copy the plan's work list into `workspace` (synchronous on `stream`).  Once
+/* Copy the plan's work lists into `workspace` (synchronous on `stream`).  Once
  * per plan and workspace, before any fq_matmul_batched on them. */
 int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *stream);
 
-/* All products of the plan in one persistent launch (Section 2's method on
- * every product).  A, B, C: DEVICE arrays of `count` device pointers to planes
- * buffers (A_p m x l, B_p l x n, C_p m x n; C_p must not alias A_p or B_p);
- * workspace: the uploaded workspace.  Enqueues one memset and one kernel on
- * `stream`; allocates nothing and never synchronises, so it may be captured in
+/* All products of the plan (Section 2's method, or the exact tensor-core
+ * contraction, per product).  A, B, C: DEVICE arrays of `count` device
+ * pointers to planes buffers (A_p m x l, B_p l x n, C_p m x n; C_p must not
+ * alias A_p or B_p); workspace: the uploaded workspace.  Enqueues, on
+ * `stream`, for tcgen05 products two conversion kernels and one persistent
+ * product kernel, then for Four-Russians items one memset and one persistent
+ * kernel; allocates nothing and never synchronises, so it may be captured in
  * a CUDA graph.  Launches sharing a workspace must not overlap on the GPU. */
 int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
                       uint64_t *const *C, void *workspace, void *stream);
@@ -218,7 +235,9 @@ int fq_batched_plan_destroy(fq_batch_plan *plan);
  * on every GPU that loads it (until the process exits), and no call allocates
  * or frees device memory.
  *   - A plan needing more than FQ_BATCH_STATIC_BYTES of workspace
- *     (fq_batched_workspace_bytes) is refused with FQ_ENOTSUP.
+ *     (fq_batched_workspace_bytes), or holding tcgen05 products (whose
+ *     arenas do not fit; build it with FQ_PATH_M4RM), is refused with
+ *     FQ_ENOTSUP.
  *   - Each call copies the plan's work list into the array on `stream` before
  *     its launch (the array keeps the previous call's contents otherwise).
  *   - All calls on a GPU share the one array: calls whose work overlaps on the

@@ -255,19 +255,47 @@ struct fq_batch_plan {
   int q;
   int count;
   std::vector<fqk::batched::Shape> shapes;
-  std::vector<fqk::batched::Item> items;
-  int64_t workspace_bytes;
-  double model_cost;  // sum of modelled item costs (adds)
+  std::vector<fqk::batched::Item> items;      // Four-Russians items
+  std::vector<fqk::BatchProd> tc_prods;       // products on the tcgen05 path
+  std::vector<int64_t> tc_a_prefix, tc_b_prefix;
+  std::vector<int32_t> tc_a_unit, tc_b_unit;  // product of each conversion unit
+  std::vector<int64_t> tc_tile_prefix;         // cumulative modelled cost of the tiles
+  std::vector<fqk::BatchTile> tc_tiles;
+  int64_t a_rows = 0, b_rows = 0;  // arena rows of 128 bytes
+  int64_t off_prods = 0, off_aprefix = 0, off_bprefix = 0, off_aunit = 0, off_bunit = 0, off_tiles = 0,
+          off_tprefix = 0;
+  int64_t off_a_arena = 0, off_b_arena = 0;
+  int64_t table_bytes = 0;      // header .. tile list (uploaded)
+  int64_t workspace_bytes = 0;  // plus the two arenas
+  double model_cost = 0;        // modelled SM-cycles of the whole plan
 };
 
-extern "C" {
+namespace {
 
-int fq_batched_plan_create(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n,
-                           fq_batch_plan **out) {
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Modelled SM-cycles per unit of the batched Four-Russians item cost (table
+// entries + rows x basis size per block), fitted to the 4096-product batch
+// on GB300: F_3 and GF(4) run two CTAs per SM.
+double m4rm_unit_cycles(int q) { return q == 3 || q == 4 ? 2.1 : (q == 5 ? 8.5 : 8.0); }
+
+// Modelled SM-cycles of one product on the tcgen05 path: tiles x 128-deep
+// k-steps at ~760 cycles, and the conversion's bytes at ~3 TB/s shared by
+// 152 SMs at 2.07 GHz.
+double tc_product_cycles(int64_t m, int64_t l, int64_t n) {
+  const int64_t la = fqk::cdiv(l, 128) * 128, nr = fqk::cdiv(n, 256) * 256;
+  const double tiles = double(fqk::cdiv(m, 128)) * double(nr / 256);
+  const double bytes = double(m + n) * double(la);
+  return tiles * double(la / 128) * 760.0 + bytes * (2.07e9 * 152.0 / 3.0e12);
+}
+
+int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n, int path,
+                fq_batch_plan **out) {
   using namespace fqk::batched;
   if (!out) return FQ_EINVAL;
   *out = nullptr;
   if (!(q == 3 || q == 4 || q == 5 || q == 7) || count < 0 || (count > 0 && (!m || !l || !n))) return FQ_EINVAL;
+  if (!(path == FQ_PATH_AUTO || path == FQ_PATH_M4RM || path == FQ_PATH_MMA)) return FQ_EINVAL;
   fq_batch_plan *plan = new (std::nothrow) fq_batch_plan();
   if (!plan) return FQ_ENOMEM;
   plan->q = q;
@@ -276,15 +304,17 @@ int fq_batched_plan_create(int q, int count, const int64_t *m, const int64_t *l,
   const int mt_max = (q == 3 || q == 4) ? fqk::batched::max_rows<fqk::F3>() : fqk::batched::max_rows<fqk::F5>();
   const int ctw = (q == 3 || q == 4) ? fqk::batched::tile_words<fqk::F3>() : fqk::batched::tile_words<fqk::F5>();
   std::vector<std::pair<double, Item>> costed;
-  plan->model_cost = 0;
   for (int p = 0; p < count; ++p) {
     if (m[p] < 0 || l[p] < 0 || n[p] < 0 || m[p] >= (int64_t(1) << 31) || l[p] >= (int64_t(1) << 31) ||
-        n[p] >= (int64_t(1) << 36)) {
+        n[p] >= (int64_t(1) << 31)) {
       delete plan;
       return FQ_EINVAL;
     }
     plan->shapes.push_back(Shape{m[p], l[p], n[p]});
     if (m[p] == 0 || n[p] == 0) continue;
+    // Four-Russians items of this product and their modelled cost
+    std::vector<std::pair<double, Item>> mine;
+    double m4rm = 0;
     const int64_t col_tiles = fq_pitch_words(n[p]) / ctw;
     const int64_t row_tiles = fqk::cdiv(m[p], mt_max);
     const int rows = int(fqk::cdiv(m[p], row_tiles));
@@ -310,29 +340,107 @@ int fq_batched_plan_create(int q, int count, const int64_t *m, const int64_t *l,
         it.col_tile = int32_t(ct);
         it.k = ct < real_tiles ? best_k : 0;
         const double cost = ct < real_tiles ? best : 1.0;
-        costed.push_back({cost, it});
-        plan->model_cost += cost;
+        mine.push_back({cost, it});
+        m4rm += cost * m4rm_unit_cycles(q);
       }
     }
+    // the path: the tcgen05 form takes F_3, F_5 and F_7 products with 0 < l
+    // within its exact range, when asked to or when its model is cheaper
+    const bool tc_ok = (q == 3 || q == 5 || q == 7) && l[p] > 0 && l[p] <= fqk::tc_max_l(q);
+    const double tc = tc_ok ? tc_product_cycles(m[p], l[p], n[p]) : 1e300;
+    const bool use_tc = tc_ok && (path == FQ_PATH_MMA || (path == FQ_PATH_AUTO && tc < m4rm));
+    if (!use_tc) {
+      for (auto &c : mine) costed.push_back(c);
+      plan->model_cost += m4rm;
+      continue;
+    }
+    fqk::BatchProd bp{};
+    bp.p = p;
+    bp.m = int32_t(m[p]);
+    bp.l = int32_t(l[p]);
+    bp.n = int32_t(n[p]);
+    bp.la = int32_t(fqk::cdiv(l[p], 128) * 128);
+    bp.nr = int32_t(fqk::cdiv(n[p], 256) * 256);
+    bp.pa = fq_pitch_words(l[p]);
+    bp.pb = fq_pitch_words(n[p]);
+    bp.pc = fq_pitch_words(n[p]);
+    bp.a_row0 = plan->a_rows;
+    bp.b_row0 = plan->b_rows;
+    // K-blocked arenas of 128-byte rows: 128-row (A) or 256-row (B^T) blocks,
+    // each holding its la / 128 k-slices one after another
+    plan->a_rows += fqk::cdiv(m[p], 128) * 128 * (bp.la / 128);
+    plan->b_rows += int64_t(bp.nr) * (bp.la / 128);
+    plan->tc_prods.push_back(bp);
+    plan->model_cost += tc;
   }
   // longest first
   std::stable_sort(costed.begin(), costed.end(),
                    [](const std::pair<double, Item> &a, const std::pair<double, Item> &b) { return a.first > b.first; });
   for (auto &c : costed) plan->items.push_back(c.second);
-  plan->workspace_bytes =
-      int64_t(sizeof(Header)) + shapes_bytes(count) + int64_t(plan->items.size()) * int64_t(sizeof(Item));
+  // tcgen05 work: conversion units (4 rows of A; 128 x 256 blocks of B^T) and
+  // tiles, a product's tiles consecutive (row block by row block); the kernel
+  // gives each CTA a contiguous run of equal modelled cost (k-steps + 2 per
+  // tile for its epilogue), so that one SM's consecutive tiles share data.
+  const int T = int(plan->tc_prods.size());
+  plan->tc_a_prefix.assign(size_t(T) + 1, 0);
+  plan->tc_b_prefix.assign(size_t(T) + 1, 0);
+  for (int i = 0; i < T; ++i) {
+    const fqk::BatchProd &bp = plan->tc_prods[size_t(i)];
+    const int64_t au = fqk::cdiv(bp.m, 4), bu = int64_t(bp.la / 128) * (bp.nr / 256);
+    plan->tc_a_prefix[size_t(i) + 1] = plan->tc_a_prefix[size_t(i)] + au;
+    plan->tc_b_prefix[size_t(i) + 1] = plan->tc_b_prefix[size_t(i)] + bu;
+    plan->tc_a_unit.insert(plan->tc_a_unit.end(), size_t(au), int32_t(i));
+    plan->tc_b_unit.insert(plan->tc_b_unit.end(), size_t(bu), int32_t(i));
+    for (int32_t mb = 0; mb < int32_t(fqk::cdiv(bp.m, 128)); ++mb)
+      for (int32_t nb = 0; nb < bp.nr / 256; ++nb) {
+        fqk::BatchTile bt{};
+        bt.prod = i;
+        bt.ksteps = bp.la / 128;
+        bt.ya = int32_t(bp.a_row0 + int64_t(mb) * (bp.la / 128) * 128);  // k-slice 0 of the row block
+        bt.yb = int32_t(bp.b_row0 + int64_t(nb) * (bp.la / 128) * 256);
+        bt.row0 = mb * 128;
+        bt.w0 = nb * 4;
+        plan->tc_tiles.push_back(bt);
+      }
+  }
+  plan->tc_tile_prefix.assign(plan->tc_tiles.size() + 1, 0);
+  for (size_t t = 0; t < plan->tc_tiles.size(); ++t)
+    plan->tc_tile_prefix[t + 1] = plan->tc_tile_prefix[t] + plan->tc_tiles[t].ksteps + 2;
+  // workspace: [header][shapes][items][products][A prefix][B prefix][unit
+  // products][tiles][tile prefix] | [A arena][B arena]
+  int64_t off = int64_t(sizeof(Header)) + shapes_bytes(count) + int64_t(plan->items.size()) * int64_t(sizeof(Item));
+  if (T > 0) {
+    plan->off_prods = off = align_up(off, 64);
+    off += int64_t(T) * int64_t(sizeof(fqk::BatchProd));
+    plan->off_aprefix = off = align_up(off, 64);
+    off += int64_t(T + 1) * 8;
+    plan->off_bprefix = off = align_up(off, 64);
+    off += int64_t(T + 1) * 8;
+    plan->off_aunit = off = align_up(off, 64);
+    off += int64_t(plan->tc_a_unit.size()) * 4;
+    plan->off_bunit = off = align_up(off, 64);
+    off += int64_t(plan->tc_b_unit.size()) * 4;
+    plan->off_tiles = off = align_up(off, 64);
+    off += int64_t(plan->tc_tiles.size()) * int64_t(sizeof(fqk::BatchTile));
+    plan->off_tprefix = off = align_up(off, 64);
+    off += int64_t(plan->tc_tile_prefix.size()) * 8;
+  }
+  plan->table_bytes = off;
+  if (T > 0) {
+    plan->off_a_arena = off = align_up(off, 1024);
+    off += plan->a_rows * 128;
+    plan->off_b_arena = off = align_up(off, 1024);
+    off += plan->b_rows * 128;
+  }
+  plan->workspace_bytes = off;
   *out = plan;
   return FQ_OK;
 }
 
-int64_t fq_batched_workspace_bytes(const fq_batch_plan *plan) { return plan ? plan->workspace_bytes : -1; }
-
-int64_t fq_batched_items(const fq_batch_plan *plan) { return plan ? int64_t(plan->items.size()) : -1; }
-
-int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *stream) {
+// The host image of a plan's tables (header .. tile list).
+std::vector<unsigned char> plan_tables(const fq_batch_plan *plan) {
   using namespace fqk::batched;
-  if (!plan || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 63u) != 0) return FQ_EINVAL;
-  std::vector<unsigned char> host(size_t(plan->workspace_bytes), 0);
+  std::vector<unsigned char> host(size_t(plan->table_bytes), 0);
   Header h{};
   h.next = 0;
   h.count = uint32_t(plan->count);
@@ -343,6 +451,65 @@ int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *str
   if (!plan->items.empty())
     memcpy(host.data() + sizeof(Header) + shapes_bytes(plan->count), plan->items.data(),
            plan->items.size() * sizeof(Item));
+  if (!plan->tc_prods.empty()) {
+    memcpy(host.data() + plan->off_prods, plan->tc_prods.data(), plan->tc_prods.size() * sizeof(fqk::BatchProd));
+    memcpy(host.data() + plan->off_aprefix, plan->tc_a_prefix.data(), plan->tc_a_prefix.size() * 8);
+    memcpy(host.data() + plan->off_bprefix, plan->tc_b_prefix.data(), plan->tc_b_prefix.size() * 8);
+    memcpy(host.data() + plan->off_aunit, plan->tc_a_unit.data(), plan->tc_a_unit.size() * 4);
+    memcpy(host.data() + plan->off_bunit, plan->tc_b_unit.data(), plan->tc_b_unit.size() * 4);
+    memcpy(host.data() + plan->off_tiles, plan->tc_tiles.data(), plan->tc_tiles.size() * sizeof(fqk::BatchTile));
+    memcpy(host.data() + plan->off_tprefix, plan->tc_tile_prefix.data(), plan->tc_tile_prefix.size() * 8);
+  }
+  return host;
+}
+
+// The tcgen05 part of a plan in the workspace `ws`.
+fqk::TcBatch tc_view(const fq_batch_plan *plan, unsigned char *ws) {
+  fqk::TcBatch b;
+  b.q = plan->q;
+  b.nprod = int(plan->tc_prods.size());
+  b.ntiles = int(plan->tc_tiles.size());
+  b.a_rows = plan->a_rows;
+  b.b_rows = plan->b_rows;
+  b.a_units = plan->tc_a_prefix.empty() ? 0 : plan->tc_a_prefix.back();
+  b.b_units = plan->tc_b_prefix.empty() ? 0 : plan->tc_b_prefix.back();
+  b.prods = reinterpret_cast<const fqk::BatchProd *>(ws + plan->off_prods);
+  b.a_prefix = reinterpret_cast<const int64_t *>(ws + plan->off_aprefix);
+  b.b_prefix = reinterpret_cast<const int64_t *>(ws + plan->off_bprefix);
+  b.a_unit_prod = reinterpret_cast<const int32_t *>(ws + plan->off_aunit);
+  b.b_unit_prod = reinterpret_cast<const int32_t *>(ws + plan->off_bunit);
+  b.tiles = reinterpret_cast<const fqk::BatchTile *>(ws + plan->off_tiles);
+  b.tile_prefix = reinterpret_cast<const int64_t *>(ws + plan->off_tprefix);
+  b.a_arena = ws + plan->off_a_arena;
+  b.b_arena = ws + plan->off_b_arena;
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fq_batched_plan_create(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n,
+                           fq_batch_plan **out) {
+  return plan_create(q, count, m, l, n, FQ_PATH_AUTO, out);
+}
+
+int fq_batched_plan_create_ex(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n, int path,
+                              fq_batch_plan **out) {
+  return plan_create(q, count, m, l, n, path, out);
+}
+
+int64_t fq_batched_workspace_bytes(const fq_batch_plan *plan) { return plan ? plan->workspace_bytes : -1; }
+
+int64_t fq_batched_items(const fq_batch_plan *plan) { return plan ? int64_t(plan->items.size()) : -1; }
+
+int64_t fq_batched_tc_products(const fq_batch_plan *plan) { return plan ? int64_t(plan->tc_prods.size()) : -1; }
+
+int64_t fq_batched_tc_tiles(const fq_batch_plan *plan) { return plan ? int64_t(plan->tc_tiles.size()) : -1; }
+
+int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *stream) {
+  if (!plan || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 63u) != 0) return FQ_EINVAL;
+  const std::vector<unsigned char> host = plan_tables(plan);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   FQ_CUDA_TRY(cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, s));
   FQ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -352,10 +519,13 @@ int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *str
 int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
                       uint64_t *const *C, void *workspace, void *stream) {
   if (!plan || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 63u) != 0) return FQ_EINVAL;
-  if (plan->items.empty()) return FQ_OK;
+  if (plan->items.empty() && plan->tc_prods.empty()) return FQ_OK;
   if (!A || !B || !C) return FQ_EINVAL;
   unsigned char *ws = static_cast<unsigned char *>(workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!plan->tc_prods.empty())
+    if (int rc = fqk::tc_batched(tc_view(plan, ws), A, B, C, s)) return rc;
+  if (plan->items.empty()) return FQ_OK;
   switch (plan->q) {
     case 3: return fqk::batched::launch_field<fqk::F3>(ws, A, B, C, s);
     case 4: return fqk::batched::launch_field<fqk::GF4>(ws, A, B, C, s);
@@ -412,9 +582,10 @@ extern "C" int fq_matmul_batched_static(const fq_batch_plan *plan, const uint64_
                                         const uint64_t *const *B, uint64_t *const *C, void *stream) {
   using namespace fqk::batched;
   if (!plan) return FQ_EINVAL;
-  if (plan->items.empty()) return FQ_OK;
+  if (plan->items.empty() && plan->tc_prods.empty()) return FQ_OK;
   if (!A || !B || !C) return FQ_EINVAL;
-  if (plan->workspace_bytes > kStaticScratchBytes) return FQ_ENOTSUP;  // does not fit the fixed array
+  // tcgen05 products need their arenas; the fixed array holds work lists only
+  if (!plan->tc_prods.empty() || plan->workspace_bytes > kStaticScratchBytes) return FQ_ENOTSUP;
   unsigned char *ws = nullptr;
   if (int rc = static_scratch(&ws)) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

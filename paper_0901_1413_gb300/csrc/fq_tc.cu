@@ -46,6 +46,7 @@ constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;  // + alignment slack
 constexpr int TMEM_COLS = ACC * BN;
 constexpr int THREADS = 256;
 constexpr int GROUP_M = 8;                     // tile order: default row blocks per group (L2 reuse)
+constexpr int THREADS_B = 384;                 // batched kernel: eight epilogue warps
 
 // ---------------------------------------------------------- conversions --
 
@@ -203,14 +204,15 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 // them in a shared 256 x 128-byte tile (16-byte chunks XOR-swizzled by row, so
 // that eight lanes hit eight bank groups); the tile leaves in 128-byte rows.
 constexpr int TK = 128, TJ = 256;
+// One 128 (k) x 256 (j) block of B^T from B's planes: bytes k0 + 16 c ..
+// of column j0 + jl go to out_block + jl * ld + 16 c, for k0 + 16 c < kcols
+// and j0 + jl < jcols.
 template <int Q, int P>
-__global__ void __launch_bounds__(256) planes_to_e4m3_t(const uint64_t *__restrict__ X, int64_t rows, int64_t pitch,
-                                                        uint8_t *__restrict__ out, int64_t ld, int64_t off,
-                                                        int64_t kcols, int sel) {
+__device__ __forceinline__ void transpose_block(const uint64_t *__restrict__ X, int64_t rows, int64_t pitch,
+                                                uint8_t *__restrict__ out_block, int64_t ld, int64_t kcols,
+                                                int64_t jcols, int sel, int64_t k0, int64_t j0, uint4 *tile) {
   using CF = ConvField<Q>;
-  __shared__ uint4 tile[TJ * TK / 16];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t k0 = int64_t(blockIdx.x) * TK, j0 = int64_t(blockIdx.y) * TJ;
   const int kq = warp & 3, jh = warp >> 2;
   const int64_t k = k0 + 32 * kq + lane;
   const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
@@ -235,9 +237,26 @@ __global__ void __launch_bounds__(256) planes_to_e4m3_t(const uint64_t *__restri
 #pragma unroll
   for (int i = threadIdx.x; i < TJ * 8; i += 256) {
     const int jl = i >> 3, c = i & 7;
-    const int64_t kk = k0 + 16 * c;
-    if (kk < kcols) *reinterpret_cast<uint4 *>(out + (j0 + jl) * ld + off + kk) = tile[jl * 8 + (c ^ (jl & 7))];
+    if (k0 + 16 * c < kcols && j0 + jl < jcols)
+      *reinterpret_cast<uint4 *>(out_block + jl * ld + 16 * c) = tile[jl * 8 + (c ^ (jl & 7))];
   }
+}
+
+// B^T as e4m3 bytes straight from B's planes: out[j * ld + off + k] = the byte
+// of B[k][j] for every column j of the planes' pitch (n_pad = 64 pitch) and
+// k < kcols (a multiple of 16; rows k >= rows read as zero).  A CTA of eight
+// warps turns a 128 (k) x 256 (j) block around: warp w loads rows k0 + 32 (w %
+// 4) + lane, 128 columns from j0 + 128 (w / 4), transposes each 32 x 32 bit
+// block across the warp, converts lane j's 32 bits into 32 bytes and puts
+// them in a shared 256 x 128-byte tile (16-byte chunks XOR-swizzled by row, so
+// that eight lanes hit eight bank groups); the tile leaves in 128-byte rows.
+template <int Q, int P>
+__global__ void __launch_bounds__(256) planes_to_e4m3_t(const uint64_t *__restrict__ X, int64_t rows, int64_t pitch,
+                                                        uint8_t *__restrict__ out, int64_t ld, int64_t off,
+                                                        int64_t kcols, int sel) {
+  __shared__ uint4 tile[TJ * TK / 16];
+  const int64_t k0 = int64_t(blockIdx.x) * TK, j0 = int64_t(blockIdx.y) * TJ;
+  transpose_block<Q, P>(X, rows, pitch, out + j0 * ld + off + k0, ld, kcols, int64_t(1) << 62, sel, k0, j0, tile);
 }
 
 // ------------------------------------------------------------------ GEMM --
@@ -326,34 +345,44 @@ __device__ __forceinline__ void tile_coords(const GemmParams &prm, int t, int &m
   nb = in / rows;
 }
 
-// One row of a 256-column accumulator (this lane's TMEM lane, from column
-// address taddr) reduced mod p and packed into plane words.
-template <int Q, int P>
-__device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&words)[P][BN / 64]) {
+// NW 64-column words of one accumulator row (this lane's TMEM lane, from
+// column address taddr), reduced mod p and packed into plane words.  Each
+// 32-value load is packed through four independent partial words, so that
+// the bit-or chains are short.
+template <int Q, int P, int NW = BN / 64>
+__device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&words)[P][NW]) {
 #pragma unroll
-  for (int p = 0; p < P; ++p)
-#pragma unroll
-    for (int w = 0; w < BN / 64; ++w) words[p][w] = 0ull;
-#pragma unroll
-  for (int c = 0; c < BN / 32; ++c) {
+  for (int c = 0; c < 2 * NW; ++c) {
     uint32_t v[32];
     tmem_ld32(taddr + uint32_t(c * 32), v);
+    uint32_t part[P][4];
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[p][j] = 0u;
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       const int x = int(__uint_as_float(v[i]));  // an exact integer
       const int mod = Q == 4 ? 2 : Q;
       int r = x % mod;
       r += r < 0 ? mod : 0;
-      const int col = c * 32 + i, w = col / 64, bit = col % 64;
       if constexpr (Q == 3) {
-        words[0][w] |= uint64_t(r != 0) << bit;
-        words[1][w] |= uint64_t(r == 2) << bit;
-      } else if constexpr (Q == 4) {
-        words[0][w] |= uint64_t(r) << bit;
+        part[0][i & 3] |= uint32_t(r != 0) << i;
+        part[1][i & 3] |= uint32_t(r == 2) << i;
+      } else if constexpr (Q == 4 || Q == 2) {
+        part[0][i & 3] |= uint32_t(r) << i;
       } else {
 #pragma unroll
-        for (int p = 0; p < P; ++p) words[p][w] |= uint64_t((r >> p) & 1) << bit;
+        for (int p = 0; p < P; ++p) part[p][i & 3] |= uint32_t((r >> p) & 1) << i;
       }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const uint64_t h = (part[p][0] | part[p][1]) | (part[p][2] | part[p][3]);
+      if (c & 1)
+        words[p][c >> 1] |= h << 32;
+      else
+        words[p][c >> 1] = h;
     }
   }
 }
@@ -700,6 +729,229 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
   }
 }
 
+// ---------------------------------------------------- batched products --
+
+// Arenas are K-blocked: rows of 128 bytes, and a product's 128-row block g
+// of A holds its la / 128 k-slices one after another (slice ks of row r at
+// arena row a_row0 + (g la / 128 + ks) 128 + r % 128), so that each TMA load
+// of a tile reads one contiguous 16 KB (A) or 32 KB (B^T, 256-row blocks).
+//
+// A of every product into the A arena: a unit is 4 rows, 64 threads a row,
+// 16 bytes a thread per step; rows m .. are not written.
+template <int Q, int P>
+__global__ void __launch_bounds__(256) batched_rows_kernel(const BatchProd *__restrict__ prods,
+                                                           const int64_t *__restrict__ prefix,
+                                                           const int32_t *__restrict__ unit_prod, int64_t units,
+                                                           const uint64_t *const *A, uint8_t *arena) {
+  using CF = ConvField<Q>;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int i = __ldg(unit_prod + u);
+    const BatchProd bp = prods[i];
+    const int64_t r = (u - __ldg(prefix + i)) * 4 + (threadIdx.x >> 6);
+    if (r >= bp.m) continue;
+    const uint32_t *X32 = reinterpret_cast<const uint32_t *>(A[bp.p]);
+    for (int piece = threadIdx.x & 63; piece * 16 < bp.la; piece += 64) {
+      uint32_t t[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) t[p] = __ldg(X32 + (p * int64_t(bp.m) + r) * bp.pa * 2 + (piece >> 1));
+      uint32_t o[CF::P2];
+      select_planes<Q, P>(t, 0, o);
+      const int64_t arow = bp.a_row0 + ((r >> 7) * (bp.la >> 7) + (piece >> 3)) * 128 + (r & 127);
+      *reinterpret_cast<uint4 *>(arena + arow * 128 + (piece & 7) * 16) = e4m3x16<Q, CF::P2>(o, 16 * (piece & 1));
+    }
+  }
+}
+
+// B^T of every product into the B arena: a unit is one 128 (k) x 256 (j)
+// block of one product; rows j >= n are not written.
+template <int Q, int P>
+__global__ void __launch_bounds__(256) batched_transpose_kernel(const BatchProd *__restrict__ prods,
+                                                                const int64_t *__restrict__ prefix,
+                                                                const int32_t *__restrict__ unit_prod,
+                                                                int64_t units, const uint64_t *const *B,
+                                                                uint8_t *arena) {
+  __shared__ uint4 tile[TJ * TK / 16];
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int i = __ldg(unit_prod + u);
+    const BatchProd bp = prods[i];
+    const int64_t kblocks = bp.la / TK, bi = u - __ldg(prefix + i);
+    const int64_t ks = bi % kblocks, g = bi / kblocks;
+    transpose_block<Q, P>(B[bp.p], bp.l, bp.pb, arena + (bp.b_row0 + (g * kblocks + ks) * TJ) * 128, 128, bp.la,
+                          bp.n, 0, ks * TK, g * TJ, tile);
+    __syncthreads();  // the shared tile is refilled by the next unit
+  }
+}
+
+struct BatchParams {
+  const BatchProd *prods;
+  const BatchTile *tiles;
+  const int64_t *tile_prefix;
+  int ntiles;
+  uint64_t *const *C;
+  unsigned *err;
+};
+
+// One row's words of a batched tile, columns past n cleared; the last column
+// tile also clears C's padding words up to the pitch.
+struct BatchOut {  // what an epilogue thread needs of its tile's product
+  uint64_t *C;
+  int64_t m, n, nr, pc;
+};
+
+template <int Q, int P>
+__device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, int64_t row, int64_t w0, int half,
+                                              uint64_t (&words)[P][2]) {
+  // this thread's two words w0 + 2 half, + 1 of a 256-column tile
+  const int64_t wa = w0 + 2 * half;
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    const int64_t c0 = (wa + w) * 64, keep = bp.n - c0;
+    const uint64_t mask = keep >= 64 ? ~0ull : (keep <= 0 ? 0ull : ((1ull << keep) - 1));
+#pragma unroll
+    for (int p = 0; p < P; ++p) words[p][w] &= mask;
+  }
+  const bool last = (w0 + BN / 64) * 64 >= bp.nr;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    uint64_t *dst = C + (int64_t(p) * bp.m + row) * bp.pc;
+    *reinterpret_cast<uint4 *>(dst + wa) = make_uint4(uint32_t(words[p][0]), uint32_t(words[p][0] >> 32),
+                                                      uint32_t(words[p][1]), uint32_t(words[p][1] >> 32));
+    if (last)  // C's padding words past the last tile, split between the two halves
+      for (int64_t w = w0 + BN / 64 + 2 * half; w < bp.pc; w += 4)
+        *reinterpret_cast<uint4 *>(dst + w) = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// First tile whose cumulative cost reaches `cost`.
+__device__ __forceinline__ int tile_at_cost(const int64_t *__restrict__ prefix, int ntiles, int64_t cost) {
+  int lo = 0, hi = ntiles;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] < cost) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// The single-SM persistent product (as tc_gemm_kernel) over the tiles of all
+// products.  CTA c takes the contiguous run of the plan's list (a product's
+// tiles row block by row block) whose cumulative modelled cost lies in
+// [c, c + 1) x total / CTAs, so that consecutive tiles on one SM share their
+// product's A rows and B^T columns through L2; each tile reads its product's
+// rows of the two arenas.
+template <int Q, int P>
+__global__ void __launch_bounds__(THREADS_B, 1)
+    tc_batched_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const BatchParams prm) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char *smem = smem_raw + (base - raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t full = base + BAR_OFF, empty = full + 8 * STAGES, accfull = empty + 8 * STAGES,
+                 accempty = accfull + 8 * ACC;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + BAR_OFF + 8 * NBARS);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + BAR_OFF + 8 * NBARS + 8);
+
+  if (tid == 0) {
+    *abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + 8 * s, 1);
+      mbar_init(empty + 8 * s, 1);
+    }
+    for (int b = 0; b < ACC; ++b) {
+      mbar_init(accfull + 8 * b, 1);
+      mbar_init(accempty + 8 * b, 8);  // eight epilogue warps
+    }
+    fence_mbar_init();
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int64_t total = prm.tile_prefix[prm.ntiles];
+  const int t_begin = tile_at_cost(prm.tile_prefix, prm.ntiles, total * int64_t(blockIdx.x) / gridDim.x);
+  const int t_end = tile_at_cost(prm.tile_prefix, prm.ntiles, total * int64_t(blockIdx.x + 1) / gridDim.x);
+
+  if (warp == 0 && lane == 0) {
+    int it = 0;
+    BatchTile nxt = t_begin < t_end ? prm.tiles[t_begin] : BatchTile{};
+    for (int t = t_begin; t < t_end && !*abort_flag; ++t) {
+      const BatchTile bt = nxt;  // this tile's record, fetched one tile ahead
+      if (t + 1 < t_end) nxt = prm.tiles[t + 1];
+      for (int ks = 0; ks < bt.ksteps; ++ks, ++it) {
+        const int s = it % STAGES;
+        if (it >= STAGES) wait_bar(empty + 8 * s, uint32_t((it / STAGES - 1) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+        const uint32_t a_dst = base + uint32_t(s * STAGE_BYTES), b_dst = a_dst + A_BYTES;
+        mbar_expect_tx(full + 8 * s, STAGE_BYTES);
+        tma_load_2d(a_dst, &tmA, full + 8 * s, 0, bt.ya + ks * BM);  // one contiguous 16 KB block
+        tma_load_2d(b_dst, &tmB, full + 8 * s, 0, bt.yb + ks * BN);  // one contiguous 32 KB block
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    int it = 0, li = 0;
+    int nks = t_begin < t_end ? prm.tiles[t_begin].ksteps : 0;
+    for (int t = t_begin; t < t_end && !*abort_flag; ++t, ++li) {
+      const int ksteps = nks;
+      if (t + 1 < t_end) nks = prm.tiles[t + 1].ksteps;
+      const int b = li % ACC;
+      if (li >= ACC) wait_bar(accempty + 8 * b, uint32_t((li / ACC - 1) & 1), abort_flag, prm.err);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t d = tmem + uint32_t(b * BN);
+      for (int ks = 0; ks < ksteps; ++ks, ++it) {
+        const int s = it % STAGES;
+        wait_bar(full + 8 * s, uint32_t((it / STAGES) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_src = base + uint32_t(s * STAGE_BYTES), b_src = a_src + A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / UK; ++kk)
+          mma_e4m3(d, smem_desc(a_src + UK * kk), smem_desc(b_src + UK * kk), (ks | kk) != 0);
+        mma_commit(empty + 8 * s);
+      }
+      mma_commit(accfull + 8 * b);
+    }
+  } else if (warp >= 4) {
+    // warps 4..11: TMEM lane quadrant warp % 4, columns 128 half .. + 127
+    const int ew = warp & 3, half = (warp - 4) >> 2;
+    int li = 0;
+    for (int t = t_begin; t < t_end; ++t, ++li) {
+      const int b = li % ACC;
+      // the tile's record, its product and C's address, read before the wait
+      const BatchTile bt = prm.tiles[t];
+      const BatchProd &pr = prm.prods[bt.prod];
+      BatchOut bo;
+      bo.m = pr.m;
+      bo.n = pr.n;
+      bo.nr = pr.nr;
+      bo.pc = pr.pc;
+      bo.C = prm.C[pr.p];
+      wait_bar(accfull + 8 * b, uint32_t((li / ACC) & 1), abort_flag, prm.err);
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t row = int64_t(bt.row0) + ew * 32 + lane;
+      uint64_t words[P][2];
+      drain_accumulator<Q, P, 2>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN + half * 128), words);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(accempty + 8 * b);
+      if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, bt.w0, half, words);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
 // ------------------------------------------------------------------ host --
 
 int make_map(CUtensorMap *map, const uint8_t *ptr, int64_t inner, int64_t rows, int box_rows) {
@@ -817,6 +1069,39 @@ int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, co
   return FQ_OK;
 }
 
+template <int Q, int P>
+int batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B, uint64_t *const *C,
+            cudaStream_t s) {
+  if (b.nprod == 0 || b.ntiles == 0) return FQ_OK;
+  unsigned *err = nullptr;
+  if (int rc = status_word(&err)) return rc;
+  const int64_t cap = 152 * 8;
+  if (b.a_units > 0)
+    batched_rows_kernel<Q, P><<<unsigned(b.a_units < cap ? b.a_units : cap), 256, 0, s>>>(
+        b.prods, b.a_prefix, b.a_unit_prod, b.a_units, A, b.a_arena);
+  if (b.b_units > 0)
+    batched_transpose_kernel<Q, P><<<unsigned(b.b_units < cap ? b.b_units : cap), 256, 0, s>>>(
+        b.prods, b.b_prefix, b.b_unit_prod, b.b_units, B, b.b_arena);
+  FQ_LAUNCH_CHECK();
+  CUtensorMap ma, mb;
+  if (int rc = make_map(&ma, b.a_arena, BK, b.a_rows, BM)) return rc;
+  if (int rc = make_map(&mb, b.b_arena, BK, b.b_rows, BN)) return rc;
+  BatchParams prm;
+  prm.prods = b.prods;
+  prm.tiles = b.tiles;
+  prm.tile_prefix = b.tile_prefix;
+  prm.ntiles = b.ntiles;
+  prm.C = C;
+  prm.err = err;
+  int dev = 0, sms = 0;
+  FQ_CUDA_TRY(cudaGetDevice(&dev));
+  FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  FQ_CUDA_TRY(cudaFuncSetAttribute(tc_batched_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+  tc_batched_kernel<Q, P><<<unsigned(b.ntiles < sms ? b.ntiles : sms), THREADS_B, SMEM, s>>>(ma, mb, prm);
+  FQ_LAUNCH_CHECK();
+  return FQ_OK;
+}
+
 }  // namespace tc
 
 // Largest l for which every partial sum stays below 2^24 in magnitude.
@@ -888,6 +1173,17 @@ int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const u
   if (rc == FQ_OK) rc = tc_multiply(q, m, l, n, mem, C, s, to);
   const int fr = scratch_free(mem, s);
   return rc ? rc : fr;
+}
+
+int tc_batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B, uint64_t *const *C,
+               cudaStream_t s) {
+  if (b.a_rows >= (int64_t(1) << 31) || b.b_rows >= (int64_t(1) << 31)) return FQ_ENOTSUP;
+  switch (b.q) {
+    case 3: return tc::batched<3, 2>(b, A, B, C, s);
+    case 5: return tc::batched<5, 3>(b, A, B, C, s);
+    case 7: return tc::batched<7, 3>(b, A, B, C, s);
+    default: return FQ_EINVAL;
+  }
 }
 
 }  // namespace fqk

@@ -60,8 +60,11 @@ def load():
             "fq_kernel_info": (i32, [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(i32)]),
             "fq_batched_plan_create": (i32, [i32, i32, vp, vp, vp, ctypes.POINTER(vp)]),
+            "fq_batched_plan_create_ex": (i32, [i32, i32, vp, vp, vp, i32, ctypes.POINTER(vp)]),
             "fq_batched_workspace_bytes": (i64, [vp]),
             "fq_batched_items": (i64, [vp]),
+            "fq_batched_tc_products": (i64, [vp]),
+            "fq_batched_tc_tiles": (i64, [vp]),
             "fq_batched_plan_upload": (i32, [vp, vp, vp]),
             "fq_matmul_batched": (i32, [vp, vp, vp, vp, vp, vp]),
             "fq_batched_plan_destroy": (i32, [vp]),
@@ -256,9 +259,10 @@ class TensorOperands:
 
 class BatchPlan:
     """fq_batched_plan_*: a plan for many products over one field, with its
-    device workspace (a torch buffer) already uploaded."""
+    device workspace (a torch buffer) already uploaded.  path: PATH_AUTO (per
+    product by the time models), PATH_M4RM or PATH_MMA."""
 
-    def __init__(self, q: int, shapes, device=None, stream=None):
+    def __init__(self, q: int, shapes, device=None, stream=None, path: int = PATH_AUTO):
         import numpy as np
         lib = load()
         sh = np.ascontiguousarray(np.asarray(shapes, dtype=np.int64).reshape(-1, 3))
@@ -266,12 +270,14 @@ class BatchPlan:
         self.shapes = sh
         m, l, n = (np.ascontiguousarray(sh[:, i]) for i in range(3))
         h = ctypes.c_void_p()
-        _check(lib.fq_batched_plan_create(q, len(sh), m.ctypes.data_as(ctypes.c_void_p),
-                                          l.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
-                                          ctypes.byref(h)), "fq_batched_plan_create")
+        _check(lib.fq_batched_plan_create_ex(q, len(sh), m.ctypes.data_as(ctypes.c_void_p),
+                                             l.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
+                                             path, ctypes.byref(h)), "fq_batched_plan_create_ex")
         self._h = h
         nbytes = lib.fq_batched_workspace_bytes(h)
         self.items = lib.fq_batched_items(h)
+        self.tc_products = lib.fq_batched_tc_products(h)
+        self.tc_tiles = lib.fq_batched_tc_tiles(h)
         dev = torch.device("cuda") if device is None else torch.device(device)
         self.workspace = torch.empty((nbytes + 63) // 64 * 8 + 8, dtype=torch.int64, device=dev)
         _check(lib.fq_batched_plan_upload(h, ctypes.c_void_p(self._ws_ptr()), _stream(stream)),

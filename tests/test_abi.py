@@ -99,11 +99,43 @@ def test_batch_plan_host_side(lib):
     l = np.array([70, 64, 5, 0], np.int64)
     n = np.array([600, 64, 9, 1100], np.int64)
     h = ctypes.c_void_p()
-    assert lib.fq_batched_plan_create(3, 4, i64p(m), i64p(l), i64p(n), ctypes.byref(h)) == fq.OK
+    assert lib.fq_batched_plan_create_ex(3, 4, i64p(m), i64p(l), i64p(n), fq.PATH_M4RM, ctypes.byref(h)) == fq.OK
     # items: one per row tile x column tile of the pitch (512-row x 512-column
     # tiles; tiles of padding only are zero-fill items): 1 x 2, 4 x 2, 0, 1 x 4
     assert lib.fq_batched_items(h) == 2 + 8 + 0 + 4
+    assert lib.fq_batched_tc_products(h) == 0
     assert lib.fq_batched_workspace_bytes(h) == 64 + 128 + 14 * 32
+    assert lib.fq_batched_plan_destroy(h) == fq.OK
+    # every product the tcgen05 form takes (l > 0; m = 0 needs no work): 100 x 70
+    # x 600 (1 x 3 tiles of 128 x 256) and 2000 x 64 x 64 (16 x 1); l = 0 stays
+    # a Four-Russians product (4 zero-fill items).  Tables: header 64, shapes 128,
+    # items 4 x 32, products 2 x 64, prefixes 2 x 24, the product of each
+    # conversion unit (25 + 500 four-row units of A, 3 + 1 blocks of B^T; 4
+    # bytes each), tiles 19 x 32, their cost prefix 20 x 8, each part 64-byte
+    # aligned -> 3520 bytes;
+    # arenas (1024-aligned) of 128-byte rows: A 128 + 2048 rows, B^T 768 + 256.
+    assert lib.fq_batched_plan_create_ex(3, 4, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.OK
+    assert lib.fq_batched_items(h) == 4
+    assert lib.fq_batched_tc_products(h) == 2
+    assert lib.fq_batched_tc_tiles(h) == 3 + 16
+    assert lib.fq_batched_workspace_bytes(h) == 4096 + 2176 * 128 + 1024 * 128
+    assert lib.fq_batched_plan_destroy(h) == fq.OK
+    assert lib.fq_batched_plan_create_ex(3, 4, i64p(m), i64p(l), i64p(n), 9, ctypes.byref(h)) == fq.EINVAL
+    assert lib.fq_batched_tc_products(None) == -1
+    # GF(4) products stay on Four Russians even when the tensor path is asked for
+    assert lib.fq_batched_plan_create_ex(4, 4, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.OK
+    assert lib.fq_batched_tc_products(h) == 0
+    assert lib.fq_batched_plan_destroy(h) == fq.OK
+    # the 4096-product batch workload: the models put (almost) every product on
+    # the tcgen05 path (a 128 x 256 tile costs ~760 cycles per 128-deep step;
+    # a Four-Russians item pays ~2000 units of set-up alone)
+    from paper_0901_1413_gb300 import inputs
+    bs = np.asarray(inputs.batch_shapes(4096, seed=3), np.int64).reshape(-1, 3)
+    bm, bl, bn = (np.ascontiguousarray(bs[:, i]) for i in range(3))
+    assert lib.fq_batched_plan_create(3, 4096, i64p(bm), i64p(bl), i64p(bn), ctypes.byref(h)) == fq.OK
+    assert lib.fq_batched_tc_products(h) > 4000
+    assert lib.fq_batched_plan_destroy(h) == fq.OK
+    assert lib.fq_batched_plan_create(3, 4, i64p(m), i64p(l), i64p(n), ctypes.byref(h)) == fq.OK
     assert lib.fq_batched_plan_upload(h, ctypes.c_void_p(8), None) == fq.EINVAL      # misaligned
     assert lib.fq_matmul_batched(h, None, None, None, ctypes.c_void_p(64), None) == fq.EINVAL
     assert lib.fq_batched_plan_destroy(h) == fq.OK

@@ -28,6 +28,9 @@ def make_batch(fq, q, shapes, seed):
     return A, B, a, b, c, ptr(a), ptr(b), ptr(c)
 
 
+PATHS = {"auto": 0, "m4rm": 1, "mma": 2}
+
+
 def check(fq, q, A, B, c):
     for p in range(len(A)):
         m, n = A[p].shape[0], B[p].shape[1]
@@ -35,29 +38,55 @@ def check(fq, q, A, B, c):
             continue
         got = fq.unpack(c[p]).cpu().numpy()
         assert np.array_equal(got, oracle.matmul(q, A[p], B[p])), "product %d %s" % (p, (m, A[p].shape[1], n))
+        # padding: bits past n and words past them are zero in every plane
+        v = c[p].planes_view().cpu().numpy().view(np.uint64)
+        w = (n + 63) // 64
+        assert not v[:, :, w:].any(), "product %d: padding words" % p
+        if n % 64:
+            assert not (v[:, :, w - 1] >> np.uint64(n % 64)).any(), "product %d: bits past n" % p
 
 
+@pytest.mark.parametrize("path", ["auto", "m4rm", "mma"])
 @pytest.mark.parametrize("q", FIELDS)
-def test_batched_matches_oracle(fq, q):
+def test_batched_matches_oracle(fq, q, path):
     rng = np.random.default_rng(q)
     shapes = [tuple(int(x) for x in rng.choice(np.arange(64, 577, 64), 3)) for _ in range(20)]
-    shapes += [(1, 1, 1), (7, 100, 70), (300, 65, 1100), (1200, 130, 90), (5, 0, 9), (0, 5, 9), (4, 9, 0)]
+    shapes += [(1, 1, 1), (7, 100, 70), (300, 65, 1100), (1200, 130, 90), (5, 0, 9), (0, 5, 9), (4, 9, 0),
+               (129, 1000, 257), (2, 3000, 300)]
     A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=q)
-    plan = fq.BatchPlan(q, shapes)
-    assert plan.items >= 24
+    plan = fq.BatchPlan(q, shapes, path=PATHS[path])
+    if path == "m4rm" or q == 4:
+        assert plan.tc_products == 0 and plan.items >= 26
+    if path == "mma" and q != 4:
+        assert plan.tc_products == len(shapes) - 3      # all but l = 0, m = 0, n = 0
     plan.run(pa, pb, pc)
     assert fq.status() == fq.OK
     check(fq, q, A, B, c)
     # l = 0: C = 0
-    assert not c[len(shapes) - 3].data.cpu().numpy()[: 2 * 5 * 16].any()
+    assert not c[len(shapes) - 5].data.cpu().numpy()[: 2 * 5 * 16].any()
 
 
+@pytest.mark.parametrize("q", [3, 5, 7])
+def test_batched_mixed_paths_in_one_plan(fq, q):
+    """An AUTO plan with products on both paths (an l = 0 product is always a
+    Four-Russians zero fill): both launches of one call give the oracle's
+    results."""
+    shapes = [(8, 8, 8), (16, 40, 24), (1024, 1024, 1024), (512, 896, 768), (64, 0, 64), (960, 320, 1000)]
+    A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=q + 20)
+    plan = fq.BatchPlan(q, shapes)
+    assert plan.tc_products == 5 and plan.items > 0
+    plan.run(pa, pb, pc)
+    assert fq.status() == fq.OK
+    check(fq, q, A, B, c)
+
+
+@pytest.mark.parametrize("path", ["m4rm", "mma"])
 @pytest.mark.parametrize("q", [3, 5])
-def test_batched_graph_capture_and_replay(fq, q):
+def test_batched_graph_capture_and_replay(fq, q, path):
     rng = np.random.default_rng(10 + q)
     shapes = [tuple(int(x) for x in rng.choice(np.arange(64, 449, 64), 3)) for _ in range(12)]
     A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=1)
-    plan = fq.BatchPlan(q, shapes)
+    plan = fq.BatchPlan(q, shapes, path=PATHS[path])
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):
@@ -93,7 +122,7 @@ def test_batched_4096_products(fq, q):
     a sample of products against the oracle, and all of them by Freivalds."""
     shapes = [tuple(int(x) for x in s) for s in inputs.batch_shapes(4096, seed=q)]
     A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=q)
-    plan = fq.BatchPlan(q, shapes)
+    plan = fq.BatchPlan(q, shapes)          # AUTO: the time models pick each product's path
     plan.run(pa, pb, pc)
     assert fq.status() == fq.OK
     sample = list(range(0, 4096, 97))

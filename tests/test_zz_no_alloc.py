@@ -50,7 +50,7 @@ def test_static_workspace_matches_workspace_entry_on_consecutive_calls(fq):
     for q, shapes, seed in cases:
         a, b = _batch(fq, q, shapes, seed)
         ref = _outputs(fq, q, shapes)
-        plan = fq.BatchPlan(q, shapes)
+        plan = fq.BatchPlan(q, shapes, path=fq.PATH_M4RM)   # work lists only: fits the fixed array
         ra, rb, rc_ = _ptrs(a), _ptrs(b), _ptrs(ref)
         plan.run(ra, rb, rc_)
         torch.cuda.synchronize()
@@ -75,5 +75,16 @@ def test_static_workspace_refuses_plans_that_do_not_fit(fq):
     shapes = np.full((40000, 3), 8, np.int64)           # 40000 products: > 1 MiB of work list
     plan = fq.BatchPlan(3, shapes)
     assert lib.fq_batched_workspace_bytes(plan._h) > (1 << 20)
+    rc = run_static(plan._h, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), None)
+    assert rc == fq.ENOTSUP
+
+
+def test_static_workspace_refuses_plans_with_tensor_core_products(fq):
+    """A plan with tcgen05 products needs its e4m3 arenas, which the fixed
+    array cannot hold: refused before anything is enqueued."""
+    lib = fq.load()
+    run_static = _entry(lib)
+    plan = fq.BatchPlan(3, [(256, 512, 512), (64, 64, 64)], path=fq.PATH_MMA)
+    assert plan.tc_products == 2
     rc = run_static(plan._h, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), None)
     assert rc == fq.ENOTSUP
