@@ -24,6 +24,10 @@ against the classical product's work).
   measured HBM copy bandwidth;
   ``m4rm.roofline``: the M4RM kernels against the integer-logic (LOP3) issue
   rate (the algorithmic LOP3 of every M4RM launch over the products' time).
+* ``batched``: 4096 independent products over F_3 and over F_5 (m, l, n
+  uniform over multiples of 64 in [64, 1024]) in one graph-captured launch
+  sequence: products/s and 2mln/s for the FQ_PATH_AUTO plan and for the
+  Four-Russians-only plan.
 * ``cpu_baseline``: the CPU oracle on a bounded sample of rows of the same
   products, all host cores.
 
@@ -107,8 +111,69 @@ def parse():
                     help="comma-separated n list (uniform square products) instead of the workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 4096-product batched workloads")
     ap.add_argument("--cpu-rows", type=int, default=48, help="oracle rows sampled per product")
     return ap.parse_args()
+
+
+def batched_leg(torch, fq, inputs, dist, dev, reps=10):
+    """The batched workloads: 4096 products over F_3 and over F_5 with m, l, n
+    uniform over multiples of 64 in [64, 1024], one plan each, its launch
+    captured in a CUDA graph and replayed (device time, CUDA events on the
+    replaying stream); the FQ_PATH_AUTO plan (per-product choice between the
+    two paths) beside the Four-Russians-only plan.  Every rank runs its own
+    batch; the slowest rank's time counts."""
+    out = {}
+    for q in (3, 5):
+        shapes = [tuple(int(x) for x in s) for s in inputs.batch_shapes(4096, seed=q)]
+        a, b, c = [], [], []
+        for p, (m, l, n) in enumerate(shapes):
+            a.append(fq.pack(q, inputs.uniform_torch(q, m, l, seed=q, stream=100 + 2 * p, device="cuda")))
+            b.append(fq.pack(q, inputs.uniform_torch(q, l, n, seed=q, stream=101 + 2 * p, device="cuda")))
+            c.append(fq.empty(q, m, n))
+        ptr = lambda xs: torch.tensor([x.data.data_ptr() for x in xs], dtype=torch.int64, device=dev)
+        pa, pb, pc = ptr(a), ptr(b), ptr(c)
+        ops = sum(2.0 * m * l * n for m, l, n in shapes)
+        rec = {"count": len(shapes), "shapes": "m, l, n uniform over multiples of 64 in [64, 1024]"}
+        results = {}
+        for name, path in (("auto", fq.PATH_AUTO), ("m4rm", fq.PATH_M4RM)):
+            plan = fq.BatchPlan(q, shapes, path=path)
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                plan.run(pa, pb, pc, stream=stream)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                plan.run(pa, pb, pc, stream=stream)
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize()
+            dist.barrier()
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                with torch.cuda.stream(stream):
+                    g.replay()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = dist.max(statistics.median(ms), dev)
+            results[name] = torch.cat([x.data for x in c]).clone()
+            entry = {"ms": t, "products_per_s": dist.world * len(shapes) / (t * 1e-3),
+                     "field_ops_per_s": dist.world * ops / (t * 1e-3),
+                     "tc_products": plan.tc_products, "m4rm_items": plan.items}
+            rec[name] = entry
+            del g, plan
+        if not torch.equal(results["auto"], results["m4rm"]):
+            raise SystemExit("batched F_%d: the two plans give different products" % q)
+        if fq.status() != fq.OK:
+            raise SystemExit("device error in the batched workload")
+        rec["speedup_auto_vs_m4rm"] = rec["m4rm"]["ms"] / rec["auto"]["ms"]
+        out["F_%d" % q] = rec
+        del a, b, c, results
+        torch.cuda.empty_cache()
+    return out
 
 
 def products_for(args):
@@ -600,6 +665,8 @@ def main():
                       "ms_per_step": p_ms, "steps": e_steps,
                       "inputs": "bit-planes (fq_pack's format) in pinned host memory; fq_matmul on the device"}
 
+    batched = None if args.no_batched else batched_leg(torch, fq, inputs, dist, dev)
+
     base = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         ops, times, cores, nrows = cpu_baseline(prods, args.cpu_rows)
@@ -633,6 +700,7 @@ def main():
             "speedup_vs_m4rm": value / m_value,
             "e2e": e2e,
             "e2e_packed": e2e_packed,
+            "batched": batched,
             "cpu_baseline": base,
             "clocks": clk,
             "gpu_launches": args.steps * sum(TC_LAUNCHES if f == "tensor" else 1 for f in forms),

@@ -304,6 +304,32 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
   const int mt_max = (q == 3 || q == 4) ? fqk::batched::max_rows<fqk::F3>() : fqk::batched::max_rows<fqk::F5>();
   const int ctw = (q == 3 || q == 4) ? fqk::batched::tile_words<fqk::F3>() : fqk::batched::tile_words<fqk::F5>();
   std::vector<std::pair<double, Item>> costed;
+  // AUTO's products that the per-product models gave to Four Russians but the
+  // tcgen05 form could take (with their costs), for the whole-plan check below
+  struct Alt {
+    int p;
+    double m4rm, tc, longest;
+  };
+  std::vector<Alt> alts;
+  auto add_tc = [&](int p) {
+    fqk::BatchProd bp{};
+    bp.p = p;
+    bp.m = int32_t(m[p]);
+    bp.l = int32_t(l[p]);
+    bp.n = int32_t(n[p]);
+    bp.la = int32_t(fqk::cdiv(l[p], 128) * 128);
+    bp.nr = int32_t(fqk::cdiv(n[p], 256) * 256);
+    bp.pa = fq_pitch_words(l[p]);
+    bp.pb = fq_pitch_words(n[p]);
+    bp.pc = fq_pitch_words(n[p]);
+    bp.a_row0 = plan->a_rows;
+    bp.b_row0 = plan->b_rows;
+    // K-blocked arenas of 128-byte rows: 128-row (A) or 256-row (B^T) blocks,
+    // each holding its la / 128 k-slices one after another
+    plan->a_rows += fqk::cdiv(m[p], 128) * 128 * (bp.la / 128);
+    plan->b_rows += int64_t(bp.nr) * (bp.la / 128);
+    plan->tc_prods.push_back(bp);
+  };
   for (int p = 0; p < count; ++p) {
     if (m[p] < 0 || l[p] < 0 || n[p] < 0 || m[p] >= (int64_t(1) << 31) || l[p] >= (int64_t(1) << 31) ||
         n[p] >= (int64_t(1) << 31)) {
@@ -350,43 +376,58 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
     const double tc = tc_ok ? tc_product_cycles(m[p], l[p], n[p]) : 1e300;
     const bool use_tc = tc_ok && (path == FQ_PATH_MMA || (path == FQ_PATH_AUTO && tc < m4rm));
     if (!use_tc) {
+      if (tc_ok && path == FQ_PATH_AUTO) {
+        double longest = 0;
+        for (auto &c : mine) longest = c.first > longest ? c.first : longest;
+        alts.push_back(Alt{p, m4rm, tc, longest * m4rm_unit_cycles(q)});
+      }
       for (auto &c : mine) costed.push_back(c);
       plan->model_cost += m4rm;
       continue;
     }
-    fqk::BatchProd bp{};
-    bp.p = p;
-    bp.m = int32_t(m[p]);
-    bp.l = int32_t(l[p]);
-    bp.n = int32_t(n[p]);
-    bp.la = int32_t(fqk::cdiv(l[p], 128) * 128);
-    bp.nr = int32_t(fqk::cdiv(n[p], 256) * 256);
-    bp.pa = fq_pitch_words(l[p]);
-    bp.pb = fq_pitch_words(n[p]);
-    bp.pc = fq_pitch_words(n[p]);
-    bp.a_row0 = plan->a_rows;
-    bp.b_row0 = plan->b_rows;
-    // K-blocked arenas of 128-byte rows: 128-row (A) or 256-row (B^T) blocks,
-    // each holding its la / 128 k-slices one after another
-    plan->a_rows += fqk::cdiv(m[p], 128) * 128 * (bp.la / 128);
-    plan->b_rows += int64_t(bp.nr) * (bp.la / 128);
-    plan->tc_prods.push_back(bp);
+    add_tc(p);
     plan->model_cost += tc;
+  }
+  // Whole plan: a Four-Russians launch for a few products cannot fill the GPU
+  // (its time is at least its longest item, plus ~20 us of launch); if the
+  // tcgen05 launch would absorb them in less time, they go there too.
+  if (!alts.empty() && !plan->tc_prods.empty()) {
+    double m4rm = 0, tc = 0, longest = 0;
+    for (const Alt &a : alts) {
+      m4rm += a.m4rm;
+      tc += a.tc;
+      longest = a.longest > longest ? a.longest : longest;
+    }
+    const double sms = 152.0;
+    const double m4rm_wall = (m4rm / sms > longest ? m4rm / sms : longest) + 40000.0;
+    if (tc / sms < m4rm_wall) {
+      std::vector<char> moved(size_t(count), 0);
+      for (const Alt &a : alts) moved[size_t(a.p)] = 1;
+      std::vector<std::pair<double, Item>> keep;
+      for (auto &c : costed)
+        if (!moved[size_t(c.second.product)]) keep.push_back(c);
+      costed.swap(keep);
+      for (const Alt &a : alts) {
+        add_tc(a.p);
+        plan->model_cost += a.tc - a.m4rm;
+      }
+    }
   }
   // longest first
   std::stable_sort(costed.begin(), costed.end(),
                    [](const std::pair<double, Item> &a, const std::pair<double, Item> &b) { return a.first > b.first; });
   for (auto &c : costed) plan->items.push_back(c.second);
-  // tcgen05 work: conversion units (4 rows of A; 128 x 256 blocks of B^T) and
+  // tcgen05 work: conversion units (256 16-byte pieces of A; 128 x 256 blocks
+  // of B^T) and
   // tiles, a product's tiles consecutive (row block by row block); the kernel
-  // gives each CTA a contiguous run of equal modelled cost (k-steps + 2 per
-  // tile for its epilogue), so that one SM's consecutive tiles share data.
+  // gives each CTA a contiguous run of equal modelled cost, so that one SM's
+  // consecutive tiles share data.
   const int T = int(plan->tc_prods.size());
   plan->tc_a_prefix.assign(size_t(T) + 1, 0);
   plan->tc_b_prefix.assign(size_t(T) + 1, 0);
   for (int i = 0; i < T; ++i) {
     const fqk::BatchProd &bp = plan->tc_prods[size_t(i)];
-    const int64_t au = fqk::cdiv(bp.m, 4), bu = int64_t(bp.la / 128) * (bp.nr / 256);
+    const int64_t au = fqk::cdiv(int64_t(bp.m) * (bp.la / 16), 256), bu = int64_t(bp.la / 128) * (bp.nr / 256);
     plan->tc_a_prefix[size_t(i) + 1] = plan->tc_a_prefix[size_t(i)] + au;
     plan->tc_b_prefix[size_t(i) + 1] = plan->tc_b_prefix[size_t(i)] + bu;
     plan->tc_a_unit.insert(plan->tc_a_unit.end(), size_t(au), int32_t(i));
@@ -403,9 +444,14 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
         plan->tc_tiles.push_back(bt);
       }
   }
+  // modelled tile cost in half k-steps: the MMAs (ksteps) overlap the previous
+  // tile's epilogue (about four k-steps' time on GB300), plus a fixed
+  // hand-over of 1.5
   plan->tc_tile_prefix.assign(plan->tc_tiles.size() + 1, 0);
-  for (size_t t = 0; t < plan->tc_tiles.size(); ++t)
-    plan->tc_tile_prefix[t + 1] = plan->tc_tile_prefix[t] + plan->tc_tiles[t].ksteps + 2;
+  for (size_t t = 0; t < plan->tc_tiles.size(); ++t) {
+    const int ks = plan->tc_tiles[t].ksteps;
+    plan->tc_tile_prefix[t + 1] = plan->tc_tile_prefix[t] + 2 * (ks > 4 ? ks : 4) + 3;
+  }
   // workspace: [header][shapes][items][products][A prefix][B prefix][unit
   // products][tiles][tile prefix] | [A arena][B arena]
   int64_t off = int64_t(sizeof(Header)) + shapes_bytes(count) + int64_t(plan->items.size()) * int64_t(sizeof(Item));

@@ -736,8 +736,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 // arena row a_row0 + (g la / 128 + ks) 128 + r % 128), so that each TMA load
 // of a tile reads one contiguous 16 KB (A) or 32 KB (B^T, 256-row blocks).
 //
-// A of every product into the A arena: a unit is 4 rows, 64 threads a row,
-// 16 bytes a thread per step; rows m .. are not written.
+// A of every product into the A arena: a unit is 256 consecutive 16-element
+// pieces of one product (row-major over m rows of la / 16 pieces), one per
+// thread; rows m .. are not written.
 template <int Q, int P>
 __global__ void __launch_bounds__(256) batched_rows_kernel(const BatchProd *__restrict__ prods,
                                                            const int64_t *__restrict__ prefix,
@@ -747,10 +748,13 @@ __global__ void __launch_bounds__(256) batched_rows_kernel(const BatchProd *__re
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int i = __ldg(unit_prod + u);
     const BatchProd bp = prods[i];
-    const int64_t r = (u - __ldg(prefix + i)) * 4 + (threadIdx.x >> 6);
-    if (r >= bp.m) continue;
+    const int per_row = bp.la >> 4;
+    const int64_t q = (u - __ldg(prefix + i)) * 256 + threadIdx.x;
+    if (q >= int64_t(bp.m) * per_row) continue;
+    const int64_t r = q / per_row;
+    const int piece = int(q - r * per_row);
     const uint32_t *X32 = reinterpret_cast<const uint32_t *>(A[bp.p]);
-    for (int piece = threadIdx.x & 63; piece * 16 < bp.la; piece += 64) {
+    {
       uint32_t t[P];
 #pragma unroll
       for (int p = 0; p < P; ++p) t[p] = __ldg(X32 + (p * int64_t(bp.m) + r) * bp.pa * 2 + (piece >> 1));

@@ -110,15 +110,15 @@ def test_batch_plan_host_side(lib):
     # x 600 (1 x 3 tiles of 128 x 256) and 2000 x 64 x 64 (16 x 1); l = 0 stays
     # a Four-Russians product (4 zero-fill items).  Tables: header 64, shapes 128,
     # items 4 x 32, products 2 x 64, prefixes 2 x 24, the product of each
-    # conversion unit (25 + 500 four-row units of A, 3 + 1 blocks of B^T; 4
-    # bytes each), tiles 19 x 32, their cost prefix 20 x 8, each part 64-byte
-    # aligned -> 3520 bytes;
+    # conversion unit (256-piece units of A: 100 x 8 and 2000 x 8 pieces -> 4 +
+    # 63; 3 + 1 blocks of B^T; 4 bytes each), tiles 19 x 32, their cost prefix
+    # 20 x 8, each part 64-byte aligned -> 1760 bytes;
     # arenas (1024-aligned) of 128-byte rows: A 128 + 2048 rows, B^T 768 + 256.
     assert lib.fq_batched_plan_create_ex(3, 4, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.OK
     assert lib.fq_batched_items(h) == 4
     assert lib.fq_batched_tc_products(h) == 2
     assert lib.fq_batched_tc_tiles(h) == 3 + 16
-    assert lib.fq_batched_workspace_bytes(h) == 4096 + 2176 * 128 + 1024 * 128
+    assert lib.fq_batched_workspace_bytes(h) == 2048 + 2176 * 128 + 1024 * 128
     assert lib.fq_batched_plan_destroy(h) == fq.OK
     assert lib.fq_batched_plan_create_ex(3, 4, i64p(m), i64p(l), i64p(n), 9, ctypes.byref(h)) == fq.EINVAL
     assert lib.fq_batched_tc_products(None) == -1
