@@ -62,7 +62,7 @@ def product_rows(q, m, l, n, paths=("m4rm",), sparse=False, reps=3):
     return out
 
 
-def batched_row(q, count=4096, reps=5):
+def batched_row(q, count=4096, reps=5, path=None):
     shapes = [tuple(int(x) for x in s) for s in inputs.batch_shapes(count, seed=q)]
     a, b, c = [], [], []
     for p, (m, l, n) in enumerate(shapes):
@@ -71,7 +71,7 @@ def batched_row(q, count=4096, reps=5):
         c.append(fq.empty(q, m, n))
     ptr = lambda xs: torch.tensor([x.data.data_ptr() for x in xs], dtype=torch.int64, device="cuda")
     pa, pb, pc = ptr(a), ptr(b), ptr(c)
-    plan = fq.BatchPlan(q, shapes)
+    plan = fq.BatchPlan(q, shapes, path=fq.PATH_AUTO if path is None else path)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         plan.run(pa, pb, pc, stream=stream)
@@ -126,6 +126,7 @@ def main():
     ap.add_argument("--case", help="time one product only: q,m,l,n[,path[,kernel]]")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--strassen", action="store_true", help="direct vs Strassen-Winograd levels only")
+    ap.add_argument("--batched", help="the 4096-product batch only: q[,auto|m4rm|mma]")
     args = ap.parse_args()
     fq.load()
     if args.case:
@@ -133,6 +134,14 @@ def main():
         return
     if args.strassen:
         strassen_table()
+        return
+    if args.batched:
+        parts = args.batched.split(",")
+        q = int(parts[0])
+        path = {"auto": fq.PATH_AUTO, "m4rm": fq.PATH_M4RM, "mma": fq.PATH_MMA}[parts[1] if len(parts) > 1 else "auto"]
+        t, pps, ops, items = batched_row(q, reps=args.reps, path=path)
+        print("| batched F_%d (%s) | %.3f ms | %.3e products/s | %.3e field-ops/s | %d items |" % (
+            q, parts[1] if len(parts) > 1 else "auto", t, pps, ops, items))
         return
     print("| configuration | path | ms | field-ops/s |")
     print("|---|---|---:|---:|")
