@@ -152,20 +152,28 @@ template <int Q, int P>
 __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64_t cols, int64_t pitch,
                              uint8_t *__restrict__ out, int64_t ld, int64_t off, int sel) {
   using CF = ConvField<Q>;
-  // grid: x over the 16-byte pieces of a row, y over groups of RPT rows (grid-stride)
+  // grid: x over the 16-byte pieces of a row, y over groups of RPT rows
+  // (grid-stride); the next group's words are loaded before this group is
+  // converted and stored
   const int64_t piece = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t c0 = piece * 16;
   if (c0 >= cols) return;
   const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
   const int64_t half = piece >> 1;    // the 32-bit half word holding the 16 elements
   const int b0 = 16 * int(piece & 1);
-  for (int64_t r0 = int64_t(blockIdx.y) * RPT; r0 < rows; r0 += int64_t(gridDim.y) * RPT) {
-    uint32_t t[RPT][P];
+  auto load = [&](int64_t r0, uint32_t (&t)[RPT][P]) {
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
 #pragma unroll
       for (int p = 0; p < P; ++p)
         t[i][p] = r0 + i < rows ? __ldg(X32 + (p * rows + r0 + i) * pitch * 2 + half) : 0u;
+  };
+  const int64_t step = int64_t(gridDim.y) * RPT;
+  int64_t r0 = int64_t(blockIdx.y) * RPT;
+  uint32_t t[RPT][P], nt[RPT][P];
+  if (r0 < rows) load(r0, t);
+  for (; r0 < rows; r0 += step) {
+    if (r0 + step < rows) load(r0 + step, nt);
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
       if (r0 + i >= rows) break;
@@ -173,13 +181,20 @@ __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64
       select_planes<Q, P>(t[i], sel, o);
       *reinterpret_cast<uint4 *>(out + (r0 + i) * ld + off + c0) = e4m3x16<Q, CF::P2>(o, b0);
     }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+      for (int p = 0; p < P; ++p) t[i][p] = nt[i][p];
   }
 }
 
-// Launch shape of rows_to_e4m3 for rows x cols (cols a multiple of 16).
+// Launch shape of rows_to_e4m3 for rows x cols (cols a multiple of 16): one
+// wave of 256-thread blocks (8 per SM on 152 SMs), each walking row groups.
 inline dim3 rows_grid(int64_t rows, int64_t cols) {
-  const int64_t pieces = cols / 16, ys = cdiv(rows, RPT);
-  return dim3(unsigned(cdiv(pieces, 256)), unsigned(ys < 65535 ? (ys > 0 ? ys : 1) : 65535));
+  const int64_t pieces = cols / 16, xs = cdiv(pieces, 256), groups = cdiv(rows, RPT);
+  const int64_t want = cdiv(int64_t(152) * 8, xs);
+  const int64_t ys = groups < want ? groups : want;
+  return dim3(unsigned(xs), unsigned(ys < 65535 ? (ys > 0 ? ys : 1) : 65535));
 }
 
 // 32 x 32 bit transpose across a warp: afterwards bit i of lane j's word is
@@ -215,13 +230,16 @@ __device__ __forceinline__ void transpose_block(const uint64_t *__restrict__ X, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kq = warp & 3, jh = warp >> 2;
   const int64_t k = k0 + 32 * kq + lane;
-  const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
-  const int64_t h0 = (j0 + 128 * jh) / 32;  // first 32-bit half word of the warp's columns
+  const int64_t w0 = (j0 + 128 * jh) / 64;  // first word of the warp's 128 columns (16-byte aligned)
   uint32_t t[4][P];
 #pragma unroll
-  for (int g = 0; g < 4; ++g)
-#pragma unroll
-    for (int p = 0; p < P; ++p) t[g][p] = k < rows ? __ldg(X32 + (p * rows + k) * pitch * 2 + h0 + g) : 0u;
+  for (int p = 0; p < P; ++p) {
+    const uint4 v = k < rows ? __ldg(reinterpret_cast<const uint4 *>(X + (p * rows + k) * pitch + w0)) : make_uint4(0u, 0u, 0u, 0u);
+    t[0][p] = v.x;
+    t[1][p] = v.y;
+    t[2][p] = v.z;
+    t[3][p] = v.w;
+  }
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     uint32_t o[CF::P2];
