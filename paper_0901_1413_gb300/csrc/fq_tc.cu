@@ -46,7 +46,7 @@ constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;  // + alignment slack
 constexpr int TMEM_COLS = ACC * BN;
 constexpr int THREADS = 256;
 constexpr int GROUP_M = 8;                     // tile order: default row blocks per group (L2 reuse)
-constexpr int THREADS_B = 384;                 // batched kernel: eight epilogue warps
+constexpr int THREADS_B = 640;                 // batched kernel: sixteen epilogue warps
 
 // ---------------------------------------------------------- conversions --
 
@@ -368,9 +368,19 @@ __device__ __forceinline__ void tile_coords(const GemmParams &prm, int t, int &m
 // 32-value load is packed through four independent partial words, so that
 // the bit-or chains are short.
 template <int Q, int P, int NW = BN / 64>
-__device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&words)[P][NW]) {
+__device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&words)[P][NW], int live = 2 * NW) {
 #pragma unroll
   for (int c = 0; c < 2 * NW; ++c) {
+    if (c >= live) {  // columns past the product's n (warp-uniform): nothing to read
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        if (c & 1)
+          words[p][c >> 1] &= 0xFFFFFFFFull;
+        else
+          words[p][c >> 1] = 0ull;
+      }
+      continue;
+    }
     uint32_t v[32];
     tmem_ld32(taddr + uint32_t(c * 32), v);
     uint32_t part[P][4];
@@ -821,26 +831,19 @@ struct BatchOut {  // what an epilogue thread needs of its tile's product
 };
 
 template <int Q, int P>
-__device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, int64_t row, int64_t w0, int half,
-                                              uint64_t (&words)[P][2]) {
-  // this thread's two words w0 + 2 half, + 1 of a 256-column tile
-  const int64_t wa = w0 + 2 * half;
-#pragma unroll
-  for (int w = 0; w < 2; ++w) {
-    const int64_t c0 = (wa + w) * 64, keep = bp.n - c0;
-    const uint64_t mask = keep >= 64 ? ~0ull : (keep <= 0 ? 0ull : ((1ull << keep) - 1));
-#pragma unroll
-    for (int p = 0; p < P; ++p) words[p][w] &= mask;
-  }
+__device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, int64_t row, int64_t w0, int quarter,
+                                              uint64_t (&words)[P][1]) {
+  // this thread's word w0 + quarter of a 256-column tile
+  const int64_t wa = w0 + quarter;
+  const int64_t keep = bp.n - wa * 64;
+  const uint64_t mask = keep >= 64 ? ~0ull : (keep <= 0 ? 0ull : ((1ull << keep) - 1));
   const bool last = (w0 + BN / 64) * 64 >= bp.nr;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     uint64_t *dst = C + (int64_t(p) * bp.m + row) * bp.pc;
-    *reinterpret_cast<uint4 *>(dst + wa) = make_uint4(uint32_t(words[p][0]), uint32_t(words[p][0] >> 32),
-                                                      uint32_t(words[p][1]), uint32_t(words[p][1] >> 32));
-    if (last)  // C's padding words past the last tile, split between the two halves
-      for (int64_t w = w0 + BN / 64 + 2 * half; w < bp.pc; w += 4)
-        *reinterpret_cast<uint4 *>(dst + w) = make_uint4(0u, 0u, 0u, 0u);
+    dst[wa] = words[p][0] & mask;
+    if (last)  // C's padding words past the last tile, split between the four quarters
+      for (int64_t w = w0 + BN / 64 + quarter; w < bp.pc; w += 4) dst[w] = 0ull;
   }
 }
 
@@ -882,7 +885,7 @@ __global__ void __launch_bounds__(THREADS_B, 1)
     }
     for (int b = 0; b < ACC; ++b) {
       mbar_init(accfull + 8 * b, 1);
-      mbar_init(accempty + 8 * b, 8);  // eight epilogue warps
+      mbar_init(accempty + 8 * b, 16);  // sixteen epilogue warps
     }
     fence_mbar_init();
   }
@@ -940,8 +943,8 @@ __global__ void __launch_bounds__(THREADS_B, 1)
       mma_commit(accfull + 8 * b);
     }
   } else if (warp >= 4) {
-    // warps 4..11: TMEM lane quadrant warp % 4, columns 128 half .. + 127
-    const int ew = warp & 3, half = (warp - 4) >> 2;
+    // warps 4..19: TMEM lane quadrant warp % 4, columns 64 quarter .. + 63
+    const int ew = warp & 3, quarter = (warp - 4) >> 2;
     int li = 0;
     for (int t = t_begin; t < t_end; ++t, ++li) {
       const int b = li % ACC;
@@ -958,12 +961,15 @@ __global__ void __launch_bounds__(THREADS_B, 1)
       if (*abort_flag) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int64_t row = int64_t(bt.row0) + ew * 32 + lane;
-      uint64_t words[P][2];
-      drain_accumulator<Q, P, 2>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN + half * 128), words);
+      const int64_t col0 = (int64_t(bt.w0) + quarter) * 64;
+      // 32-column chunks holding columns < n
+      const int live = bo.n <= col0 ? 0 : (bo.n - col0 > 32 ? 2 : 1);
+      uint64_t words[P][1];
+      drain_accumulator<Q, P, 1>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN + quarter * 64), words, live);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_cta(accempty + 8 * b);
-      if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, bt.w0, half, words);
+      if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, bt.w0, quarter, words);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
