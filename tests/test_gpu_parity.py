@@ -348,14 +348,17 @@ def test_tcgen05_exact_near_its_range(fq):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("m", [3, 260])
 @pytest.mark.parametrize("q, l, codes", [(7, None, (1, 2, 3)), (3, 1 << 22, (0, 1))])
-def test_tcgen05_exact_with_random_low_bits(fq, q, l, codes):
+def test_tcgen05_exact_with_random_low_bits(fq, q, l, codes, m):
     """Rows of A all +3 (F_7) or all +1 (F_3) against random positive B: every
     step of the tensor-core sum adds a random amount, so an accumulation that
     dropped low bits anywhere on the way to 2^24 (F_7 at its longest exact l)
-    or 2^22 (F_3) would change the residues.  C = A B is a column sum of B."""
+    or 2^22 (F_3) would change the residues.  C = A B is a column sum of B.
+    m = 3 runs the single-SM kernel, m = 260 the SM-pair kernel (its second
+    pair tile half outside m)."""
     l = l or _tc_max_l(fq, q)
-    m, n = 3, 70
+    n = 70
     a = 3 if q == 7 else 1
     A = np.full((m, l), a, np.uint8)
     B = np.random.default_rng(q).choice(np.array(codes, np.uint8), size=(l, n))
