@@ -28,8 +28,11 @@ against the classical product's work).
   uniform over multiples of 64 in [64, 1024]) in one graph-captured launch
   sequence: products/s and 2mln/s for the FQ_PATH_AUTO plan and for the
   Four-Russians-only plan.
+* ``pack_unpack``: fq_pack of the step's operands and fq_unpack of its results,
+  timed apart from the product (the metric excludes them).
 * ``cpu_baseline``: the CPU oracle on a bounded sample of rows of the same
-  products, all host cores.
+  products, all host cores (and single-threaded on a smaller sample), with
+  the host CPU's model.
 
 ``--impl reference`` times the oracle alone (the reference arm).  Under
 torchrun with N > 1 ranks every rank runs the whole workload on its own GPU
@@ -351,8 +354,29 @@ def make_inputs(torch, inputs, prods, seed=0):
     return out
 
 
-def cpu_baseline(prods, rows_per_product, seed=0, steps=1):
-    """The oracle (as it stands) on the first rows_per_product rows of every product."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), best effort."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
+def cpu_baseline(prods, rows_per_product, seed=0, steps=1, threads=0):
+    """The oracle (as it stands) on the first rows_per_product rows of every
+    product, on `threads` host threads (0: all)."""
     import numpy as np
 
     import oracle
@@ -369,10 +393,10 @@ def cpu_baseline(prods, rows_per_product, seed=0, steps=1):
     for _ in range(steps):
         t0 = time.perf_counter()
         for (A, B, _, _, _) in work:
-            C = oracle.matmul(Q, A, B)
+            C = oracle.matmul(Q, A, B, threads)
             assert C.dtype == np.uint8
         times.append(time.perf_counter() - t0)
-    return ops, times, oracle.threads_used(0), sum(r for (_, _, r, _, _) in work)
+    return ops, times, oracle.threads_used(threads), sum(r for (_, _, r, _, _) in work)
 
 
 def run_reference(args, dist):
@@ -390,7 +414,7 @@ def run_reference(args, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.sizes else "F_3 square n=" + args.sizes, "q": Q,
                    "sample": "first %d rows of each product" % rows},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                          "sample": "first %d rows of each of the %d products (%d rows total)"
                                    % (rows, len(prods), nrows)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -489,6 +513,39 @@ def main():
     per_product = [sum(stage[s_][j][0] + stage[s_][j][1] for s_ in range(args.steps)) / args.steps
                    for j in range(len(prods))]
     product_ms = [sum(stage[s_][j][1] for s_ in range(args.steps)) / args.steps for j in range(len(prods))]
+
+    # Pack and unpack, reported apart from the product: the step's eight
+    # operands packed from device-resident residues, its four results unpacked.
+    def pack_unpack_ms(reps=10):
+        outs = [torch.empty((m, n), dtype=torch.uint8, device=dev) for (m, l, n, _) in prods]
+        tp, tu = [], []
+        for _ in range(reps + 2):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            for (A, B), (a, b, c) in zip(res, packed):
+                fq.pack(Q, A, out=a)
+                fq.pack(Q, B, out=b)
+            e[1].record(stream)
+            for (a, b, c), o in zip(packed, outs):
+                fq.unpack(c, out=o)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            tp.append(e[0].elapsed_time(e[1]))
+            tu.append(e[1].elapsed_time(e[2]))
+        if fq.status() != fq.OK:
+            raise SystemExit("device error in pack / unpack")
+        in_bytes = sum(m * l + l * n for (m, l, n, _) in prods)
+        out_bytes = sum(m * n for (m, l, n, _) in prods)
+        p_ms, u_ms = statistics.median(tp[2:]), statistics.median(tu[2:])
+        planes = lambda r, c: 2 * r * pitch_words(c) * 8
+        p_bytes = in_bytes + sum(planes(m, l) + planes(l, n) for (m, l, n, _) in prods)
+        u_bytes = out_bytes + sum(planes(m, n) for (m, l, n, _) in prods)
+        return {"pack_ms": p_ms, "unpack_ms": u_ms, "pack_gbs": p_bytes / (p_ms * 1e-3) / 1e9,
+                "unpack_gbs": u_bytes / (u_ms * 1e-3) / 1e9,
+                "note": "per step: 8 operands packed (residues in, planes out), 4 results unpacked; "
+                        "bytes = residues + planes; median of 10 after 2 warm-ups"}
+
+    pack_unpack = pack_unpack_ms()
 
     # Roofline of the dominant kernel, the tcgen05 product: 2 m l n flops (e4m3
     # operands, fp32 sums) per launch over the product stage's event time.
@@ -670,9 +727,13 @@ def main():
     base = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         ops, times, cores, nrows = cpu_baseline(prods, args.cpu_rows)
-        base = {"value": ops / times[0], "unit": UNIT, "cores": cores, "kind": "oracle",
+        rows1 = max(1, args.cpu_rows // 6)
+        ops1, times1, _, nrows1 = cpu_baseline(prods, rows1, threads=1)
+        base = {"value": ops / times[0], "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                 "sample": "first %d rows of each of the %d products (%d rows), one pass"
-                          % (args.cpu_rows, len(prods), nrows)}
+                          % (args.cpu_rows, len(prods), nrows),
+                "single_thread": {"value": ops1 / times1[0], "unit": UNIT, "cores": 1,
+                                  "sample": "first %d rows of each product (%d rows), one pass" % (rows1, nrows1)}}
 
     if dist.rank == 0:
         line = {
@@ -698,6 +759,7 @@ def main():
             "product_stage_ms": product_ms,
             "m4rm": m4rm,
             "speedup_vs_m4rm": value / m_value,
+            "pack_unpack": pack_unpack,
             "e2e": e2e,
             "e2e_packed": e2e_packed,
             "batched": batched,
