@@ -107,8 +107,9 @@ typedef struct fq_options {
   int variant;   /* M4RM rows per CTA: 0 = planner, else 1 .. the kernel's maximum;
                     tcgen05 path: row blocks per group of the tile order (0 = 8) */
   int kernel;    /* M4RM kernel: 0 = planner, i + 1 = compiled kernel i of field q;
-                    tensor-core path: 0 = tcgen05 (SM pairs when m > 128),
-                    1 = the mma.sync s8 form, 2 = tcgen05 on single SMs       */
+                    tensor-core path: 0 = tcgen05 by shape, 1 = the mma.sync
+                    s8 form, 2 = tcgen05 on single SMs (128 x 256 tiles),
+                    3 = on SM pairs (256 x 256), 4 = on SM pairs (256 x 512) */
   int strassen;  /* Strassen-Winograd levels over the base-field products: 0 = the
                     time model decides, -1 = none, L > 0 = L levels (each needs
                     m, l, n to be multiples of 2048 at that level)               */

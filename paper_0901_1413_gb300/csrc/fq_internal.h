@@ -22,8 +22,8 @@ int launch_mma(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const 
 // The tcgen05 form of the tensor-core path (fq_tc.cu): FQ_ENOTSUP when l is
 // beyond the exact fp32 range of the field (tc_max_l).
 struct TcOptions {
-  bool single_sm = false;  // the single-SM kernel even where SM pairs would run
-  int group = 0;           // row blocks per group of the tile order (0: 8)
+  int form = 0;   // 0: by shape; 2: single SMs; 3: SM pairs, 256-column tiles; 4: SM pairs, 512-column tiles
+  int group = 0;  // row blocks per group of the tile order (0: 8)
 };
 int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
               cudaStream_t s, const TcOptions &to = TcOptions());

@@ -563,11 +563,28 @@ __global__ void __launch_bounds__(THREADS, 1)
 // leader's barrier.  Per flop, each SM moves two thirds of the operand bytes
 // of the single-CTA kernel.
 
-constexpr int STAGES2 = 6;
-constexpr int A2_BYTES = 128 * BK, B2_BYTES = 128 * BK, STAGE2_BYTES = A2_BYTES + B2_BYTES;
-constexpr int BAR2_OFF = STAGES2 * STAGE2_BYTES;
-constexpr int NBARS2 = 2 * STAGES2 + 2 * ACC;
-constexpr int SMEM2 = BAR2_OFF + 8 * NBARS2 + 16 + 1024;
+constexpr int A2_BYTES = 128 * BK, B2_BYTES = 128 * BK;  // a CTA's 128 rows of A, or of one B^T block
+constexpr int kWideKsteps = 96;  // k-slices from which the wide pair form runs (l > 12160)
+
+// Geometry of the SM-pair kernels.  The standard form owns 256 x 256 tiles
+// with two 256-column accumulators (the epilogue overlaps the next tile); the
+// wide form owns 256 x 512 tiles with one 512-column accumulator: each CTA
+// stages two 128-row B^T blocks per k-slice and the leader issues two MMAs
+// (N = 256 each) per 32-deep step, so a k-slice brings 48 KB for 1024 MMA
+// cycles instead of 32 KB for 512 (a third more time to cover a load's
+// latency with the same 192 KB ring), at the price of an epilogue that no
+// MMA overlaps.
+template <bool WIDE>
+struct PairGeo {
+  static constexpr int NB = WIDE ? 512 : 256;       // columns of C per pair tile
+  static constexpr int BBLK = NB / 256;             // 128-row B^T blocks per CTA per stage
+  static constexpr int STAGE = A2_BYTES + BBLK * B2_BYTES;
+  static constexpr int STAGES = WIDE ? 4 : 6;
+  static constexpr int NACC = WIDE ? 1 : 2;         // accumulators of NB columns (NB * NACC = 512)
+  static constexpr int BAR_OFF = STAGES * STAGE;
+  static constexpr int NBARS = 2 * STAGES + 2 * NACC;
+  static constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;
+};
 // kind::f8f6f4, fp32 accumulator, e4m3 A and B, K-major, N = 256, M = 256
 constexpr uint32_t kIdesc2 = (1u << 4) | (uint32_t(BN >> 3) << 17) | (uint32_t(256 >> 4) << 24);
 
@@ -640,10 +657,11 @@ __device__ __forceinline__ void wait_bar_cluster(uint32_t bar, uint32_t parity, 
   }
 }
 
-template <int Q, int P>
+template <int Q, int P, bool WIDE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     tc_gemm2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const GemmParams prm) {
+  using G = PairGeo<WIDE>;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned (128-byte swizzle atoms)
@@ -651,18 +669,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
-  const uint32_t full = base + BAR2_OFF, empty = full + 8 * STAGES2, accfull = empty + 8 * STAGES2,
-                 accempty = accfull + 8 * ACC;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + BAR2_OFF + 8 * NBARS2);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + BAR2_OFF + 8 * NBARS2 + 8);
+  const uint32_t full = base + G::BAR_OFF, empty = full + 8 * G::STAGES, accfull = empty + 8 * G::STAGES,
+                 accempty = accfull + 8 * G::NACC;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + G::BAR_OFF + 8 * G::NBARS);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + G::BAR_OFF + 8 * G::NBARS + 8);
 
   if (tid == 0) {
     *abort_flag = 0;
-    for (int s = 0; s < STAGES2; ++s) {
+    for (int s = 0; s < G::STAGES; ++s) {
       mbar_init(full + 8 * s, 1);   // the leader's producer arrives; both CTAs' bytes complete it
       mbar_init(empty + 8 * s, 1);  // one multicast commit
     }
-    for (int b = 0; b < ACC; ++b) {
+    for (int b = 0; b < G::NACC; ++b) {
       mbar_init(accfull + 8 * b, 1);
       mbar_init(accempty + 8 * b, 8);  // four epilogue warps in each CTA (the leader's barrier)
     }
@@ -682,42 +700,48 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
   const int cl = int(blockIdx.x >> 1), ncl = int(gridDim.x >> 1);
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer (both CTAs): this CTA's halves of A and B^T
+    // ---- TMA producer (both CTAs): this CTA's rows of A and of each B^T block
     int it = 0;
     for (int t = cl; t < prm.tiles && !*abort_flag; t += ncl) {
       int mb, nb;
       tile_coords(prm, t, mb, nb);
       for (int ks = 0; ks < prm.ksteps; ++ks, ++it) {
-        const int s = it % STAGES2;
-        if (it >= STAGES2) wait_bar(empty + 8 * s, uint32_t((it / STAGES2 - 1) & 1), abort_flag, prm.err);
+        const int s = it % G::STAGES;
+        if (it >= G::STAGES) wait_bar(empty + 8 * s, uint32_t((it / G::STAGES - 1) & 1), abort_flag, prm.err);
         if (*abort_flag) break;
-        if (leader) mbar_expect_tx(full + 8 * s, 2 * STAGE2_BYTES);
+        if (leader) mbar_expect_tx(full + 8 * s, 2 * G::STAGE);
         const uint32_t bar = map_to_rank(full + 8 * s, 0);
-        const uint32_t a_dst = base + uint32_t(s * STAGE2_BYTES), b_dst = a_dst + A2_BYTES;
+        const uint32_t a_dst = base + uint32_t(s * G::STAGE), b_dst = a_dst + A2_BYTES;
         tma_load_2d_pair(a_dst, &tmA, bar, ks * BK, mb * 256 + 128 * int(rank));
-        tma_load_2d_pair(b_dst, &tmB, bar, ks * BK, nb * 256 + 128 * int(rank));
+#pragma unroll
+        for (int j = 0; j < G::BBLK; ++j)
+          tma_load_2d_pair(b_dst + uint32_t(j * B2_BYTES), &tmB, bar, ks * BK, nb * G::NB + 256 * j + 128 * int(rank));
       }
     }
     // the last commits to this CTA's stage barriers have landed before it exits
-    for (int j = it > STAGES2 ? it - STAGES2 : 0; j < it; ++j)
-      wait_bar(empty + 8 * (j % STAGES2), uint32_t((j / STAGES2) & 1), abort_flag, prm.err);
+    for (int j = it > G::STAGES ? it - G::STAGES : 0; j < it; ++j)
+      wait_bar(empty + 8 * (j % G::STAGES), uint32_t((j / G::STAGES) & 1), abort_flag, prm.err);
   } else if (warp == 1 && lane == 0 && leader) {
     // ---- MMA issuer (the leader CTA only)
     int it = 0, li = 0;
     for (int t = cl; t < prm.tiles && !*abort_flag; t += ncl, ++li) {
-      const int b = li % ACC;
-      if (li >= ACC) wait_bar_cluster(accempty + 8 * b, uint32_t((li / ACC - 1) & 1), abort_flag, prm.err);
+      const int b = li % G::NACC;
+      if (li >= G::NACC)
+        wait_bar_cluster(accempty + 8 * b, uint32_t((li / G::NACC - 1) & 1), abort_flag, prm.err);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t d = tmem + uint32_t(b * BN);
+      const uint32_t d = tmem + uint32_t(b * G::NB);
       for (int ks = 0; ks < prm.ksteps; ++ks, ++it) {
-        const int s = it % STAGES2;
-        wait_bar(full + 8 * s, uint32_t((it / STAGES2) & 1), abort_flag, prm.err);
+        const int s = it % G::STAGES;
+        wait_bar(full + 8 * s, uint32_t((it / G::STAGES) & 1), abort_flag, prm.err);
         if (*abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a_src = base + uint32_t(s * STAGE2_BYTES), b_src = a_src + A2_BYTES;
+        const uint32_t a_src = base + uint32_t(s * G::STAGE), b_src = a_src + A2_BYTES;
 #pragma unroll
         for (int kk = 0; kk < BK / UK; ++kk)
-          mma_e4m3_pair(d, smem_desc(a_src + UK * kk), smem_desc(b_src + UK * kk), (ks | kk) != 0);
+#pragma unroll
+          for (int j = 0; j < G::BBLK; ++j)  // B^T block j -> accumulator columns 256 j ..
+            mma_e4m3_pair(d + uint32_t(256 * j), smem_desc(a_src + UK * kk),
+                          smem_desc(b_src + uint32_t(j * B2_BYTES) + UK * kk), (ks | kk) != 0);
         mma_commit_pair(empty + 8 * s);  // both CTAs' stage s is free once these MMAs have read it
       }
       mma_commit_pair(accfull + 8 * b);  // this tile's accumulators are complete in both CTAs
@@ -728,15 +752,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     const uint32_t back = leader ? accempty : map_to_rank(accempty, 0);
     int li = 0;
     for (int t = cl; t < prm.tiles; t += ncl, ++li) {
-      const int b = li % ACC;
-      wait_bar(accfull + 8 * b, uint32_t((li / ACC) & 1), abort_flag, prm.err);
+      const int b = li % G::NACC;
+      wait_bar(accfull + 8 * b, uint32_t((li / G::NACC) & 1), abort_flag, prm.err);
       if (*abort_flag) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       int mb, nb;
       tile_coords(prm, t, mb, nb);
       const int64_t row = int64_t(mb) * 256 + 128 * int(rank) + ew * 32 + lane;
-      uint64_t words[P][BN / 64];
-      drain_accumulator<Q, P>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN), words);
+#pragma unroll 1
+      for (int j = 0; j < G::BBLK; ++j) {  // 256 columns at a time
+        uint64_t words[P][BN / 64];
+        drain_accumulator<Q, P>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * G::NB + 256 * j), words);
+        if (row < prm.m) store_words<Q, P>(prm, row, int64_t(nb) * (G::NB / 64) + 4 * j, words);
+      }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
@@ -745,7 +773,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
         else
           mbar_arrive_cluster(back + 8 * b);
       }
-      if (row < prm.m) store_words<Q, P>(prm, row, int64_t(nb) * (BN / 64), words);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1003,8 +1030,12 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
   unsigned *err = nullptr;
   if (int rc = status_word(&err)) return rc;
   // SM pairs take 256 x 256 tiles; a product of at most 128 rows would leave
-  // half of every pair idle, so it runs on single SMs (128 x 256 tiles).
-  const bool pair = !to.single_sm && m > BM;
+  // half of every pair idle, so it runs on single SMs (128 x 256 tiles).  Deep
+  // products (at least kWideKsteps k-slices) take the wide pair form (256 x
+  // 512), whose extra latency cover outweighs its unoverlapped epilogue.
+  const int ksteps = int(la / BK);
+  const int form = to.form ? to.form : (m <= BM ? 2 : (ksteps >= kWideKsteps ? 4 : 3));
+  const bool pair = form == 3 || form == 4, wide = form == 4;
   const int rows = pair ? 2 * BM : BM;
   CUtensorMap ma, mb;
   if (int rc = make_map(&ma, Ab, la, m, BM)) return rc;
@@ -1015,7 +1046,7 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
   prm.pc = pc;
   prm.ksteps = int(la / BK);
   prm.mblocks = int(cdiv(m, rows));
-  prm.nblocks = int(npad / BN);
+  prm.nblocks = int(npad / (wide ? 2 * BN : BN));
   const int64_t tiles = int64_t(prm.mblocks) * prm.nblocks;
   if (tiles >= (int64_t(1) << 31)) return FQ_ENOTSUP;
   prm.tiles = int(tiles);
@@ -1026,10 +1057,17 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
   FQ_CUDA_TRY(cudaGetDevice(&dev));
   FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (pair) {
-    FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm2_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2));
     const int64_t pairs = sms / 2 > 0 ? sms / 2 : 1;
     const int grid = 2 * int(tiles < pairs ? tiles : pairs);
-    tc_gemm2_kernel<Q, P><<<grid, THREADS, SMEM2, s>>>(ma, mb, prm);
+    if (wide) {
+      FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm2_kernel<Q, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       PairGeo<true>::SMEM));
+      tc_gemm2_kernel<Q, P, true><<<grid, THREADS, PairGeo<true>::SMEM, s>>>(ma, mb, prm);
+    } else {
+      FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm2_kernel<Q, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       PairGeo<false>::SMEM));
+      tc_gemm2_kernel<Q, P, false><<<grid, THREADS, PairGeo<false>::SMEM, s>>>(ma, mb, prm);
+    }
   } else {
     FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
     const int grid = int(tiles < sms ? tiles : sms);

@@ -299,13 +299,16 @@ def test_mma_sync_form_matches_oracle(fq, q, mln):
     _check_product(fq, q, *mln, seed=sum(mln) + 11 * q, path=fq.PATH_MMA, kernel=1)
 
 
+@pytest.mark.parametrize("kernel", [2, 3, 4])
 @pytest.mark.parametrize("q", FIELDS)
-@pytest.mark.parametrize("mln", [(1, 1, 1), (128, 300, 257), (129, 300, 257), (300, 500, 260), (513, 257, 1025)])
-def test_tcgen05_single_sm_form_matches_oracle(fq, q, mln):
-    """fq_options.kernel = 2: the single-SM tcgen05 kernel (128 x 256 tiles)
-    where SM pairs would otherwise run; equal to the oracle and to the pair
-    kernel's result."""
-    got, c1 = _check_product(fq, q, *mln, seed=sum(mln) + 13 * q, path=fq.PATH_MMA, kernel=2)
+@pytest.mark.parametrize("mln", [(1, 1, 1), (128, 300, 257), (129, 300, 257), (300, 500, 260), (513, 257, 1025),
+                                 (260, 1300, 1100)])
+def test_tcgen05_forms_match_oracle(fq, q, mln, kernel):
+    """fq_options.kernel = 2, 3, 4: the single-SM tcgen05 kernel (128 x 256
+    tiles), the SM-pair kernel (256 x 256) and the wide SM-pair kernel (256 x
+    512), each forced whatever the shape; equal to the oracle and to the form
+    the shape takes by default."""
+    got, c1 = _check_product(fq, q, *mln, seed=sum(mln) + 13 * q, path=fq.PATH_MMA, kernel=kernel)
     m, l, n = mln
     A = inputs.uniform(q, m, l, seed=sum(mln) + 13 * q, stream=inputs.STREAM_A)
     B = inputs.uniform(q, l, n, seed=sum(mln) + 13 * q, stream=inputs.STREAM_B)
