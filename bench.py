@@ -750,7 +750,7 @@ def main():
                          "frac": achieved / peaks["fp8"], "traffic": traffic,
                          "peak_note": peaks["note"],
                          "kernel": "tc_gemm2_kernel (tcgen05.mma.cta_group::2 kind::f8f6f4 e4m3 on SM pairs, "
-                                   "persistent; 256x256 tiles, 256x512 for l >= 12288)",
+                                   "persistent; 256x512 tiles for l >= 8192, 256x256 below)",
                          "kernel_ms_per_step": sum(product_ms)},
             "prepare": {"bound": "hbm", "ms_per_step": prep_ms, "bytes": prep_bytes, "achieved": prep_gbs,
                         "peak": peaks["hbm"], "unit": "GB/s", "frac": prep_gbs / peaks["hbm"],

@@ -417,28 +417,28 @@ __device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&wor
 
 // Store one row's packed words at word w0 of C's row.  GF(4): plane < 0
 // writes the F_2 result into both planes, else XORs it into that plane.
-template <int Q, int P>
+template <int Q, int P, int NW = BN / 64>
 __device__ __forceinline__ void store_words(const GemmParams &prm, int64_t row, int64_t w0,
-                                            const uint64_t (&words)[P][BN / 64]) {
+                                            const uint64_t (&words)[P][NW]) {
   if constexpr (Q == 4) {
     if (prm.plane < 0) {
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + w0;
 #pragma unroll
-        for (int w = 0; w < BN / 64; ++w) dst[w] = words[0][w];
+        for (int w = 0; w < NW; ++w) dst[w] = words[0][w];
       }
     } else {
       uint64_t *dst = prm.C + (int64_t(prm.plane) * prm.m + row) * prm.pc + w0;
 #pragma unroll
-      for (int w = 0; w < BN / 64; ++w) dst[w] ^= words[0][w];
+      for (int w = 0; w < NW; ++w) dst[w] ^= words[0][w];
     }
   } else {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       uint64_t *dst = prm.C + (int64_t(p) * prm.m + row) * prm.pc + w0;
 #pragma unroll
-      for (int w = 0; w < BN / 64; ++w) dst[w] = words[p][w];
+      for (int w = 0; w < NW; ++w) dst[w] = words[p][w];
     }
   }
 }
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 // of the single-CTA kernel.
 
 constexpr int A2_BYTES = 128 * BK, B2_BYTES = 128 * BK;  // a CTA's 128 rows of A, or of one B^T block
-constexpr int kWideKsteps = 96;  // k-slices from which the wide pair form runs (l > 12160)
+constexpr int kWideKsteps = 64;  // k-slices from which the wide pair form runs (l > 8064)
 
 // Geometry of the SM-pair kernels.  The standard form owns 256 x 256 tiles
 // with two 256-column accumulators (the epilogue overlaps the next tile); the
@@ -584,6 +584,8 @@ struct PairGeo {
   static constexpr int BAR_OFF = STAGES * STAGE;
   static constexpr int NBARS = 2 * STAGES + 2 * NACC;
   static constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;
+  static constexpr int EPI = WIDE ? 8 : 4;          // epilogue warps (the wide form's is exposed: twice as many)
+  static constexpr int THREADS = 128 + 32 * EPI;
 };
 // kind::f8f6f4, fp32 accumulator, e4m3 A and B, K-major, N = 256, M = 256
 constexpr uint32_t kIdesc2 = (1u << 4) | (uint32_t(BN >> 3) << 17) | (uint32_t(256 >> 4) << 24);
@@ -658,7 +660,7 @@ __device__ __forceinline__ void wait_bar_cluster(uint32_t bar, uint32_t parity, 
 }
 
 template <int Q, int P, bool WIDE>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairGeo<WIDE>::THREADS, 1)
     tc_gemm2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const GemmParams prm) {
   using G = PairGeo<WIDE>;
@@ -682,7 +684,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < G::NACC; ++b) {
       mbar_init(accfull + 8 * b, 1);
-      mbar_init(accempty + 8 * b, 8);  // four epilogue warps in each CTA (the leader's barrier)
+      mbar_init(accempty + 8 * b, 2 * G::EPI);  // the epilogue warps of both CTAs (the leader's barrier)
     }
     fence_mbar_init();
   }
@@ -747,8 +749,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       mma_commit_pair(accfull + 8 * b);  // this tile's accumulators are complete in both CTAs
     }
   } else if (warp >= 4) {
-    // ---- epilogue (both CTAs): rows 128 rank + 32 (warp - 4) + lane of the tile
-    const int ew = warp - 4;
+    // ---- epilogue (both CTAs): rows 128 rank + 32 (warp % 4) + lane of the
+    // tile; with eight epilogue warps, group (warp - 4) / 4 takes 128 of
+    // every 256 columns
+    constexpr int CW = 256 / (G::EPI / 4);  // columns per warp per 256-column block
+    const int ew = warp & 3, grp = (warp - 4) >> 2;
     const uint32_t back = leader ? accempty : map_to_rank(accempty, 0);
     int li = 0;
     for (int t = cl; t < prm.tiles; t += ncl, ++li) {
@@ -760,10 +765,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       tile_coords(prm, t, mb, nb);
       const int64_t row = int64_t(mb) * 256 + 128 * int(rank) + ew * 32 + lane;
 #pragma unroll 1
-      for (int j = 0; j < G::BBLK; ++j) {  // 256 columns at a time
-        uint64_t words[P][BN / 64];
-        drain_accumulator<Q, P>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * G::NB + 256 * j), words);
-        if (row < prm.m) store_words<Q, P>(prm, row, int64_t(nb) * (G::NB / 64) + 4 * j, words);
+      for (int j = 0; j < G::BBLK; ++j) {  // one 256-column block at a time
+        uint64_t words[P][CW / 64];
+        drain_accumulator<Q, P, CW / 64>(
+            tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * G::NB + 256 * j + CW * grp), words);
+        if (row < prm.m)
+          store_words<Q, P, CW / 64>(prm, row, int64_t(nb) * (G::NB / 64) + 4 * j + (CW / 64) * grp, words);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -1062,11 +1069,11 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
     if (wide) {
       FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm2_kernel<Q, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        PairGeo<true>::SMEM));
-      tc_gemm2_kernel<Q, P, true><<<grid, THREADS, PairGeo<true>::SMEM, s>>>(ma, mb, prm);
+      tc_gemm2_kernel<Q, P, true><<<grid, PairGeo<true>::THREADS, PairGeo<true>::SMEM, s>>>(ma, mb, prm);
     } else {
       FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm2_kernel<Q, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        PairGeo<false>::SMEM));
-      tc_gemm2_kernel<Q, P, false><<<grid, THREADS, PairGeo<false>::SMEM, s>>>(ma, mb, prm);
+      tc_gemm2_kernel<Q, P, false><<<grid, PairGeo<false>::THREADS, PairGeo<false>::SMEM, s>>>(ma, mb, prm);
     }
   } else {
     FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
