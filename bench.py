@@ -292,10 +292,18 @@ class ClockSampler:
 
 
 def sources_digest(names):
+    """Digest of the code in these sources: comments, blank lines and trailing
+    blanks do not count, so that counters stay attached to a kernel whose
+    commentary changes."""
+    import re
     h = hashlib.sha256()
     for name in names:
-        with open(name, "rb") as f:
-            h.update(f.read())
+        with open(name, encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [line.rstrip() for line in text.splitlines()]
+        h.update("\n".join(line for line in lines if line).encode())
     return h.hexdigest()[:16]
 
 
