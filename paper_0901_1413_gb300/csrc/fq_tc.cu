@@ -19,14 +19,18 @@
 //
 // Layout.  The operands are first converted from planes to e4m3 bytes: A as m
 // rows of la = roundup(l, 128) values, B transposed to n_pad rows of la values
-// (K contiguous for both, as the tensor core reads them), zero past l.  One
-// persistent CTA per SM walks 128 x 256 tiles of C in groups of 8 row blocks:
-// one thread issues TMA loads of 128-byte slices of A and B into a 4-stage
-// ring (128-byte swizzle), one thread issues the tcgen05.mma instructions
-// (M = 128, N = 256, K = 32) into one of two 256-column TMEM accumulators,
-// and a warpgroup reads the other accumulator back (tcgen05.ld) and writes
-// the packed codes, so a tile's epilogue overlaps the next tile's products.
-// Every mbarrier wait is bounded.
+// (K contiguous for both, as the tensor core reads them), zero past l.  Three
+// persistent product kernels read them through TMA (128-byte swizzle) and keep
+// their fp32 sums in TMEM; one thread issues the MMAs and a group of warps
+// drains the accumulators (tcgen05.ld) and writes the packed codes:
+//   - single SMs (m <= 128): 128 x 256 tiles, two 256-column accumulators, so
+//     a tile's epilogue overlaps the next tile's products;
+//   - SM pairs (cta_group::2): 256 x 256 tiles, each CTA staging its own
+//     halves of A and B^T, also double-buffered;
+//   - SM pairs, wide (from 64 k-slices): 256 x 512 tiles, two MMAs per step
+//     into one 512-column accumulator, for a third more load-latency cover.
+// The batched form converts many products into two shared arenas and runs
+// one persistent kernel over all their tiles.  Every mbarrier wait is bounded.
 #include <cstring>
 
 #include "../../include/fq.h"
