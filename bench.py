@@ -352,6 +352,22 @@ def measured_peaks():
     return {"bf16": bf16, "fp8": 2.0 * bf16, "note": note, "hbm": hbm, "hbm_note": hbm_note}
 
 
+# The f8f6f4 tensor pipe's own peak, as the hardware counters state it
+# (sm__ops_path_tensor_op_utcqmma_src_fp8_dst_fp32...peak_sustained).
+FP8_OPS_PER_CLK_PER_SM = 16384
+SMS = 152
+
+
+def pipe_peak(achieved_tflops, clk):
+    """A second roofline denominator for the tensor-core product: the fp8 pipe's
+    peak at the SM clock sampled in the timed region (the measured bf16 figure
+    was taken at a lower, power-capped clock)."""
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak = FP8_OPS_PER_CLK_PER_SM * SMS * mhz * 1e6 / 1e12
+    return {"peak": peak, "unit": "TFLOP/s", "frac": achieved_tflops / peak, "sm_mhz": mhz,
+            "note": "16384 fp8 ops/clk/SM (ncu peak_sustained) x 152 SMs x the median SM clock of the timed region"}
+
+
 def make_inputs(torch, inputs, prods, seed=0):
     out = []
     for (m, l, n, law) in prods:
@@ -759,7 +775,8 @@ def main():
                          "peak_note": peaks["note"],
                          "kernel": "tc_gemm2_kernel (tcgen05.mma.cta_group::2 kind::f8f6f4 e4m3 on SM pairs, "
                                    "persistent; 256x512 tiles for l >= 8192, 256x256 below)",
-                         "kernel_ms_per_step": sum(product_ms)},
+                         "kernel_ms_per_step": sum(product_ms),
+                         "pipe": pipe_peak(achieved, clk)},
             "prepare": {"bound": "hbm", "ms_per_step": prep_ms, "bytes": prep_bytes, "achieved": prep_gbs,
                         "peak": peaks["hbm"], "unit": "GB/s", "frac": prep_gbs / peaks["hbm"],
                         "peak_note": peaks["hbm_note"]},
