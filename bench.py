@@ -115,7 +115,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-product batched workloads")
-    ap.add_argument("--cpu-rows", type=int, default=48, help="oracle rows sampled per product")
+    ap.add_argument("--cpu-rows", type=int, default=1024,
+                    help="oracle rows sampled per product (about 11 s of oracle work on 16 cores)")
     return ap.parse_args()
 
 
@@ -751,7 +752,7 @@ def main():
     base = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         ops, times, cores, nrows = cpu_baseline(prods, args.cpu_rows)
-        rows1 = max(1, args.cpu_rows // 6)
+        rows1 = max(1, args.cpu_rows // 48)
         ops1, times1, _, nrows1 = cpu_baseline(prods, rows1, threads=1)
         base = {"value": ops / times[0], "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                 "sample": "first %d rows of each of the %d products (%d rows), one pass"
