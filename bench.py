@@ -775,7 +775,7 @@ def main():
                          "frac": achieved / peaks["fp8"], "traffic": traffic,
                          "peak_note": peaks["note"],
                          "kernel": "tc_gemm2_kernel (tcgen05.mma.cta_group::2 kind::f8f6f4 e4m3 on SM pairs, "
-                                   "persistent; 256x512 tiles for l >= 8192, 256x256 below)",
+                                   "persistent; 256x512 tiles for l >= 4096, 256x256 below)",
                          "kernel_ms_per_step": sum(product_ms),
                          "pipe": pipe_peak(achieved, clk)},
             "prepare": {"bound": "hbm", "ms_per_step": prep_ms, "bytes": prep_bytes, "achieved": prep_gbs,

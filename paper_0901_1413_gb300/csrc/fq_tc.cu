@@ -27,7 +27,7 @@
 //     a tile's epilogue overlaps the next tile's products;
 //   - SM pairs (cta_group::2): 256 x 256 tiles, each CTA staging its own
 //     halves of A and B^T, also double-buffered;
-//   - SM pairs, wide (from 64 k-slices): 256 x 512 tiles, two MMAs per step
+//   - SM pairs, wide (from 32 k-slices): 256 x 512 tiles, two MMAs per step
 //     into one 512-column accumulator, for a third more load-latency cover.
 // The batched form converts many products into two shared arenas and runs
 // one persistent kernel over all their tiles.  Every mbarrier wait is bounded.
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 // of the single-CTA kernel.
 
 constexpr int A2_BYTES = 128 * BK, B2_BYTES = 128 * BK;  // a CTA's 128 rows of A, or of one B^T block
-constexpr int kWideKsteps = 64;  // k-slices from which the wide pair form runs (l > 8064)
+constexpr int kWideKsteps = 32;  // k-slices from which the wide pair form runs (l > 3968)
 
 // Geometry of the SM-pair kernels.  The standard form owns 256 x 256 tiles
 // with two 256-column accumulators (the epilogue overlaps the next tile); the
