@@ -55,7 +55,7 @@ extern "C" {
 #define FQ_EVALUE 2    /* a residue >= q was passed to fq_pack (device-detected)   */
 #define FQ_ECUDA 3     /* a CUDA call failed; see fq_last_cuda_error()            */
 #define FQ_ETIMEOUT 4  /* a bounded device wait gave up (device-detected)          */
-#define FQ_ENOTSUP 5   /* valid request this build does not support               */
+#define FQ_ENOTSUP 5   /* valid request the library does not support              */
 #define FQ_ENOMEM 6    /* host allocation failed                                   */
 
 /* ---- product paths (fq_options.path) --------------------------------------- */
