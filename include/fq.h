@@ -180,7 +180,8 @@ int fq_tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *workspace
  * their time models (or as the caller asks):
  *   - Four Russians: work items (rows x a column tile of one product) with a
  *     block size k chosen per item by the planner's cost model, longest first;
- *   - tcgen05 (F_3, F_5, F_7 with 0 < l within the exact range): the
+ *   - tcgen05 (F_3, F_5, F_7 with 0 < l within the exact range and
+ *     n <= 2^30): the
  *     product's A and B^T in e4m3 in two arenas of the workspace, and its
  *     128 x 256 tiles in one list, deepest first.
  * The plan is host memory owned by the library. */
@@ -191,7 +192,9 @@ typedef struct fq_batch_plan fq_batch_plan;
  * models), FQ_PATH_M4RM (every product by Four Russians) or FQ_PATH_MMA (every
  * product the tcgen05 form can take; GF(4) and the rest by Four Russians);
  * fq_batched_plan_create is path FQ_PATH_AUTO.  Returns FQ_EINVAL on a bad q,
- * path or sizes, FQ_ENOMEM on allocation failure. */
+ * path or sizes, FQ_ENOMEM on host allocation failure, and FQ_ENOTSUP for a
+ * plan beyond the kernels' 32-bit indices: 2^31 or more work items, tcgen05
+ * tiles, or 128-byte rows in either arena.  No plan is made on an error. */
 int fq_batched_plan_create(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n,
                            fq_batch_plan **plan);
 int fq_batched_plan_create_ex(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n, int path,
@@ -243,8 +246,8 @@ int fq_batched_plan_destroy(fq_batch_plan *plan);
  *     its launch (the array keeps the previous call's contents otherwise).
  *   - All calls on a GPU share the one array: calls whose work overlaps on the
  *     GPU (for example on two streams) race and give wrong results.
- *   - The first call on a device looks up the array's device address; make that
- *     first call before capturing any stream into a graph.
+ *   - Each call copies the work list from host memory, which a graph replay
+ *     could not repeat: FQ_ENOTSUP while `stream` is being captured.
  * The paper has no counterpart: this is an interface for allocation-free
  * callers, with the arguments and results of fq_matmul_batched. */
 int fq_matmul_batched_static(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,

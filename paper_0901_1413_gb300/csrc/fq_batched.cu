@@ -11,6 +11,8 @@
 // launch allocates nothing and never waits on the host, so it can be captured
 // in a CUDA graph and replayed.
 #include <algorithm>
+#include <exception>
+#include <memory>
 #include <cstdlib>
 #include <mutex>
 #include <new>
@@ -296,7 +298,7 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
   *out = nullptr;
   if (!(q == 3 || q == 4 || q == 5 || q == 7) || count < 0 || (count > 0 && (!m || !l || !n))) return FQ_EINVAL;
   if (!(path == FQ_PATH_AUTO || path == FQ_PATH_M4RM || path == FQ_PATH_MMA)) return FQ_EINVAL;
-  fq_batch_plan *plan = new (std::nothrow) fq_batch_plan();
+  std::unique_ptr<fq_batch_plan> plan(new (std::nothrow) fq_batch_plan());
   if (!plan) return FQ_ENOMEM;
   plan->q = q;
   plan->count = count;
@@ -332,10 +334,8 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
   };
   for (int p = 0; p < count; ++p) {
     if (m[p] < 0 || l[p] < 0 || n[p] < 0 || m[p] >= (int64_t(1) << 31) || l[p] >= (int64_t(1) << 31) ||
-        n[p] >= (int64_t(1) << 31)) {
-      delete plan;
+        n[p] >= (int64_t(1) << 31))
       return FQ_EINVAL;
-    }
     plan->shapes.push_back(Shape{m[p], l[p], n[p]});
     if (m[p] == 0 || n[p] == 0) continue;
     // Four-Russians items of this product and their modelled cost
@@ -371,8 +371,10 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
       }
     }
     // the path: the tcgen05 form takes F_3, F_5 and F_7 products with 0 < l
-    // within its exact range, when asked to or when its model is cheaper
-    const bool tc_ok = (q == 3 || q == 5 || q == 7) && l[p] > 0 && l[p] <= fqk::tc_max_l(q);
+    // within its exact range (and n <= 2^30, so that n rounded up to 256 stays
+    // a 32-bit count), when asked to or when its model is cheaper
+    const bool tc_ok = (q == 3 || q == 5 || q == 7) && l[p] > 0 && l[p] <= fqk::tc_max_l(q) &&
+                       n[p] <= (int64_t(1) << 30);
     const double tc = tc_ok ? tc_product_cycles(m[p], l[p], n[p]) : 1e300;
     const bool use_tc = tc_ok && (path == FQ_PATH_MMA || (path == FQ_PATH_AUTO && tc < m4rm));
     if (!use_tc) {
@@ -413,6 +415,13 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
       }
     }
   }
+  // The kernels index items, tiles and arena rows with 32-bit numbers (the
+  // queue counter, the tile records' TMA coordinates): larger plans are refused.
+  constexpr int64_t kMax32 = (int64_t(1) << 31) - 1;
+  int64_t tiles = 0;
+  for (const fqk::BatchProd &bp : plan->tc_prods) tiles += fqk::cdiv(bp.m, 128) * (bp.nr / 256);
+  if (int64_t(costed.size()) > kMax32 || plan->a_rows > kMax32 || plan->b_rows > kMax32 || tiles > kMax32)
+    return FQ_ENOTSUP;
   // longest first
   std::stable_sort(costed.begin(), costed.end(),
                    [](const std::pair<double, Item> &a, const std::pair<double, Item> &b) { return a.first > b.first; });
@@ -479,8 +488,19 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
     off += plan->b_rows * 128;
   }
   plan->workspace_bytes = off;
-  *out = plan;
+  *out = plan.release();
   return FQ_OK;
+}
+
+// The C entry points return status codes: host allocation failures of the
+// plan's tables (std::bad_alloc, std::length_error) become FQ_ENOMEM.
+template <class Fn>
+int host_guard(Fn &&fn) {
+  try {
+    return fn();
+  } catch (const std::exception &) {
+    return FQ_ENOMEM;
+  }
 }
 
 // The host image of a plan's tables (header .. tile list).
@@ -537,12 +557,12 @@ extern "C" {
 
 int fq_batched_plan_create(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n,
                            fq_batch_plan **out) {
-  return plan_create(q, count, m, l, n, FQ_PATH_AUTO, out);
+  return host_guard([&] { return plan_create(q, count, m, l, n, FQ_PATH_AUTO, out); });
 }
 
 int fq_batched_plan_create_ex(int q, int count, const int64_t *m, const int64_t *l, const int64_t *n, int path,
                               fq_batch_plan **out) {
-  return plan_create(q, count, m, l, n, path, out);
+  return host_guard([&] { return plan_create(q, count, m, l, n, path, out); });
 }
 
 int64_t fq_batched_workspace_bytes(const fq_batch_plan *plan) { return plan ? plan->workspace_bytes : -1; }
@@ -555,11 +575,13 @@ int64_t fq_batched_tc_tiles(const fq_batch_plan *plan) { return plan ? int64_t(p
 
 int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *stream) {
   if (!plan || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 63u) != 0) return FQ_EINVAL;
-  const std::vector<unsigned char> host = plan_tables(plan);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  FQ_CUDA_TRY(cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, s));
-  FQ_CUDA_TRY(cudaStreamSynchronize(s));
-  return FQ_OK;
+  return host_guard([&] {
+    const std::vector<unsigned char> host = plan_tables(plan);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FQ_CUDA_TRY(cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    FQ_CUDA_TRY(cudaStreamSynchronize(s));
+    return FQ_OK;
+  });
 }
 
 int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
@@ -632,9 +654,14 @@ extern "C" int fq_matmul_batched_static(const fq_batch_plan *plan, const uint64_
   if (!A || !B || !C) return FQ_EINVAL;
   // tcgen05 products need their arenas; the fixed array holds work lists only
   if (!plan->tc_prods.empty() || plan->workspace_bytes > kStaticScratchBytes) return FQ_ENOTSUP;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the work list is copied from host memory at every call, which a captured
+  // graph could not repeat
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  FQ_CUDA_TRY(cudaStreamIsCapturing(s, &capture));
+  if (capture != cudaStreamCaptureStatusNone) return FQ_ENOTSUP;
   unsigned char *ws = nullptr;
   if (int rc = static_scratch(&ws)) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // The array holds whatever the previous call left: write this plan's header
   // (queue counter 0), shapes and items before the launch, in stream order.
   Header h{};

@@ -1,6 +1,7 @@
 // Measured autotuning of fq_matmul: time every compiled Four-Russians kernel of
 // the field and the tensor-core path on the caller's operands, keep the
 // fastest per (q, m, l, n), and let FQ_PATH_AUTO calls of that shape use it.
+#include <exception>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -80,7 +81,10 @@ int fq_autotune(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const
   fqk::m4rm_variants(q, &nk);
   cudaEvent_t e0, e1;
   FQ_CUDA_TRY(cudaEventCreate(&e0));
-  FQ_CUDA_TRY(cudaEventCreate(&e1));
+  if (const cudaError_t e = cudaEventCreate(&e1); e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fqk::record_cuda_error(e);
+  }
   fq_tune_result best{};
   best.ms = -1.0f;
   int rc = FQ_OK;
@@ -96,10 +100,18 @@ int fq_autotune(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const
       break;
     }
     float ms = 0.0f;
-    if (cudaEventRecord(e0, s) != cudaSuccess || fq_matmul_ex(q, m, l, n, A, B, C, stream, &o) != FQ_OK ||
-        cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-      rc = fqk::record_cuda_error(cudaGetLastError());
+    cudaError_t e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) {
+      if ((r = fq_matmul_ex(q, m, l, n, A, B, C, stream, &o)) != FQ_OK) {
+        rc = r;
+        break;
+      }
+      e = cudaEventRecord(e1, s);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = fqk::record_cuda_error(e);
       break;
     }
     if (c == 0) best.ms_planner = ms;
@@ -114,9 +126,11 @@ int fq_autotune(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const
   cudaEventDestroy(e1);
   if (rc != FQ_OK) return rc;
   if (best.ms < 0) return FQ_ENOTSUP;
-  {
+  try {
     std::lock_guard<std::mutex> lock(fqk::g_tune_mu);
     fqk::g_tuned[std::make_tuple(q, m, l, n)] = fqk::Choice{best.path, best.kernel};
+  } catch (const std::exception &) {
+    return FQ_ENOMEM;  // the cache could not grow (or its lock failed); nothing remembered
   }
   if (out) *out = best;
   return FQ_OK;

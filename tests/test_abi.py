@@ -90,6 +90,36 @@ def test_kernel_table(lib):
     assert lib.fq_kernel_info(3, 10_000, ctypes.byref(k), None, None, None) == fq.EINVAL
 
 
+def test_batch_plan_32_bit_limits(lib):
+    """The batched kernels address arena rows with 32-bit TMA coordinates: a
+    plan whose A arena would reach 2^31 rows of 128 bytes is refused (and none
+    is made); n above 2^30 keeps a product off the tcgen05 path."""
+    import numpy as np
+    from paper_0901_1413_gb300 import fq
+    i64p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    la = (1 << 24) - 128            # within F_3's exact fp32 range; 131071 k-slices
+    n = np.array([64], np.int64)
+    l = np.array([la], np.int64)
+    h = ctypes.c_void_p()
+    # 16512 rows (129 row blocks) x 131071 k-slices = 2^31 + 16.6e6 arena rows
+    m = np.array([16512], np.int64)
+    assert lib.fq_batched_plan_create_ex(3, 1, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.ENOTSUP
+    assert not h.value
+    # 128 rows of the same depth: 131071 arena rows, accepted
+    m = np.array([128], np.int64)
+    assert lib.fq_batched_plan_create_ex(3, 1, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.OK
+    assert lib.fq_batched_tc_products(h) == 1
+    assert lib.fq_batched_tc_tiles(h) == 1
+    assert lib.fq_batched_workspace_bytes(h) > (128 + 256) * la
+    assert lib.fq_batched_plan_destroy(h) == fq.OK
+    # n = 2^30 + 64: Four Russians even when the tensor path is asked for
+    m, l, n = (np.array([v], np.int64) for v in (1, 64, (1 << 30) + 64))
+    assert lib.fq_batched_plan_create_ex(3, 1, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.OK
+    assert lib.fq_batched_tc_products(h) == 0
+    assert lib.fq_batched_items(h) == fq.pitch_words((1 << 30) + 64) // 8
+    assert lib.fq_batched_plan_destroy(h) == fq.OK
+
+
 def test_batch_plan_host_side(lib):
     """Plan creation is host-only: sizes, item count, workspace bytes, errors."""
     import numpy as np

@@ -88,3 +88,28 @@ def test_static_workspace_refuses_plans_with_tensor_core_products(fq):
     assert plan.tc_products == 2
     rc = run_static(plan._h, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), None)
     assert rc == fq.ENOTSUP
+
+
+def test_static_workspace_refuses_capture(fq):
+    """The static entry copies its work list from host memory at every call,
+    which a graph replay could not repeat: refused while the stream captures,
+    with nothing enqueued (the rest of the capture stays valid)."""
+    lib = fq.load()
+    run_static = _entry(lib)
+    q, shapes = 3, [(64, 64, 64)]
+    a, b = _batch(fq, q, shapes, 7)
+    out = _outputs(fq, q, shapes)
+    plan = fq.BatchPlan(q, shapes, path=fq.PATH_M4RM)
+    pa, pb, pc = _ptrs(a), _ptrs(b), _ptrs(out)
+    x = torch.zeros(1, device="cuda")
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        x.add_(1)
+        rc = run_static(plan._h, ctypes.c_void_p(pa.data_ptr()), ctypes.c_void_p(pb.data_ptr()),
+                        ctypes.c_void_p(pc.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    assert rc == fq.ENOTSUP
+    g.replay()
+    torch.cuda.synchronize()
+    assert x.item() == 1.0
+    assert fq.status() == fq.OK
