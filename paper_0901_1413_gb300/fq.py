@@ -67,6 +67,7 @@ def load():
             "fq_batched_tc_tiles": (i64, [vp]),
             "fq_batched_plan_upload": (i32, [vp, vp, vp]),
             "fq_matmul_batched": (i32, [vp, vp, vp, vp, vp, vp]),
+            "fq_matmul_batched_static": (i32, [vp, vp, vp, vp, vp]),
             "fq_batched_plan_destroy": (i32, [vp]),
             "fq_autotune": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, vp]),
             "fq_autotune_lookup": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
@@ -292,6 +293,16 @@ class BatchPlan:
         _check(load().fq_matmul_batched(self._h, ctypes.c_void_p(A_ptrs.data_ptr()),
                                         ctypes.c_void_p(B_ptrs.data_ptr()), ctypes.c_void_p(C_ptrs.data_ptr()),
                                         ctypes.c_void_p(self._ws_ptr()), _stream(stream)), "fq_matmul_batched")
+
+    def run_static(self, A_ptrs: torch.Tensor, B_ptrs: torch.Tensor, C_ptrs: torch.Tensor, stream=None):
+        """fq_matmul_batched_static: the same products with the work list in the
+        library's fixed device array instead of this plan's workspace (plans of
+        Four-Russians items within FQ_BATCH_STATIC_BYTES; not while the stream
+        is being captured)."""
+        _check(load().fq_matmul_batched_static(self._h, ctypes.c_void_p(A_ptrs.data_ptr()),
+                                               ctypes.c_void_p(B_ptrs.data_ptr()),
+                                               ctypes.c_void_p(C_ptrs.data_ptr()), _stream(stream)),
+               "fq_matmul_batched_static")
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -168,6 +168,8 @@ def test_batch_plan_host_side(lib):
     assert lib.fq_batched_plan_create(3, 4, i64p(m), i64p(l), i64p(n), ctypes.byref(h)) == fq.OK
     assert lib.fq_batched_plan_upload(h, ctypes.c_void_p(8), None) == fq.EINVAL      # misaligned
     assert lib.fq_matmul_batched(h, None, None, None, ctypes.c_void_p(64), None) == fq.EINVAL
+    assert lib.fq_matmul_batched_static(h, None, None, None, None) == fq.EINVAL
+    assert lib.fq_matmul_batched_static(None, None, None, None, None) == fq.EINVAL
     assert lib.fq_batched_plan_destroy(h) == fq.OK
     bad = np.array([-1], np.int64)
     assert lib.fq_batched_plan_create(3, 1, i64p(bad), i64p(bad), i64p(bad), ctypes.byref(h)) == fq.EINVAL
