@@ -90,6 +90,69 @@ def test_kernel_table(lib):
     assert lib.fq_kernel_info(3, 10_000, ctypes.byref(k), None, None, None) == fq.EINVAL
 
 
+def _plan_layout_model(q, shapes, path):
+    """Workspace bytes, items, tcgen05 products and tiles of a batched plan
+    forced onto one path, from the layout include/fq.h describes: header 64,
+    shapes 24 each (64-aligned), Four-Russians items 32 each (tiles of C's
+    pitch: 512 rows x 512 columns for F_3 and GF(4), 256 x 1024 for F_5 and
+    F_7); for tcgen05 products 64-byte records, two
+    unit prefixes, the product of each conversion unit (A: 256 pieces of 16
+    elements; B^T: 128 x 256 blocks), 32-byte tiles of 128 x 256 and their
+    cost prefix, each part 64-aligned; then the two arenas, 1024-aligned, of
+    128-byte rows (m up to 128 and n up to 256, times l up to 128 / 128)."""
+    from paper_0901_1413_gb300 import fq
+    cdiv = lambda a, b: -(-a // b)
+    up = lambda x, a: cdiv(x, a) * a
+    tc_max_l = ((1 << 24) - 1) // max(1, (q - 1) // 2) ** 2
+    # Four-Russians item tiles: rows x 64-bit words (two-plane fields / three-plane fields)
+    mt, ctw = (512, 8) if q in (3, 4) else (256, 16)
+    items = prods = tiles = a_units = b_units = a_rows = b_rows = 0
+    for m, l, n in shapes:
+        if m == 0 or n == 0:
+            continue
+        if path == fq.PATH_MMA and q in (3, 5, 7) and 0 < l <= tc_max_l and n <= (1 << 30):
+            la, nr = up(l, 128), up(n, 256)
+            prods += 1
+            tiles += cdiv(m, 128) * (nr // 256)
+            a_units += cdiv(m * (la // 16), 256)
+            b_units += (la // 128) * (nr // 256)
+            a_rows += up(m, 128) * (la // 128)
+            b_rows += nr * (la // 128)
+        else:
+            items += cdiv(m, mt) * (fq.pitch_words(n) // ctw)
+    off = 64 + up(24 * len(shapes), 64) + 32 * items
+    if prods:
+        for size in (64 * prods, 8 * (prods + 1), 8 * (prods + 1), 4 * a_units, 4 * b_units, 32 * tiles,
+                     8 * (tiles + 1)):
+            off = up(off, 64) + size
+        off = up(off, 1024) + 128 * a_rows
+        off = up(off, 1024) + 128 * b_rows
+    return off, items, prods, tiles
+
+
+def test_batch_plan_layout_matches_model(lib):
+    """Random shape sets (ragged sizes, empty products, l = 0) on both forced
+    paths: the library's plan has the model's workspace bytes and counts."""
+    import numpy as np
+    from paper_0901_1413_gb300 import fq
+    i64p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rng = np.random.default_rng(2024)
+    for trial in range(40):
+        q = (3, 5, 7, 4)[trial % 4]
+        count = int(rng.integers(1, 60))
+        sh = rng.integers(0, 1500, size=(count, 3)).astype(np.int64)
+        sh[rng.random((count, 3)) < 0.05] = 0
+        m, l, n = (np.ascontiguousarray(sh[:, i]) for i in range(3))
+        for path in (fq.PATH_M4RM, fq.PATH_MMA):
+            h = ctypes.c_void_p()
+            assert lib.fq_batched_plan_create_ex(q, count, i64p(m), i64p(l), i64p(n), path, ctypes.byref(h)) == fq.OK
+            want = _plan_layout_model(q, sh.tolist(), path)
+            got = (lib.fq_batched_workspace_bytes(h), lib.fq_batched_items(h), lib.fq_batched_tc_products(h),
+                   lib.fq_batched_tc_tiles(h))
+            assert lib.fq_batched_plan_destroy(h) == fq.OK
+            assert got == want, (q, path, trial)
+
+
 def test_batch_plan_32_bit_limits(lib):
     """The batched kernels address arena rows with 32-bit TMA coordinates: a
     plan whose A arena would reach 2^31 rows of 128 bytes is refused (and none
