@@ -21,8 +21,9 @@ library imports nothing from it.
 * ``encoding``: the bitsliced representation (Sections 3-4).
 * ``bitslice``: the paper's element formulas.
 * ``m4rm``: the Section 2 method itself, step by step, for small sizes.
-* ``freivalds`` / ``matmul_rows``: checks for sizes too large for the full
-  product (a randomized identity test and exact sampled rows).
+* ``freivalds`` / ``matmul_rows`` / ``matmul_cols``: checks for sizes too
+  large for the full product (a randomized identity test, exact sampled rows
+  and exact sampled columns).
 """
 from __future__ import annotations
 
@@ -170,6 +171,13 @@ def matmul_rows(q: int, A: np.ndarray, B: np.ndarray, rows, threads: int = 0) ->
     return matmul(q, np.asarray(A)[rows], B, threads)
 
 
+def matmul_cols(q: int, A: np.ndarray, B: np.ndarray, cols, threads: int = 0) -> np.ndarray:
+    """Exact columns ``cols`` of A B, as a len(A) x len(cols) matrix: column j of
+    the product is A times column j of B, independent of the other columns."""
+    cols = np.asarray(cols, dtype=np.int64)
+    return matmul(q, A, np.ascontiguousarray(np.asarray(B)[:, cols]), threads)
+
+
 def gf4_karatsuba(A: np.ndarray, B: np.ndarray, threads: int = 0) -> np.ndarray:
     """GF(4) product by Section 4.3: with A = A0 + alpha A1 and B = B0 + alpha B1,
     AB = (A0 B0 + A1 B1) + alpha ((A0 + A1)(B0 + B1) + A0 B0), three F_2 products."""
@@ -185,55 +193,70 @@ def gf4_karatsuba(A: np.ndarray, B: np.ndarray, threads: int = 0) -> np.ndarray:
     return (c0 | (c1 << 1)).astype(np.uint8)
 
 
-def _gf4_matvec(M: np.ndarray, x: np.ndarray) -> np.ndarray:
-    """y = M x over GF(4) via the Section 4.3 decomposition on F_2 mat-vecs."""
-    M0, M1 = (M & 1).astype(np.int64), ((M >> 1) & 1).astype(np.int64)
-    x0, x1 = (x & 1).astype(np.int64), ((x >> 1) & 1).astype(np.int64)
-    p00 = (M0 @ x0) & 1
-    p11 = (M1 @ x1) & 1
-    pss = ((M0 ^ M1) @ (x0 ^ x1)) & 1
-    return ((p00 ^ p11) | ((pss ^ p00) << 1)).astype(np.int64)
+# Largest integer below which every float64 value is exact: the library
+# matmul below only ever adds non-negative integers, so while the longest sum
+# stays under this bound no rounding can happen, whatever the summation order.
+_FLOAT64_EXACT = 2 ** 53
 
 
-def _ext_matvec(q: int, M: np.ndarray, x: np.ndarray, table: np.ndarray) -> np.ndarray:
-    """y = M x over an extension field: products from the element table, summed
-    coefficient by coefficient mod p."""
-    p, n, _ = EXTENSIONS[q]
-    prods = table[np.asarray(M, dtype=np.int64), np.asarray(x, dtype=np.int64)[None, :]].astype(np.int64)
-    return sum((((prods // p ** j) % p).sum(axis=1) % p) * p ** j for j in range(n))
-
-
-def _matvec_mod(q: int, M: np.ndarray, x: np.ndarray, rows_per_chunk: int = 2048, table=None) -> np.ndarray:
-    """M x over F_q (GF(4), extension fields), row chunk by row chunk to bound memory."""
-    out = np.empty(M.shape[0], dtype=np.int64)
-    for r in range(0, M.shape[0], rows_per_chunk):
-        blk = M[r:r + rows_per_chunk]
-        if q == 4:
-            out[r:r + rows_per_chunk] = _gf4_matvec(blk, x)
-        elif q in EXTENSIONS:
-            out[r:r + rows_per_chunk] = _ext_matvec(q, blk, x, table)
-        else:
-            out[r:r + rows_per_chunk] = (blk.astype(np.int64) @ x) % q
+def _fp_matmul(p: int, M: np.ndarray, X: np.ndarray, chunk_bytes: int = 1 << 28) -> np.ndarray:
+    """(M X) mod p for M with entries in [0, p) (uint8) and X with entries in
+    [0, p) (int64), by a float64 library matmul over row chunks of M.  Each
+    entry of M X is a sum of cols(M) products of at most (p - 1)^2, so it is an
+    exact float64 integer while cols(M) (p - 1)^2 < 2^53."""
+    M = np.asarray(M)
+    r, c = M.shape
+    if c * (p - 1) ** 2 >= _FLOAT64_EXACT:
+        raise ValueError("sums of %d terms could exceed 2^53" % c)
+    Xf = np.asarray(X, dtype=np.float64)
+    out = np.empty((r, Xf.shape[1]), dtype=np.int64)
+    step = max(1, chunk_bytes // max(1, 8 * c))
+    for i in range(0, r, step):
+        out[i:i + step] = np.mod(M[i:i + step].astype(np.float64) @ Xf, p).astype(np.int64)
     return out
 
 
-def freivalds(q: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, trials: int = 32,
-              seed: int = 0) -> bool:
-    """Randomized check that C = A B: for random x, A (B x) == C x over F_q.
+def _field_matmul(q: int, M: np.ndarray, X: np.ndarray, chunk_bytes: int = 1 << 28) -> np.ndarray:
+    """M X over F_q on codes (M uint8, X int64), for the randomized check.
 
-    A wrong C passes one trial with probability at most 1/q (Freivalds), so the
-    false-pass probability is at most q^-trials.
+    F_p: ``_fp_matmul``.  F_{p^n} (GF(4) included): with M = sum_a M_a x^a and
+    X = sum_b X_b x^b over F_p (the code digits), the polynomial product's
+    coefficient k is sum_{a + b = k} M_a X_b (schoolbook, n^2 base-field
+    products), and x^k for k >= n is replaced, highest first, using the defining
+    polynomial x^n = r_0 + r_1 x + ... (Section 4.3's extension fields)."""
+    if q not in EXTENSIONS:
+        return _fp_matmul(q, M, X, chunk_bytes)
+    p, n, r = EXTENSIONS[q]
+    M = np.asarray(M, dtype=np.uint8)
+    ms = [(M // p ** j) % p for j in range(n)]
+    xs = [((np.asarray(X, dtype=np.int64) // p ** j) % p) for j in range(n)]
+    c = [0] * (2 * n - 1)
+    for a in range(n):
+        for b in range(n):
+            c[a + b] = c[a + b] + _fp_matmul(p, ms[a], xs[b], chunk_bytes)
+    for k in range(2 * n - 2, n - 1, -1):
+        for j in range(n):
+            c[k - n + j] = c[k - n + j] + r[j] * c[k]
+        c[k] = 0
+    return sum(np.mod(c[j], p) * p ** j for j in range(n))
+
+
+def freivalds(q: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, trials: int = 32,
+              seed: int = 0, chunk_bytes: int = 1 << 28) -> bool:
+    """Randomized check that C = A B over F_q (Freivalds): for a random n x trials
+    matrix X over F_q, A (B X) == C X.
+
+    Each column of X is an independent uniform vector; if C != A B, one column
+    passes with probability at most 1/q, so a wrong C passes with probability at
+    most q^-trials.  All products are computed exactly (``_field_matmul``).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     A = np.asarray(A)
     B = np.asarray(B)
     C = np.asarray(C)
-    n = B.shape[1]
-    table = ext_mul_table(q) if q in EXTENSIONS and q != 4 else None
-    for _ in range(trials):
-        x = rng.integers(0, q, size=n, dtype=np.int64)
-        lhs = _matvec_mod(q, A, _matvec_mod(q, B, x, table=table), table=table)
-        rhs = _matvec_mod(q, C, x, table=table)
-        if not np.array_equal(lhs, rhs):
-            return False
-    return True
+    if A.shape[1] != B.shape[0] or C.shape != (A.shape[0], B.shape[1]):
+        raise ValueError("shape mismatch")
+    X = rng.integers(0, q, size=(B.shape[1], trials), dtype=np.int64)
+    lhs = _field_matmul(q, A, _field_matmul(q, B, X, chunk_bytes), chunk_bytes)
+    rhs = _field_matmul(q, C, X, chunk_bytes)
+    return bool(np.array_equal(lhs, rhs))

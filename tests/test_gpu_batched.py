@@ -118,8 +118,9 @@ def test_batched_graph_capture_and_replay(fq, q, path):
 @pytest.mark.slow
 @pytest.mark.parametrize("q", [3, 5])
 def test_batched_4096_products(fq, q):
-    """4096 products with m, l, n uniform over multiples of 64 in [64, 1024];
-    a sample of products against the oracle, and all of them by Freivalds."""
+    """4096 products with m, l, n uniform over multiples of 64 in [64, 1024]:
+    every 97th product against the full oracle, every 7th by a 32-trial
+    Freivalds check."""
     shapes = [tuple(int(x) for x in s) for s in inputs.batch_shapes(4096, seed=q)]
     A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=q)
     plan = fq.BatchPlan(q, shapes)          # AUTO: the time models pick each product's path
@@ -129,4 +130,63 @@ def test_batched_4096_products(fq, q):
     check(fq, q, [A[i] for i in sample], [B[i] for i in sample], [c[i] for i in sample])
     for p in range(0, 4096, 7):
         got = fq.unpack(c[p]).cpu().numpy()
-        assert oracle.freivalds(q, A[p], B[p], got, trials=2, seed=p)
+        assert oracle.freivalds(q, A[p], B[p], got, trials=32, seed=p)
+
+
+def _tc_max_l(fq, q):
+    """Longest l the tcgen05 form takes for q (found through the workspace query)."""
+    lib = fq.load()
+    lo, hi = 1, 1 << 26
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if lib.fq_tc_workspace_bytes(q, 1, mid, 1) >= 0:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("q, l, codes", [(7, None, (1, 2, 3)), (3, 1 << 22, (0, 1))])
+def test_batched_tensor_core_exact_at_its_range(fq, q, l, codes):
+    """The batched tcgen05 kernel at the end of the exact fp32 range.  Deep
+    products whose rows of A are all +3 (F_7, at the longest l the form takes:
+    partial sums up to 2^24 - 1) or all +1 (F_3, l = 2^22) against random
+    positive B, so every step of the tensor-core sum adds a random amount and
+    an accumulation that dropped low bits would change the residues; C = A B
+    is then a column sum of B.  Short products share the plan, and the deep
+    ones are on one and on two 128-row blocks."""
+    l = l or _tc_max_l(fq, q)
+    a_val = 3 if q == 7 else 1
+    n = 70
+    rng = np.random.default_rng(q)
+    deep = [(3, l, n), (130, l, n)]
+    short = [(64, 128, 64), (200, 300, 100)]
+    shapes = deep + short
+    A, B, a, b, c = [], [], [], [], []
+    for p, (m, ll, nn) in enumerate(shapes):
+        if p < len(deep):
+            Ap = np.full((m, ll), a_val, np.uint8)
+            Bp = rng.choice(np.array(codes, np.uint8), size=(ll, nn))
+        else:
+            Ap = inputs.uniform(q, m, ll, seed=3, stream=2 * p)
+            Bp = inputs.uniform(q, ll, nn, seed=3, stream=2 * p + 1)
+        A.append(Ap)
+        B.append(Bp)
+        a.append(fq.pack(q, torch.from_numpy(Ap).cuda()))
+        b.append(fq.pack(q, torch.from_numpy(Bp).cuda()))
+        out = fq.empty(q, m, nn)
+        out.data.fill_(-1)
+        c.append(out)
+    ptr = lambda xs: torch.tensor([x.data.data_ptr() for x in xs], dtype=torch.int64, device="cuda")
+    plan = fq.BatchPlan(q, shapes, path=fq.PATH_MMA)
+    assert plan.tc_products == len(shapes) and plan.items == 0
+    plan.run(ptr(a), ptr(b), ptr(c))
+    assert fq.status() == fq.OK
+    for p, (m, ll, nn) in enumerate(shapes):
+        got = fq.unpack(c[p]).cpu().numpy()
+        if p < len(deep):
+            want = (a_val * B[p].sum(axis=0, dtype=np.int64)) % q
+            assert (got == want[None, :]).all(), "deep product %d" % p
+        else:
+            assert np.array_equal(got, oracle.matmul(q, A[p], B[p])), "product %d" % p

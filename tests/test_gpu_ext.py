@@ -173,12 +173,19 @@ def test_product_1024_full_oracle(fq, q):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("q", (8, 9, 125))
-def test_product_4096_sampled_rows_and_freivalds(fq, q):
+@pytest.mark.parametrize("q", EXT)
+def test_product_4096_sampled_rows_cols_and_freivalds(fq, q):
+    """4096^3 over every extension field: 256 exact oracle rows and 256 exact
+    oracle columns (the last of each among them) and a 32-trial Freivalds
+    check (a wrong product passes with probability at most q^-32)."""
     n = 4096
     A = inputs.uniform(q, n, n, seed=1, stream=inputs.STREAM_A)
     B = inputs.uniform(q, n, n, seed=1, stream=inputs.STREAM_B)
     got = fq.unpack(fq.matmul(fq.pack(q, to_dev(A)), fq.pack(q, to_dev(B)))).cpu().numpy()
-    rows = np.random.default_rng(q).choice(n, size=16, replace=False)
+    assert fq.status() == fq.OK
+    rng = np.random.default_rng(q)
+    rows = np.unique(np.append(rng.choice(n, size=255, replace=False), n - 1))
+    cols = np.unique(np.append(rng.choice(n, size=255, replace=False), n - 1))
     assert np.array_equal(got[rows], oracle.matmul_rows(q, A, B, rows))
-    assert oracle.freivalds(q, A, B, got, trials=2)
+    assert np.array_equal(got[:, cols], oracle.matmul_cols(q, A, B, cols))
+    assert oracle.freivalds(q, A, B, got, trials=32, seed=q)

@@ -209,25 +209,6 @@ def test_identity_and_permutation(fq, q):
     assert np.array_equal(got, B[perm])
 
 
-@pytest.mark.slow
-@pytest.mark.parametrize("q", FIELDS)
-def test_product_4096_full_oracle(fq, q):
-    _check_product(fq, q, 4096, 4096, 4096, seed=q)
-
-
-@pytest.mark.slow
-@pytest.mark.parametrize("n", [8192, 16384])
-def test_f3_large_sampled_rows_and_freivalds(fq, n):
-    """F_3 at n = 8192 and 16384: exact oracle rows for a sample, plus Freivalds."""
-    q = 3
-    A = inputs.uniform(q, n, n, seed=0, stream=inputs.STREAM_A)
-    B = inputs.uniform(q, n, n, seed=0, stream=inputs.STREAM_B)
-    got, _ = gpu_product(fq, q, A, B)
-    rows = np.random.default_rng(n).choice(n, size=24, replace=False)
-    assert np.array_equal(got[rows], oracle.matmul_rows(q, A, B, rows))
-    assert oracle.freivalds(q, A, B, got, trials=4)
-
-
 @pytest.mark.parametrize("q,k", [(2, 6), (2, 7), (2, 9), (2, 10), (3, 6), (3, 7), (3, 9), (3, 10),
                                  (4, 6), (4, 9), (4, 10), (5, 6), (5, 7), (7, 6), (7, 7)])
 def test_every_block_size(fq, q, k):
@@ -475,34 +456,3 @@ def test_auto_choice_follows_autotune(fq, q):
     res = fq.autotune(a, b)
     assert fq.auto_choice(q, 300, 200, 100) == (res["path"], res["kernel"])
     lib.fq_autotune_clear()
-
-
-def _large_case(fq, q, m, l, n, rows=16):
-    """M4RM and the tensor-core path on a large product: the two agree bit for
-    bit, sampled rows equal the oracle, and Freivalds accepts the whole result."""
-    A = inputs.uniform_torch(q, m, l, seed=5, stream=inputs.STREAM_A)
-    B = inputs.uniform_torch(q, l, n, seed=5, stream=inputs.STREAM_B)
-    a, b = fq.pack(q, A), fq.pack(q, B)
-    c1 = fq.matmul(a, b, path=fq.PATH_M4RM)
-    c2 = fq.matmul(a, b, path=fq.PATH_MMA)
-    assert fq.status() == fq.OK
-    assert torch.equal(c1.data, c2.data)
-    del c2
-    C = fq.unpack(c1).cpu().numpy()
-    Bh = B.cpu().numpy()
-    sample = np.random.default_rng(m + n).choice(m, size=rows, replace=False)
-    Ah = inputs.uniform(q, 1, l, seed=5, stream=inputs.STREAM_A, row0=0)  # row 0 drawn on the host
-    assert np.array_equal(Ah[0], A[0].cpu().numpy())                      # same draws as on the GPU
-    Arows = A[torch.from_numpy(sample).cuda()].cpu().numpy()
-    assert np.array_equal(C[sample], oracle.matmul(q, Arows, Bh))
-    assert oracle.freivalds(q, A.cpu().numpy(), Bh, C, trials=1, seed=q)
-
-
-@pytest.mark.slow
-def test_large_f5_32768_both_paths(fq):
-    _large_case(fq, 5, 32768, 32768, 32768)
-
-
-@pytest.mark.slow
-def test_large_f3_rectangular_65536_4096_4096(fq):
-    _large_case(fq, 3, 65536, 4096, 4096, rows=32)

@@ -206,21 +206,69 @@ def test_extension_codes_round_trip(q):
 # --- checks used at sizes the full oracle cannot reach ---
 
 @pytest.mark.parametrize("q", FIELDS)
+def test_randomized_check_products_equal_the_oracle(q):
+    """The exact product the randomized check uses (float64 library matmul by
+    row chunks; polynomial coefficients for extension fields) equals the C
+    oracle's row combination, with chunks of one row and of several rows."""
+    rng = np.random.default_rng(70 + q)
+    M = pins.rand(rng, q, 37, 53)
+    X = pins.rand(rng, q, 53, 11)
+    want = oracle.matmul(q, M, X)
+    for chunk in (1, 8 * 53 * 5, 1 << 28):
+        got = oracle._field_matmul(q, M, X.astype(np.int64), chunk_bytes=chunk)
+        assert got.dtype == np.int64
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("q", FIELDS)
 def test_freivalds_accepts_product_and_rejects_one_wrong_entry(q):
     rng = np.random.default_rng(7)
     A, B = pins.rand(rng, q, 40, 50), pins.rand(rng, q, 50, 30)
     C = oracle.matmul(q, A, B)
-    assert oracle.freivalds(q, A, B, C, trials=16)
-    bad = C.copy()
-    bad[13, 17] = (int(bad[13, 17]) + 1) % q
-    assert not oracle.freivalds(q, A, B, bad, trials=16)
+    assert oracle.freivalds(q, A, B, C, trials=32)
+    assert oracle.freivalds(q, A, B, C, trials=32, chunk_bytes=8 * 50 * 3)
+    for (i, j) in ((0, 0), (13, 17), (39, 29)):
+        for delta in range(1, q):
+            bad = C.copy()
+            bad[i, j] = (int(bad[i, j]) + delta) % q
+            assert not oracle.freivalds(q, A, B, bad, trials=32, chunk_bytes=8 * 50 * 3)
 
 
-def test_matmul_rows_is_a_slice():
+@pytest.mark.parametrize("q", [2, 3])
+def test_freivalds_trials_are_independent(q):
+    """One wrong entry e at (i, j): a trial passes exactly when x_j = 0, with
+    probability 1/q, so over many seeds t trials pass about q^-t of the time
+    (a check whose vectors were fixed or not uniform would pass always or never)."""
+    rng = np.random.default_rng(11)
+    A, B = pins.rand(rng, q, 12, 10), pins.rand(rng, q, 10, 9)
+    bad = oracle.matmul(q, A, B)
+    bad[4, 5] = (int(bad[4, 5]) + 1) % q
+    seeds = range(600)
+    for t in (1, 2):
+        passed = sum(oracle.freivalds(q, A, B, bad, trials=t, seed=s) for s in seeds)
+        expect = len(seeds) / q ** t
+        assert abs(passed - expect) < 5 * (expect * (1 - q ** -t)) ** 0.5, (t, passed, expect)
+
+
+def test_freivalds_refuses_sums_beyond_float64():
+    """Sums of l products of at most (p - 1)^2 are exact float64 integers only
+    while l (p - 1)^2 < 2^53: longer rows are refused (a broadcast view has the
+    shape without the memory)."""
+    wide = np.broadcast_to(np.zeros(1, np.uint8), (1, 1 << 48))
+    with pytest.raises(ValueError):
+        oracle._fp_matmul(7, wide, np.zeros((1, 1), np.int64))
+    ok = np.broadcast_to(np.zeros(1, np.uint8), (1, 3))
+    assert oracle._fp_matmul(7, ok, np.ones((3, 1), np.int64)).tolist() == [[0]]
+
+
+@pytest.mark.parametrize("q", [5, 4, 9])
+def test_matmul_rows_and_cols_are_slices(q):
     rng = np.random.default_rng(8)
-    A, B = pins.rand(rng, 5, 30, 20), pins.rand(rng, 5, 20, 10)
-    rows = [0, 7, 29]
-    assert np.array_equal(oracle.matmul_rows(5, A, B, rows), oracle.matmul(5, A, B)[rows])
+    A, B = pins.rand(rng, q, 30, 20), pins.rand(rng, q, 20, 10)
+    C = oracle.matmul(q, A, B)
+    rows, cols = [0, 7, 29], [9, 0, 4, 4]
+    assert np.array_equal(oracle.matmul_rows(q, A, B, rows), C[rows])
+    assert np.array_equal(oracle.matmul_cols(q, A, B, cols), C[:, cols])
 
 
 def test_thread_count_does_not_change_result():
