@@ -27,7 +27,14 @@ against the classical product's work).
 * ``batched``: 4096 independent products over F_3 and over F_5 (m, l, n
   uniform over multiples of 64 in [64, 1024]) in one graph-captured launch
   sequence: products/s and 2mln/s for the FQ_PATH_AUTO plan and for the
-  Four-Russians-only plan.
+  Four-Russians-only plan; the AUTO plan's stages timed one by one, with the
+  tcgen05 tile kernel against the fp8 peak and the e4m3 conversions against
+  HBM.
+* ``more_workloads``: F_5, F_7 and GF(4) at n = 8192, then F_5 32768^3 and F_3
+  65536 x 4096 x 4096, each product on both paths (the tcgen05 form as
+  conversion + product kernel, the Four-Russians path), each with its
+  roofline (fp8 tensor peak, HBM, LOP3 issue rate) and the two results
+  compared bit for bit.
 * ``pack_unpack``: fq_pack of the step's operands and fq_unpack of its results,
   timed apart from the product (the metric excludes them).
 * ``cpu_baseline``: the CPU oracle on a bounded sample of rows of the same
@@ -60,11 +67,27 @@ PRODUCTS = [(4096, 4096, 4096, "uniform"), (8192, 8192, 8192, "uniform"),
             (16384, 16384, 16384, "uniform"), (8192, 8192, 8192, "sparse90")]
 WORKLOAD = "F_3 square products n=4096, 8192, 16384 uniform + n=8192 with A 90% zeros"
 
+# The other workloads, each product timed on both paths: F_5, F_7 and GF(4) at
+# n = 8192; the large F_5 32768^3 and F_3 65536 x 4096 x 4096.
+MORE_WORKLOADS = [
+    ("F_5, F_7 and GF(4) square products n=8192 uniform",
+     [(5, 8192, 8192, 8192), (7, 8192, 8192, 8192), (4, 8192, 8192, 8192)]),
+    ("large: F_5 square n=32768 and F_3 65536 x 4096 x 4096, uniform",
+     [(5, 32768, 32768, 32768), (3, 65536, 4096, 4096)]),
+]
+
 # Integer-logic issue rate: 64 LOP3 lane-ops per clock per SM (the ALU pipe;
 # measured 63.99 on this GPU), 152 SMs, 2070 MHz maximum SM clock.
 ALU_PEAK_TLOPS = 64 * 152 * 2.070e9 / 1e12
-LOP3_PER_ADD = 4     # F_3 add and subtract are four LOP3s per 32-element word pair
-BASIS = 2            # F_3 additive basis {1, -1}
+# Algorithmic LOP3 lane-ops of the Four-Russians arithmetic per 32-column word:
+# LOOKUP_LOP3 for one row and k-row block (its D lookups accumulated: F_3 an
+# add and a subtract of four LOP3s each; GF(4) two three-input XORs and one
+# XOR; F_7 two carry-save adders mod 7 and one add; F_5 two carry-save adders
+# and an end-around add mod 15, then fold5), TABLE_LOP3 for one table entry
+# (one bitsliced add: F_3 4, GF(4) 2, F_7 10, F_5 11).
+LOOKUP_LOP3 = {3: 8, 4: 3, 5: 35, 7: 22}
+TABLE_LOP3 = {3: 4, 4: 2, 5: 11, 7: 10}
+PLANES = {2: 1, 3: 2, 4: 2, 5: 3, 7: 3}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -81,20 +104,40 @@ def pitch_words(cols):
     return cdiv(max(cols, 1), 1024) * 16
 
 
-def prepare_bytes(m, l, n, planes=2):
-    """Algorithmic DRAM bytes of the F_3 operand conversion: both planes of A
-    and of B read, e4m3 A and B^T written."""
+def prepare_bytes(m, l, n, q=3):
+    """Algorithmic DRAM bytes of the operand conversion: every plane of A and
+    of B read, e4m3 A and B^T written (GF(4): three rounds, one per F_2
+    product)."""
     la, npad = cdiv(l, 128) * 128, pitch_words(n) * 64
-    return planes * (m * pitch_words(l) + l * pitch_words(n)) * 8 + (m + npad) * la
+    rounds = 3 if q == 4 else 1
+    return rounds * (PLANES[q] * (m * pitch_words(l) + l * pitch_words(n)) * 8 + (m + npad) * la)
 
 
-def algorithmic_lop3(m, l, n, k):
-    """LOP3 lane-ops of one F_3 product by M4RM: every (row, block, basis element)
-    lookup adds one table row (ceil(n/32) word pairs), and every block's table of
-    2^k - 1 nonzero combinations is built once."""
+def tensor_flops(q, m, l, n):
+    """Tensor-pipe work of one product: 2 m l n (three F_2 products for GF(4))."""
+    return (3 if q == 4 else 1) * 2.0 * m * l * n
+
+
+def algorithmic_lop3(m, l, n, k, q=3):
+    """LOP3 lane-ops of one product by M4RM: for every row and k-row block the
+    D lookups are accumulated into ceil(n/32) column words (LOOKUP_LOP3 each),
+    and every block's table of 2^k - 1 nonzero combinations is built once
+    (one bitsliced add per entry and word)."""
     words = cdiv(n, 32)
     blocks = cdiv(l, k)
-    return LOP3_PER_ADD * words * blocks * (m * BASIS + (2 ** k - 1))
+    return words * blocks * (m * LOOKUP_LOP3[q] + (2 ** k - 1) * TABLE_LOP3[q])
+
+
+def batched_conversion_bytes(q, shapes):
+    """Algorithmic DRAM bytes of the batched conversions for the products on
+    the tcgen05 path: A's planes over la = l rounded up to 128 columns and B's
+    over nr = n rounded up to 256 columns read, e4m3 A (m x la) and B^T (n x
+    la) written."""
+    total = 0
+    for (m, l, n) in shapes:
+        la, nr = cdiv(l, 128) * 128, cdiv(n, 256) * 256
+        total += PLANES[q] * (m * la + l * nr) // 8 + (m + n) * la
+    return total
 
 
 def our_launches(levels):
@@ -115,6 +158,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-product batched workloads")
+    ap.add_argument("--no-more", action="store_true",
+                    help="skip the F_5/F_7/GF(4) 8192 and the large F_5 / F_3 workloads")
     ap.add_argument("--cpu-rows", type=int, default=1024,
                     help="oracle rows sampled per product (about 11 s of oracle work on 16 cores)")
     return ap.parse_args()
@@ -167,6 +212,8 @@ def batched_leg(torch, fq, inputs, dist, dev, reps=10):
             entry = {"ms": t, "products_per_s": dist.world * len(shapes) / (t * 1e-3),
                      "field_ops_per_s": dist.world * ops / (t * 1e-3),
                      "tc_products": plan.tc_products, "m4rm_items": plan.items}
+            if name == "auto" and plan.tc_products > 0:
+                entry.update(batched_stage_rooflines(torch, fq, plan, q, shapes, pa, pb, pc, stream, reps))
             rec[name] = entry
             del g, plan
         if not torch.equal(results["auto"], results["m4rm"]):
@@ -177,6 +224,131 @@ def batched_leg(torch, fq, inputs, dist, dev, reps=10):
         out["F_%d" % q] = rec
         del a, b, c, results
         torch.cuda.empty_cache()
+    return out
+
+
+def batched_stage_rooflines(torch, fq, plan, q, shapes, pa, pb, pc, stream, reps):
+    """The AUTO plan's launch stages timed one at a time (fq_matmul_batched_stages,
+    CUDA events on the launching stream, median of `reps`): the two e4m3
+    conversions against HBM, the persistent tcgen05 tile kernel against the fp8
+    tensor peak, the Four-Russians kernel (if the plan has items)."""
+    peaks = measured_peaks()
+    tc = [sh for sh, path in zip(shapes, plan.product_paths()) if path == fq.PATH_MMA]
+    ms = {"convert": [], "tile": [], "m4rm": []}
+    for r in range(reps + 2):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            plan.run_stages(pa, pb, pc, fq.STAGE_CONVERT, stream=stream)
+            ev[1].record(stream)
+            plan.run_stages(pa, pb, pc, fq.STAGE_TC, stream=stream)
+            ev[2].record(stream)
+            plan.run_stages(pa, pb, pc, fq.STAGE_M4RM, stream=stream)
+            ev[3].record(stream)
+        torch.cuda.synchronize()
+        if r >= 2:
+            ms["convert"].append(ev[0].elapsed_time(ev[1]))
+            ms["tile"].append(ev[1].elapsed_time(ev[2]))
+            ms["m4rm"].append(ev[2].elapsed_time(ev[3]))
+    if fq.status() != fq.OK:
+        raise SystemExit("device error in the batched stages")
+    conv_ms, tile_ms = statistics.median(ms["convert"]), statistics.median(ms["tile"])
+    flops = sum(2.0 * m * l * n for (m, l, n) in tc)
+    conv_bytes = batched_conversion_bytes(q, tc)
+    tile_tflops = flops / (tile_ms * 1e-3) / 1e12
+    conv_gbs = conv_bytes / (conv_ms * 1e-3) / 1e9
+    return {
+        "stages_ms": {k: statistics.median(v) for k, v in ms.items()},
+        "tile_roofline": {"bound": "tensor", "kernel": "tc_batched_kernel", "achieved": tile_tflops,
+                          "peak": peaks["fp8"], "unit": "TFLOP/s", "frac": tile_tflops / peaks["fp8"],
+                          "peak_note": peaks["note"], "flops": flops},
+        "conversion_roofline": {"bound": "hbm", "kernels": "batched_rows_kernel + batched_transpose_kernel",
+                                "achieved": conv_gbs, "peak": peaks["hbm"], "unit": "GB/s",
+                                "frac": conv_gbs / peaks["hbm"], "bytes": conv_bytes, "peak_note": peaks["hbm_note"]},
+        "stages_note": "each stage called on its own (fq_matmul_batched_stages), median of %d; the graph "
+                       "replay above runs them back to back" % reps,
+    }
+
+
+def product_leg(torch, fq, inputs, dist, dev, flush, workload, prods, clk, reps=3, warmup=1):
+    """One product at a time, on both paths, inputs resident in HBM and L2
+    flushed before every timed product: the tcgen05 form as its two stages
+    (conversion, product kernel) and the plain bitsliced Four-Russians path,
+    each against its roofline; the two results must agree bit for bit."""
+    peaks = measured_peaks()
+    stream = torch.cuda.current_stream()
+    out = {"workload": workload, "products": []}
+    tot_tc = tot_m4 = 0.0
+    ops_all = 0.0
+    for (q, m, l, n) in prods:
+        A = inputs.uniform_torch(q, m, l, seed=0, stream=inputs.STREAM_A, device=dev)
+        B = inputs.uniform_torch(q, l, n, seed=0, stream=inputs.STREAM_B, device=dev)
+        a, b = fq.pack(q, A), fq.pack(q, B)
+        del A, B
+        c_tc, c_m4 = fq.empty(q, m, n), fq.empty(q, m, n)
+        ops = fq.TensorOperands(a, b)
+        t_prep, t_mul, t_m4 = [], [], []
+        for r in range(warmup + reps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            flush.fill_(r)
+            ev[0].record(stream)
+            ops.prepare(a, b)
+            ev[1].record(stream)
+            ops.multiply(out=c_tc)
+            ev[2].record(stream)
+            flush.fill_(r + 1)
+            ev[3].record(stream)
+            fq.matmul(a, b, out=c_m4, path=fq.PATH_M4RM)
+            ev[4].record(stream)
+            torch.cuda.synchronize()
+            if r >= warmup:
+                t_prep.append(ev[0].elapsed_time(ev[1]))
+                t_mul.append(ev[1].elapsed_time(ev[2]))
+                t_m4.append(ev[3].elapsed_time(ev[4]))
+        if fq.status() != fq.OK:
+            raise SystemExit("device error in the F_%d %dx%dx%d product" % (q, m, l, n))
+        agree = bool(torch.equal(c_tc.data, c_m4.data))
+        if not agree:
+            raise SystemExit("F_%d %dx%dx%d: the two paths give different products" % (q, m, l, n))
+        prep_ms = dist.max(statistics.median(t_prep), dev)
+        mul_ms = dist.max(statistics.median(t_mul), dev)
+        m4_ms = dist.max(statistics.median(t_m4), dev)
+        field_ops = 2.0 * m * l * n
+        tflops = tensor_flops(q, m, l, n) / (mul_ms * 1e-3) / 1e12
+        pbytes = prepare_bytes(m, l, n, q)
+        levels = fq.strassen_levels(q, m, l, n, path=fq.PATH_M4RM)
+        leaf = (m >> levels, l >> levels, n >> levels)
+        k = fq.planned_kernel(q, *leaf, path=fq.PATH_M4RM)["k"]
+        lop3 = 7 ** levels * algorithmic_lop3(*leaf, k, q)
+        lop3_t = lop3 / (m4_ms * 1e-3) / 1e12
+        out["products"].append({
+            "q": q, "m": m, "l": l, "n": n, "paths_agree": agree,
+            "tensor": {"ms": prep_ms + mul_ms, "prepare_ms": prep_ms, "multiply_ms": mul_ms,
+                       "field_ops_per_s": dist.world * field_ops / ((prep_ms + mul_ms) * 1e-3),
+                       "roofline": {"bound": "tensor", "achieved": tflops, "peak": peaks["fp8"], "unit": "TFLOP/s",
+                                    "frac": tflops / peaks["fp8"], "peak_note": peaks["note"],
+                                    "pipe": pipe_peak(tflops, clk)},
+                       "prepare_roofline": {"bound": "hbm", "achieved": pbytes / (prep_ms * 1e-3) / 1e9,
+                                            "peak": peaks["hbm"], "unit": "GB/s",
+                                            "frac": pbytes / (prep_ms * 1e-3) / 1e9 / peaks["hbm"],
+                                            "bytes": pbytes}},
+            "m4rm": {"ms": m4_ms, "field_ops_per_s": dist.world * field_ops / (m4_ms * 1e-3),
+                     "strassen_levels": levels, "k": k,
+                     "roofline": {"bound": "alu", "achieved": lop3_t, "peak": ALU_PEAK_TLOPS, "unit": "Tlop3/s",
+                                  "frac": lop3_t / ALU_PEAK_TLOPS, "lop3": lop3,
+                                  "peak_note": "derived: 64 LOP3 lanes/clk/SM x 152 SMs x 2070 MHz"}},
+            "speedup_tensor_vs_m4rm": m4_ms / (prep_ms + mul_ms),
+        })
+        tot_tc += prep_ms + mul_ms
+        tot_m4 += m4_ms
+        ops_all += field_ops
+        del ops, a, b, c_tc, c_m4
+        torch.cuda.empty_cache()
+    out["tensor_field_ops_per_s"] = dist.world * ops_all / (tot_tc * 1e-3)
+    out["m4rm_field_ops_per_s"] = dist.world * ops_all / (tot_m4 * 1e-3)
+    out["speedup_tensor_vs_m4rm"] = tot_m4 / tot_tc
+    out["timing"] = ("per product: median of %d after %d warm-up, CUDA events on the launching stream, L2 flushed "
+                     "(256 MiB write) before each path" % (reps, warmup))
     return out
 
 
@@ -601,11 +773,16 @@ def main():
             if evs is not None:
                 evs[j][2].record(stream)
 
+    auto_results = [c.data.clone() for (a, b, c) in packed]
     m_steps = max(3, min(args.steps, 5))
     m_stage, m_ms = timed(m4rm_step, m_steps, 3)
+    for ref, (a, b, c) in zip(auto_results, packed):
+        if not torch.equal(ref, c.data):
+            raise SystemExit("the Four-Russians path and the headline path give different products")
+    del auto_results
     m_value = ops_step * dist.world / (m_ms * 1e-3)
     m_per_product = [sum(m_stage[s_][j][1] for s_ in range(m_steps)) / m_steps for j in range(len(prods))]
-    lop3_step = sum(7 ** lv * algorithmic_lop3(m >> lv, l >> lv, n >> lv, k)
+    lop3_step = sum(7 ** lv * algorithmic_lop3(m >> lv, l >> lv, n >> lv, k, Q)
                     for lv, k, (m, l, n, _) in zip(m_levels, leaf_k, prods))
     m_achieved = lop3_step / (sum(m_per_product) * 1e-3) / 1e12
     m_traffic_rec = measured_traffic("m4rm_f3_dram_traffic.json", kernel_sources_digest())
@@ -749,6 +926,11 @@ def main():
 
     batched = None if args.no_batched else batched_leg(torch, fq, inputs, dist, dev)
 
+    more = None
+    if not args.sizes and not args.no_more:
+        torch.cuda.empty_cache()
+        more = [product_leg(torch, fq, inputs, dist, dev, flush, name, ps, clk) for name, ps in MORE_WORKLOADS]
+
     base = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         ops, times, cores, nrows = cpu_baseline(prods, args.cpu_rows)
@@ -789,6 +971,7 @@ def main():
             "e2e": e2e,
             "e2e_packed": e2e_packed,
             "batched": batched,
+            "more_workloads": more,
             "cpu_baseline": base,
             "clocks": clk,
             "gpu_launches": args.steps * sum(TC_LAUNCHES if f == "tensor" else 1 for f in forms),

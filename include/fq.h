@@ -225,6 +225,26 @@ int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *str
 int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
                       uint64_t *const *C, void *workspace, void *stream);
 
+/* fq_matmul_batched in its launch stages, so that each can be timed on its
+ * own: `stages` is a bit mask of
+ *   FQ_BATCH_STAGE_CONVERT  the tcgen05 products' operands to e4m3 (two kernels),
+ *   FQ_BATCH_STAGE_TC       their persistent tile kernel, which reads the
+ *                           arenas the last CONVERT stage on this workspace wrote,
+ *   FQ_BATCH_STAGE_M4RM     the queue reset and the persistent Four-Russians kernel;
+ * stages run in that order.  fq_matmul_batched is FQ_BATCH_STAGE_ALL.  Same
+ * arguments and rules as fq_matmul_batched; FQ_EINVAL for a mask outside
+ * 0 .. FQ_BATCH_STAGE_ALL. */
+#define FQ_BATCH_STAGE_CONVERT 1
+#define FQ_BATCH_STAGE_TC 2
+#define FQ_BATCH_STAGE_M4RM 4
+#define FQ_BATCH_STAGE_ALL 7
+int fq_matmul_batched_stages(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
+                             uint64_t *const *C, void *workspace, void *stream, int stages);
+
+/* The path a plan gives product p: FQ_PATH_MMA (tcgen05) or FQ_PATH_M4RM;
+ * -FQ_EINVAL for a NULL plan or p outside 0 .. count - 1.  Host only. */
+int fq_batched_product_path(const fq_batch_plan *plan, int p);
+
 /* Free a plan (NULL is fine). */
 int fq_batched_plan_destroy(fq_batch_plan *plan);
 
@@ -310,6 +330,18 @@ int fq_release_scratch(void);
 /* Wait for `stream`, then return and clear the first error kernels recorded on
  * the current device (FQ_EVALUE, FQ_ETIMEOUT), or FQ_OK.  Synchronous. */
 int fq_status(void *stream);
+
+/* Failure-path hook: the Four-Russians kernels launched after this call give
+ * up each bounded device wait (an mbarrier hand-over between the warps of a
+ * CTA, normally bounded at about two seconds) after `ns` nanoseconds instead;
+ * ns <= 0 restores the default.  A wait that gives up records FQ_ETIMEOUT for
+ * fq_status(); the CTA then stops issuing copies, waits (with the default
+ * bound) for the copies it already issued, skips the lookups whose tables it
+ * never received and exits, so the product is garbage but the device stays
+ * usable.  Process-wide host setting, read at each launch (a captured graph
+ * keeps the value of its capture).  It exists so that tests can drive the
+ * timeout path on purpose; no product needs it.  Host only. */
+int fq_debug_wait_limit(int64_t ns);
 
 /* Static text for a status code. */
 const char *fq_error_string(int status);

@@ -1,5 +1,6 @@
 // The C ABI of include/fq.h: argument checks, the per-device status word and
 // dispatch to the kernels.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -22,6 +23,9 @@ std::mutex g_mu;
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
+// The wait limit later Four-Russians launches carry (fq_debug_wait_limit).
+std::atomic<uint64_t> g_wait_limit_ns{kWaitLimitNs};
+
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Fields with their own kernels: F_2, F_3, F_5, F_7 and GF(4).
@@ -30,6 +34,8 @@ bool base_q(int q) { return q == 2 || q == 3 || q == 4 || q == 5 || q == 7; }
 bool valid_q(int q) { return base_q(q) || ext_field(q) != nullptr; }
 
 }  // namespace
+
+uint64_t wait_limit_ns() { return g_wait_limit_ns.load(std::memory_order_relaxed); }
 
 int record_cuda_error(cudaError_t e) {
   snprintf(t_last_cuda_error, sizeof(t_last_cuda_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
@@ -327,5 +333,10 @@ const char *fq_error_string(int status) {
 }
 
 const char *fq_last_cuda_error(void) { return fqk::t_last_cuda_error; }
+
+int fq_debug_wait_limit(int64_t ns) {
+  fqk::g_wait_limit_ns.store(ns > 0 ? uint64_t(ns) : fqk::kWaitLimitNs, std::memory_order_relaxed);
+  return FQ_OK;
+}
 
 }  // extern "C"

@@ -584,16 +584,18 @@ int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *str
   });
 }
 
-int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
-                      uint64_t *const *C, void *workspace, void *stream) {
+int fq_matmul_batched_stages(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
+                             uint64_t *const *C, void *workspace, void *stream, int stages) {
   if (!plan || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 63u) != 0) return FQ_EINVAL;
+  if (stages < 0 || stages > FQ_BATCH_STAGE_ALL) return FQ_EINVAL;
   if (plan->items.empty() && plan->tc_prods.empty()) return FQ_OK;
   if (!A || !B || !C) return FQ_EINVAL;
   unsigned char *ws = static_cast<unsigned char *>(workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (!plan->tc_prods.empty())
-    if (int rc = fqk::tc_batched(tc_view(plan, ws), A, B, C, s)) return rc;
-  if (plan->items.empty()) return FQ_OK;
+  const int tc_stages = (stages & FQ_BATCH_STAGE_CONVERT ? 1 : 0) | (stages & FQ_BATCH_STAGE_TC ? 2 : 0);
+  if (!plan->tc_prods.empty() && tc_stages)
+    if (int rc = fqk::tc_batched(tc_view(plan, ws), A, B, C, s, tc_stages)) return rc;
+  if (plan->items.empty() || !(stages & FQ_BATCH_STAGE_M4RM)) return FQ_OK;
   switch (plan->q) {
     case 3: return fqk::batched::launch_field<fqk::F3>(ws, A, B, C, s);
     case 4: return fqk::batched::launch_field<fqk::GF4>(ws, A, B, C, s);
@@ -601,6 +603,18 @@ int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const
     case 7: return fqk::batched::launch_field<fqk::F7>(ws, A, B, C, s);
     default: return FQ_EINVAL;
   }
+}
+
+int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
+                      uint64_t *const *C, void *workspace, void *stream) {
+  return fq_matmul_batched_stages(plan, A, B, C, workspace, stream, FQ_BATCH_STAGE_ALL);
+}
+
+int fq_batched_product_path(const fq_batch_plan *plan, int p) {
+  if (!plan || p < 0 || p >= plan->count) return -FQ_EINVAL;
+  for (const fqk::BatchProd &bp : plan->tc_prods)
+    if (bp.p == p) return FQ_PATH_MMA;
+  return FQ_PATH_M4RM;
 }
 
 int fq_batched_plan_destroy(fq_batch_plan *plan) {

@@ -33,6 +33,12 @@ int status_word(unsigned **out);
 // Encoder for TMA tensor maps, fetched from the driver once.
 int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000 *out);
 
+// How long a bounded device wait lasts before it gives up, in nanoseconds.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+// The limit the Four-Russians kernels are launched with: kWaitLimitNs unless
+// fq_debug_wait_limit set another (process-wide).
+uint64_t wait_limit_ns();
+
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // --------------------------------------------------------------- device side --
@@ -77,10 +83,11 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// Waits for phase `parity` of the mbarrier to complete.  Gives up after about
-// two seconds of wall time and returns false; the caller records FQ_ETIMEOUT
-// and leaves the kernel.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Waits for phase `parity` of the mbarrier to complete.  Gives up after
+// `limit_ns` of wall time (about two seconds by default) and returns false; the
+// caller records FQ_ETIMEOUT and leaves the kernel.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
   uint32_t done = 0;
   asm volatile(
       "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -92,7 +99,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
         : "=r"(done) : "r"(bar), "r"(parity) : "memory");
     if (done) return true;
-    if (globaltimer_ns() - t0 > 2000000000ull) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 

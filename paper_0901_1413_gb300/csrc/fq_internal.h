@@ -67,8 +67,9 @@ struct TcBatch {
   const int64_t *tile_prefix = nullptr;           // device, ntiles + 1: cumulative modelled tile cost
   uint8_t *a_arena = nullptr, *b_arena = nullptr; // device
 };
+// stages: bit 0 the two operand conversions, bit 1 the tile kernel (both by default).
 int tc_batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B, uint64_t *const *C,
-               cudaStream_t s);
+               cudaStream_t s, int stages = 3);
 
 // One compiled M4RM kernel shape of a field (the planner's candidates).
 struct Variant {

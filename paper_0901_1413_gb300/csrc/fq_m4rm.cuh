@@ -94,6 +94,7 @@ struct M4rmParams {
   int mt;           // rows per CTA (== MT except in tests)
   uint32_t one;     // the constant 1, as data (keeps address arithmetic on IMAD)
   unsigned *err;
+  uint64_t wait_ns; // bound of the builders' waits for B blocks
 };
 
 __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
@@ -413,10 +414,15 @@ __global__ void __launch_bounds__(Cfg::NT, 1)
     for (int b = 0; b < nb; ++b) {
       const int64_t s = c0 + b;
       const int buf = int(s & 1);
-      if (builder && !mbar_wait_bounded(bar_s + 8 * buf, uint32_t((s >> 1) & 1))) s_abort = 1;
+      if (builder && !mbar_wait_bounded(bar_s + 8 * buf, uint32_t((s >> 1) & 1), prm.wait_ns)) s_abort = 1;
       __syncthreads();  // table free; this block's B rows visible to the builders
       if (s_abort) {
-        if (tid == 0) record_error(prm.err, FQ_ETIMEOUT);
+        // Block s's copy is the only one in flight (block s + 1's is issued
+        // below): wait for it with the default bound before the CTA exits.
+        if (tid == 0) {
+          record_error(prm.err, FQ_ETIMEOUT);
+          mbar_wait_bounded(bar_s + 8 * buf, uint32_t((s >> 1) & 1));
+        }
         cp_async_wait_all();
         return;
       }
@@ -457,6 +463,7 @@ int launch_cfg(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_
   prm.mt = mt;
   prm.one = 1u;
   prm.err = err;
+  prm.wait_ns = wait_limit_ns();
 
   CUtensorMap map;
   memset(&map, 0, sizeof(map));

@@ -21,9 +21,12 @@
 // read table s mod NBUF, producers
 // fill the next ones, and the offsets of chunk c + 1 are written while chunk c
 // is consumed.  Hand-over is by mbarriers (tfull: 128
-// producer arrivals; tempty: 384 consumer arrivals).  Every wait is bounded;
-// on a timeout the CTA records FQ_ETIMEOUT, stops waiting and runs out its
-// loops without further synchronisation hazards.
+// producer arrivals; tempty: 384 consumer arrivals).  Every wait is bounded
+// (Params::wait_ns); on a timeout the CTA records FQ_ETIMEOUT and runs out its
+// loops without waiting again: consumers skip the lookups of tables they did
+// not receive (so every shared-memory address stays valid), the TMA thread
+// issues no further copies and, before the CTA exits, waits for the copies it
+// had issued.
 #pragma once
 
 #include <cstring>
@@ -98,6 +101,7 @@ struct Params {
   int mt;           // rows per CTA (<= MT)
   uint32_t one;     // the constant 1 as data: address adds stay on IMAD
   unsigned *err;
+  uint64_t wait_ns; // bound of each hand-over wait
 };
 
 __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
@@ -126,6 +130,7 @@ __device__ __forceinline__ void sts128(uint32_t addr, const uint32_t (&v)[4]) {
 
 // Bounded wait that also gives up at once when the CTA has aborted.  A phase
 // that is already complete returns without reading the shared abort flag.
+// True when the phase completed, false when the CTA has given up.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t done = 0;
   asm volatile(
@@ -133,14 +138,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "=r"(done) : "r"(bar), "r"(parity) : "memory");
   return done != 0;
 }
-__device__ __forceinline__ void wait_or_abort(uint32_t bar, uint32_t parity, volatile int &abort_flag,
-                                              unsigned *err) {
-  if (mbar_try(bar, parity)) return;
-  if (abort_flag) return;
-  if (!mbar_wait_bounded(bar, parity)) {
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int &abort_flag,
+                                              unsigned *err, uint64_t limit_ns) {
+  if (mbar_try(bar, parity)) return true;
+  if (abort_flag) return false;
+  if (!mbar_wait_bounded(bar, parity, limit_ns)) {
     abort_flag = 1;
     record_error(err, FQ_ETIMEOUT);
+    return false;
   }
+  return true;
 }
 
 // ------------------------------------------------------------- producers --
@@ -395,8 +402,10 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
     const int ptid = tid;
     const int builder = warp * C::GPW + grp;
     const uint32_t tbl_lane0 = base + C::TABLE_OFF + uint32_t(gl * 16);
+    // copies thread 0 has issued: B blocks 0 .. b_issued - 1 (in order), A chunks 0 .. a_issued - 1
+    int64_t b_issued = 0, a_issued = 0;
     if (ptid == 0) {
-      for (int64_t s = 0; s < C::NSTAGE && s < prm.nblocks; ++s) {
+      for (int64_t s = 0; s < C::NSTAGE && s < prm.nblocks; ++s, ++b_issued) {
         mbar_expect_tx(bfull + 8 * uint32_t(s), C::STAGE_BYTES);
         tma_load_3d(base + C::BSTAGE_OFF + uint32_t(s) * C::STAGE_STRIDE, &tmB, bfull + 8 * uint32_t(s), int(w0),
                     int(s * C::K), 0);
@@ -409,14 +418,18 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
     uint32_t aphase = 0;  // completed uses of afull
     // prologue: offsets of chunk 0, A words of chunk 1 in flight
     if (prm.nblocks > 0) {
-      if (ptid == 0) stage_a<C>(&tmA, astage, afull, row0, 0);
-      wait_or_abort(afull, aphase & 1, abort_flag, prm.err);
+      if (ptid == 0) {
+        stage_a<C>(&tmA, astage, afull, row0, 0);
+        ++a_issued;
+      }
+      wait_or_abort(afull, aphase & 1, abort_flag, prm.err, prm.wait_ns);
       ++aphase;
       build_offsets<C>(prm, astage_p, offs0, rows_here, 0, int(prm.nblocks < C::NB ? prm.nblocks : C::NB), ptid);
       producer_sync<C::NPT>();  // the A stage is free
       if (ptid == 0 && nchunks > 1 && !abort_flag) {
         fence_proxy_async_smem();
         stage_a<C>(&tmA, astage, afull, row0, C::NB);
+        ++a_issued;
       }
     }
     for (int64_t s = 0; s < prm.nblocks; ++s) {
@@ -429,8 +442,8 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
         // then prefetch the A words of chunk c + 2
         const int64_t c = s / C::NB;
         if (c + 1 < nchunks) {
-          if (s >= C::NBUF) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
-          wait_or_abort(afull, aphase & 1, abort_flag, prm.err);
+          if (s >= C::NBUF) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err, prm.wait_ns);
+          wait_or_abort(afull, aphase & 1, abort_flag, prm.err, prm.wait_ns);
           ++aphase;
           const int64_t c1 = (c + 1) * C::NB;
           build_offsets<C>(prm, astage_p, offs0 + ((c + 1) & 1) * (C::OFFS_BYTES / 4), rows_here, c1,
@@ -439,12 +452,13 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
           if (ptid == 0 && c + 2 < nchunks && !abort_flag) {
             fence_proxy_async_smem();
             stage_a<C>(&tmA, astage, afull, row0, (c + 2) * C::NB);
+            ++a_issued;
           }
         }
       }
-      if (s >= C::NBUF) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err);
+      if (s >= C::NBUF) wait_or_abort(tempty + 8 * buf, (use - 1) & 1, abort_flag, prm.err, prm.wait_ns);
       const int sb = int(s % C::NSTAGE);
-      wait_or_abort(bfull + 8 * sb, uint32_t(s / C::NSTAGE) & 1, abort_flag, prm.err);
+      wait_or_abort(bfull + 8 * sb, uint32_t(s / C::NSTAGE) & 1, abort_flag, prm.err, prm.wait_ns);
       build_table<C>(tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), base + C::BSTAGE_OFF + sb * C::STAGE_STRIDE,
                      builder, gl);
       producer_sync<C::NPT>();  // every producer is done with this B stage
@@ -453,8 +467,20 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
         mbar_expect_tx(bfull + 8 * sb, C::STAGE_BYTES);
         tma_load_3d(base + C::BSTAGE_OFF + sb * C::STAGE_STRIDE, &tmB, bfull + 8 * sb, int(w0),
                     int((s + C::NSTAGE) * C::K), 0);
+        ++b_issued;
       }
       mbar_arrive(tfull + 8 * buf);
+    }
+    // After a wait gave up, copies thread 0 issued may still be landing in
+    // this CTA's shared memory; the CTA must not exit before they have.
+    // Thread 0 issues a copy into a stage only after its own wait saw the
+    // stage's previous copy complete, so only the last copy of each stage can
+    // be outstanding: wait for those (with the default bound -- issued copies
+    // always complete).
+    if (ptid == 0 && abort_flag) {
+      for (int64_t j = b_issued > C::NSTAGE ? b_issued - C::NSTAGE : 0; j < b_issued; ++j)
+        mbar_wait_bounded(bfull + 8 * uint32_t(j % C::NSTAGE), uint32_t(j / C::NSTAGE) & 1);
+      if (a_issued > 0) mbar_wait_bounded(afull, uint32_t(a_issued - 1) & 1);
     }
   } else {
     // ------------------------------------------------------- consumers
@@ -468,11 +494,13 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
       for (int j = 0; j < 4; ++j) acc[i][j] = 0u;
     for (int64_t s = 0; s < prm.nblocks; ++s) {
       const int buf = int(s % C::NBUF);
-      wait_or_abort(tfull + 8 * buf, uint32_t(s / C::NBUF) & 1, abort_flag, prm.err);
+      // after a wait that gave up, the offsets may never have been written:
+      // no lookup (the result is garbage then, but every address stays valid)
+      const bool have = wait_or_abort(tfull + 8 * buf, uint32_t(s / C::NBUF) & 1, abort_flag, prm.err, prm.wait_ns);
       const int64_t c = s / C::NB;
       const uint32_t offs_s =
           base + C::OFFS_OFF + uint32_t(c & 1) * C::OFFS_BYTES + uint32_t((s - c * C::NB) * C::MT) * 4u;
-      lookup_block<C>(acc, tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), offs_s, cw, grp, prm.one);
+      if (have) lookup_block<C>(acc, tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), offs_s, cw, grp, prm.one);
       mbar_arrive(tempty + 8 * buf);
     }
     // epilogue: canonical codes (F_3 and GF(4) codes are already canonical)
@@ -512,6 +540,7 @@ int launch(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B
   prm.mt = mt;
   prm.one = 1u;
   prm.err = err;
+  prm.wait_ns = wait_limit_ns();
   CUtensorMap map, amap;
   memset(&map, 0, sizeof(map));
   memset(&amap, 0, sizeof(amap));

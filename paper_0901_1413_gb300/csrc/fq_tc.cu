@@ -44,8 +44,8 @@ namespace tc {
 constexpr int BM = 128, BN = 256, BK = 128, UK = 32, STAGES = 4;  // BK, UK: k per stage, per MMA (bytes)
 constexpr int A_BYTES = BM * BK, B_BYTES = BN * BK, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int ACC = 2;                         // TMEM accumulators (epilogue overlaps the next tile)
-constexpr int BAR_OFF = STAGES * STAGE_BYTES;  // full[S], empty[S], accfull[ACC], accempty[ACC], tmem slot, abort
-constexpr int NBARS = 2 * STAGES + 2 * ACC;
+constexpr int BAR_OFF = STAGES * STAGE_BYTES;  // full[S], empty[S], accfull[ACC], accempty[ACC], drain, tmem slot, abort
+constexpr int NBARS = 2 * STAGES + 2 * ACC + 1;
 constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;  // + alignment slack
 constexpr int TMEM_COLS = ACC * BN;
 constexpr int THREADS = 256;
@@ -345,6 +345,19 @@ __device__ __forceinline__ void wait_bar(uint32_t bar, uint32_t parity, volatile
   }
 }
 
+// Exit path after a wait gave up.  Copies the producer issued land in this
+// CTA's shared memory and MMAs the issuing thread started read it and write
+// TMEM, so neither may outlive the CTA or its TMEM allocation.
+//  * drain_copies: the producer issues a stage's next copy only after its
+//    wait saw the stage consumed (and so its previous copy landed), so only
+//    the last `stages` copies can be in flight: wait for their full phases.
+//  * drain_mmas: one commit after all the thread's MMAs, waited for.
+// Both wait with the default bound and ignore the abort flag.
+__device__ __forceinline__ void drain_copies(uint32_t full, int issued, int stages) {
+  for (int j = issued > stages ? issued - stages : 0; j < issued; ++j)
+    mbar_wait_bounded(full + 8 * uint32_t(j % stages), uint32_t((j / stages) & 1));
+}
+
 struct GemmParams {
   uint64_t *C;
   int64_t m, pc;   // rows of C, pitch words of C
@@ -475,6 +488,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(accfull + 8 * b, 1);
       mbar_init(accempty + 8 * b, 4);  // one arrival per epilogue warp
     }
+    mbar_init(accempty + 8 * ACC, 1);  // the MMA drain
     fence_mbar_init();
   }
   if (warp == 2) {
@@ -504,6 +518,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         tma_load_2d(b_dst, &tmB, full + 8 * s, ks * BK, nb * BN);
       }
     }
+    if (*abort_flag) drain_copies(full, it, STAGES);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     int it = 0, li = 0;
@@ -524,6 +539,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         mma_commit(empty + 8 * s);  // the stage is free once these MMAs have read it
       }
       mma_commit(accfull + 8 * b);  // this tile's accumulator is complete
+    }
+    if (*abort_flag) {  // the MMAs issued so far complete before TMEM is freed
+      mma_commit(accempty + 8 * ACC);
+      mbar_wait_bounded(accempty + 8 * ACC, 0);
     }
   } else if (warp >= 4) {
     // ---- epilogue
@@ -586,7 +605,7 @@ struct PairGeo {
   static constexpr int STAGES = WIDE ? 4 : 6;
   static constexpr int NACC = WIDE ? 1 : 2;         // accumulators of NB columns (NB * NACC = 512)
   static constexpr int BAR_OFF = STAGES * STAGE;
-  static constexpr int NBARS = 2 * STAGES + 2 * NACC;
+  static constexpr int NBARS = 2 * STAGES + 2 * NACC + 1;  // + the MMA drain barrier
   static constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;
   static constexpr int EPI = WIDE ? 8 : 4;          // epilogue warps (the wide form's is exposed: twice as many)
   static constexpr int THREADS = 128 + 32 * EPI;
@@ -690,6 +709,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairGeo<WIDE>::THREA
       mbar_init(accfull + 8 * b, 1);
       mbar_init(accempty + 8 * b, 2 * G::EPI);  // the epilogue warps of both CTAs (the leader's barrier)
     }
+    mbar_init(accempty + 8 * G::NACC, 1);  // the leader's MMA drain
     fence_mbar_init();
   }
   if (warp == 2) {  // one warp of each CTA allocates the pair's columns together
@@ -724,9 +744,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairGeo<WIDE>::THREA
           tma_load_2d_pair(b_dst + uint32_t(j * B2_BYTES), &tmB, bar, ks * BK, nb * G::NB + 256 * j + 128 * int(rank));
       }
     }
-    // the last commits to this CTA's stage barriers have landed before it exits
+    // The last commits to this CTA's stage barriers have landed before it
+    // exits.  After a wait gave up these waits still run (default bound): this
+    // CTA's copies count on the leader's full barrier, which it cannot watch,
+    // but a stage's commit comes only after its copies have landed, and a
+    // copy that never gets one was issued at least the whole bound earlier.
     for (int j = it > G::STAGES ? it - G::STAGES : 0; j < it; ++j)
-      wait_bar(empty + 8 * (j % G::STAGES), uint32_t((j / G::STAGES) & 1), abort_flag, prm.err);
+      mbar_wait_bounded(empty + 8 * uint32_t(j % G::STAGES), uint32_t((j / G::STAGES) & 1));
   } else if (warp == 1 && lane == 0 && leader) {
     // ---- MMA issuer (the leader CTA only)
     int it = 0, li = 0;
@@ -751,6 +775,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairGeo<WIDE>::THREA
         mma_commit_pair(empty + 8 * s);  // both CTAs' stage s is free once these MMAs have read it
       }
       mma_commit_pair(accfull + 8 * b);  // this tile's accumulators are complete in both CTAs
+    }
+    if (*abort_flag) {  // the pair's MMAs complete before either CTA frees its TMEM
+      asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       accempty + 8 * G::NACC)
+                   : "memory");
+      mbar_wait_bounded(accempty + 8 * G::NACC, 0);
     }
   } else if (warp >= 4) {
     // ---- epilogue (both CTAs): rows 128 rank + 32 (warp % 4) + lane of the
@@ -925,6 +955,7 @@ __global__ void __launch_bounds__(THREADS_B, 1)
       mbar_init(accfull + 8 * b, 1);
       mbar_init(accempty + 8 * b, 16);  // sixteen epilogue warps
     }
+    mbar_init(accempty + 8 * ACC, 1);  // the MMA drain
     fence_mbar_init();
   }
   if (warp == 2) {
@@ -957,6 +988,7 @@ __global__ void __launch_bounds__(THREADS_B, 1)
         tma_load_2d(b_dst, &tmB, full + 8 * s, 0, bt.yb + ks * BN);  // one contiguous 32 KB block
       }
     }
+    if (*abort_flag) drain_copies(full, it, STAGES);
   } else if (warp == 1 && lane == 0) {
     int it = 0, li = 0;
     int nks = t_begin < t_end ? prm.tiles[t_begin].ksteps : 0;
@@ -979,6 +1011,10 @@ __global__ void __launch_bounds__(THREADS_B, 1)
         mma_commit(empty + 8 * s);
       }
       mma_commit(accfull + 8 * b);
+    }
+    if (*abort_flag) {  // the MMAs issued so far complete before TMEM is freed
+      mma_commit(accempty + 8 * ACC);
+      mbar_wait_bounded(accempty + 8 * ACC, 0);
     }
   } else if (warp >= 4) {
     // warps 4..19: TMEM lane quadrant warp % 4, columns 64 quarter .. + 63
@@ -1148,18 +1184,21 @@ int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, co
 
 template <int Q, int P>
 int batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B, uint64_t *const *C,
-            cudaStream_t s) {
+            cudaStream_t s, int stages) {
   if (b.nprod == 0 || b.ntiles == 0) return FQ_OK;
   unsigned *err = nullptr;
   if (int rc = status_word(&err)) return rc;
   const int64_t cap = 152 * 8;
-  if (b.a_units > 0)
-    batched_rows_kernel<Q, P><<<unsigned(b.a_units < cap ? b.a_units : cap), 256, 0, s>>>(
-        b.prods, b.a_prefix, b.a_unit_prod, b.a_units, A, b.a_arena);
-  if (b.b_units > 0)
-    batched_transpose_kernel<Q, P><<<unsigned(b.b_units < cap ? b.b_units : cap), 256, 0, s>>>(
-        b.prods, b.b_prefix, b.b_unit_prod, b.b_units, B, b.b_arena);
-  FQ_LAUNCH_CHECK();
+  if (stages & 1) {
+    if (b.a_units > 0)
+      batched_rows_kernel<Q, P><<<unsigned(b.a_units < cap ? b.a_units : cap), 256, 0, s>>>(
+          b.prods, b.a_prefix, b.a_unit_prod, b.a_units, A, b.a_arena);
+    if (b.b_units > 0)
+      batched_transpose_kernel<Q, P><<<unsigned(b.b_units < cap ? b.b_units : cap), 256, 0, s>>>(
+          b.prods, b.b_prefix, b.b_unit_prod, b.b_units, B, b.b_arena);
+    FQ_LAUNCH_CHECK();
+  }
+  if (!(stages & 2)) return FQ_OK;
   CUtensorMap ma, mb;
   if (int rc = make_map(&ma, b.a_arena, BK, b.a_rows, BM)) return rc;
   if (int rc = make_map(&mb, b.b_arena, BK, b.b_rows, BN)) return rc;
@@ -1253,12 +1292,12 @@ int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const u
 }
 
 int tc_batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B, uint64_t *const *C,
-               cudaStream_t s) {
+               cudaStream_t s, int stages) {
   if (b.a_rows >= (int64_t(1) << 31) || b.b_rows >= (int64_t(1) << 31)) return FQ_ENOTSUP;
   switch (b.q) {
-    case 3: return tc::batched<3, 2>(b, A, B, C, s);
-    case 5: return tc::batched<5, 3>(b, A, B, C, s);
-    case 7: return tc::batched<7, 3>(b, A, B, C, s);
+    case 3: return tc::batched<3, 2>(b, A, B, C, s, stages);
+    case 5: return tc::batched<5, 3>(b, A, B, C, s, stages);
+    case 7: return tc::batched<7, 3>(b, A, B, C, s, stages);
     default: return FQ_EINVAL;
   }
 }

@@ -19,6 +19,7 @@ from . import build as _build
 
 OK, EINVAL, EVALUE, ECUDA, ETIMEOUT, ENOTSUP, ENOMEM = range(7)
 PATH_AUTO, PATH_M4RM, PATH_MMA, PATH_KARATSUBA = 0, 1, 2, 3
+STAGE_CONVERT, STAGE_TC, STAGE_M4RM, STAGE_ALL = 1, 2, 4, 7
 
 _lib = None
 
@@ -68,6 +69,9 @@ def load():
             "fq_batched_plan_upload": (i32, [vp, vp, vp]),
             "fq_matmul_batched": (i32, [vp, vp, vp, vp, vp, vp]),
             "fq_matmul_batched_static": (i32, [vp, vp, vp, vp, vp]),
+            "fq_matmul_batched_stages": (i32, [vp, vp, vp, vp, vp, vp, i32]),
+            "fq_batched_product_path": (i32, [vp, i32]),
+            "fq_debug_wait_limit": (i32, [i64]),
             "fq_batched_plan_destroy": (i32, [vp]),
             "fq_autotune": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, vp]),
             "fq_autotune_lookup": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
@@ -293,6 +297,20 @@ class BatchPlan:
         _check(load().fq_matmul_batched(self._h, ctypes.c_void_p(A_ptrs.data_ptr()),
                                         ctypes.c_void_p(B_ptrs.data_ptr()), ctypes.c_void_p(C_ptrs.data_ptr()),
                                         ctypes.c_void_p(self._ws_ptr()), _stream(stream)), "fq_matmul_batched")
+
+    def run_stages(self, A_ptrs: torch.Tensor, B_ptrs: torch.Tensor, C_ptrs: torch.Tensor, stages: int,
+                   stream=None):
+        """fq_matmul_batched_stages: only the launch stages in the mask
+        (STAGE_CONVERT, STAGE_TC, STAGE_M4RM), for timing them apart."""
+        _check(load().fq_matmul_batched_stages(self._h, ctypes.c_void_p(A_ptrs.data_ptr()),
+                                               ctypes.c_void_p(B_ptrs.data_ptr()),
+                                               ctypes.c_void_p(C_ptrs.data_ptr()), ctypes.c_void_p(self._ws_ptr()),
+                                               _stream(stream), int(stages)), "fq_matmul_batched_stages")
+
+    def product_paths(self) -> list[int]:
+        """fq_batched_product_path of every product: PATH_MMA or PATH_M4RM."""
+        lib = load()
+        return [lib.fq_batched_product_path(self._h, p) for p in range(len(self.shapes))]
 
     def run_static(self, A_ptrs: torch.Tensor, B_ptrs: torch.Tensor, C_ptrs: torch.Tensor, stream=None):
         """fq_matmul_batched_static: the same products with the work list in the

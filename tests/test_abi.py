@@ -212,6 +212,15 @@ def test_batch_plan_host_side(lib):
     assert lib.fq_batched_tc_products(h) == 2
     assert lib.fq_batched_tc_tiles(h) == 3 + 16
     assert lib.fq_batched_workspace_bytes(h) == 2048 + 2176 * 128 + 1024 * 128
+    assert [lib.fq_batched_product_path(h, p) for p in range(4)] == [fq.PATH_MMA, fq.PATH_MMA, fq.PATH_M4RM,
+                                                                     fq.PATH_M4RM]
+    assert lib.fq_batched_product_path(h, 4) == -fq.EINVAL
+    assert lib.fq_batched_product_path(h, -1) == -fq.EINVAL
+    assert lib.fq_batched_product_path(None, 0) == -fq.EINVAL
+    # stage masks outside 0 .. FQ_BATCH_STAGE_ALL are refused before any launch
+    for bad_mask in (-1, 8, 100):
+        assert lib.fq_matmul_batched_stages(h, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8),
+                                            ctypes.c_void_p(64), None, bad_mask) == fq.EINVAL
     assert lib.fq_batched_plan_destroy(h) == fq.OK
     assert lib.fq_batched_plan_create_ex(3, 4, i64p(m), i64p(l), i64p(n), 9, ctypes.byref(h)) == fq.EINVAL
     assert lib.fq_batched_tc_products(None) == -1
@@ -285,3 +294,12 @@ def test_autotune_cache_host_side(lib):
     for q in (8, 9, 25, 27, 49, 125):
         assert lib.fq_auto_choice(q, 100, 100, 100, ctypes.byref(p), ctypes.byref(k)) == fq.OK
         assert (p.value, k.value) == (fq.PATH_KARATSUBA, 0)
+
+
+def test_wait_limit_hook_is_host_only(lib):
+    """fq_debug_wait_limit only stores the bound later launches carry: it needs
+    no device, accepts any value and 0 restores the default."""
+    from paper_0901_1413_gb300 import fq
+    assert lib.fq_debug_wait_limit(1) == fq.OK
+    assert lib.fq_debug_wait_limit(-5) == fq.OK
+    assert lib.fq_debug_wait_limit(0) == fq.OK

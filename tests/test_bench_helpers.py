@@ -40,3 +40,31 @@ def test_prepare_bytes_counts_planes_in_and_e4m3_out():
     assert bench.prepare_bytes(8192, 8192, 8192) == 2 * (2 * 8192 * 128 * 8) + 2 * 8192 * 8192
     # ragged: l rounded up to 128, n's rows of B^T to the 1024-column pitch
     assert bench.prepare_bytes(100, 200, 300) == 2 * (100 * 16 + 200 * 16) * 8 + (100 + 1024) * 256
+
+
+def test_prepare_bytes_other_fields():
+    bench = _bench()
+    # F_5 / F_7: three planes read; GF(4): three rounds (one per F_2 product)
+    # of both planes read and e4m3 written
+    assert bench.prepare_bytes(8192, 8192, 8192, q=5) == 3 * (2 * 8192 * 128 * 8) + 2 * 8192 * 8192
+    assert bench.prepare_bytes(8192, 8192, 8192, q=4) == 3 * (2 * (2 * 8192 * 128 * 8) + 2 * 8192 * 8192)
+    assert bench.tensor_flops(4, 2, 3, 5) == 3 * 60.0 and bench.tensor_flops(7, 2, 3, 5) == 60.0
+
+
+def test_algorithmic_lop3_counts():
+    bench = _bench()
+    # F_3 at k = 8: ceil(l/8) blocks x ceil(n/32) words x (8 LOP3 per row + 4 per table entry)
+    assert bench.algorithmic_lop3(64, 16, 64, 8) == 2 * 2 * (64 * 8 + 255 * 4)
+    assert bench.algorithmic_lop3(64, 16, 64, 8, q=3) == bench.algorithmic_lop3(64, 16, 64, 8)
+    # ragged: l = 17 needs three blocks, n = 33 two words
+    assert bench.algorithmic_lop3(1, 17, 33, 8, q=5) == 3 * 2 * (35 + 255 * 11)
+    assert bench.algorithmic_lop3(10, 7, 32, 7, q=7) == 1 * 1 * (10 * 22 + 127 * 10)
+    assert bench.algorithmic_lop3(10, 7, 32, 7, q=4) == 10 * 3 + 127 * 2
+
+
+def test_batched_conversion_bytes():
+    bench = _bench()
+    # one F_3 product 100 x 200 x 300: la = 256, nr = 512; planes of A over la
+    # columns and of B over nr columns read (2 bits per element), e4m3 written
+    assert bench.batched_conversion_bytes(3, [(100, 200, 300)]) == 2 * (100 * 256 + 200 * 512) // 8 + 400 * 256
+    assert bench.batched_conversion_bytes(5, [(64, 128, 256)] * 2) == 2 * (3 * (64 * 128 + 128 * 256) // 8 + 320 * 128)
