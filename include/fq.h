@@ -39,6 +39,12 @@
  * enqueued.  Errors a kernel detects while running (a residue >= q in fq_pack, a
  * bounded device wait that gave up) are recorded on the device and returned by
  * fq_status().
+ *
+ * Debug build: compiled with -DFQ_DEBUG (libfq_gb300_debug.so, same ABI), the
+ * kernels also check every table index of a Four-Russians lookup against the
+ * table (idx < 2^k) and every store of C against its rows and row pitch; a
+ * failed check records FQ_EBOUNDS and the access is skipped (or made to entry
+ * 0 of the table).  The release library has no such checks.
  */
 #ifndef FQ_H
 #define FQ_H
@@ -57,6 +63,7 @@ extern "C" {
 #define FQ_ETIMEOUT 4  /* a bounded device wait gave up (device-detected)          */
 #define FQ_ENOTSUP 5   /* valid request the library does not support              */
 #define FQ_ENOMEM 6    /* host allocation failed                                   */
+#define FQ_EBOUNDS 7   /* a bounds check of the FQ_DEBUG build failed (device-detected) */
 
 /* ---- product paths (fq_options.path) --------------------------------------- */
 #define FQ_PATH_AUTO 0 /* planner's choice                                         */
@@ -267,7 +274,17 @@ int fq_batched_plan_destroy(fq_batch_plan *plan);
  *   - All calls on a GPU share the one array: calls whose work overlaps on the
  *     GPU (for example on two streams) race and give wrong results.
  *   - Each call copies the work list from host memory, which a graph replay
- *     could not repeat: FQ_ENOTSUP while `stream` is being captured.
+ *     could not repeat: FQ_ENOTSUP while `stream` is being captured.  The
+ *     copies are from pageable host memory, so a call must also not run
+ *     while another thread captures a stream in cudaStreamCaptureModeGlobal
+ *     (such a copy would invalidate that capture).
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current).  Under CUDA's lazy module
+ *     loading that first use also loads the library's device code and the
+ *     array on that device, which synchronises like an allocation: make the
+ *     first call during set-up, before any timing-critical section.
+ *   - The looked-up address (like the status word's) is kept for the life of
+ *     the process: the library does not survive cudaDeviceReset.
  * The paper has no counterpart: this is an interface for allocation-free
  * callers, with the arguments and results of fq_matmul_batched. */
 int fq_matmul_batched_static(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
@@ -290,6 +307,18 @@ typedef struct fq_tune_result {
 
 int fq_autotune(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                 void *stream, fq_tune_result *out);
+/* The cache as a file, so that measurements survive the process:
+ * fq_autotune_save writes every remembered choice to `path` as JSON,
+ *   {"format": "fq-autotune-1", "entries": [[q, m, l, n, path, kernel], ...]};
+ * fq_autotune_load merges such a file into the cache (its entries replace
+ * remembered choices of the same shapes).  A file that is not exactly that
+ * document, or holds an entry the library cannot honour (a field without
+ * kernels, a negative size, a path other than FQ_PATH_M4RM / FQ_PATH_MMA, a
+ * kernel outside the field's compiled ones, a tensor-core entry with a
+ * kernel), is refused whole with FQ_EINVAL and nothing is merged; I/O
+ * failures are FQ_EINVAL too, host allocation failures FQ_ENOMEM.  Host only. */
+int fq_autotune_save(const char *path);
+int fq_autotune_load(const char *path);
 /* FQ_OK and the remembered choice for (q, m, l, n), or FQ_ENOTSUP if none. */
 int fq_autotune_lookup(int q, int64_t m, int64_t l, int64_t n, int *path, int *kernel);
 int fq_autotune_clear(void);
@@ -331,17 +360,25 @@ int fq_release_scratch(void);
  * the current device (FQ_EVALUE, FQ_ETIMEOUT), or FQ_OK.  Synchronous. */
 int fq_status(void *stream);
 
-/* Failure-path hook: the Four-Russians kernels launched after this call give
- * up each bounded device wait (an mbarrier hand-over between the warps of a
- * CTA, normally bounded at about two seconds) after `ns` nanoseconds instead;
- * ns <= 0 restores the default.  A wait that gives up records FQ_ETIMEOUT for
- * fq_status(); the CTA then stops issuing copies, waits (with the default
- * bound) for the copies it already issued, skips the lookups whose tables it
- * never received and exits, so the product is garbage but the device stays
- * usable.  Process-wide host setting, read at each launch (a captured graph
- * keeps the value of its capture).  It exists so that tests can drive the
- * timeout path on purpose; no product needs it.  Host only. */
+/* Failure-path hooks, so that tests can drive the timeout path on purpose; no
+ * product needs them.  Process-wide host settings read at each launch of the
+ * Four-Russians kernels (a captured graph keeps the values of its capture).
+ * Host only.
+ *   fq_debug_wait_limit: later launches give up each bounded device wait (an
+ *     mbarrier hand-over between the warps of a CTA, normally bounded at about
+ *     two seconds) after `ns` nanoseconds of polling instead; ns <= 0 restores
+ *     the default.  (A wait polls with mbarrier.try_wait, which may itself
+ *     suspend the thread for a hardware-defined time, so a short wait can
+ *     complete although it outlasts a very small limit.)
+ *   fq_debug_stall_block: in later launches one thread of every CTA, on
+ *     reaching k-row block `block`, also waits on a barrier that nothing ever
+ *     completes -- a wait that always gives up; block < 0 turns it off.
+ * A wait that gives up records FQ_ETIMEOUT for fq_status(); the CTA then stops
+ * issuing copies, waits (with the default bound) for the copies it already
+ * issued, skips the lookups whose tables it never received and exits: the
+ * product is garbage but the device stays usable. */
 int fq_debug_wait_limit(int64_t ns);
+int fq_debug_stall_block(int64_t block);
 
 /* Static text for a status code. */
 const char *fq_error_string(int status);

@@ -25,6 +25,8 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 // The wait limit later Four-Russians launches carry (fq_debug_wait_limit).
 std::atomic<uint64_t> g_wait_limit_ns{kWaitLimitNs};
+// The block of the injected wait that nothing completes (fq_debug_stall_block).
+std::atomic<int64_t> g_stall_block{-1};
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -36,6 +38,7 @@ bool valid_q(int q) { return base_q(q) || ext_field(q) != nullptr; }
 }  // namespace
 
 uint64_t wait_limit_ns() { return g_wait_limit_ns.load(std::memory_order_relaxed); }
+int64_t stall_block() { return g_stall_block.load(std::memory_order_relaxed); }
 
 int record_cuda_error(cudaError_t e) {
   snprintf(t_last_cuda_error, sizeof(t_last_cuda_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
@@ -328,6 +331,7 @@ const char *fq_error_string(int status) {
     case FQ_ETIMEOUT: return "bounded device wait timed out";
     case FQ_ENOTSUP: return "not supported";
     case FQ_ENOMEM: return "out of host memory";
+    case FQ_EBOUNDS: return "bounds check failed (debug build)";
     default: return "unknown status";
   }
 }
@@ -336,6 +340,11 @@ const char *fq_last_cuda_error(void) { return fqk::t_last_cuda_error; }
 
 int fq_debug_wait_limit(int64_t ns) {
   fqk::g_wait_limit_ns.store(ns > 0 ? uint64_t(ns) : fqk::kWaitLimitNs, std::memory_order_relaxed);
+  return FQ_OK;
+}
+
+int fq_debug_stall_block(int64_t block) {
+  fqk::g_stall_block.store(block >= 0 ? block : -1, std::memory_order_relaxed);
   return FQ_OK;
 }
 

@@ -111,7 +111,7 @@ __device__ __noinline__ void run_item(const M4rmParams &prm, const uint64_t *B, 
         stage_b<Cfg>(B, prm.l, prm.pc, bstage_s + (buf ^ 1) * Cfg::STAGE_STRIDE, w0, s + 1, tid);
       if (builder) build_table<Cfg>(tbl_lane, bstage_s + buf * Cfg::STAGE_STRIDE, warp * Cfg::GPW + grp, gl);
       __syncthreads();  // table complete
-      lookup_block<Cfg, true>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one, slots);
+      lookup_block<Cfg, true>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one, prm.err, slots);
     }
   }
   cp_async_wait_all();
@@ -151,6 +151,8 @@ __global__ void __launch_bounds__(C8::NT, C8::P == 2 ? 2 : 1)
     prm.mt = it.rows;
     prm.one = 1u;
     prm.err = err;
+    prm.wait_ns = kWaitLimitNs;  // the item body stages B with cp.async: no mbarrier waits
+    prm.stall = -1;
     const uint64_t *B = Bptr[it.product];
     const int64_t w0 = int64_t(it.col_tile) * C8::CTW;
     if (it.k == 0) {  // padding columns only: C's words there are zero

@@ -38,6 +38,9 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 // The limit the Four-Russians kernels are launched with: kWaitLimitNs unless
 // fq_debug_wait_limit set another (process-wide).
 uint64_t wait_limit_ns();
+// The k-row block at which the Four-Russians kernels launched next make their
+// injected wait (fq_debug_stall_block), or -1 for none.
+int64_t stall_block();
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -46,6 +49,23 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // First error wins; later ones are dropped.
 __device__ __forceinline__ void record_error(unsigned *err, unsigned code) {
   atomicCAS(err, 0u, code);
+}
+
+// Bounds checks of the FQ_DEBUG build: `ok` is the condition an access needs;
+// a failed check records FQ_EBOUNDS and returns false so that the caller can
+// skip (or redirect) the access.  In the release build every check is true
+// and compiles away.
+#ifdef FQ_DEBUG
+constexpr bool kDebug = true;
+#else
+constexpr bool kDebug = false;
+#endif
+__device__ __forceinline__ bool debug_ok(bool ok, unsigned *err) {
+  if constexpr (kDebug) {
+    if (!ok) record_error(err, FQ_EBOUNDS);
+    return ok;
+  }
+  return true;
 }
 
 // Three-input logic op.  LUT bytes: a -> 0xF0, b -> 0xCC, c -> 0xAA.

@@ -78,8 +78,8 @@ struct M4rmCfg {
   static constexpr int ASTAGE_OFF = BSTAGE_OFF + 2 * STAGE_STRIDE;  // [p][r][2] uint64
   static constexpr int ASTAGE_BYTES = P * MT * 16;
   static constexpr int OFFS_OFF = ASTAGE_OFF + ASTAGE_BYTES;
-  static constexpr int BAR_OFF = OFFS_OFF + NB * MT * int(sizeof(Off));
-  static constexpr int ABORT_OFF = BAR_OFF + 16;
+  static constexpr int BAR_OFF = OFFS_OFF + NB * MT * int(sizeof(Off));  // B stages [2], stall
+  static constexpr int ABORT_OFF = BAR_OFF + 24;
   static constexpr int SMEM = ABORT_OFF + 16;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -95,6 +95,7 @@ struct M4rmParams {
   uint32_t one;     // the constant 1, as data (keeps address arithmetic on IMAD)
   unsigned *err;
   uint64_t wait_ns; // bound of the builders' waits for B blocks
+  int64_t stall;    // block of the injected wait that nothing completes (-1: none)
 };
 
 __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
@@ -287,7 +288,7 @@ __device__ __forceinline__ void build_table(uint32_t tbl_lane, uint32_t stage, i
 template <class Cfg, bool PARTIAL = false>
 __device__ __forceinline__ void lookup_block(uint32_t (&acc)[Cfg::RS][Cfg::PW], uint32_t tbl_lane,
                                              const typename Cfg::Off *offs_b, int warp, int grp, uint32_t one,
-                                             int slots = Cfg::RS) {
+                                             unsigned *err, int slots = Cfg::RS) {
   using F = typename Cfg::Field;
   constexpr int P = Cfg::P, D = Cfg::D, WPL = Cfg::WPL, PW = Cfg::PW, CH = Cfg::CH, VW = Cfg::VW;
 #pragma unroll
@@ -308,6 +309,8 @@ __device__ __forceinline__ void lookup_block(uint32_t (&acc)[Cfg::RS][Cfg::PW], 
       uint32_t t[D][PW];
 #pragma unroll
       for (int d = 0; d < D; ++d) {
+        if constexpr (kDebug)  // every offset is a table entry (idx < 2^k): else entry 0
+          if (!debug_ok(od[d] < uint32_t(Cfg::ENTRIES * Cfg::ENTRY), err)) od[d] = 0u;
         const uint32_t addr = imad(od[d], one, tbl_lane);
 #pragma unroll
         for (int c = 0; c < CH; ++c) lds_vec<VW>(addr + c * 128, &t[d][c * VW]);
@@ -337,7 +340,7 @@ __device__ __forceinline__ void store_tile(uint32_t (&acc)[Cfg::RS][Cfg::PW], co
 #pragma unroll
   for (int i = 0; i < Cfg::RS; ++i) {
     const int r = i * Cfg::ROWS_PER_SLOT + warp * Cfg::GPW + grp;
-    if (r < rows_here) {
+    if (r < rows_here && debug_ok(row0 + r < prm.m && w0 + Cfg::CTW <= prm.pc, prm.err)) {
       const int64_t row = row0 + r;
 #pragma unroll
       for (int w = 0; w < WPL; ++w) {
@@ -388,6 +391,7 @@ __global__ void __launch_bounds__(Cfg::NT, 1)
     s_abort = 0;
     mbar_init(bar_s, 1);
     mbar_init(bar_s + 8, 1);
+    mbar_init(bar_s + 16, 1);  // never arrived on
     fence_mbar_init();
   }
   __syncthreads();
@@ -415,6 +419,7 @@ __global__ void __launch_bounds__(Cfg::NT, 1)
       const int64_t s = c0 + b;
       const int buf = int(s & 1);
       if (builder && !mbar_wait_bounded(bar_s + 8 * buf, uint32_t((s >> 1) & 1), prm.wait_ns)) s_abort = 1;
+      if (tid == 0 && s == prm.stall && !mbar_wait_bounded(bar_s + 16, 0, prm.wait_ns)) s_abort = 1;  // injected
       __syncthreads();  // table free; this block's B rows visible to the builders
       if (s_abort) {
         // Block s's copy is the only one in flight (block s + 1's is issued
@@ -435,9 +440,9 @@ __global__ void __launch_bounds__(Cfg::NT, 1)
       if (builder) build_table<Cfg>(tbl_lane, bstage_s + buf * Cfg::STAGE_STRIDE, warp * Cfg::GPW + grp, gl);
       __syncthreads();  // table complete
       if (rows_here == Cfg::MT)
-        lookup_block<Cfg>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one);
+        lookup_block<Cfg>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one, prm.err);
       else
-        lookup_block<Cfg, true>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one,
+        lookup_block<Cfg, true>(acc, tbl_lane, offs + b * Cfg::MT, warp, grp, prm.one, prm.err,
                                 (rows_here + Cfg::ROWS_PER_SLOT - 1) / Cfg::ROWS_PER_SLOT);
     }
   }
@@ -464,6 +469,7 @@ int launch_cfg(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_
   prm.one = 1u;
   prm.err = err;
   prm.wait_ns = wait_limit_ns();
+  prm.stall = stall_block();
 
   CUtensorMap map;
   memset(&map, 0, sizeof(map));

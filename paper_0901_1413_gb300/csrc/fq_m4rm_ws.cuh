@@ -86,8 +86,8 @@ struct Cfg {
   static constexpr int OFFS_OFF = NBUF * TABLE_BYTES;
   static constexpr int BSTAGE_OFF = OFFS_OFF + 2 * OFFS_BYTES;
   static constexpr int ASTAGE_OFF = BSTAGE_OFF + NSTAGE * STAGE_STRIDE;
-  static constexpr int BAR_OFF = ASTAGE_OFF + ASTAGE_BYTES;  // bfull[NSTAGE], tfull[NBUF], tempty[NBUF], afull
-  static constexpr int ABORT_OFF = BAR_OFF + 8 * (NSTAGE + 2 * NBUF + 1);
+  static constexpr int BAR_OFF = ASTAGE_OFF + ASTAGE_BYTES;  // bfull[NSTAGE], tfull[NBUF], tempty[NBUF], afull, stall
+  static constexpr int ABORT_OFF = BAR_OFF + 8 * (NSTAGE + 2 * NBUF + 2);
   static constexpr int SMEM = ABORT_OFF + 16;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -102,6 +102,7 @@ struct Params {
   uint32_t one;     // the constant 1 as data: address adds stay on IMAD
   unsigned *err;
   uint64_t wait_ns; // bound of each hand-over wait
+  int64_t stall;    // block of the injected wait that nothing completes (-1: none)
 };
 
 __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
@@ -326,13 +327,21 @@ __device__ __forceinline__ void build_table(uint32_t tbl_lane, uint32_t stage, i
 
 template <class C>
 __device__ __forceinline__ void lookup_block(uint32_t (&acc)[C::RS][4], uint32_t tbl_lane, uint32_t offs_s, int cw,
-                                             int grp, uint32_t one) {
+                                             int grp, uint32_t one, unsigned *err) {
   using F = typename C::Field;
 #pragma unroll
   for (int j = 0; j < C::RS / 2; ++j) {
     uint32_t o[2];
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
                  : "=r"(o[0]), "=r"(o[1]) : "r"(offs_s + uint32_t(((j * C::ROWS_PER_SLOT) + cw * C::GPW + grp) * 8)));
+    if constexpr (kDebug) {  // every offset is a table entry (idx < 2^k): else entry 0
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool ok = C::D == 1 ? o[h] < uint32_t(C::TABLE_BYTES)
+                                  : ((o[h] & 0xFFFFu) < uint32_t(C::TABLE_BYTES) && (o[h] >> 16) < uint32_t(C::TABLE_BYTES));
+        if (!debug_ok(ok, err)) o[h] = 0u;
+      }
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int i = 2 * j + h;
@@ -381,7 +390,7 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
 
   const uint32_t base = smem_u32(smem);
   const uint32_t bfull = base + C::BAR_OFF, tfull = bfull + 8 * C::NSTAGE, tempty = tfull + 8 * C::NBUF,
-                 afull = tempty + 8 * C::NBUF;
+                 afull = tempty + 8 * C::NBUF, stall = afull + 8;
   volatile int &abort_flag = *reinterpret_cast<int *>(smem + C::ABORT_OFF);
 
   if (tid == 0) {
@@ -392,6 +401,7 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
       mbar_init(tempty + 8 * i, C::NCW * 32);
     }
     mbar_init(afull, 1);
+    mbar_init(stall, 1);  // never arrived on
     fence_mbar_init();
   }
   __syncthreads();
@@ -435,6 +445,10 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
     for (int64_t s = 0; s < prm.nblocks; ++s) {
       const int buf = int(s % C::NBUF);
       const uint32_t use = uint32_t(s / C::NBUF);
+      if (s == prm.stall && ptid == 0 && !mbar_wait_bounded(stall, 0, prm.wait_ns)) {  // injected failure
+        abort_flag = 1;
+        record_error(prm.err, FQ_ETIMEOUT);
+      }
       if (s % C::NB == C::NBUF - 1) {
         // block NBUF - 1 of chunk c: write the offsets of chunk c + 1 into the
         // buffer chunk c - 1 used -- consumers are done with it once block
@@ -500,14 +514,14 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
       const int64_t c = s / C::NB;
       const uint32_t offs_s =
           base + C::OFFS_OFF + uint32_t(c & 1) * C::OFFS_BYTES + uint32_t((s - c * C::NB) * C::MT) * 4u;
-      if (have) lookup_block<C>(acc, tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), offs_s, cw, grp, prm.one);
+      if (have) lookup_block<C>(acc, tbl_lane0 + uint32_t(buf * C::TABLE_BYTES), offs_s, cw, grp, prm.one, prm.err);
       mbar_arrive(tempty + 8 * buf);
     }
     // epilogue: canonical codes (F_3 and GF(4) codes are already canonical)
 #pragma unroll
     for (int i = 0; i < C::RS; ++i) {
       const int r = i * C::ROWS_PER_SLOT + cw * C::GPW + grp;
-      if (r < rows_here) {
+      if (r < rows_here && debug_ok(row0 + r < prm.m && w0 + C::CTW <= prm.pc, prm.err)) {
         const int64_t row = row0 + r;
 #pragma unroll
         for (int p = 0; p < C::P; ++p) {
@@ -541,6 +555,7 @@ int launch(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B
   prm.one = 1u;
   prm.err = err;
   prm.wait_ns = wait_limit_ns();
+  prm.stall = stall_block();
   CUtensorMap map, amap;
   memset(&map, 0, sizeof(map));
   memset(&amap, 0, sizeof(amap));

@@ -437,6 +437,7 @@ __device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&wor
 template <int Q, int P, int NW = BN / 64>
 __device__ __forceinline__ void store_words(const GemmParams &prm, int64_t row, int64_t w0,
                                             const uint64_t (&words)[P][NW]) {
+  if (!debug_ok(row < prm.m && w0 + NW <= prm.pc, prm.err)) return;
   if constexpr (Q == 4) {
     if (prm.plane < 0) {
 #pragma unroll
@@ -900,12 +901,13 @@ struct BatchOut {  // what an epilogue thread needs of its tile's product
 
 template <int Q, int P>
 __device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, int64_t row, int64_t w0, int quarter,
-                                              uint64_t (&words)[P][1]) {
+                                              uint64_t (&words)[P][1], unsigned *err) {
   // this thread's word w0 + quarter of a 256-column tile
   const int64_t wa = w0 + quarter;
   const int64_t keep = bp.n - wa * 64;
   const uint64_t mask = keep >= 64 ? ~0ull : (keep <= 0 ? 0ull : ((1ull << keep) - 1));
   const bool last = (w0 + BN / 64) * 64 >= bp.nr;
+  if (!debug_ok(row < bp.m && wa < bp.pc, err)) return;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     uint64_t *dst = C + (int64_t(p) * bp.m + row) * bp.pc;
@@ -1043,7 +1045,7 @@ __global__ void __launch_bounds__(THREADS_B, 1)
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_cta(accempty + 8 * b);
-      if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, bt.w0, quarter, words);
+      if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, bt.w0, quarter, words, prm.err);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -1,10 +1,16 @@
 // Measured autotuning of fq_matmul: time every compiled Four-Russians kernel of
 // the field and the tensor-core path on the caller's operands, keep the
 // fastest per (q, m, l, n), and let FQ_PATH_AUTO calls of that shape use it.
+#include <array>
+#include <cctype>
+#include <cstdio>
+#include <cstdlib>
 #include <exception>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
+#include <vector>
 
 #include "fq_common.cuh"
 #include "fq_internal.h"
@@ -69,9 +75,150 @@ double m4rm_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
   return best + 20000.0;
 }
 
+// ---- the cache as JSON: {"format": "fq-autotune-1", "entries": [[q, m, l, n, path, kernel], ...]}
+
+constexpr const char *kTuneFormat = "fq-autotune-1";
+
+// A small reader for exactly that document (whitespace anywhere, keys in any
+// order, other keys refused): fills `out` or returns false.
+struct TuneReader {
+  const std::string &t;
+  size_t i = 0;
+  explicit TuneReader(const std::string &text) : t(text) {}
+  void ws() {
+    while (i < t.size() && isspace(static_cast<unsigned char>(t[i]))) ++i;
+  }
+  bool lit(char c) {
+    ws();
+    if (i < t.size() && t[i] == c) {
+      ++i;
+      return true;
+    }
+    return false;
+  }
+  bool str(std::string *out) {
+    if (!lit('"')) return false;
+    out->clear();
+    while (i < t.size() && t[i] != '"') {
+      if (t[i] == '\\' || static_cast<unsigned char>(t[i]) < 0x20) return false;  // no escapes needed
+      out->push_back(t[i++]);
+    }
+    if (i >= t.size()) return false;
+    ++i;
+    return true;
+  }
+  bool integer(int64_t *out) {
+    ws();
+    const size_t b = i;
+    if (i < t.size() && t[i] == '-') ++i;
+    while (i < t.size() && isdigit(static_cast<unsigned char>(t[i]))) ++i;
+    if (i == b || (i == b + 1 && t[b] == '-') || i - b > 19) return false;
+    *out = strtoll(t.c_str() + b, nullptr, 10);
+    return true;
+  }
+  bool entries(std::vector<std::array<int64_t, 6>> *out) {
+    if (!lit('[')) return false;
+    if (lit(']')) return true;
+    do {
+      std::array<int64_t, 6> e{};
+      if (!lit('[')) return false;
+      for (int k = 0; k < 6; ++k)
+        if ((k > 0 && !lit(',')) || !integer(&e[size_t(k)])) return false;
+      if (!lit(']')) return false;
+      out->push_back(e);
+    } while (lit(','));
+    return lit(']');
+  }
+  bool document(std::vector<std::array<int64_t, 6>> *out) {
+    bool have_format = false, have_entries = false;
+    if (!lit('{')) return false;
+    do {
+      std::string key;
+      if (!str(&key) || !lit(':')) return false;
+      if (key == "format" && !have_format) {
+        std::string v;
+        if (!str(&v) || v != kTuneFormat) return false;
+        have_format = true;
+      } else if (key == "entries" && !have_entries) {
+        if (!entries(out)) return false;
+        have_entries = true;
+      } else {
+        return false;
+      }
+    } while (lit(','));
+    if (!lit('}')) return false;
+    ws();
+    return have_format && have_entries && i == t.size();
+  }
+};
+
+// A remembered choice the library can honour: a field with kernels, sizes >= 0,
+// the M4RM path with a compiled kernel (or the planner) or the tensor-core path.
+bool valid_entry(const std::array<int64_t, 6> &e) {
+  const int64_t q = e[0], path = e[4], kernel = e[5];
+  if (!(q == 2 || q == 3 || q == 4 || q == 5 || q == 7) || e[1] < 0 || e[2] < 0 || e[3] < 0) return false;
+  if (path == FQ_PATH_MMA) return kernel == 0;
+  if (path != FQ_PATH_M4RM) return false;
+  int nv = 0;
+  m4rm_variants(int(q), &nv);
+  return kernel >= 0 && kernel <= nv;
+}
+
 }  // namespace fqk
 
 extern "C" {
+
+int fq_autotune_save(const char *path) {
+  if (!path) return FQ_EINVAL;
+  try {
+    std::string text = std::string("{\"format\": \"") + fqk::kTuneFormat + "\", \"entries\": [";
+    {
+      std::lock_guard<std::mutex> lock(fqk::g_tune_mu);
+      bool first = true;
+      for (const auto &kv : fqk::g_tuned) {
+        char line[160];
+        snprintf(line, sizeof(line), "%s\n  [%d, %lld, %lld, %lld, %d, %d]", first ? "" : ",", std::get<0>(kv.first),
+                 static_cast<long long>(std::get<1>(kv.first)), static_cast<long long>(std::get<2>(kv.first)),
+                 static_cast<long long>(std::get<3>(kv.first)), kv.second.path, kv.second.kernel);
+        text += line;
+        first = false;
+      }
+    }
+    text += "\n]}\n";
+    FILE *f = fopen(path, "wb");
+    if (!f) return FQ_EINVAL;
+    const bool ok = fwrite(text.data(), 1, text.size(), f) == text.size();
+    return (fclose(f) == 0 && ok) ? FQ_OK : FQ_EINVAL;
+  } catch (const std::exception &) {
+    return FQ_ENOMEM;
+  }
+}
+
+int fq_autotune_load(const char *path) {
+  if (!path) return FQ_EINVAL;
+  try {
+    FILE *f = fopen(path, "rb");
+    if (!f) return FQ_EINVAL;
+    std::string text;
+    char buf[4096];
+    size_t got = 0;
+    while ((got = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+    const bool read_ok = ferror(f) == 0;
+    fclose(f);
+    if (!read_ok) return FQ_EINVAL;
+    std::vector<std::array<int64_t, 6>> entries;
+    fqk::TuneReader reader(text);
+    if (!reader.document(&entries)) return FQ_EINVAL;
+    for (const auto &e : entries)
+      if (!fqk::valid_entry(e)) return FQ_EINVAL;
+    std::lock_guard<std::mutex> lock(fqk::g_tune_mu);
+    for (const auto &e : entries)
+      fqk::g_tuned[std::make_tuple(int(e[0]), e[1], e[2], e[3])] = fqk::Choice{int(e[4]), int(e[5])};
+    return FQ_OK;
+  } catch (const std::exception &) {
+    return FQ_ENOMEM;
+  }
+}
 
 int fq_autotune(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
                 void *stream, fq_tune_result *out) {

@@ -17,7 +17,7 @@ import torch
 
 from . import build as _build
 
-OK, EINVAL, EVALUE, ECUDA, ETIMEOUT, ENOTSUP, ENOMEM = range(7)
+OK, EINVAL, EVALUE, ECUDA, ETIMEOUT, ENOTSUP, ENOMEM, EBOUNDS = range(8)
 PATH_AUTO, PATH_M4RM, PATH_MMA, PATH_KARATSUBA = 0, 1, 2, 3
 STAGE_CONVERT, STAGE_TC, STAGE_M4RM, STAGE_ALL = 1, 2, 4, 7
 
@@ -39,58 +39,77 @@ class Options(ctypes.Structure):
                 ("reserved", ctypes.c_int * 3)]
 
 
+_lib_debug = None
+
+
 def load():
     """Build (if stale) and load the CUDA library; returns the ctypes handle."""
     global _lib
     if _lib is None:
-        path = _build.build()
-        lib = ctypes.CDLL(path)
-        i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
-        sig = {
-            "fq_planes": (i32, [i32]),
-            "fq_pitch_words": (i64, [i64]),
-            "fq_planes_words": (i64, [i32, i64, i64]),
-            "fq_pack": (i32, [i32, i64, i64, vp, i64, vp, vp]),
-            "fq_unpack": (i32, [i32, i64, i64, vp, vp, i64, vp]),
-            "fq_add": (i32, [i32, i64, i64, vp, vp, vp, i32, vp]),
-            "fq_matmul": (i32, [i32, i64, i64, i64, vp, vp, vp, vp]),
-            "fq_matmul_ex": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, ctypes.POINTER(Options)]),
-            "fq_status": (i32, [vp]),
-            "fq_release_scratch": (i32, []),
-            "fq_kernel_count": (i32, [i32]),
-            "fq_kernel_info": (i32, [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                     ctypes.POINTER(i32)]),
-            "fq_batched_plan_create": (i32, [i32, i32, vp, vp, vp, ctypes.POINTER(vp)]),
-            "fq_batched_plan_create_ex": (i32, [i32, i32, vp, vp, vp, i32, ctypes.POINTER(vp)]),
-            "fq_batched_workspace_bytes": (i64, [vp]),
-            "fq_batched_items": (i64, [vp]),
-            "fq_batched_tc_products": (i64, [vp]),
-            "fq_batched_tc_tiles": (i64, [vp]),
-            "fq_batched_plan_upload": (i32, [vp, vp, vp]),
-            "fq_matmul_batched": (i32, [vp, vp, vp, vp, vp, vp]),
-            "fq_matmul_batched_static": (i32, [vp, vp, vp, vp, vp]),
-            "fq_matmul_batched_stages": (i32, [vp, vp, vp, vp, vp, vp, i32]),
-            "fq_batched_product_path": (i32, [vp, i32]),
-            "fq_debug_wait_limit": (i32, [i64]),
-            "fq_batched_plan_destroy": (i32, [vp]),
-            "fq_autotune": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, vp]),
-            "fq_autotune_lookup": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
-            "fq_autotune_clear": (i32, []),
-            "fq_auto_choice": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
-            "fq_strassen_levels": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
-            "fq_planned_kernel": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
-            "fq_tc_workspace_bytes": (i64, [i32, i64, i64, i64]),
-            "fq_tc_prepare": (i32, [i32, i64, i64, i64, vp, vp, vp, vp]),
-            "fq_tc_multiply": (i32, [i32, i64, i64, i64, vp, vp, vp]),
-            "fq_error_string": (ctypes.c_char_p, [i32]),
-            "fq_last_cuda_error": (ctypes.c_char_p, []),
-        }
-        for name, (res, args) in sig.items():
-            fn = getattr(lib, name)
-            fn.restype = res
-            fn.argtypes = args
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(_build.build()))
     return _lib
+
+
+def load_debug():
+    """Build (if stale) and load the FQ_DEBUG library (same ABI; its kernels
+    bounds-check table indices and stores and record FQ_EBOUNDS); returns its
+    own ctypes handle, independent of load()'s."""
+    global _lib_debug
+    if _lib_debug is None:
+        _lib_debug = _bind(ctypes.CDLL(_build.build(debug=True)))
+    return _lib_debug
+
+
+def _bind(lib):
+    """Argument and result types of every entry point of include/fq.h."""
+    i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+    sig = {
+        "fq_planes": (i32, [i32]),
+        "fq_pitch_words": (i64, [i64]),
+        "fq_planes_words": (i64, [i32, i64, i64]),
+        "fq_pack": (i32, [i32, i64, i64, vp, i64, vp, vp]),
+        "fq_unpack": (i32, [i32, i64, i64, vp, vp, i64, vp]),
+        "fq_add": (i32, [i32, i64, i64, vp, vp, vp, i32, vp]),
+        "fq_matmul": (i32, [i32, i64, i64, i64, vp, vp, vp, vp]),
+        "fq_matmul_ex": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, ctypes.POINTER(Options)]),
+        "fq_status": (i32, [vp]),
+        "fq_release_scratch": (i32, []),
+        "fq_kernel_count": (i32, [i32]),
+        "fq_kernel_info": (i32, [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                 ctypes.POINTER(i32)]),
+        "fq_batched_plan_create": (i32, [i32, i32, vp, vp, vp, ctypes.POINTER(vp)]),
+        "fq_batched_plan_create_ex": (i32, [i32, i32, vp, vp, vp, i32, ctypes.POINTER(vp)]),
+        "fq_batched_workspace_bytes": (i64, [vp]),
+        "fq_batched_items": (i64, [vp]),
+        "fq_batched_tc_products": (i64, [vp]),
+        "fq_batched_tc_tiles": (i64, [vp]),
+        "fq_batched_plan_upload": (i32, [vp, vp, vp]),
+        "fq_matmul_batched": (i32, [vp, vp, vp, vp, vp, vp]),
+        "fq_matmul_batched_static": (i32, [vp, vp, vp, vp, vp]),
+        "fq_matmul_batched_stages": (i32, [vp, vp, vp, vp, vp, vp, i32]),
+        "fq_batched_product_path": (i32, [vp, i32]),
+        "fq_debug_wait_limit": (i32, [i64]),
+        "fq_debug_stall_block": (i32, [i64]),
+        "fq_batched_plan_destroy": (i32, [vp]),
+        "fq_autotune": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, vp]),
+        "fq_autotune_lookup": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "fq_autotune_clear": (i32, []),
+        "fq_autotune_save": (i32, [ctypes.c_char_p]),
+        "fq_autotune_load": (i32, [ctypes.c_char_p]),
+        "fq_auto_choice": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "fq_strassen_levels": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
+        "fq_planned_kernel": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
+        "fq_tc_workspace_bytes": (i64, [i32, i64, i64, i64]),
+        "fq_tc_prepare": (i32, [i32, i64, i64, i64, vp, vp, vp, vp]),
+        "fq_tc_multiply": (i32, [i32, i64, i64, i64, vp, vp, vp]),
+        "fq_error_string": (ctypes.c_char_p, [i32]),
+        "fq_last_cuda_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
 
 
 def _check(rc: int, what: str):

@@ -76,6 +76,7 @@ def test_argument_errors_return_before_any_launch(lib):
 def test_error_strings(lib):
     assert lib.fq_error_string(0) == b"ok"
     assert lib.fq_error_string(4) == b"bounded device wait timed out"
+    assert lib.fq_error_string(7) == b"bounds check failed (debug build)"
     assert lib.fq_error_string(99) == b"unknown status"
 
 
@@ -297,9 +298,68 @@ def test_autotune_cache_host_side(lib):
 
 
 def test_wait_limit_hook_is_host_only(lib):
-    """fq_debug_wait_limit only stores the bound later launches carry: it needs
-    no device, accepts any value and 0 restores the default."""
+    """fq_debug_wait_limit and fq_debug_stall_block only store what later
+    launches carry: they need no device, accept any value, and 0 (-1) turn
+    them off."""
     from paper_0901_1413_gb300 import fq
     assert lib.fq_debug_wait_limit(1) == fq.OK
     assert lib.fq_debug_wait_limit(-5) == fq.OK
     assert lib.fq_debug_wait_limit(0) == fq.OK
+    assert lib.fq_debug_stall_block(3) == fq.OK
+    assert lib.fq_debug_stall_block(-1) == fq.OK
+
+
+def test_autotune_cache_save_and_load(lib, tmp_path):
+    """The autotune cache round-trips through its JSON file (host only); a
+    malformed file or an entry the library cannot honour is refused whole."""
+    import json
+    from paper_0901_1413_gb300 import fq
+    nk3 = lib.fq_kernel_count(3)
+    good = {"format": "fq-autotune-1",
+            "entries": [[3, 100, 200, 300, fq.PATH_M4RM, nk3], [5, 8192, 8192, 8192, fq.PATH_MMA, 0],
+                        [2, 1, 1, 1, fq.PATH_M4RM, 0]]}
+    src = tmp_path / "tune.json"
+    src.write_text(json.dumps(good, indent=3))
+    assert lib.fq_autotune_clear() == fq.OK
+    assert lib.fq_autotune_load(str(src).encode()) == fq.OK
+    path, kernel = ctypes.c_int(), ctypes.c_int()
+    for q, m, l, n, p, k in good["entries"]:
+        assert lib.fq_autotune_lookup(q, m, l, n, ctypes.byref(path), ctypes.byref(kernel)) == fq.OK
+        assert (path.value, kernel.value) == (p, k)
+    dst = tmp_path / "saved.json"
+    assert lib.fq_autotune_save(str(dst).encode()) == fq.OK
+    saved = json.loads(dst.read_text())
+    assert saved["format"] == "fq-autotune-1"
+    assert sorted(map(tuple, saved["entries"])) == sorted(map(tuple, good["entries"]))
+    # loading merges: a later file replaces the choice of the same shape
+    src.write_text(json.dumps({"entries": [[3, 100, 200, 300, fq.PATH_MMA, 0]], "format": "fq-autotune-1"}))
+    assert lib.fq_autotune_load(str(src).encode()) == fq.OK
+    assert lib.fq_autotune_lookup(3, 100, 200, 300, ctypes.byref(path), ctypes.byref(kernel)) == fq.OK
+    assert (path.value, kernel.value) == (fq.PATH_MMA, 0)
+    before = dst.read_text()
+    bad_docs = [
+        "", "{}", "[]", '{"format": "fq-autotune-1"}', '{"entries": []}',
+        '{"format": "fq-autotune-2", "entries": []}',
+        '{"format": "fq-autotune-1", "entries": [[3, 1, 1, 1, 1]]}',            # five numbers
+        '{"format": "fq-autotune-1", "entries": [[3, 1, 1, 1, 1, 0]], "x": 1}',  # unknown key
+        '{"format": "fq-autotune-1", "entries": [[3, 1, 1, 1, 1, 0]]} trailing',
+        '{"format": "fq-autotune-1", "entries": [[6, 1, 1, 1, 1, 0]]}',          # no F_6
+        '{"format": "fq-autotune-1", "entries": [[9, 1, 1, 1, 1, 0]]}',          # F_9: no kernels of its own
+        '{"format": "fq-autotune-1", "entries": [[3, -1, 1, 1, 1, 0]]}',         # negative size
+        '{"format": "fq-autotune-1", "entries": [[3, 1, 1, 1, 3, 0]]}',          # Karatsuba is no tuned path
+        '{"format": "fq-autotune-1", "entries": [[3, 1, 1, 1, 2, 1]]}',          # tensor path with a kernel
+        '{"format": "fq-autotune-1", "entries": [[3, 1, 1, 1, 1, %d]]}' % (nk3 + 1),  # no such kernel
+        '{"format": "fq-autotune-1", "entries": [[3, 7, 7, 7, 1, 0], [3, 1, 1, 1, 1, -1]]}',  # one bad entry
+    ]
+    for doc in bad_docs:
+        src.write_text(doc)
+        assert lib.fq_autotune_load(str(src).encode()) == fq.EINVAL, doc
+    assert lib.fq_autotune_lookup(3, 7, 7, 7, None, None) == fq.ENOTSUP       # nothing of a refused file merged
+    assert lib.fq_autotune_load(str(tmp_path / "missing.json").encode()) == fq.EINVAL
+    assert lib.fq_autotune_load(None) == fq.EINVAL
+    assert lib.fq_autotune_save(None) == fq.EINVAL
+    assert lib.fq_autotune_save(str(tmp_path / "no" / "dir.json").encode()) == fq.EINVAL
+    assert lib.fq_autotune_clear() == fq.OK
+    assert lib.fq_autotune_save(str(dst).encode()) == fq.OK
+    assert json.loads(dst.read_text())["entries"] == []
+    assert before  # the earlier save was a full document
