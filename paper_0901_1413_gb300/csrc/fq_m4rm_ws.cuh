@@ -23,10 +23,9 @@
 // is consumed.  Hand-over is by mbarriers (tfull: 128
 // producer arrivals; tempty: 384 consumer arrivals).  Every wait is bounded
 // (Params::wait_ns); on a timeout the CTA records FQ_ETIMEOUT and runs out its
-// loops without waiting again: consumers skip the lookups of tables they did
-// not receive (so every shared-memory address stays valid), the TMA thread
-// issues no further copies and, before the CTA exits, waits for the copies it
-// had issued.
+// loops without waiting again: consumers make no further lookups (so every
+// shared-memory address stays valid), the TMA thread issues no further copies
+// and, before the CTA exits, waits for the copies it had issued.
 #pragma once
 
 #include <cstring>
@@ -508,9 +507,14 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
       for (int j = 0; j < 4; ++j) acc[i][j] = 0u;
     for (int64_t s = 0; s < prm.nblocks; ++s) {
       const int buf = int(s % C::NBUF);
-      // after a wait that gave up, the offsets may never have been written:
-      // no lookup (the result is garbage then, but every address stays valid)
-      const bool have = wait_or_abort(tfull + 8 * buf, uint32_t(s / C::NBUF) & 1, abort_flag, prm.err, prm.wait_ns);
+      // No lookup once the CTA has given up.  A consumer that skipped a wait
+      // is ahead of the producers, and a later parity test can then pass on
+      // an older phase (waiting for parity 1 passes on a barrier still in
+      // phase 0): its offsets may never have been written, and unwritten
+      // offsets are not table addresses.  No consumer skips a wait before the
+      // flag is set, so while it is clear every completed wait is in order.
+      const bool have = wait_or_abort(tfull + 8 * buf, uint32_t(s / C::NBUF) & 1, abort_flag, prm.err, prm.wait_ns) &&
+                        !abort_flag;
       const int64_t c = s / C::NB;
       const uint32_t offs_s =
           base + C::OFFS_OFF + uint32_t(c & 1) * C::OFFS_BYTES + uint32_t((s - c * C::NB) * C::MT) * 4u;
