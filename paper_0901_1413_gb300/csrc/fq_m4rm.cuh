@@ -419,7 +419,10 @@ __global__ void __launch_bounds__(Cfg::NT, 1)
       const int64_t s = c0 + b;
       const int buf = int(s & 1);
       if (builder && !mbar_wait_bounded(bar_s + 8 * buf, uint32_t((s >> 1) & 1), prm.wait_ns)) s_abort = 1;
-      if (tid == 0 && s == prm.stall && !mbar_wait_bounded(bar_s + 16, 0, prm.wait_ns)) s_abort = 1;  // injected
+      if (warp == 0 && s == prm.stall) {  // injected failure: the whole warp waits in lockstep
+        if (!mbar_wait_bounded(bar_s + 16, 0, prm.wait_ns)) s_abort = 1;
+        __syncwarp();
+      }
       __syncthreads();  // table free; this block's B rows visible to the builders
       if (s_abort) {
         // Block s's copy is the only one in flight (block s + 1's is issued

@@ -444,9 +444,16 @@ __global__ void __launch_bounds__(C::NT, 1) m4rm_ws_kernel(const __grid_constant
     for (int64_t s = 0; s < prm.nblocks; ++s) {
       const int buf = int(s % C::NBUF);
       const uint32_t use = uint32_t(s / C::NBUF);
-      if (s == prm.stall && ptid == 0 && !mbar_wait_bounded(stall, 0, prm.wait_ns)) {  // injected failure
-        abort_flag = 1;
-        record_error(prm.err, FQ_ETIMEOUT);
+      if (s == prm.stall && warp == 0) {
+        // Injected failure: a wait that nothing completes.  The whole warp
+        // waits in lockstep (every lane polls the same barrier and clock), so
+        // it does not diverge, and it reconverges before the producers' named
+        // barrier, which all 32 lanes of a warp must reach together.
+        if (!mbar_wait_bounded(stall, 0, prm.wait_ns)) {
+          abort_flag = 1;
+          record_error(prm.err, FQ_ETIMEOUT);
+        }
+        __syncwarp();
       }
       if (s % C::NB == C::NBUF - 1) {
         // block NBUF - 1 of chunk c: write the offsets of chunk c + 1 into the
