@@ -28,8 +28,8 @@ against the classical product's work).
   uniform over multiples of 64 in [64, 1024]) in one graph-captured launch
   sequence: products/s and 2mln/s for the FQ_PATH_AUTO plan and for the
   Four-Russians-only plan; the AUTO plan's stages timed one by one, with the
-  tcgen05 tile kernel against the fp8 peak and the e4m3 conversions against
-  HBM.
+  persistent tcgen05 kernel (conversion and tiles in one launch) against the
+  fp8 peak and against HBM.
 * ``more_workloads``: F_5, F_7 and GF(4) at n = 8192, then F_5 32768^3 and F_3
   65536 x 4096 x 4096, each product on both paths (the tcgen05 form as
   conversion + product kernel, the Four-Russians path), each with its
@@ -128,15 +128,15 @@ def algorithmic_lop3(m, l, n, k, q=3):
     return words * blocks * (m * LOOKUP_LOP3[q] + (2 ** k - 1) * TABLE_LOP3[q])
 
 
-def batched_conversion_bytes(q, shapes):
-    """Algorithmic DRAM bytes of the batched conversions for the products on
-    the tcgen05 path: A's planes over la = l rounded up to 128 columns and B's
-    over nr = n rounded up to 256 columns read, e4m3 A (m x la) and B^T (n x
-    la) written."""
+def batched_compulsory_bytes(q, shapes):
+    """Compulsory DRAM bytes of the batched tcgen05 kernel for its products:
+    A's planes over la = l rounded up to 128 columns and B's over nr = n
+    rounded up to 256 columns read once (the e4m3 operands never leave L2),
+    C's planes written (its row pitch of 64-bit words)."""
     total = 0
     for (m, l, n) in shapes:
         la, nr = cdiv(l, 128) * 128, cdiv(n, 256) * 256
-        total += PLANES[q] * (m * la + l * nr) // 8 + (m + n) * la
+        total += PLANES[q] * (m * la + l * nr) // 8 + PLANES[q] * m * pitch_words(n) * 8
     return total
 
 
@@ -229,42 +229,40 @@ def batched_leg(torch, fq, inputs, dist, dev, reps=10):
 
 def batched_stage_rooflines(torch, fq, plan, q, shapes, pa, pb, pc, stream, reps):
     """The AUTO plan's launch stages timed one at a time (fq_matmul_batched_stages,
-    CUDA events on the launching stream, median of `reps`): the two e4m3
-    conversions against HBM, the persistent tcgen05 tile kernel against the fp8
-    tensor peak, the Four-Russians kernel (if the plan has items)."""
+    CUDA events on the launching stream, median of `reps`): the persistent
+    tcgen05 kernel (operand conversion and tiles in one launch) against the
+    fp8 tensor peak and against HBM for its compulsory bytes, then the
+    Four-Russians kernel (if the plan has items)."""
     peaks = measured_peaks()
     tc = [sh for sh, path in zip(shapes, plan.product_paths()) if path == fq.PATH_MMA]
-    ms = {"convert": [], "tile": [], "m4rm": []}
+    ms = {"tcgen05": [], "m4rm": []}
     for r in range(reps + 2):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         with torch.cuda.stream(stream):
             ev[0].record(stream)
-            plan.run_stages(pa, pb, pc, fq.STAGE_CONVERT, stream=stream)
-            ev[1].record(stream)
             plan.run_stages(pa, pb, pc, fq.STAGE_TC, stream=stream)
-            ev[2].record(stream)
+            ev[1].record(stream)
             plan.run_stages(pa, pb, pc, fq.STAGE_M4RM, stream=stream)
-            ev[3].record(stream)
+            ev[2].record(stream)
         torch.cuda.synchronize()
         if r >= 2:
-            ms["convert"].append(ev[0].elapsed_time(ev[1]))
-            ms["tile"].append(ev[1].elapsed_time(ev[2]))
-            ms["m4rm"].append(ev[2].elapsed_time(ev[3]))
+            ms["tcgen05"].append(ev[0].elapsed_time(ev[1]))
+            ms["m4rm"].append(ev[1].elapsed_time(ev[2]))
     if fq.status() != fq.OK:
         raise SystemExit("device error in the batched stages")
-    conv_ms, tile_ms = statistics.median(ms["convert"]), statistics.median(ms["tile"])
+    tc_ms = statistics.median(ms["tcgen05"])
     flops = sum(2.0 * m * l * n for (m, l, n) in tc)
-    conv_bytes = batched_conversion_bytes(q, tc)
-    tile_tflops = flops / (tile_ms * 1e-3) / 1e12
-    conv_gbs = conv_bytes / (conv_ms * 1e-3) / 1e9
+    dram = batched_compulsory_bytes(q, tc)
+    tflops = flops / (tc_ms * 1e-3) / 1e12
+    gbs = dram / (tc_ms * 1e-3) / 1e9
     return {
         "stages_ms": {k: statistics.median(v) for k, v in ms.items()},
-        "tile_roofline": {"bound": "tensor", "kernel": "tc_batched_kernel", "achieved": tile_tflops,
-                          "peak": peaks["fp8"], "unit": "TFLOP/s", "frac": tile_tflops / peaks["fp8"],
+        "tile_roofline": {"bound": "tensor", "kernel": "tc_batched_kernel", "achieved": tflops,
+                          "peak": peaks["fp8"], "unit": "TFLOP/s", "frac": tflops / peaks["fp8"],
                           "peak_note": peaks["note"], "flops": flops},
-        "conversion_roofline": {"bound": "hbm", "kernels": "batched_rows_kernel + batched_transpose_kernel",
-                                "achieved": conv_gbs, "peak": peaks["hbm"], "unit": "GB/s",
-                                "frac": conv_gbs / peaks["hbm"], "bytes": conv_bytes, "peak_note": peaks["hbm_note"]},
+        "hbm_roofline": {"bound": "hbm", "kernel": "tc_batched_kernel", "achieved": gbs, "peak": peaks["hbm"],
+                         "unit": "GB/s", "frac": gbs / peaks["hbm"], "bytes": dram, "peak_note": peaks["hbm_note"],
+                         "note": "compulsory bytes: the planes of A and B read once, C's planes written"},
         "stages_note": "each stage called on its own (fq_matmul_batched_stages), median of %d; the graph "
                        "replay above runs them back to back" % reps,
     }

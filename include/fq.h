@@ -188,9 +188,14 @@ int fq_tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *workspace
  *   - Four Russians: work items (rows x a column tile of one product) with a
  *     block size k chosen per item by the planner's cost model, longest first;
  *   - tcgen05 (F_3, F_5, F_7 with 0 < l within the exact range and
- *     n <= 2^30): the
- *     product's A and B^T in e4m3 in two arenas of the workspace, and its
- *     128 x 256 tiles in one list, deepest first.
+ *     n <= 2^30): whole products are given to 152 persistent CTAs (longest
+ *     first, each to the least-loaded CTA by the model; a CTA then takes its
+ *     products smallest first).  A CTA's converter warps write each
+ *     product's A and B^T as e4m3 bytes into one of the CTA's two scratch
+ *     buffers in the workspace while its tensor-core warps compute the
+ *     previous product's 128 x 256 tiles from the other, so the operands
+ *     stay in L2.  A product runs on one SM: a batch of a few very large
+ *     products is better served by fq_matmul.
  * The plan is host memory owned by the library. */
 typedef struct fq_batch_plan fq_batch_plan;
 
@@ -208,10 +213,11 @@ int fq_batched_plan_create_ex(int q, int count, const int64_t *m, const int64_t 
                               fq_batch_plan **plan);
 
 /* Bytes of device workspace the plan needs (64-byte aligned, caller-owned:
- * the work lists, and for tcgen05 products the e4m3 arenas, (m rounded up to
- * 128 + n rounded up to 256) x (l rounded up to 128) bytes per product), the
+ * the work lists, and for tcgen05 products each CTA's two scratch buffers,
+ * buffer b holding (m rounded up to 128 + n rounded up to 256) x (l rounded up
+ * to 128) bytes for the largest of the CTA's products b, b + 2, ...), the
  * number of Four-Russians work items, of products on the tcgen05 path and of
- * their tiles; -1 for a NULL plan. */
+ * their 128 x 256 tiles; -1 for a NULL plan. */
 int64_t fq_batched_workspace_bytes(const fq_batch_plan *plan);
 int64_t fq_batched_items(const fq_batch_plan *plan);
 int64_t fq_batched_tc_products(const fq_batch_plan *plan);
@@ -225,8 +231,8 @@ int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *str
  * contraction, per product).  A, B, C: DEVICE arrays of `count` device
  * pointers to planes buffers (A_p m x l, B_p l x n, C_p m x n; C_p must not
  * alias A_p or B_p); workspace: the uploaded workspace.  Enqueues, on
- * `stream`, for tcgen05 products two conversion kernels and one persistent
- * product kernel, then for Four-Russians items one memset and one persistent
+ * `stream`, for tcgen05 products one persistent kernel (conversion and
+ * products), then for Four-Russians items one memset and one persistent
  * kernel; allocates nothing and never synchronises, so it may be captured in
  * a CUDA graph.  Launches sharing a workspace must not overlap on the GPU. */
 int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
@@ -234,17 +240,15 @@ int fq_matmul_batched(const fq_batch_plan *plan, const uint64_t *const *A, const
 
 /* fq_matmul_batched in its launch stages, so that each can be timed on its
  * own: `stages` is a bit mask of
- *   FQ_BATCH_STAGE_CONVERT  the tcgen05 products' operands to e4m3 (two kernels),
- *   FQ_BATCH_STAGE_TC       their persistent tile kernel, which reads the
- *                           arenas the last CONVERT stage on this workspace wrote,
- *   FQ_BATCH_STAGE_M4RM     the queue reset and the persistent Four-Russians kernel;
+ *   FQ_BATCH_STAGE_TC    the persistent tcgen05 kernel of the tcgen05 products
+ *                        (operand conversion and tiles, one launch),
+ *   FQ_BATCH_STAGE_M4RM  the queue reset and the persistent Four-Russians kernel;
  * stages run in that order.  fq_matmul_batched is FQ_BATCH_STAGE_ALL.  Same
  * arguments and rules as fq_matmul_batched; FQ_EINVAL for a mask outside
  * 0 .. FQ_BATCH_STAGE_ALL. */
-#define FQ_BATCH_STAGE_CONVERT 1
-#define FQ_BATCH_STAGE_TC 2
-#define FQ_BATCH_STAGE_M4RM 4
-#define FQ_BATCH_STAGE_ALL 7
+#define FQ_BATCH_STAGE_TC 1
+#define FQ_BATCH_STAGE_M4RM 2
+#define FQ_BATCH_STAGE_ALL 3
 int fq_matmul_batched_stages(const fq_batch_plan *plan, const uint64_t *const *A, const uint64_t *const *B,
                              uint64_t *const *C, void *workspace, void *stream, int stages);
 

@@ -261,16 +261,14 @@ struct fq_batch_plan {
   std::vector<fqk::batched::Shape> shapes;
   std::vector<fqk::batched::Item> items;      // Four-Russians items
   std::vector<fqk::BatchProd> tc_prods;       // products on the tcgen05 path
-  std::vector<int64_t> tc_a_prefix, tc_b_prefix;
-  std::vector<int32_t> tc_a_unit, tc_b_unit;  // product of each conversion unit
-  std::vector<int64_t> tc_tile_prefix;         // cumulative modelled cost of the tiles
-  std::vector<fqk::BatchTile> tc_tiles;
-  int64_t a_rows = 0, b_rows = 0;  // arena rows of 128 bytes
-  int64_t off_prods = 0, off_aprefix = 0, off_bprefix = 0, off_aunit = 0, off_bunit = 0, off_tiles = 0,
-          off_tprefix = 0;
-  int64_t off_a_arena = 0, off_b_arena = 0;
-  int64_t table_bytes = 0;      // header .. tile list (uploaded)
-  int64_t workspace_bytes = 0;  // plus the two arenas
+  std::vector<int32_t> tc_cta_begin;          // kTcCtas + 1
+  std::vector<int32_t> tc_cta_list;           // product indices, each CTA's in the order it computes them
+  std::vector<int64_t> tc_cta_rows;           // kTcCtas x 2: first scratch row of each CTA's buffers
+  int64_t tc_tiles = 0;                       // 128 x 256 tiles of the tcgen05 products
+  int64_t scratch_rows = 0;                   // 128-byte rows of all CTAs' buffers
+  int64_t off_prods = 0, off_cta_begin = 0, off_cta_list = 0, off_cta_rows = 0, off_scratch = 0;
+  int64_t table_bytes = 0;      // header .. CTA rows (uploaded)
+  int64_t workspace_bytes = 0;  // plus the scratch buffers
   double model_cost = 0;        // modelled SM-cycles of the whole plan
 };
 
@@ -326,12 +324,8 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
     bp.pa = fq_pitch_words(l[p]);
     bp.pb = fq_pitch_words(n[p]);
     bp.pc = fq_pitch_words(n[p]);
-    bp.a_row0 = plan->a_rows;
-    bp.b_row0 = plan->b_rows;
-    // K-blocked arenas of 128-byte rows: 128-row (A) or 256-row (B^T) blocks,
-    // each holding its la / 128 k-slices one after another
-    plan->a_rows += fqk::cdiv(m[p], 128) * 128 * (bp.la / 128);
-    plan->b_rows += int64_t(bp.nr) * (bp.la / 128);
+    bp.a_row0 = 0;
+    bp.b_row0 = 0;
     plan->tc_prods.push_back(bp);
   };
   for (int p = 0; p < count; ++p) {
@@ -417,77 +411,79 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
       }
     }
   }
-  // The kernels index items, tiles and arena rows with 32-bit numbers (the
-  // queue counter, the tile records' TMA coordinates): larger plans are refused.
+  // The Four-Russians kernel numbers items with a 32-bit queue counter: larger
+  // plans are refused.
   constexpr int64_t kMax32 = (int64_t(1) << 31) - 1;
-  int64_t tiles = 0;
-  for (const fqk::BatchProd &bp : plan->tc_prods) tiles += fqk::cdiv(bp.m, 128) * (bp.nr / 256);
-  if (int64_t(costed.size()) > kMax32 || plan->a_rows > kMax32 || plan->b_rows > kMax32 || tiles > kMax32)
-    return FQ_ENOTSUP;
+  if (int64_t(costed.size()) > kMax32) return FQ_ENOTSUP;
   // longest first
   std::stable_sort(costed.begin(), costed.end(),
                    [](const std::pair<double, Item> &a, const std::pair<double, Item> &b) { return a.first > b.first; });
   for (auto &c : costed) plan->items.push_back(c.second);
-  // tcgen05 work: conversion units (256 16-byte pieces of A; 128 x 256 blocks
-  // of B^T) and
-  // tiles, a product's tiles consecutive (row block by row block); the kernel
-  // gives each CTA a contiguous run of equal modelled cost, so that one SM's
-  // consecutive tiles share data.
+  // tcgen05 work: whole products to the kTcCtas persistent CTAs, longest
+  // first, each to the least-loaded CTA by the modelled cost; a CTA then takes
+  // its products smallest first (the first one's conversion is the only one
+  // no MMA overlaps).  Each CTA owns two scratch buffers, buffer b sized for
+  // the largest of its products b, b + 2, ...
   const int T = int(plan->tc_prods.size());
-  plan->tc_a_prefix.assign(size_t(T) + 1, 0);
-  plan->tc_b_prefix.assign(size_t(T) + 1, 0);
-  for (int i = 0; i < T; ++i) {
-    const fqk::BatchProd &bp = plan->tc_prods[size_t(i)];
-    const int64_t au = fqk::cdiv(int64_t(bp.m) * (bp.la / 16), 256), bu = int64_t(bp.la / 128) * (bp.nr / 256);
-    plan->tc_a_prefix[size_t(i) + 1] = plan->tc_a_prefix[size_t(i)] + au;
-    plan->tc_b_prefix[size_t(i) + 1] = plan->tc_b_prefix[size_t(i)] + bu;
-    plan->tc_a_unit.insert(plan->tc_a_unit.end(), size_t(au), int32_t(i));
-    plan->tc_b_unit.insert(plan->tc_b_unit.end(), size_t(bu), int32_t(i));
-    for (int32_t mb = 0; mb < int32_t(fqk::cdiv(bp.m, 128)); ++mb)
-      for (int32_t nb = 0; nb < bp.nr / 256; ++nb) {
-        fqk::BatchTile bt{};
-        bt.prod = i;
-        bt.ksteps = bp.la / 128;
-        bt.ya = int32_t(bp.a_row0 + int64_t(mb) * (bp.la / 128) * 128);  // k-slice 0 of the row block
-        bt.yb = int32_t(bp.b_row0 + int64_t(nb) * (bp.la / 128) * 256);
-        bt.row0 = mb * 128;
-        bt.w0 = nb * 4;
-        plan->tc_tiles.push_back(bt);
+  constexpr int NC = fqk::kTcCtas;
+  plan->tc_cta_begin.assign(NC + 1, 0);
+  plan->tc_cta_rows.assign(2 * NC, 0);
+  if (T > 0) {
+    std::vector<double> cost(size_t(T), 0.0);
+    std::vector<int> order(size_t(T), 0);
+    for (int i = 0; i < T; ++i) {
+      const fqk::BatchProd &bp = plan->tc_prods[size_t(i)];
+      cost[size_t(i)] = tc_product_cycles(bp.m, bp.l, bp.n);
+      order[size_t(i)] = i;
+      plan->tc_tiles += fqk::cdiv(bp.m, 128) * (bp.nr / 256);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[size_t(x)] > cost[size_t(y)]; });
+    std::vector<double> load(NC, 0.0);
+    std::vector<std::vector<int32_t>> per(NC);
+    for (int i : order) {
+      int c = 0;
+      for (int k = 1; k < NC; ++k)
+        if (load[size_t(k)] < load[size_t(c)]) c = k;
+      per[size_t(c)].push_back(int32_t(i));
+      load[size_t(c)] += cost[size_t(i)];
+    }
+    int64_t rows = 0;
+    for (int c = 0; c < NC; ++c) {
+      std::vector<int32_t> &list = per[size_t(c)];
+      std::reverse(list.begin(), list.end());
+      int64_t size[2] = {0, 0};
+      for (size_t j = 0; j < list.size(); ++j) {
+        const fqk::BatchProd &bp = plan->tc_prods[size_t(list[j])];
+        const int64_t need = fqk::batch_a_rows(bp.m, bp.la) + fqk::batch_bt_rows(bp.nr, bp.la);
+        size[j & 1] = need > size[j & 1] ? need : size[j & 1];
       }
+      plan->tc_cta_begin[size_t(c) + 1] = plan->tc_cta_begin[size_t(c)] + int32_t(list.size());
+      plan->tc_cta_list.insert(plan->tc_cta_list.end(), list.begin(), list.end());
+      plan->tc_cta_rows[2 * size_t(c)] = rows;
+      plan->tc_cta_rows[2 * size_t(c) + 1] = rows + size[0];
+      rows += size[0] + size[1];
+    }
+    plan->scratch_rows = rows;
   }
-  // modelled tile cost in half k-steps: the MMAs (ksteps) overlap the previous
-  // tile's epilogue (about four k-steps' time on GB300), plus a fixed
-  // hand-over of 1.5
-  plan->tc_tile_prefix.assign(plan->tc_tiles.size() + 1, 0);
-  for (size_t t = 0; t < plan->tc_tiles.size(); ++t) {
-    const int ks = plan->tc_tiles[t].ksteps;
-    plan->tc_tile_prefix[t + 1] = plan->tc_tile_prefix[t] + 2 * (ks > 4 ? ks : 4) + 3;
-  }
-  // workspace: [header][shapes][items][products][A prefix][B prefix][unit
-  // products][tiles][tile prefix] | [A arena][B arena]
+  // the kernel's TMA coordinates are 32-bit scratch rows
+  if (plan->scratch_rows > kMax32) return FQ_ENOTSUP;
+  // workspace: [header][shapes][items][products][CTA begins][CTA lists][CTA
+  // rows] | [scratch buffers]
   int64_t off = int64_t(sizeof(Header)) + shapes_bytes(count) + int64_t(plan->items.size()) * int64_t(sizeof(Item));
   if (T > 0) {
     plan->off_prods = off = align_up(off, 64);
     off += int64_t(T) * int64_t(sizeof(fqk::BatchProd));
-    plan->off_aprefix = off = align_up(off, 64);
-    off += int64_t(T + 1) * 8;
-    plan->off_bprefix = off = align_up(off, 64);
-    off += int64_t(T + 1) * 8;
-    plan->off_aunit = off = align_up(off, 64);
-    off += int64_t(plan->tc_a_unit.size()) * 4;
-    plan->off_bunit = off = align_up(off, 64);
-    off += int64_t(plan->tc_b_unit.size()) * 4;
-    plan->off_tiles = off = align_up(off, 64);
-    off += int64_t(plan->tc_tiles.size()) * int64_t(sizeof(fqk::BatchTile));
-    plan->off_tprefix = off = align_up(off, 64);
-    off += int64_t(plan->tc_tile_prefix.size()) * 8;
+    plan->off_cta_begin = off = align_up(off, 64);
+    off += int64_t(NC + 1) * 4;
+    plan->off_cta_list = off = align_up(off, 64);
+    off += int64_t(T) * 4;
+    plan->off_cta_rows = off = align_up(off, 64);
+    off += int64_t(2 * NC) * 8;
   }
   plan->table_bytes = off;
   if (T > 0) {
-    plan->off_a_arena = off = align_up(off, 1024);
-    off += plan->a_rows * 128;
-    plan->off_b_arena = off = align_up(off, 1024);
-    off += plan->b_rows * 128;
+    plan->off_scratch = off = align_up(off, 1024);
+    off += plan->scratch_rows * 128;
   }
   plan->workspace_bytes = off;
   *out = plan.release();
@@ -521,12 +517,9 @@ std::vector<unsigned char> plan_tables(const fq_batch_plan *plan) {
            plan->items.size() * sizeof(Item));
   if (!plan->tc_prods.empty()) {
     memcpy(host.data() + plan->off_prods, plan->tc_prods.data(), plan->tc_prods.size() * sizeof(fqk::BatchProd));
-    memcpy(host.data() + plan->off_aprefix, plan->tc_a_prefix.data(), plan->tc_a_prefix.size() * 8);
-    memcpy(host.data() + plan->off_bprefix, plan->tc_b_prefix.data(), plan->tc_b_prefix.size() * 8);
-    memcpy(host.data() + plan->off_aunit, plan->tc_a_unit.data(), plan->tc_a_unit.size() * 4);
-    memcpy(host.data() + plan->off_bunit, plan->tc_b_unit.data(), plan->tc_b_unit.size() * 4);
-    memcpy(host.data() + plan->off_tiles, plan->tc_tiles.data(), plan->tc_tiles.size() * sizeof(fqk::BatchTile));
-    memcpy(host.data() + plan->off_tprefix, plan->tc_tile_prefix.data(), plan->tc_tile_prefix.size() * 8);
+    memcpy(host.data() + plan->off_cta_begin, plan->tc_cta_begin.data(), plan->tc_cta_begin.size() * 4);
+    memcpy(host.data() + plan->off_cta_list, plan->tc_cta_list.data(), plan->tc_cta_list.size() * 4);
+    memcpy(host.data() + plan->off_cta_rows, plan->tc_cta_rows.data(), plan->tc_cta_rows.size() * 8);
   }
   return host;
 }
@@ -536,20 +529,12 @@ fqk::TcBatch tc_view(const fq_batch_plan *plan, unsigned char *ws) {
   fqk::TcBatch b;
   b.q = plan->q;
   b.nprod = int(plan->tc_prods.size());
-  b.ntiles = int(plan->tc_tiles.size());
-  b.a_rows = plan->a_rows;
-  b.b_rows = plan->b_rows;
-  b.a_units = plan->tc_a_prefix.empty() ? 0 : plan->tc_a_prefix.back();
-  b.b_units = plan->tc_b_prefix.empty() ? 0 : plan->tc_b_prefix.back();
+  b.scratch_rows = plan->scratch_rows;
   b.prods = reinterpret_cast<const fqk::BatchProd *>(ws + plan->off_prods);
-  b.a_prefix = reinterpret_cast<const int64_t *>(ws + plan->off_aprefix);
-  b.b_prefix = reinterpret_cast<const int64_t *>(ws + plan->off_bprefix);
-  b.a_unit_prod = reinterpret_cast<const int32_t *>(ws + plan->off_aunit);
-  b.b_unit_prod = reinterpret_cast<const int32_t *>(ws + plan->off_bunit);
-  b.tiles = reinterpret_cast<const fqk::BatchTile *>(ws + plan->off_tiles);
-  b.tile_prefix = reinterpret_cast<const int64_t *>(ws + plan->off_tprefix);
-  b.a_arena = ws + plan->off_a_arena;
-  b.b_arena = ws + plan->off_b_arena;
+  b.cta_begin = reinterpret_cast<const int32_t *>(ws + plan->off_cta_begin);
+  b.cta_list = reinterpret_cast<const int32_t *>(ws + plan->off_cta_list);
+  b.cta_rows = reinterpret_cast<const int64_t *>(ws + plan->off_cta_rows);
+  b.scratch = ws + plan->off_scratch;
   return b;
 }
 
@@ -573,7 +558,7 @@ int64_t fq_batched_items(const fq_batch_plan *plan) { return plan ? int64_t(plan
 
 int64_t fq_batched_tc_products(const fq_batch_plan *plan) { return plan ? int64_t(plan->tc_prods.size()) : -1; }
 
-int64_t fq_batched_tc_tiles(const fq_batch_plan *plan) { return plan ? int64_t(plan->tc_tiles.size()) : -1; }
+int64_t fq_batched_tc_tiles(const fq_batch_plan *plan) { return plan ? plan->tc_tiles : -1; }
 
 int fq_batched_plan_upload(const fq_batch_plan *plan, void *workspace, void *stream) {
   if (!plan || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 63u) != 0) return FQ_EINVAL;
@@ -594,9 +579,8 @@ int fq_matmul_batched_stages(const fq_batch_plan *plan, const uint64_t *const *A
   if (!A || !B || !C) return FQ_EINVAL;
   unsigned char *ws = static_cast<unsigned char *>(workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int tc_stages = (stages & FQ_BATCH_STAGE_CONVERT ? 1 : 0) | (stages & FQ_BATCH_STAGE_TC ? 2 : 0);
-  if (!plan->tc_prods.empty() && tc_stages)
-    if (int rc = fqk::tc_batched(tc_view(plan, ws), A, B, C, s, tc_stages)) return rc;
+  if (!plan->tc_prods.empty() && (stages & FQ_BATCH_STAGE_TC))
+    if (int rc = fqk::tc_batched(tc_view(plan, ws), A, B, C, s)) return rc;
   if (plan->items.empty() || !(stages & FQ_BATCH_STAGE_M4RM)) return FQ_OK;
   switch (plan->q) {
     case 3: return fqk::batched::launch_field<fqk::F3>(ws, A, B, C, s);

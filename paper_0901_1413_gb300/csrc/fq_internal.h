@@ -37,39 +37,38 @@ int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t
                 const TcOptions &to = TcOptions());
 double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms);
 
-// Batched products on the tcgen05 path.  Each product's A and B^T are
-// converted into two shared arenas of 128-byte rows, K-blocked (a 128-row
-// block of A, or a 256-row block of B^T, holds its 128-deep k-slices one
-// after another), one tensor map each; then one persistent kernel computes
-// all 128 x 256 tiles of all products.
+// Batched products on the tcgen05 path.  The plan gives every product to one
+// of kTcCtas persistent CTAs (longest first, each to the least-loaded CTA).  A
+// CTA works through its products in turn: its converter warps write a
+// product's A and B^T as e4m3 bytes into one of the CTA's two scratch buffers
+// (K-blocked rows of 128 bytes: a 128-row block of A, or a 256-row block of
+// B^T, holds its 128-deep k-slices one after another) while its TMA, MMA and
+// epilogue warps compute the previous product's 128 x 256 tiles from the
+// other buffer.  The buffers are small enough to stay in L2.
+constexpr int kTcCtas = 152;
 struct BatchProd {
   int32_t p;              // index into the caller's pointer arrays
   int32_t m, l, n;
   int32_t la;             // l rounded up to 128 (bytes of an arena row used)
   int32_t nr;             // n rounded up to 256 (B^T rows reserved)
   int64_t pa, pb, pc;     // pitch words of A, B, C
-  int64_t a_row0, b_row0; // first arena rows (128 bytes each)
-};
-struct BatchTile {
-  int32_t prod, ksteps;   // product index, 128-deep k-steps
-  int32_t ya, yb;         // first arena rows of the tile's A and B^T slices
-  int32_t row0, w0;       // first row and word of the tile in C
-  int32_t pad[2];
+  int64_t a_row0, b_row0; // unused (kept for the record layout)
 };
 struct TcBatch {
   int q = 0;
-  int nprod = 0, ntiles = 0;
-  int64_t a_rows = 0, b_rows = 0, a_units = 0, b_units = 0;  // arena rows of 128 bytes; conversion units
-  const BatchProd *prods = nullptr;               // device
-  const int64_t *a_prefix = nullptr, *b_prefix = nullptr;  // device, nprod + 1 each
-  const int32_t *a_unit_prod = nullptr, *b_unit_prod = nullptr;  // device, product of each unit
-  const BatchTile *tiles = nullptr;               // device
-  const int64_t *tile_prefix = nullptr;           // device, ntiles + 1: cumulative modelled tile cost
-  uint8_t *a_arena = nullptr, *b_arena = nullptr; // device
+  int nprod = 0;
+  int64_t scratch_rows = 0;            // rows of 128 bytes of all CTAs' buffers together
+  const BatchProd *prods = nullptr;    // device
+  const int32_t *cta_begin = nullptr;  // device, kTcCtas + 1: products of CTA c are cta_list[begin[c] .. begin[c+1])
+  const int32_t *cta_list = nullptr;   // device, nprod product indices, each CTA's in the order it computes them
+  const int64_t *cta_rows = nullptr;   // device, kTcCtas x 2: first scratch row of each CTA's buffers 0 and 1
+  uint8_t *scratch = nullptr;          // device, scratch_rows x 128 bytes (1024-byte aligned)
 };
-// stages: bit 0 the two operand conversions, bit 1 the tile kernel (both by default).
+// Rows of 128 bytes a product's operands take in a scratch buffer: A, then B^T.
+__host__ __device__ inline int64_t batch_a_rows(int m, int la) { return int64_t((m + 127) / 128) * la; }
+__host__ __device__ inline int64_t batch_bt_rows(int nr, int la) { return int64_t(nr) * (la / 128); }
 int tc_batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B, uint64_t *const *C,
-               cudaStream_t s, int stages = 3);
+               cudaStream_t s);
 
 // One compiled M4RM kernel shape of a field (the planner's candidates).
 struct Variant {

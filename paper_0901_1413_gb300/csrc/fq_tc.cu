@@ -827,67 +827,129 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairGeo<WIDE>::THREA
 }
 
 // ---------------------------------------------------- batched products --
-
-// Arenas are K-blocked: rows of 128 bytes, and a product's 128-row block g
-// of A holds its la / 128 k-slices one after another (slice ks of row r at
-// arena row a_row0 + (g la / 128 + ks) 128 + r % 128), so that each TMA load
-// of a tile reads one contiguous 16 KB (A) or 32 KB (B^T, 256-row blocks).
 //
-// A of every product into the A arena: a unit is 256 consecutive 16-element
-// pieces of one product (row-major over m rows of la / 16 pieces), one per
-// thread; rows m .. are not written.
+// One persistent CTA per slot (kTcCtas) works through its own products, in the
+// order the plan lists them.  Product i of a CTA uses the CTA's scratch buffer
+// i mod 2: its A as K-blocked rows of 128 bytes (a 128-row block of A holds its
+// la / 128 k-slices one after another: slice ks of row r at row (r / 128 *
+// la / 128 + ks) * 128 + r % 128), then its B^T likewise in 256-row blocks.
+// Converter warps fill one buffer while the TMA, MMA and epilogue warps
+// compute the previous product from the other, so the operands are written
+// and read back through L2 instead of a DRAM arena.
+//
+// Warps: 0 (one thread) TMA loads, 1 (one thread) MMAs, 2 TMEM allocation,
+// 4..19 epilogue (TMEM lane quadrant warp % 4, 64-column quarter (warp - 4) /
+// 4), 20..27 converters.  Hand-overs between them:
+//   conv_full[b]   converters -> TMA thread: the product's operands are in
+//                  buffer b (each converter thread orders its global writes
+//                  before the async proxy's reads, then arrives);
+//   conv_empty[b]  MMA thread -> converters: every copy out of buffer b has
+//                  landed in shared memory (arrived after the product's last
+//                  full-stage wait), so the buffer may be refilled.
+constexpr int CONV_WARPS = 8, CONV_THREADS = 32 * CONV_WARPS;
+constexpr int FIRST_CONV_WARP = 20;
+constexpr int THREADS_F = 32 * FIRST_CONV_WARP + CONV_THREADS;
+constexpr int NBARS_F = NBARS + 4;  // + conv_full[2], conv_empty[2]
+constexpr int SMEM_F = BAR_OFF + 8 * NBARS_F + 16 + 1024;
+
+// A's planes to the K-blocked e4m3 rows of a buffer: converter thread ct takes
+// the 16-element pieces ct, ct + CONV_THREADS, ... (row-major over m rows of
+// la / 16 pieces), loading UNR pieces' words before converting any.  A
+// thread's (row, piece) advances by the stride's quotient and remainder, so
+// no division runs per piece.  Pieces past l read the planes' zero padding
+// (la / 64 words fit the row pitch), so the depth padding is zero.
 template <int Q, int P>
-__global__ void __launch_bounds__(256) batched_rows_kernel(const BatchProd *__restrict__ prods,
-                                                           const int64_t *__restrict__ prefix,
-                                                           const int32_t *__restrict__ unit_prod, int64_t units,
-                                                           const uint64_t *const *A, uint8_t *arena) {
+__device__ __forceinline__ void convert_a(const BatchProd &bp, const uint64_t *__restrict__ X, uint8_t *buf,
+                                          int ct) {
   using CF = ConvField<Q>;
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int i = __ldg(unit_prod + u);
-    const BatchProd bp = prods[i];
-    const int per_row = bp.la >> 4;
-    const int64_t q = (u - __ldg(prefix + i)) * 256 + threadIdx.x;
-    if (q >= int64_t(bp.m) * per_row) continue;
-    const int64_t r = q / per_row;
-    const int piece = int(q - r * per_row);
-    const uint32_t *X32 = reinterpret_cast<const uint32_t *>(A[bp.p]);
-    {
-      uint32_t t[P];
+  constexpr int UNR = 4;
+  const int per_row = bp.la >> 4, kb = bp.la >> 7;
+  const int radv = CONV_THREADS / per_row, padv = CONV_THREADS % per_row;
+  const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
+  int r = ct / per_row, piece = ct % per_row;
+  while (r < bp.m) {
+    uint32_t t[UNR][P];
+    int rr[UNR], pp[UNR];
 #pragma unroll
-      for (int p = 0; p < P; ++p) t[p] = __ldg(X32 + (p * int64_t(bp.m) + r) * bp.pa * 2 + (piece >> 1));
+    for (int u = 0; u < UNR; ++u) {
+      rr[u] = r;
+      pp[u] = piece;
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        t[u][p] = r < bp.m ? __ldg(X32 + (p * int64_t(bp.m) + r) * bp.pa * 2 + (piece >> 1)) : 0u;
+      r += radv;
+      piece += padv;
+      if (piece >= per_row) {
+        piece -= per_row;
+        ++r;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      if (rr[u] >= bp.m) break;
       uint32_t o[CF::P2];
-      select_planes<Q, P>(t, 0, o);
-      const int64_t arow = bp.a_row0 + ((r >> 7) * (bp.la >> 7) + (piece >> 3)) * 128 + (r & 127);
-      *reinterpret_cast<uint4 *>(arena + arow * 128 + (piece & 7) * 16) = e4m3x16<Q, CF::P2>(o, 16 * (piece & 1));
+      select_planes<Q, P>(t[u], 0, o);
+      const int64_t row = int64_t((rr[u] >> 7) * kb + (pp[u] >> 3)) * 128 + (rr[u] & 127);
+      *reinterpret_cast<uint4 *>(buf + row * 128 + (pp[u] & 7) * 16) = e4m3x16<Q, CF::P2>(o, 16 * (pp[u] & 1));
     }
   }
 }
 
-// B^T of every product into the B arena: a unit is one 128 (k) x 256 (j)
-// block of one product; rows j >= n are not written.
+// B's planes to B^T's K-blocked e4m3 rows: converter warp cw takes the units
+// cw, cw + CONV_WARPS, ... of 32 (k) x 128 (j) bits.  Lane i loads row k = 32
+// kq + i (zero past l), each 32 x 32 bit block is transposed across the warp
+// (lane j then holds column j's 32 k-values) and each lane writes its
+// column's 32 bytes into that column's row.  Columns up to nr read the
+// planes' zero padding (nr / 64 words fit the row pitch).
 template <int Q, int P>
-__global__ void __launch_bounds__(256) batched_transpose_kernel(const BatchProd *__restrict__ prods,
-                                                                const int64_t *__restrict__ prefix,
-                                                                const int32_t *__restrict__ unit_prod,
-                                                                int64_t units, const uint64_t *const *B,
-                                                                uint8_t *arena) {
-  __shared__ uint4 tile[TJ * TK / 16];
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int i = __ldg(unit_prod + u);
-    const BatchProd bp = prods[i];
-    const int64_t kblocks = bp.la / TK, bi = u - __ldg(prefix + i);
-    const int64_t ks = bi % kblocks, g = bi / kblocks;
-    transpose_block<Q, P>(B[bp.p], bp.l, bp.pb, arena + (bp.b_row0 + (g * kblocks + ks) * TJ) * 128, 128, bp.la,
-                          bp.n, 0, ks * TK, g * TJ, tile);
-    __syncthreads();  // the shared tile is refilled by the next unit
+__device__ __forceinline__ void convert_bt(const BatchProd &bp, const uint64_t *__restrict__ X, uint8_t *buf,
+                                           int cw, int lane) {
+  using CF = ConvField<Q>;
+  const int kb = bp.la >> 7, kgroups = bp.la >> 5, units = kgroups * (bp.nr >> 7);
+  for (int u = cw; u < units; u += CONV_WARPS) {
+    const int kq = u % kgroups, jw = u / kgroups;
+    const int k = 32 * kq + lane;
+    uint32_t t[4][P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const uint4 v = k < bp.l ? __ldg(reinterpret_cast<const uint4 *>(X + (p * int64_t(bp.l) + k) * bp.pb + 2 * jw))
+                               : make_uint4(0u, 0u, 0u, 0u);
+      t[0][p] = v.x;
+      t[1][p] = v.y;
+      t[2][p] = v.z;
+      t[3][p] = v.w;
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      uint32_t o[CF::P2];
+      select_planes<Q, P>(t[g], 0, o);
+#pragma unroll
+      for (int p = 0; p < CF::P2; ++p) o[p] = transpose32(o[p], lane);
+      const int j = 128 * jw + 32 * g + lane;
+      const int64_t row = int64_t((j >> 8) * kb + (kq >> 2)) * 256 + (j & 255);
+      uint8_t *dst = buf + row * 128 + (kq & 3) * 32;
+      *reinterpret_cast<uint4 *>(dst) = e4m3x16<Q, CF::P2>(o, 0);
+      *reinterpret_cast<uint4 *>(dst + 16) = e4m3x16<Q, CF::P2>(o, 16);
+    }
+  }
+}
+
+// Starts copying `bytes` at `p` (16-byte aligned, a multiple of 16) into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, int64_t bytes) {
+  const char *c = static_cast<const char *>(p);
+  for (int64_t off = 0; off < bytes; off += 65536) {
+    const int64_t n = bytes - off < 65536 ? bytes - off : 65536;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + off), "r"(uint32_t(n)) : "memory");
   }
 }
 
 struct BatchParams {
   const BatchProd *prods;
-  const BatchTile *tiles;
-  const int64_t *tile_prefix;
-  int ntiles;
+  const int32_t *cta_begin, *cta_list;  // products of CTA c: cta_list[cta_begin[c] .. cta_begin[c + 1])
+  const int64_t *cta_rows;              // kTcCtas x 2: first tensor-map row of each CTA's buffer 0 and buffer 1
+  uint8_t *scratch;
+  const uint64_t *const *A;
+  const uint64_t *const *B;
   uint64_t *const *C;
   unsigned *err;
 };
@@ -917,24 +979,11 @@ __device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, i
   }
 }
 
-// First tile whose cumulative cost reaches `cost`.
-__device__ __forceinline__ int tile_at_cost(const int64_t *__restrict__ prefix, int ntiles, int64_t cost) {
-  int lo = 0, hi = ntiles;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (prefix[mid] < cost) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-// The single-SM persistent product (as tc_gemm_kernel) over the tiles of all
-// products.  CTA c takes the contiguous run of the plan's list (a product's
-// tiles row block by row block) whose cumulative modelled cost lies in
-// [c, c + 1) x total / CTAs, so that consecutive tiles on one SM share their
-// product's A rows and B^T columns through L2; each tile reads its product's
-// rows of the two arenas.
+// The persistent batched kernel: CTA c computes the products of its list, one
+// after another, 128 x 256 tiles each (row block by row block), from the e4m3
+// operands its converter warps write into its two scratch buffers.
 template <int Q, int P>
-__global__ void __launch_bounds__(THREADS_B, 1)
+__global__ void __launch_bounds__(THREADS_F, 1)
     tc_batched_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const BatchParams prm) {
   extern __shared__ unsigned char smem_raw[];
@@ -943,9 +992,10 @@ __global__ void __launch_bounds__(THREADS_B, 1)
   unsigned char *smem = smem_raw + (base - raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t full = base + BAR_OFF, empty = full + 8 * STAGES, accfull = empty + 8 * STAGES,
-                 accempty = accfull + 8 * ACC;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + BAR_OFF + 8 * NBARS);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + BAR_OFF + 8 * NBARS + 8);
+                 accempty = accfull + 8 * ACC, drain = accempty + 8 * ACC, conv_full = drain + 8,
+                 conv_empty = conv_full + 16;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + BAR_OFF + 8 * NBARS_F);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + BAR_OFF + 8 * NBARS_F + 8);
 
   if (tid == 0) {
     *abort_flag = 0;
@@ -957,7 +1007,11 @@ __global__ void __launch_bounds__(THREADS_B, 1)
       mbar_init(accfull + 8 * b, 1);
       mbar_init(accempty + 8 * b, 16);  // sixteen epilogue warps
     }
-    mbar_init(accempty + 8 * ACC, 1);  // the MMA drain
+    mbar_init(drain, 1);  // the MMA drain
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(conv_full + 8 * b, CONV_THREADS);
+      mbar_init(conv_empty + 8 * b, 1);
+    }
     fence_mbar_init();
   }
   if (warp == 2) {
@@ -970,82 +1024,120 @@ __global__ void __launch_bounds__(THREADS_B, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int64_t total = prm.tile_prefix[prm.ntiles];
-  const int t_begin = tile_at_cost(prm.tile_prefix, prm.ntiles, total * int64_t(blockIdx.x) / gridDim.x);
-  const int t_end = tile_at_cost(prm.tile_prefix, prm.ntiles, total * int64_t(blockIdx.x + 1) / gridDim.x);
+  const int cta = blockIdx.x;
+  const int first = prm.cta_begin[cta], count = prm.cta_begin[cta + 1] - first;
+  const int64_t row_buf[2] = {prm.cta_rows[2 * cta], prm.cta_rows[2 * cta + 1]};
 
   if (warp == 0 && lane == 0) {
+    // ---- TMA: the tiles of each product, from its buffer once it is filled
     int it = 0;
-    BatchTile nxt = t_begin < t_end ? prm.tiles[t_begin] : BatchTile{};
-    for (int t = t_begin; t < t_end && !*abort_flag; ++t) {
-      const BatchTile bt = nxt;  // this tile's record, fetched one tile ahead
-      if (t + 1 < t_end) nxt = prm.tiles[t + 1];
-      for (int ks = 0; ks < bt.ksteps; ++ks, ++it) {
-        const int s = it % STAGES;
-        if (it >= STAGES) wait_bar(empty + 8 * s, uint32_t((it / STAGES - 1) & 1), abort_flag, prm.err);
-        if (*abort_flag) break;
-        const uint32_t a_dst = base + uint32_t(s * STAGE_BYTES), b_dst = a_dst + A_BYTES;
-        mbar_expect_tx(full + 8 * s, STAGE_BYTES);
-        tma_load_2d(a_dst, &tmA, full + 8 * s, 0, bt.ya + ks * BM);  // one contiguous 16 KB block
-        tma_load_2d(b_dst, &tmB, full + 8 * s, 0, bt.yb + ks * BN);  // one contiguous 32 KB block
-      }
+    for (int i = 0; i < count && !*abort_flag; ++i) {
+      const int b = i & 1;
+      wait_bar(conv_full + 8 * b, uint32_t((i >> 1) & 1), abort_flag, prm.err);
+      if (*abort_flag) break;
+      const BatchProd bp = prm.prods[prm.cta_list[first + i]];
+      const int kb = bp.la >> 7, mbs = (bp.m + 127) >> 7, nbs = bp.nr >> 8;
+      const int ya = int(row_buf[b]), yb = int(row_buf[b] + batch_a_rows(bp.m, bp.la));
+      for (int mb = 0; mb < mbs && !*abort_flag; ++mb)
+        for (int nb = 0; nb < nbs && !*abort_flag; ++nb)
+          for (int ks = 0; ks < kb; ++ks, ++it) {
+            const int s = it % STAGES;
+            if (it >= STAGES) wait_bar(empty + 8 * s, uint32_t((it / STAGES - 1) & 1), abort_flag, prm.err);
+            if (*abort_flag) break;
+            const uint32_t a_dst = base + uint32_t(s * STAGE_BYTES), b_dst = a_dst + A_BYTES;
+            mbar_expect_tx(full + 8 * s, STAGE_BYTES);
+            tma_load_2d(a_dst, &tmA, full + 8 * s, 0, ya + (mb * kb + ks) * BM);  // one contiguous 16 KB block
+            tma_load_2d(b_dst, &tmB, full + 8 * s, 0, yb + (nb * kb + ks) * BN);  // one contiguous 32 KB block
+          }
     }
     if (*abort_flag) drain_copies(full, it, STAGES);
   } else if (warp == 1 && lane == 0) {
+    // ---- MMAs; after a product's last stage has landed its buffer is free
     int it = 0, li = 0;
-    int nks = t_begin < t_end ? prm.tiles[t_begin].ksteps : 0;
-    for (int t = t_begin; t < t_end && !*abort_flag; ++t, ++li) {
-      const int ksteps = nks;
-      if (t + 1 < t_end) nks = prm.tiles[t + 1].ksteps;
-      const int b = li % ACC;
-      if (li >= ACC) wait_bar(accempty + 8 * b, uint32_t((li / ACC - 1) & 1), abort_flag, prm.err);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t d = tmem + uint32_t(b * BN);
-      for (int ks = 0; ks < ksteps; ++ks, ++it) {
-        const int s = it % STAGES;
-        wait_bar(full + 8 * s, uint32_t((it / STAGES) & 1), abort_flag, prm.err);
-        if (*abort_flag) break;
+    bool issued = false;
+    for (int i = 0; i < count && !*abort_flag; ++i) {
+      const BatchProd bp = prm.prods[prm.cta_list[first + i]];
+      const int kb = bp.la >> 7, tiles = ((bp.m + 127) >> 7) * (bp.nr >> 8);
+      for (int t = 0; t < tiles && !*abort_flag; ++t, ++li) {
+        const int ab = li % ACC;
+        if (li >= ACC) wait_bar(accempty + 8 * ab, uint32_t((li / ACC - 1) & 1), abort_flag, prm.err);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a_src = base + uint32_t(s * STAGE_BYTES), b_src = a_src + A_BYTES;
+        const uint32_t d = tmem + uint32_t(ab * BN);
+        for (int ks = 0; ks < kb; ++ks, ++it) {
+          const int s = it % STAGES;
+          wait_bar(full + 8 * s, uint32_t((it / STAGES) & 1), abort_flag, prm.err);
+          if (*abort_flag) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_src = base + uint32_t(s * STAGE_BYTES), b_src = a_src + A_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < BK / UK; ++kk)
-          mma_e4m3(d, smem_desc(a_src + UK * kk), smem_desc(b_src + UK * kk), (ks | kk) != 0);
-        mma_commit(empty + 8 * s);
+          for (int kk = 0; kk < BK / UK; ++kk)
+            mma_e4m3(d, smem_desc(a_src + UK * kk), smem_desc(b_src + UK * kk), (ks | kk) != 0);
+          mma_commit(empty + 8 * s);
+          issued = true;
+        }
+        mma_commit(accfull + 8 * ab);
       }
-      mma_commit(accfull + 8 * b);
+      if (!*abort_flag) mbar_arrive_cta(conv_empty + 8 * (i & 1));
     }
-    if (*abort_flag) {  // the MMAs issued so far complete before TMEM is freed
-      mma_commit(accempty + 8 * ACC);
-      mbar_wait_bounded(accempty + 8 * ACC, 0);
+    if (*abort_flag && issued) {  // the MMAs issued so far complete before TMEM is freed
+      mma_commit(drain);
+      mbar_wait_bounded(drain, 0);
     }
-  } else if (warp >= 4) {
-    // warps 4..19: TMEM lane quadrant warp % 4, columns 64 quarter .. + 63
+  } else if (warp >= 4 && warp < FIRST_CONV_WARP) {
+    // ---- epilogue: warps 4..19, TMEM lane quadrant warp % 4, columns 64 quarter .. + 63
     const int ew = warp & 3, quarter = (warp - 4) >> 2;
     int li = 0;
-    for (int t = t_begin; t < t_end; ++t, ++li) {
-      const int b = li % ACC;
-      // the tile's record, its product and C's address, read before the wait
-      const BatchTile bt = prm.tiles[t];
-      const BatchProd &pr = prm.prods[bt.prod];
+    for (int i = 0; i < count && !*abort_flag; ++i) {
+      const BatchProd bp = prm.prods[prm.cta_list[first + i]];
       BatchOut bo;
-      bo.m = pr.m;
-      bo.n = pr.n;
-      bo.nr = pr.nr;
-      bo.pc = pr.pc;
-      bo.C = prm.C[pr.p];
-      wait_bar(accfull + 8 * b, uint32_t((li / ACC) & 1), abort_flag, prm.err);
-      if (*abort_flag) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t row = int64_t(bt.row0) + ew * 32 + lane;
-      const int64_t col0 = (int64_t(bt.w0) + quarter) * 64;
-      // 32-column chunks holding columns < n
-      const int live = bo.n <= col0 ? 0 : (bo.n - col0 > 32 ? 2 : 1);
-      uint64_t words[P][1];
-      drain_accumulator<Q, P, 1>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN + quarter * 64), words, live);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive_cta(accempty + 8 * b);
-      if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, bt.w0, quarter, words, prm.err);
+      bo.m = bp.m;
+      bo.n = bp.n;
+      bo.nr = bp.nr;
+      bo.pc = bp.pc;
+      bo.C = prm.C[bp.p];
+      const int nbs = bp.nr >> 8, tiles = ((bp.m + 127) >> 7) * nbs;
+      for (int t = 0; t < tiles; ++t, ++li) {
+        const int ab = li % ACC;
+        wait_bar(accfull + 8 * ab, uint32_t((li / ACC) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int mb = t / nbs, nb = t - mb * nbs;
+        const int64_t row = int64_t(mb) * BM + ew * 32 + lane;
+        const int64_t w0 = int64_t(nb) * (BN / 64);
+        const int64_t col0 = (w0 + quarter) * 64;
+        // 32-column chunks holding columns < n
+        const int live = bo.n <= col0 ? 0 : (bo.n - col0 > 32 ? 2 : 1);
+        uint64_t words[P][1];
+        drain_accumulator<Q, P, 1>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(ab * BN + quarter * 64), words, live);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cta(accempty + 8 * ab);
+        if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, w0, quarter, words, prm.err);
+      }
+    }
+  } else if (warp >= FIRST_CONV_WARP) {
+    // ---- converters: product i into buffer i mod 2, once the product two
+    // before it has left that buffer; the next product's planes are fetched
+    // into L2 meanwhile
+    const int ct = tid - 32 * FIRST_CONV_WARP, cw = ct >> 5;
+    for (int i = 0; i < count && !*abort_flag; ++i) {
+      const int b = i & 1;
+      if (i >= 2) {
+        wait_bar(conv_empty + 8 * b, uint32_t(((i - 2) >> 1) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+      }
+      const BatchProd bp = prm.prods[prm.cta_list[first + i]];
+      if (ct == 0 && i + 1 < count) {
+        const BatchProd nx = prm.prods[prm.cta_list[first + i + 1]];
+        prefetch_l2(prm.A[nx.p], int64_t(P) * nx.m * nx.pa * 8);
+        prefetch_l2(prm.B[nx.p], int64_t(P) * nx.l * nx.pb * 8);
+      }
+      uint8_t *buf = prm.scratch + row_buf[b] * 128;
+      convert_a<Q, P>(bp, prm.A[bp.p], buf, ct);
+      convert_bt<Q, P>(bp, prm.B[bp.p], buf + batch_a_rows(bp.m, bp.la) * 128, cw, lane);
+      // this thread's writes are visible to the TMA loads that follow the hand-over
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      mbar_arrive_cta(conv_full + 8 * b);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1186,36 +1278,25 @@ int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, co
 
 template <int Q, int P>
 int batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B, uint64_t *const *C,
-            cudaStream_t s, int stages) {
-  if (b.nprod == 0 || b.ntiles == 0) return FQ_OK;
+            cudaStream_t s) {
+  if (b.nprod == 0) return FQ_OK;
   unsigned *err = nullptr;
   if (int rc = status_word(&err)) return rc;
-  const int64_t cap = 152 * 8;
-  if (stages & 1) {
-    if (b.a_units > 0)
-      batched_rows_kernel<Q, P><<<unsigned(b.a_units < cap ? b.a_units : cap), 256, 0, s>>>(
-          b.prods, b.a_prefix, b.a_unit_prod, b.a_units, A, b.a_arena);
-    if (b.b_units > 0)
-      batched_transpose_kernel<Q, P><<<unsigned(b.b_units < cap ? b.b_units : cap), 256, 0, s>>>(
-          b.prods, b.b_prefix, b.b_unit_prod, b.b_units, B, b.b_arena);
-    FQ_LAUNCH_CHECK();
-  }
-  if (!(stages & 2)) return FQ_OK;
   CUtensorMap ma, mb;
-  if (int rc = make_map(&ma, b.a_arena, BK, b.a_rows, BM)) return rc;
-  if (int rc = make_map(&mb, b.b_arena, BK, b.b_rows, BN)) return rc;
+  if (int rc = make_map(&ma, b.scratch, BK, b.scratch_rows, BM)) return rc;
+  if (int rc = make_map(&mb, b.scratch, BK, b.scratch_rows, BN)) return rc;
   BatchParams prm;
   prm.prods = b.prods;
-  prm.tiles = b.tiles;
-  prm.tile_prefix = b.tile_prefix;
-  prm.ntiles = b.ntiles;
+  prm.cta_begin = b.cta_begin;
+  prm.cta_list = b.cta_list;
+  prm.cta_rows = b.cta_rows;
+  prm.scratch = b.scratch;
+  prm.A = A;
+  prm.B = B;
   prm.C = C;
   prm.err = err;
-  int dev = 0, sms = 0;
-  FQ_CUDA_TRY(cudaGetDevice(&dev));
-  FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  FQ_CUDA_TRY(cudaFuncSetAttribute(tc_batched_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-  tc_batched_kernel<Q, P><<<unsigned(b.ntiles < sms ? b.ntiles : sms), THREADS_B, SMEM, s>>>(ma, mb, prm);
+  FQ_CUDA_TRY(cudaFuncSetAttribute(tc_batched_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_F));
+  tc_batched_kernel<Q, P><<<kTcCtas, THREADS_F, SMEM_F, s>>>(ma, mb, prm);
   FQ_LAUNCH_CHECK();
   return FQ_OK;
 }
@@ -1294,12 +1375,12 @@ int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const u
 }
 
 int tc_batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B, uint64_t *const *C,
-               cudaStream_t s, int stages) {
-  if (b.a_rows >= (int64_t(1) << 31) || b.b_rows >= (int64_t(1) << 31)) return FQ_ENOTSUP;
+               cudaStream_t s) {
+  if (b.scratch_rows >= (int64_t(1) << 31)) return FQ_ENOTSUP;
   switch (b.q) {
-    case 3: return tc::batched<3, 2>(b, A, B, C, s, stages);
-    case 5: return tc::batched<5, 3>(b, A, B, C, s, stages);
-    case 7: return tc::batched<7, 3>(b, A, B, C, s, stages);
+    case 3: return tc::batched<3, 2>(b, A, B, C, s);
+    case 5: return tc::batched<5, 3>(b, A, B, C, s);
+    case 7: return tc::batched<7, 3>(b, A, B, C, s);
     default: return FQ_EINVAL;
   }
 }

@@ -19,7 +19,7 @@ from . import build as _build
 
 OK, EINVAL, EVALUE, ECUDA, ETIMEOUT, ENOTSUP, ENOMEM, EBOUNDS = range(8)
 PATH_AUTO, PATH_M4RM, PATH_MMA, PATH_KARATSUBA = 0, 1, 2, 3
-STAGE_CONVERT, STAGE_TC, STAGE_M4RM, STAGE_ALL = 1, 2, 4, 7
+STAGE_TC, STAGE_M4RM, STAGE_ALL = 1, 2, 3
 
 _lib = None
 
@@ -320,7 +320,7 @@ class BatchPlan:
     def run_stages(self, A_ptrs: torch.Tensor, B_ptrs: torch.Tensor, C_ptrs: torch.Tensor, stages: int,
                    stream=None):
         """fq_matmul_batched_stages: only the launch stages in the mask
-        (STAGE_CONVERT, STAGE_TC, STAGE_M4RM), for timing them apart."""
+        (STAGE_TC, STAGE_M4RM), for timing them apart."""
         _check(load().fq_matmul_batched_stages(self._h, ctypes.c_void_p(A_ptrs.data_ptr()),
                                                ctypes.c_void_p(B_ptrs.data_ptr()),
                                                ctypes.c_void_p(C_ptrs.data_ptr()), ctypes.c_void_p(self._ws_ptr()),

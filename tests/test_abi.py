@@ -96,39 +96,48 @@ def _plan_layout_model(q, shapes, path):
     forced onto one path, from the layout include/fq.h describes: header 64,
     shapes 24 each (64-aligned), Four-Russians items 32 each (tiles of C's
     pitch: 512 rows x 512 columns for F_3 and GF(4), 256 x 1024 for F_5 and
-    F_7); for tcgen05 products 64-byte records, two
-    unit prefixes, the product of each conversion unit (A: 256 pieces of 16
-    elements; B^T: 128 x 256 blocks), 32-byte tiles of 128 x 256 and their
-    cost prefix, each part 64-aligned; then the two arenas, 1024-aligned, of
-    128-byte rows (m up to 128 and n up to 256, times l up to 128 / 128)."""
+    F_7); for tcgen05 products 64-byte records, the 153 CTA list starts and
+    the product list (4 bytes each), the 2 x 152 buffer starts (8 bytes), each
+    part 64-aligned; then the CTAs' scratch buffers, 1024-aligned, of 128-byte
+    rows.  Products go to 152 CTAs longest first, each to the least-loaded
+    one by the plan's cost model; a CTA takes its products in the reverse
+    order, and its buffer b holds the largest of its products b, b + 2, ...:
+    m rounded up to 128 plus n rounded up to 256, times l rounded up to 128
+    over 128, rows."""
     from paper_0901_1413_gb300 import fq
     cdiv = lambda a, b: -(-a // b)
     up = lambda x, a: cdiv(x, a) * a
     tc_max_l = ((1 << 24) - 1) // max(1, (q - 1) // 2) ** 2
     # Four-Russians item tiles: rows x 64-bit words (two-plane fields / three-plane fields)
     mt, ctw = (512, 8) if q in (3, 4) else (256, 16)
-    items = prods = tiles = a_units = b_units = a_rows = b_rows = 0
+    items = tiles = 0
+    tc = []
     for m, l, n in shapes:
         if m == 0 or n == 0:
             continue
         if path == fq.PATH_MMA and q in (3, 5, 7) and 0 < l <= tc_max_l and n <= (1 << 30):
             la, nr = up(l, 128), up(n, 256)
-            prods += 1
             tiles += cdiv(m, 128) * (nr // 256)
-            a_units += cdiv(m * (la // 16), 256)
-            b_units += (la // 128) * (nr // 256)
-            a_rows += up(m, 128) * (la // 128)
-            b_rows += nr * (la // 128)
+            cycles = (cdiv(m, 128) * (nr // 256)) * (la // 128) * 760.0 + float((m + n) * la) * (2.07e9 * 152.0 / 3.0e12)
+            tc.append((cycles, cdiv(m, 128) * la + nr * (la // 128)))
         else:
             items += cdiv(m, mt) * (fq.pitch_words(n) // ctw)
     off = 64 + up(24 * len(shapes), 64) + 32 * items
-    if prods:
-        for size in (64 * prods, 8 * (prods + 1), 8 * (prods + 1), 4 * a_units, 4 * b_units, 32 * tiles,
-                     8 * (tiles + 1)):
+    if tc:
+        order = sorted(range(len(tc)), key=lambda i: -tc[i][0])
+        load, per = [0.0] * 152, [[] for _ in range(152)]
+        for i in order:
+            c = min(range(152), key=lambda k: (load[k], k))
+            per[c].append(i)
+            load[c] += tc[i][0]
+        rows = 0
+        for c in range(152):
+            lst = per[c][::-1]
+            rows += max([tc[i][1] for i in lst[0::2]] or [0]) + max([tc[i][1] for i in lst[1::2]] or [0])
+        for size in (64 * len(tc), 4 * 153, 4 * len(tc), 8 * 304):
             off = up(off, 64) + size
-        off = up(off, 1024) + 128 * a_rows
-        off = up(off, 1024) + 128 * b_rows
-    return off, items, prods, tiles
+        off = up(off, 1024) + 128 * rows
+    return off, items, len(tc), tiles
 
 
 def test_batch_plan_layout_matches_model(lib):
@@ -155,9 +164,10 @@ def test_batch_plan_layout_matches_model(lib):
 
 
 def test_batch_plan_32_bit_limits(lib):
-    """The batched kernels address arena rows with 32-bit TMA coordinates: a
-    plan whose A arena would reach 2^31 rows of 128 bytes is refused (and none
-    is made); n above 2^30 keeps a product off the tcgen05 path."""
+    """The batched tcgen05 kernel addresses scratch rows with 32-bit TMA
+    coordinates: a plan whose scratch would reach 2^31 rows of 128 bytes is
+    refused (and none is made); n above 2^30 keeps a product off the tcgen05
+    path."""
     import numpy as np
     from paper_0901_1413_gb300 import fq
     i64p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
@@ -165,11 +175,11 @@ def test_batch_plan_32_bit_limits(lib):
     n = np.array([64], np.int64)
     l = np.array([la], np.int64)
     h = ctypes.c_void_p()
-    # 16512 rows (129 row blocks) x 131071 k-slices = 2^31 + 16.6e6 arena rows
+    # 16512 rows (129 row blocks) x 131071 k-slices = 2^31 + 16.6e6 scratch rows for A alone
     m = np.array([16512], np.int64)
     assert lib.fq_batched_plan_create_ex(3, 1, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.ENOTSUP
     assert not h.value
-    # 128 rows of the same depth: 131071 arena rows, accepted
+    # 128 rows of the same depth: 16.8e6 rows of A and 33.6e6 of B^T, accepted
     m = np.array([128], np.int64)
     assert lib.fq_batched_plan_create_ex(3, 1, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.OK
     assert lib.fq_batched_tc_products(h) == 1
@@ -203,23 +213,23 @@ def test_batch_plan_host_side(lib):
     # every product the tcgen05 form takes (l > 0; m = 0 needs no work): 100 x 70
     # x 600 (1 x 3 tiles of 128 x 256) and 2000 x 64 x 64 (16 x 1); l = 0 stays
     # a Four-Russians product (4 zero-fill items).  Tables: header 64, shapes 128,
-    # items 4 x 32, products 2 x 64, prefixes 2 x 24, the product of each
-    # conversion unit (256-piece units of A: 100 x 8 and 2000 x 8 pieces -> 4 +
-    # 63; 3 + 1 blocks of B^T; 4 bytes each), tiles 19 x 32, their cost prefix
-    # 20 x 8, each part 64-byte aligned -> 1760 bytes;
-    # arenas (1024-aligned) of 128-byte rows: A 128 + 2048 rows, B^T 768 + 256.
+    # items 4 x 32, products 2 x 64, CTA list starts 153 x 4, CTA lists 2 x 4,
+    # buffer starts 304 x 8, each part 64-byte aligned -> 3456 bytes; scratch
+    # (1024-aligned): the larger product (2000 x 64 x 64: 16 row blocks x 128
+    # rows of A + 256 rows of B^T) on CTA 0, the other on CTA 1, each in its
+    # buffer 0: 2304 and 128 + 768 rows of 128 bytes.
     assert lib.fq_batched_plan_create_ex(3, 4, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.OK
     assert lib.fq_batched_items(h) == 4
     assert lib.fq_batched_tc_products(h) == 2
     assert lib.fq_batched_tc_tiles(h) == 3 + 16
-    assert lib.fq_batched_workspace_bytes(h) == 2048 + 2176 * 128 + 1024 * 128
+    assert lib.fq_batched_workspace_bytes(h) == 4096 + (2304 + 896) * 128
     assert [lib.fq_batched_product_path(h, p) for p in range(4)] == [fq.PATH_MMA, fq.PATH_MMA, fq.PATH_M4RM,
                                                                      fq.PATH_M4RM]
     assert lib.fq_batched_product_path(h, 4) == -fq.EINVAL
     assert lib.fq_batched_product_path(h, -1) == -fq.EINVAL
     assert lib.fq_batched_product_path(None, 0) == -fq.EINVAL
     # stage masks outside 0 .. FQ_BATCH_STAGE_ALL are refused before any launch
-    for bad_mask in (-1, 8, 100):
+    for bad_mask in (-1, 4, 100):
         assert lib.fq_matmul_batched_stages(h, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8),
                                             ctypes.c_void_p(64), None, bad_mask) == fq.EINVAL
     assert lib.fq_batched_plan_destroy(h) == fq.OK

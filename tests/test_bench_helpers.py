@@ -62,9 +62,11 @@ def test_algorithmic_lop3_counts():
     assert bench.algorithmic_lop3(10, 7, 32, 7, q=4) == 10 * 3 + 127 * 2
 
 
-def test_batched_conversion_bytes():
+def test_batched_compulsory_bytes():
     bench = _bench()
     # one F_3 product 100 x 200 x 300: la = 256, nr = 512; planes of A over la
-    # columns and of B over nr columns read (2 bits per element), e4m3 written
-    assert bench.batched_conversion_bytes(3, [(100, 200, 300)]) == 2 * (100 * 256 + 200 * 512) // 8 + 400 * 256
-    assert bench.batched_conversion_bytes(5, [(64, 128, 256)] * 2) == 2 * (3 * (64 * 128 + 128 * 256) // 8 + 320 * 128)
+    # columns and of B over nr columns read (2 bits per element), C's two
+    # planes of 100 rows x 16 words written
+    assert bench.batched_compulsory_bytes(3, [(100, 200, 300)]) == 2 * (100 * 256 + 200 * 512) // 8 + 2 * 100 * 16 * 8
+    assert bench.batched_compulsory_bytes(5, [(64, 128, 256)] * 2) == 2 * (3 * (64 * 128 + 128 * 256) // 8
+                                                                          + 3 * 64 * 16 * 8)

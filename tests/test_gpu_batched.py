@@ -194,15 +194,15 @@ def test_batched_tensor_core_exact_at_its_range(fq, q, l, codes):
 
 @pytest.mark.parametrize("q", [3, 5])
 def test_batched_stages_one_at_a_time(fq, q):
-    """fq_matmul_batched_stages: the conversions, the tcgen05 tile kernel and
-    the Four-Russians kernel run as separate calls give the oracle's results,
-    like one fq_matmul_batched; a plan's product paths are reported."""
+    """fq_matmul_batched_stages: the tcgen05 kernel and the Four-Russians
+    kernel run as separate calls give the oracle's results, like one
+    fq_matmul_batched; a plan's product paths are reported."""
     shapes = [(8, 8, 8), (1024, 1024, 1024), (512, 896, 768), (64, 0, 64), (300, 200, 520)]
     A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=q + 40)
     plan = fq.BatchPlan(q, shapes)
     paths = plan.product_paths()
     assert paths.count(fq.PATH_MMA) == plan.tc_products and paths[3] == fq.PATH_M4RM
-    for stage in (fq.STAGE_CONVERT, fq.STAGE_TC, fq.STAGE_M4RM):
+    for stage in (fq.STAGE_TC, fq.STAGE_M4RM):
         plan.run_stages(pa, pb, pc, stage)
     assert fq.status() == fq.OK
     check(fq, q, A, B, c)
