@@ -830,106 +830,109 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairGeo<WIDE>::THREA
 //
 // One persistent CTA per slot (kTcCtas) works through its own products, in the
 // order the plan lists them.  Product i of a CTA uses the CTA's scratch buffer
-// i mod 2: its A as K-blocked rows of 128 bytes (a 128-row block of A holds its
-// la / 128 k-slices one after another: slice ks of row r at row (r / 128 *
-// la / 128 + ks) * 128 + r % 128), then its B^T likewise in 256-row blocks.
-// Converter warps fill one buffer while the TMA, MMA and epilogue warps
-// compute the previous product from the other, so the operands are written
-// and read back through L2 instead of a DRAM arena.
+// i mod 2, rows of 128 bytes, both operands K-blocked in 128-row blocks:
+//   A (K-major): the 128-element chunk c of k of row r at row
+//       ((r / 128) * kb + c) * 128 + r % 128        (kb = la / 128 k-slices);
+//   B (N-major, B as it is, no transpose): the 128-element chunk c of n of
+//       row k at row (c * kb + k / 128) * 128 + k % 128, after A's rows;
+//       rows k in [l, la) are zero (the depth padding).
+// A stage of the tile kernel is one 128-row block of A and two of B (the two
+// 128-column halves of a 256-column tile), 16 KB each, so every TMA copy is
+// one contiguous 16 KB block.  Converter warps fill one buffer while the
+// TMA, MMA and epilogue warps compute the previous product from the other,
+// so the operands are written and read back through L2 instead of a DRAM
+// arena.
 //
 // Warps: 0 (one thread) TMA loads, 1 (one thread) MMAs, 2 TMEM allocation,
-// 4..19 epilogue (TMEM lane quadrant warp % 4, 64-column quarter (warp - 4) /
-// 4), 20..27 converters.  Hand-overs between them:
+// 4..11 epilogue (TMEM lane quadrant warp % 4, 128-column half (warp - 4) /
+// 4), 12..27 converters.  Hand-overs between them:
 //   conv_full[b]   converters -> TMA thread: the product's operands are in
 //                  buffer b (each converter thread orders its global writes
 //                  before the async proxy's reads, then arrives);
 //   conv_empty[b]  MMA thread -> converters: every copy out of buffer b has
 //                  landed in shared memory (arrived after the product's last
 //                  full-stage wait), so the buffer may be refilled.
-constexpr int CONV_WARPS = 8, CONV_THREADS = 32 * CONV_WARPS;
-constexpr int FIRST_CONV_WARP = 20;
+constexpr int EPI_WARPS_B = 8;
+constexpr int CONV_WARPS = 16, CONV_THREADS = 32 * CONV_WARPS;
+constexpr int FIRST_CONV_WARP = 4 + EPI_WARPS_B;
 constexpr int THREADS_F = 32 * FIRST_CONV_WARP + CONV_THREADS;
 constexpr int NBARS_F = NBARS + 4;  // + conv_full[2], conv_empty[2]
 constexpr int SMEM_F = BAR_OFF + 8 * NBARS_F + 16 + 1024;
+// kind::f8f6f4, fp32 accumulator, e4m3 A (K-major) and B (N-major), N = 256, M = 128
+constexpr uint32_t kIdescMn = kIdesc | (1u << 16);
 
-// A's planes to the K-blocked e4m3 rows of a buffer: converter thread ct takes
-// the 16-element pieces ct, ct + CONV_THREADS, ... (row-major over m rows of
-// la / 16 pieces), loading UNR pieces' words before converting any.  A
-// thread's (row, piece) advances by the stride's quotient and remainder, so
-// no division runs per piece.  Pieces past l read the planes' zero padding
-// (la / 64 words fit the row pitch), so the depth padding is zero.
-template <int Q, int P>
-__device__ __forceinline__ void convert_a(const BatchProd &bp, const uint64_t *__restrict__ X, uint8_t *buf,
-                                          int ct) {
+// Shared-memory descriptor of an N-major operand with the 128-byte swizzle:
+// 128-column atoms (128 bytes wide, one per 16 KB block of 128 k-rows),
+// leading byte offset 16 KB between the atoms along N, stride byte offset
+// 1024 bytes between groups of 8 k-rows.
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr) {
+  uint64_t d = 0;
+  d |= uint64_t((addr >> 4) & 0x3FFFu);
+  d |= uint64_t(16384 >> 4) << 16;        // leading byte offset: the next 128 columns
+  d |= uint64_t(1024 >> 4) << 32;         // stride byte offset: the next 8 k-rows
+  d |= uint64_t(1) << 46;                 // version
+  d |= uint64_t(2) << 61;                 // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_e4m3_mn(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdescMn), "r"(accumulate)
+      : "memory");
+}
+
+// A planes matrix of `rows_valid` rows (pitch words, P planes; rows up to
+// `rows` read as zero) as e4m3 bytes in 128-element chunks: chunk c of row r
+// (c < chunks) becomes the 128-byte scratch row row_of(r, c).  Converter
+// thread ct takes the chunks ct, ct + CONV_THREADS, ... (row-major), two at a
+// time with both chunks' words loaded first; a thread's (row, chunk)
+// advances by the stride's quotient and remainder, so no division runs per
+// chunk.  Each chunk is one 16-byte load per plane and eight 16-byte stores
+// into one 128-byte row.
+template <int Q, int P, class RowOf>
+__device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int rows_valid, int rows, int64_t pitch,
+                                             int chunks, uint8_t *buf, int ct, RowOf row_of) {
   using CF = ConvField<Q>;
-  constexpr int UNR = 4;
-  const int per_row = bp.la >> 4, kb = bp.la >> 7;
-  const int radv = CONV_THREADS / per_row, padv = CONV_THREADS % per_row;
-  const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
-  int r = ct / per_row, piece = ct % per_row;
-  while (r < bp.m) {
-    uint32_t t[UNR][P];
-    int rr[UNR], pp[UNR];
+  constexpr int UNR = 2;
+  const int radv = CONV_THREADS / chunks, cadv = CONV_THREADS % chunks;
+  int r = ct / chunks, c = ct % chunks;
+  while (r < rows) {
+    uint32_t t[UNR][4][P];
+    int rr[UNR], cc[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       rr[u] = r;
-      pp[u] = piece;
+      cc[u] = c;
 #pragma unroll
-      for (int p = 0; p < P; ++p)
-        t[u][p] = r < bp.m ? __ldg(X32 + (p * int64_t(bp.m) + r) * bp.pa * 2 + (piece >> 1)) : 0u;
+      for (int p = 0; p < P; ++p) {
+        const uint4 v = r < rows_valid
+                            ? __ldg(reinterpret_cast<const uint4 *>(X + (p * int64_t(rows_valid) + r) * pitch + 2 * c))
+                            : make_uint4(0u, 0u, 0u, 0u);
+        t[u][0][p] = v.x;
+        t[u][1][p] = v.y;
+        t[u][2][p] = v.z;
+        t[u][3][p] = v.w;
+      }
       r += radv;
-      piece += padv;
-      if (piece >= per_row) {
-        piece -= per_row;
+      c += cadv;
+      if (c >= chunks) {
+        c -= chunks;
         ++r;
       }
     }
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
-      if (rr[u] >= bp.m) break;
-      uint32_t o[CF::P2];
-      select_planes<Q, P>(t[u], 0, o);
-      const int64_t row = int64_t((rr[u] >> 7) * kb + (pp[u] >> 3)) * 128 + (rr[u] & 127);
-      *reinterpret_cast<uint4 *>(buf + row * 128 + (pp[u] & 7) * 16) = e4m3x16<Q, CF::P2>(o, 16 * (pp[u] & 1));
-    }
-  }
-}
-
-// B's planes to B^T's K-blocked e4m3 rows: converter warp cw takes the units
-// cw, cw + CONV_WARPS, ... of 32 (k) x 128 (j) bits.  Lane i loads row k = 32
-// kq + i (zero past l), each 32 x 32 bit block is transposed across the warp
-// (lane j then holds column j's 32 k-values) and each lane writes its
-// column's 32 bytes into that column's row.  Columns up to nr read the
-// planes' zero padding (nr / 64 words fit the row pitch).
-template <int Q, int P>
-__device__ __forceinline__ void convert_bt(const BatchProd &bp, const uint64_t *__restrict__ X, uint8_t *buf,
-                                           int cw, int lane) {
-  using CF = ConvField<Q>;
-  const int kb = bp.la >> 7, kgroups = bp.la >> 5, units = kgroups * (bp.nr >> 7);
-  for (int u = cw; u < units; u += CONV_WARPS) {
-    const int kq = u % kgroups, jw = u / kgroups;
-    const int k = 32 * kq + lane;
-    uint32_t t[4][P];
+      if (rr[u] >= rows) break;
+      uint8_t *dst = buf + row_of(rr[u], cc[u]) * 128;
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const uint4 v = k < bp.l ? __ldg(reinterpret_cast<const uint4 *>(X + (p * int64_t(bp.l) + k) * bp.pb + 2 * jw))
-                               : make_uint4(0u, 0u, 0u, 0u);
-      t[0][p] = v.x;
-      t[1][p] = v.y;
-      t[2][p] = v.z;
-      t[3][p] = v.w;
-    }
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      uint32_t o[CF::P2];
-      select_planes<Q, P>(t[g], 0, o);
-#pragma unroll
-      for (int p = 0; p < CF::P2; ++p) o[p] = transpose32(o[p], lane);
-      const int j = 128 * jw + 32 * g + lane;
-      const int64_t row = int64_t((j >> 8) * kb + (kq >> 2)) * 256 + (j & 255);
-      uint8_t *dst = buf + row * 128 + (kq & 3) * 32;
-      *reinterpret_cast<uint4 *>(dst) = e4m3x16<Q, CF::P2>(o, 0);
-      *reinterpret_cast<uint4 *>(dst + 16) = e4m3x16<Q, CF::P2>(o, 16);
+      for (int j = 0; j < 4; ++j) {
+        uint32_t o[CF::P2];
+        select_planes<Q, P>(t[u][j], 0, o);
+        *reinterpret_cast<uint4 *>(dst + 32 * j) = e4m3x16<Q, CF::P2>(o, 0);
+        *reinterpret_cast<uint4 *>(dst + 32 * j + 16) = e4m3x16<Q, CF::P2>(o, 16);
+      }
     }
   }
 }
@@ -962,20 +965,23 @@ struct BatchOut {  // what an epilogue thread needs of its tile's product
 };
 
 template <int Q, int P>
-__device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, int64_t row, int64_t w0, int quarter,
-                                              uint64_t (&words)[P][1], unsigned *err) {
-  // this thread's word w0 + quarter of a 256-column tile
-  const int64_t wa = w0 + quarter;
-  const int64_t keep = bp.n - wa * 64;
-  const uint64_t mask = keep >= 64 ? ~0ull : (keep <= 0 ? 0ull : ((1ull << keep) - 1));
+__device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, int64_t row, int64_t w0, int half,
+                                              uint64_t (&words)[P][2], unsigned *err) {
+  // this thread's words w0 + 2 half, + 1 of a 256-column tile
+  const int64_t wa = w0 + 2 * half;
   const bool last = (w0 + BN / 64) * 64 >= bp.nr;
-  if (!debug_ok(row < bp.m && wa < bp.pc, err)) return;
+  if (!debug_ok(row < bp.m && wa + 1 < bp.pc, err)) return;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     uint64_t *dst = C + (int64_t(p) * bp.m + row) * bp.pc;
-    dst[wa] = words[p][0] & mask;
-    if (last)  // C's padding words past the last tile, split between the four quarters
-      for (int64_t w = w0 + BN / 64 + quarter; w < bp.pc; w += 4) dst[w] = 0ull;
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int64_t keep = bp.n - (wa + w) * 64;
+      const uint64_t mask = keep >= 64 ? ~0ull : (keep <= 0 ? 0ull : ((1ull << keep) - 1));
+      dst[wa + w] = words[p][w] & mask;
+    }
+    if (last)  // C's padding words past the last tile, split between the two halves
+      for (int64_t w = w0 + BN / 64 + half; w < bp.pc; w += 2) dst[w] = 0ull;
   }
 }
 
@@ -984,8 +990,7 @@ __device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, i
 // operands its converter warps write into its two scratch buffers.
 template <int Q, int P>
 __global__ void __launch_bounds__(THREADS_F, 1)
-    tc_batched_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      const BatchParams prm) {
+    tc_batched_kernel(const __grid_constant__ CUtensorMap tmA, const BatchParams prm) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -1005,7 +1010,7 @@ __global__ void __launch_bounds__(THREADS_F, 1)
     }
     for (int b = 0; b < ACC; ++b) {
       mbar_init(accfull + 8 * b, 1);
-      mbar_init(accempty + 8 * b, 16);  // sixteen epilogue warps
+      mbar_init(accempty + 8 * b, EPI_WARPS_B);
     }
     mbar_init(drain, 1);  // the MMA drain
     for (int b = 0; b < 2; ++b) {
@@ -1046,8 +1051,10 @@ __global__ void __launch_bounds__(THREADS_F, 1)
             if (*abort_flag) break;
             const uint32_t a_dst = base + uint32_t(s * STAGE_BYTES), b_dst = a_dst + A_BYTES;
             mbar_expect_tx(full + 8 * s, STAGE_BYTES);
-            tma_load_2d(a_dst, &tmA, full + 8 * s, 0, ya + (mb * kb + ks) * BM);  // one contiguous 16 KB block
-            tma_load_2d(b_dst, &tmB, full + 8 * s, 0, yb + (nb * kb + ks) * BN);  // one contiguous 32 KB block
+            // three contiguous 16 KB blocks: A's rows, then B's two 128-column halves
+            tma_load_2d(a_dst, &tmA, full + 8 * s, 0, ya + (mb * kb + ks) * 128);
+            tma_load_2d(b_dst, &tmA, full + 8 * s, 0, yb + ((2 * nb) * kb + ks) * 128);
+            tma_load_2d(b_dst + 16384, &tmA, full + 8 * s, 0, yb + ((2 * nb + 1) * kb + ks) * 128);
           }
     }
     if (*abort_flag) drain_copies(full, it, STAGES);
@@ -1070,8 +1077,8 @@ __global__ void __launch_bounds__(THREADS_F, 1)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a_src = base + uint32_t(s * STAGE_BYTES), b_src = a_src + A_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < BK / UK; ++kk)
-            mma_e4m3(d, smem_desc(a_src + UK * kk), smem_desc(b_src + UK * kk), (ks | kk) != 0);
+          for (int kk = 0; kk < BK / UK; ++kk)  // B: 32 k-rows of 128 bytes per step
+            mma_e4m3_mn(d, smem_desc(a_src + UK * kk), smem_desc_mn(b_src + 128 * UK * kk), (ks | kk) != 0);
           mma_commit(empty + 8 * s);
           issued = true;
         }
@@ -1084,8 +1091,8 @@ __global__ void __launch_bounds__(THREADS_F, 1)
       mbar_wait_bounded(drain, 0);
     }
   } else if (warp >= 4 && warp < FIRST_CONV_WARP) {
-    // ---- epilogue: warps 4..19, TMEM lane quadrant warp % 4, columns 64 quarter .. + 63
-    const int ew = warp & 3, quarter = (warp - 4) >> 2;
+    // ---- epilogue: TMEM lane quadrant warp % 4, columns 128 half .. + 127
+    const int ew = warp & 3, half = (warp - 4) >> 2;
     int li = 0;
     for (int i = 0; i < count && !*abort_flag; ++i) {
       const BatchProd bp = prm.prods[prm.cta_list[first + i]];
@@ -1104,22 +1111,23 @@ __global__ void __launch_bounds__(THREADS_F, 1)
         const int mb = t / nbs, nb = t - mb * nbs;
         const int64_t row = int64_t(mb) * BM + ew * 32 + lane;
         const int64_t w0 = int64_t(nb) * (BN / 64);
-        const int64_t col0 = (w0 + quarter) * 64;
+        const int64_t col0 = (w0 + 2 * half) * 64;
         // 32-column chunks holding columns < n
-        const int live = bo.n <= col0 ? 0 : (bo.n - col0 > 32 ? 2 : 1);
-        uint64_t words[P][1];
-        drain_accumulator<Q, P, 1>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(ab * BN + quarter * 64), words, live);
+        const int64_t rest = bo.n - col0;
+        const int live = rest <= 0 ? 0 : (rest >= 128 ? 4 : int((rest + 31) / 32));
+        uint64_t words[P][2];
+        drain_accumulator<Q, P, 2>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(ab * BN + half * 128), words, live);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive_cta(accempty + 8 * ab);
-        if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, w0, quarter, words, prm.err);
+        if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, w0, half, words, prm.err);
       }
     }
   } else if (warp >= FIRST_CONV_WARP) {
     // ---- converters: product i into buffer i mod 2, once the product two
     // before it has left that buffer; the next product's planes are fetched
     // into L2 meanwhile
-    const int ct = tid - 32 * FIRST_CONV_WARP, cw = ct >> 5;
+    const int ct = tid - 32 * FIRST_CONV_WARP;
     for (int i = 0; i < count && !*abort_flag; ++i) {
       const int b = i & 1;
       if (i >= 2) {
@@ -1133,8 +1141,12 @@ __global__ void __launch_bounds__(THREADS_F, 1)
         prefetch_l2(prm.B[nx.p], int64_t(P) * nx.l * nx.pb * 8);
       }
       uint8_t *buf = prm.scratch + row_buf[b] * 128;
-      convert_a<Q, P>(bp, prm.A[bp.p], buf, ct);
-      convert_bt<Q, P>(bp, prm.B[bp.p], buf + batch_a_rows(bp.m, bp.la) * 128, cw, lane);
+      const int kb = bp.la >> 7;
+      convert_rows<Q, P>(prm.A[bp.p], bp.m, bp.m, bp.pa, kb, buf, ct, [kb](int r, int c) {
+        return int64_t((r >> 7) * kb + c) * 128 + (r & 127);
+      });
+      convert_rows<Q, P>(prm.B[bp.p], bp.l, bp.la, bp.pb, bp.nr >> 7, buf + batch_a_rows(bp.m, bp.la) * 128, ct,
+                         [kb](int r, int c) { return int64_t(c * kb + (r >> 7)) * 128 + (r & 127); });
       // this thread's writes are visible to the TMA loads that follow the hand-over
       asm volatile("fence.proxy.async.global;" ::: "memory");
       mbar_arrive_cta(conv_full + 8 * b);
@@ -1282,9 +1294,8 @@ int batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B
   if (b.nprod == 0) return FQ_OK;
   unsigned *err = nullptr;
   if (int rc = status_word(&err)) return rc;
-  CUtensorMap ma, mb;
+  CUtensorMap ma;  // 128-row blocks of 128 bytes: A's and B's alike
   if (int rc = make_map(&ma, b.scratch, BK, b.scratch_rows, BM)) return rc;
-  if (int rc = make_map(&mb, b.scratch, BK, b.scratch_rows, BN)) return rc;
   BatchParams prm;
   prm.prods = b.prods;
   prm.cta_begin = b.cta_begin;
@@ -1296,7 +1307,7 @@ int batched(const TcBatch &b, const uint64_t *const *A, const uint64_t *const *B
   prm.C = C;
   prm.err = err;
   FQ_CUDA_TRY(cudaFuncSetAttribute(tc_batched_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_F));
-  tc_batched_kernel<Q, P><<<kTcCtas, THREADS_F, SMEM_F, s>>>(ma, mb, prm);
+  tc_batched_kernel<Q, P><<<kTcCtas, THREADS_F, SMEM_F, s>>>(ma, prm);
   FQ_LAUNCH_CHECK();
   return FQ_OK;
 }
