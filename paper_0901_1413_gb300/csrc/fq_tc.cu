@@ -885,54 +885,46 @@ __device__ __forceinline__ void mma_e4m3_mn(uint32_t d_tmem, uint64_t a, uint64_
 
 // A planes matrix of `rows_valid` rows (pitch words, P planes; rows up to
 // `rows` read as zero) as e4m3 bytes in 128-element chunks: chunk c of row r
-// (c < chunks) becomes the 128-byte scratch row row_of(r, c).  Converter
-// thread ct takes the chunks ct, ct + CONV_THREADS, ... (row-major), two at a
-// time with both chunks' words loaded first; a thread's (row, chunk)
-// advances by the stride's quotient and remainder, so no division runs per
-// chunk.  Each chunk is one 16-byte load per plane and eight 16-byte stores
-// into one 128-byte row.
+// (c < chunks) becomes the 128-byte scratch row row_of(r, c).  The work is
+// split in 16-element pieces, eight to a chunk, so that eight consecutive
+// threads write one 128-byte row (a warp's 16-byte stores cover four whole
+// rows).  Converter thread ct takes the pieces ct, ct + CONV_THREADS, ...
+// (row-major), UNR at a time with all their words loaded first; a thread's
+// (row, piece) advances by the stride's quotient and remainder, so no
+// division runs per piece.
 template <int Q, int P, class RowOf>
 __device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int rows_valid, int rows, int64_t pitch,
                                              int chunks, uint8_t *buf, int ct, RowOf row_of) {
   using CF = ConvField<Q>;
-  constexpr int UNR = 2;
-  const int radv = CONV_THREADS / chunks, cadv = CONV_THREADS % chunks;
-  int r = ct / chunks, c = ct % chunks;
+  constexpr int UNR = 4;
+  const int per_row = 8 * chunks;
+  const int radv = CONV_THREADS / per_row, padv = CONV_THREADS % per_row;
+  const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
+  int r = ct / per_row, piece = ct % per_row;
   while (r < rows) {
-    uint32_t t[UNR][4][P];
-    int rr[UNR], cc[UNR];
+    uint32_t t[UNR][P];
+    int rr[UNR], pp[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       rr[u] = r;
-      cc[u] = c;
+      pp[u] = piece;
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const uint4 v = r < rows_valid
-                            ? __ldg(reinterpret_cast<const uint4 *>(X + (p * int64_t(rows_valid) + r) * pitch + 2 * c))
-                            : make_uint4(0u, 0u, 0u, 0u);
-        t[u][0][p] = v.x;
-        t[u][1][p] = v.y;
-        t[u][2][p] = v.z;
-        t[u][3][p] = v.w;
-      }
+      for (int p = 0; p < P; ++p)
+        t[u][p] = r < rows_valid ? __ldg(X32 + (p * int64_t(rows_valid) + r) * pitch * 2 + (piece >> 1)) : 0u;
       r += radv;
-      c += cadv;
-      if (c >= chunks) {
-        c -= chunks;
+      piece += padv;
+      if (piece >= per_row) {
+        piece -= per_row;
         ++r;
       }
     }
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       if (rr[u] >= rows) break;
-      uint8_t *dst = buf + row_of(rr[u], cc[u]) * 128;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        uint32_t o[CF::P2];
-        select_planes<Q, P>(t[u][j], 0, o);
-        *reinterpret_cast<uint4 *>(dst + 32 * j) = e4m3x16<Q, CF::P2>(o, 0);
-        *reinterpret_cast<uint4 *>(dst + 32 * j + 16) = e4m3x16<Q, CF::P2>(o, 16);
-      }
+      uint32_t o[CF::P2];
+      select_planes<Q, P>(t[u], 0, o);
+      *reinterpret_cast<uint4 *>(buf + row_of(rr[u], pp[u] >> 3) * 128 + (pp[u] & 7) * 16) =
+          e4m3x16<Q, CF::P2>(o, 16 * (pp[u] & 1));
     }
   }
 }
