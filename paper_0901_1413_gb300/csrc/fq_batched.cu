@@ -84,11 +84,11 @@ __device__ __noinline__ void run_item(const M4rmParams &prm, const uint64_t *B, 
   const bool builder = warp < Cfg::NBW;
   const int slots = (rows_here + Cfg::ROWS_PER_SLOT - 1) / Cfg::ROWS_PER_SLOT;  // slots holding rows
 
-  uint32_t acc[Cfg::RS][Cfg::PW];
+  uint32_t acc[Cfg::RS][Cfg::APW];
 #pragma unroll
   for (int i = 0; i < Cfg::RS; ++i)
 #pragma unroll
-    for (int j = 0; j < Cfg::PW; ++j) acc[i][j] = 0u;
+    for (int j = 0; j < Cfg::APW; ++j) acc[i][j] = 0u;
 
   if (prm.nblocks > 0) {
     stage_b<Cfg>(B, prm.l, prm.pc, bstage_s, w0, 0, tid);

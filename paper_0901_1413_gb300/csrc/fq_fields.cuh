@@ -3,9 +3,11 @@
 // code of element b.
 //
 // Each field type gives P (planes), D (size of the additive basis, Section 2),
-// add / sub on one column word, `accumulate` (acc += sum_d alpha_d t_d, the
-// Four-Russians inner step), `canon` (canonical codes) and `phi` (the binary
-// maps phi_d of Section 2 on 64-bit words of A's planes).
+// AP (planes of the Four-Russians accumulator: P, or 4 for F_5), add / sub on
+// one column word, `accumulate` (acc += sum_d alpha_d t_d, the Four-Russians
+// inner step), `finish` (the accumulator to canonical codes), `canon`
+// (canonical codes) and `phi` (the binary maps phi_d of Section 2 on 64-bit
+// words of A's planes).
 #pragma once
 
 #include "fq_common.cuh"
@@ -17,13 +19,14 @@ namespace fqk {
 // element itself); addition is XOR.  The base field of GF(4) and F_8 in the
 // matrix-level products of Section 4.3.
 struct F2 {
-  static constexpr int Q = 2, P = 1, D = 1;
+  static constexpr int Q = 2, P = 1, D = 1, AP = P;
   __device__ __forceinline__ static void add(uint32_t (&x)[P], const uint32_t (&y)[P]) { x[0] ^= y[0]; }
   __device__ __forceinline__ static void sub(uint32_t (&x)[P], const uint32_t (&y)[P]) { x[0] ^= y[0]; }
   __device__ __forceinline__ static void accumulate(uint32_t (&acc)[P], const uint32_t (&t)[D][P]) {
     acc[0] ^= t[0][0];
   }
   __device__ __forceinline__ static void canon(uint32_t (&)[P]) {}
+  __device__ __forceinline__ static void finish(const uint32_t (&acc)[AP], uint32_t (&x)[P]) { x[0] = acc[0]; }
   __device__ __forceinline__ static void phi(const uint64_t (&a)[P], uint64_t (&ph)[D]) { ph[0] = a[0]; }
 };
 
@@ -31,7 +34,7 @@ struct F2 {
 // Codes (x0, x1): 0 = (0,0), 1 = (1,0), -1 = (1,1) (Section 4.1); basis {1, -1},
 // phi_0(a) = [a = 1], phi_1(a) = [a = -1].
 struct F3 {
-  static constexpr int Q = 3, P = 2, D = 2;
+  static constexpr int Q = 3, P = 2, D = 2, AP = P;
 
   // x += y.  Section 4.1's six-gate add, with its outputs in the order that
   // makes it exact (x0 = unit, x1 = sign), fused into four LOP3s:
@@ -66,6 +69,10 @@ struct F3 {
     sub(acc[0], acc[1], t[1][0], t[1][1]);
   }
   __device__ __forceinline__ static void canon(uint32_t (&)[P]) {}
+  __device__ __forceinline__ static void finish(const uint32_t (&acc)[AP], uint32_t (&x)[P]) {
+    x[0] = acc[0];
+    x[1] = acc[1];
+  }
   __device__ __forceinline__ static void phi(const uint64_t (&a)[P], uint64_t (&ph)[D]) {
     ph[0] = a[0] & ~a[1];
     ph[1] = a[0] & a[1];
@@ -76,7 +83,7 @@ struct F3 {
 // GF(4) = F_2[x]/(x^2+x+1), element a0 + alpha a1, codes (a0, a1) (Section 4.3);
 // basis {1, alpha}, phi_d(a) = a_d; addition is XOR.
 struct GF4 {
-  static constexpr int Q = 4, P = 2, D = 2;
+  static constexpr int Q = 4, P = 2, D = 2, AP = P;
   __device__ __forceinline__ static void add(uint32_t (&x)[P], const uint32_t (&y)[P]) {
     x[0] ^= y[0];
     x[1] ^= y[1];
@@ -88,6 +95,10 @@ struct GF4 {
     acc[1] = lop3<0x96>(acc[1], t[0][1], t[1][0]) ^ t[1][1];
   }
   __device__ __forceinline__ static void canon(uint32_t (&)[P]) {}
+  __device__ __forceinline__ static void finish(const uint32_t (&acc)[AP], uint32_t (&x)[P]) {
+    x[0] = acc[0];
+    x[1] = acc[1];
+  }
   __device__ __forceinline__ static void phi(const uint64_t (&a)[P], uint64_t (&ph)[D]) {
     ph[0] = a[0];
     ph[1] = a[1];
@@ -110,7 +121,7 @@ __device__ __forceinline__ void ripple3(const uint32_t (&x)[3], const uint32_t (
 
 // ------------------------------------------------------------------ F_7 ----
 struct F7 {
-  static constexpr int Q = 7, P = 3, D = 3;
+  static constexpr int Q = 7, P = 3, D = 3, AP = P;
   // x += y: s = add(x, y); x = add(s2 s1 s0, s3) -- the carry out of bit 2 is the
   // unit bit mod 7 (Section 4.2); the second add never carries out.
   __device__ __forceinline__ static void add(uint32_t (&x)[P], const uint32_t (&y)[P]) {
@@ -160,6 +171,11 @@ struct F7 {
     x[1] ^= c;
     x[2] ^= c;
   }
+  __device__ __forceinline__ static void finish(const uint32_t (&acc)[AP], uint32_t (&x)[P]) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) x[p] = acc[p];
+    canon(x);
+  }
   __device__ __forceinline__ static void phi(const uint64_t (&a)[P], uint64_t (&ph)[D]) {
     const uint64_t c = a[0] & a[1] & a[2];
     ph[0] = a[0] ^ c;
@@ -170,7 +186,8 @@ struct F7 {
 
 // ------------------------------------------------------------------ F_5 ----
 struct F5 {
-  static constexpr int Q = 5, P = 3, D = 3;
+  // the accumulator is a four-bit value mod 15 (= 3 x 5), folded to a code once
+  static constexpr int Q = 5, P = 3, D = 3, AP = 4;
   // fold5: the 4-bit s3 s2 s1 s0 folded to three bits with the same value mod 5
   // (Section 4.2, its eight-operation form).
   __device__ __forceinline__ static void fold5(uint32_t s0, uint32_t s1, uint32_t s2, uint32_t s3,
@@ -200,13 +217,15 @@ struct F5 {
     neg(y, n);
     add(x, n);
   }
-  // acc += t0 + 2 t1 + 4 t2, computed mod 15 = 3 * 5 and folded back to F_5.
-  // Mod 15 (16 = 1) doubling a 4-bit number rotates it and carry-save adders
-  // wrap their carry, as for F_7 mod 7: 2 t1 = (0, t1_0, t1_1, t1_2) and
-  // 4 t2 = (t2_2, 0, t2_0, t2_1) as 4-bit numbers.  Two carry-save adders take
-  // acc, t0, 2 t1, 4 t2 to two 4-bit numbers, one end-around add to one, and
-  // fold5 (Section 4.2) to a 3-bit code with the same value mod 5.
-  __device__ __forceinline__ static void accumulate(uint32_t (&acc)[P], const uint32_t (&t)[D][P]) {
+  // acc += t0 + 2 t1 + 4 t2 for a four-bit accumulator mod 15 = 3 * 5 (its
+  // value mod 5 is the F_5 element).  Mod 15 (16 = 1) doubling a 4-bit number
+  // rotates it and carry-save adders wrap their carry, as for F_7 mod 7:
+  // 2 t1 = (0, t1_0, t1_1, t1_2) and 4 t2 = (t2_2, 0, t2_0, t2_1) as 4-bit
+  // numbers.  Two carry-save adders take acc, t0, 2 t1, 4 t2 to two 4-bit
+  // numbers and one end-around add to one (at most 15: u + w <= 30, so the
+  // carry added back at bit 0 cannot carry out again).  No fold per step:
+  // `finish` applies Section 4.2's fold5 once, when the product is stored.
+  __device__ __forceinline__ static void accumulate(uint32_t (&acc)[AP], const uint32_t (&t)[D][P]) {
     // first carry-save adder on x = t0, y = 2 t1, z = 4 t2 (zero bits dropped)
     uint32_t s[4], m[4];
     s[0] = t[0][0] ^ t[2][2];
@@ -219,15 +238,13 @@ struct F5 {
     m[3] = t[1][2] & t[2][1];
     // carry vector rotated: weight 16 = 1 mod 15
     const uint32_t c[4] = {m[3], m[0], m[1], m[2]};
-    // second carry-save adder with acc (3 bits)
+    // second carry-save adder with acc (4 bits)
     uint32_t u[4], v[4];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
       u[i] = lop3<0x96>(acc[i], s[i], c[i]);
       v[i] = lop3<0xE8>(acc[i], s[i], c[i]);
     }
-    u[3] = s[3] ^ c[3];
-    v[3] = s[3] & c[3];
     const uint32_t w[4] = {v[3], v[0], v[1], v[2]};
     // u + w mod 15: 4-bit add, then the carry out added back at bit 0
     uint32_t r[4];
@@ -240,11 +257,15 @@ struct F5 {
     }
     const uint32_t a0 = r[0] & k;
     const uint32_t b0 = r[1] & a0;
-    const uint32_t q0 = r[0] ^ k;
-    const uint32_t q1 = r[1] ^ a0;
-    const uint32_t q2 = r[2] ^ b0;
-    const uint32_t q3 = r[3] ^ (r[2] & b0);
-    fold5(q0, q1, q2, q3, acc);
+    acc[0] = r[0] ^ k;
+    acc[1] = r[1] ^ a0;
+    acc[2] = r[2] ^ b0;
+    acc[3] = r[3] ^ (r[2] & b0);
+  }
+  // The accumulator (mod 15) to a canonical F_5 code: fold5, then canon.
+  __device__ __forceinline__ static void finish(const uint32_t (&acc)[AP], uint32_t (&x)[P]) {
+    fold5(acc[0], acc[1], acc[2], acc[3], x);
+    canon(x);
   }
   // Canonical code: 5, 6, 7 -> 0, 1, 2 (c marks codes >= 5).  Section 4.2's
   // printed reduce is not a reduction; this one is derived from the code table.

@@ -48,9 +48,11 @@ struct M4rmCfg {
   static constexpr int RS = RS_;    // row slots per warp
   static constexpr int NW = NW_;    // warps per CTA
   static constexpr int P = F::P, D = F::D;
+  static constexpr int AP = F::AP;            // accumulator planes (F_5: four, mod 15)
   static constexpr int GPW = 32 / LPR;
   static constexpr int NT = NW * 32;
   static constexpr int PW = P * WPL;          // 32-bit words per lane per entry
+  static constexpr int APW = AP * WPL;        // 32-bit accumulator words per lane and row slot
   static constexpr int VB = 128 / LPR;        // bytes per lane per load
   static constexpr int VW = VB / 4;           // 32-bit words per lane per load
   static_assert(PW % VW == 0, "lane data must be whole vector loads");
@@ -286,11 +288,11 @@ __device__ __forceinline__ void build_table(uint32_t tbl_lane, uint32_t stage, i
 // pipeline.  PARTIAL = true: slots from `slots` on hold no row of the tile and
 // are skipped (tiles much shorter than the kernel's height).
 template <class Cfg, bool PARTIAL = false>
-__device__ __forceinline__ void lookup_block(uint32_t (&acc)[Cfg::RS][Cfg::PW], uint32_t tbl_lane,
+__device__ __forceinline__ void lookup_block(uint32_t (&acc)[Cfg::RS][Cfg::APW], uint32_t tbl_lane,
                                              const typename Cfg::Off *offs_b, int warp, int grp, uint32_t one,
                                              unsigned *err, int slots = Cfg::RS) {
   using F = typename Cfg::Field;
-  constexpr int P = Cfg::P, D = Cfg::D, WPL = Cfg::WPL, PW = Cfg::PW, CH = Cfg::CH, VW = Cfg::VW;
+  constexpr int P = Cfg::P, D = Cfg::D, AP = Cfg::AP, WPL = Cfg::WPL, PW = Cfg::PW, CH = Cfg::CH, VW = Cfg::VW;
 #pragma unroll
   for (int i = 0; i < Cfg::RS; ++i) {
     if (!PARTIAL || i < slots) {
@@ -317,51 +319,51 @@ __device__ __forceinline__ void lookup_block(uint32_t (&acc)[Cfg::RS][Cfg::PW], 
       }
 #pragma unroll
       for (int w = 0; w < WPL; ++w) {
-        uint32_t a[P], tt[D][P];
+        uint32_t a[AP], tt[D][P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-          a[p] = acc[i][p * WPL + w];
+        for (int p = 0; p < AP; ++p) a[p] = acc[i][p * WPL + w];
+#pragma unroll
+        for (int p = 0; p < P; ++p)
 #pragma unroll
           for (int d = 0; d < D; ++d) tt[d][p] = t[d][p * WPL + w];
-        }
         F::accumulate(a, tt);
 #pragma unroll
-        for (int p = 0; p < P; ++p) acc[i][p * WPL + w] = a[p];
+        for (int p = 0; p < AP; ++p) acc[i][p * WPL + w] = a[p];
       }
     }
   }
 }
 
 template <class Cfg>
-__device__ __forceinline__ void store_tile(uint32_t (&acc)[Cfg::RS][Cfg::PW], const M4rmParams &prm,
+__device__ __forceinline__ void store_tile(uint32_t (&acc)[Cfg::RS][Cfg::APW], const M4rmParams &prm,
                                            int64_t row0, int rows_here, int64_t w0, int warp, int grp, int gl) {
   using F = typename Cfg::Field;
-  constexpr int P = Cfg::P, WPL = Cfg::WPL;
+  constexpr int P = Cfg::P, AP = Cfg::AP, WPL = Cfg::WPL;
 #pragma unroll
   for (int i = 0; i < Cfg::RS; ++i) {
     const int r = i * Cfg::ROWS_PER_SLOT + warp * Cfg::GPW + grp;
     if (r < rows_here && debug_ok(row0 + r < prm.m && w0 + Cfg::CTW <= prm.pc, prm.err)) {
       const int64_t row = row0 + r;
+      uint32_t out[P * WPL];  // canonical codes, plane-major like the accumulator
 #pragma unroll
       for (int w = 0; w < WPL; ++w) {
-        uint32_t a[P];
+        uint32_t a[AP], x[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) a[p] = acc[i][p * WPL + w];
-        F::canon(a);
+        for (int p = 0; p < AP; ++p) a[p] = acc[i][p * WPL + w];
+        F::finish(a, x);
 #pragma unroll
-        for (int p = 0; p < P; ++p) acc[i][p * WPL + w] = a[p];
+        for (int p = 0; p < P; ++p) out[p * WPL + w] = x[p];
       }
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         uint32_t *dst = reinterpret_cast<uint32_t *>(prm.C + (p * prm.m + row) * prm.pc + w0) + gl * WPL;
         if constexpr (WPL == 4) {
-          *reinterpret_cast<uint4 *>(dst) =
-              make_uint4(acc[i][p * 4 + 0], acc[i][p * 4 + 1], acc[i][p * 4 + 2], acc[i][p * 4 + 3]);
+          *reinterpret_cast<uint4 *>(dst) = make_uint4(out[p * 4 + 0], out[p * 4 + 1], out[p * 4 + 2], out[p * 4 + 3]);
         } else if constexpr (WPL == 2) {
-          *reinterpret_cast<uint2 *>(dst) = make_uint2(acc[i][p * 2 + 0], acc[i][p * 2 + 1]);
+          *reinterpret_cast<uint2 *>(dst) = make_uint2(out[p * 2 + 0], out[p * 2 + 1]);
         } else {
           static_assert(WPL == 1, "lane slice of one, two or four words");
-          dst[0] = acc[i][p];
+          dst[0] = out[p];
         }
       }
     }
@@ -401,11 +403,11 @@ __global__ void __launch_bounds__(Cfg::NT, 1)
   }
   if (prm.nblocks > 0) stage_a<Cfg>(prm, astage_s, row0, rows_here, 0, tid);
 
-  uint32_t acc[Cfg::RS][Cfg::PW];
+  uint32_t acc[Cfg::RS][Cfg::APW];
 #pragma unroll
   for (int i = 0; i < Cfg::RS; ++i)
 #pragma unroll
-    for (int j = 0; j < Cfg::PW; ++j) acc[i][j] = 0u;
+    for (int j = 0; j < Cfg::APW; ++j) acc[i][j] = 0u;
 
   for (int64_t c0 = 0; c0 < prm.nblocks; c0 += Cfg::NB) {
     const int nb = int(prm.nblocks - c0 < Cfg::NB ? prm.nblocks - c0 : Cfg::NB);
