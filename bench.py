@@ -83,9 +83,10 @@ ALU_PEAK_TLOPS = 64 * 152 * 2.070e9 / 1e12
 # LOOKUP_LOP3 for one row and k-row block (its D lookups accumulated: F_3 an
 # add and a subtract of four LOP3s each; GF(4) two three-input XORs and one
 # XOR; F_7 two carry-save adders mod 7 and one add; F_5 two carry-save adders
-# and an end-around add mod 15, then fold5), TABLE_LOP3 for one table entry
-# (one bitsliced add: F_3 4, GF(4) 2, F_7 10, F_5 11).
-LOOKUP_LOP3 = {3: 8, 4: 3, 5: 35, 7: 22}
+# and an end-around add into a four-bit accumulator mod 15, folded once at the
+# store), TABLE_LOP3 for one table entry (one bitsliced add: F_3 4, GF(4) 2,
+# F_7 10, F_5 11).
+LOOKUP_LOP3 = {3: 8, 4: 3, 5: 30, 7: 22}
 TABLE_LOP3 = {3: 4, 4: 2, 5: 11, 7: 10}
 PLANES = {2: 1, 3: 2, 4: 2, 5: 3, 7: 3}
 L2_FLUSH_BYTES = 256 << 20
