@@ -384,6 +384,13 @@ int fq_status(void *stream);
 int fq_debug_wait_limit(int64_t ns);
 int fq_debug_stall_block(int64_t block);
 
+/* Failure-path hook for host memory: after `after` further host allocation
+ * points of batched-plan building (creation and fq_batched_plan_upload's host
+ * image of the tables), the next one fails as an exhausted heap would, and
+ * the call returns FQ_ENOMEM with no plan made and nothing enqueued; the hook
+ * then disarms.  after < 0 disarms it.  Process-wide; host only; for tests. */
+int fq_debug_fail_host_alloc(int64_t after);
+
 /* Static text for a status code. */
 const char *fq_error_string(int status);
 

@@ -11,6 +11,7 @@
 // launch allocates nothing and never waits on the host, so it can be captured
 // in a CUDA graph and replayed.
 #include <algorithm>
+#include <atomic>
 #include <exception>
 #include <memory>
 #include <cstdlib>
@@ -276,6 +277,22 @@ namespace {
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// fq_debug_fail_host_alloc: the countdown of host allocation points before
+// one fails (-1: none armed).
+std::atomic<int64_t> g_fail_alloc{-1};
+
+// A host allocation point of plan building: throws std::bad_alloc, as a
+// failed allocation would, when the armed countdown reaches it.
+void host_alloc_point() {
+  int64_t left = g_fail_alloc.load(std::memory_order_relaxed);
+  while (left >= 0) {
+    if (g_fail_alloc.compare_exchange_weak(left, left - 1, std::memory_order_relaxed)) {
+      if (left == 0) throw std::bad_alloc();
+      return;
+    }
+  }
+}
+
 // Modelled SM-cycles per unit of the batched Four-Russians item cost (table
 // entries + rows x basis size per block), fitted to the 4096-product batch
 // on GB300: F_3 and GF(4) run two CTAs per SM.
@@ -298,6 +315,7 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
   *out = nullptr;
   if (!(q == 3 || q == 4 || q == 5 || q == 7) || count < 0 || (count > 0 && (!m || !l || !n))) return FQ_EINVAL;
   if (!(path == FQ_PATH_AUTO || path == FQ_PATH_M4RM || path == FQ_PATH_MMA)) return FQ_EINVAL;
+  host_alloc_point();
   std::unique_ptr<fq_batch_plan> plan(new (std::nothrow) fq_batch_plan());
   if (!plan) return FQ_ENOMEM;
   plan->q = q;
@@ -326,12 +344,14 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
     bp.pc = fq_pitch_words(n[p]);
     bp.a_row0 = 0;
     bp.b_row0 = 0;
+    host_alloc_point();
     plan->tc_prods.push_back(bp);
   };
   for (int p = 0; p < count; ++p) {
     if (m[p] < 0 || l[p] < 0 || n[p] < 0 || m[p] >= (int64_t(1) << 31) || l[p] >= (int64_t(1) << 31) ||
         n[p] >= (int64_t(1) << 31))
       return FQ_EINVAL;
+    host_alloc_point();
     plan->shapes.push_back(Shape{m[p], l[p], n[p]});
     if (m[p] == 0 || n[p] == 0) continue;
     // Four-Russians items of this product and their modelled cost
@@ -418,7 +438,10 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
   // longest first
   std::stable_sort(costed.begin(), costed.end(),
                    [](const std::pair<double, Item> &a, const std::pair<double, Item> &b) { return a.first > b.first; });
-  for (auto &c : costed) plan->items.push_back(c.second);
+  for (auto &c : costed) {
+    host_alloc_point();
+    plan->items.push_back(c.second);
+  }
   // tcgen05 work: whole products to the kTcCtas persistent CTAs, longest
   // first, each to the least-loaded CTA by the modelled cost; a CTA then takes
   // its products smallest first (the first one's conversion is the only one
@@ -504,6 +527,7 @@ int host_guard(Fn &&fn) {
 // The host image of a plan's tables (header .. tile list).
 std::vector<unsigned char> plan_tables(const fq_batch_plan *plan) {
   using namespace fqk::batched;
+  host_alloc_point();
   std::vector<unsigned char> host(size_t(plan->table_bytes), 0);
   Header h{};
   h.next = 0;
@@ -601,6 +625,11 @@ int fq_batched_product_path(const fq_batch_plan *plan, int p) {
   for (const fqk::BatchProd &bp : plan->tc_prods)
     if (bp.p == p) return FQ_PATH_MMA;
   return FQ_PATH_M4RM;
+}
+
+int fq_debug_fail_host_alloc(int64_t after) {
+  g_fail_alloc.store(after >= 0 ? after : -1, std::memory_order_relaxed);
+  return FQ_OK;
 }
 
 int fq_batched_plan_destroy(fq_batch_plan *plan) {

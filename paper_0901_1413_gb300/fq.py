@@ -90,6 +90,7 @@ def _bind(lib):
         "fq_batched_product_path": (i32, [vp, i32]),
         "fq_debug_wait_limit": (i32, [i64]),
         "fq_debug_stall_block": (i32, [i64]),
+        "fq_debug_fail_host_alloc": (i32, [i64]),
         "fq_batched_plan_destroy": (i32, [vp]),
         "fq_autotune": (i32, [i32, i64, i64, i64, vp, vp, vp, vp, vp]),
         "fq_autotune_lookup": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),

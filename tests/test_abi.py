@@ -373,3 +373,37 @@ def test_autotune_cache_save_and_load(lib, tmp_path):
     assert lib.fq_autotune_save(str(dst).encode()) == fq.OK
     assert json.loads(dst.read_text())["entries"] == []
     assert before  # the earlier save was a full document
+
+
+def test_injected_host_allocation_failure(lib):
+    """Every host allocation point of plan building, made to fail in turn,
+    gives FQ_ENOMEM and no plan; past the last point the plan is made; the
+    upload's host image of the tables fails before any device call."""
+    import numpy as np
+    from paper_0901_1413_gb300 import fq
+    i64p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    m = np.array([100, 2000, 0, 64], np.int64)
+    l = np.array([70, 64, 5, 0], np.int64)
+    n = np.array([600, 64, 9, 1100], np.int64)
+    h = ctypes.c_void_p()
+    failures = 0
+    try:
+        for after in range(200):
+            assert lib.fq_debug_fail_host_alloc(after) == fq.OK
+            rc = lib.fq_batched_plan_create_ex(3, 4, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h))
+            if rc == fq.OK:
+                break
+            assert rc == fq.ENOMEM
+            assert not h.value
+            failures += 1
+        else:
+            raise AssertionError("plan creation never succeeded")
+        assert failures >= 6          # the plan object, four shapes, a tcgen05 product, an item ...
+        lib.fq_debug_fail_host_alloc(-1)
+        assert lib.fq_batched_tc_products(h) == 2
+        lib.fq_debug_fail_host_alloc(0)
+        assert lib.fq_batched_plan_upload(h, ctypes.c_void_p(64), None) == fq.ENOMEM
+    finally:
+        lib.fq_debug_fail_host_alloc(-1)
+        if h.value:
+            lib.fq_batched_plan_destroy(h)
