@@ -116,7 +116,9 @@ typedef struct fq_options {
   int kernel;    /* M4RM kernel: 0 = planner, i + 1 = compiled kernel i of field q;
                     tensor-core path: 0 = tcgen05 by shape, 1 = the mma.sync
                     s8 form, 2 = tcgen05 on single SMs (128 x 256 tiles),
-                    3 = on SM pairs (256 x 256), 4 = on SM pairs (256 x 512) */
+                    3 = on SM pairs (256 x 256), 4 = on SM pairs (256 x 512),
+                    all three from e4m3 operands; 5 = on SM pairs (256 x 448)
+                    from packed e2m1 operands (kind::mxf4)                  */
   int strassen;  /* Strassen-Winograd levels over the base-field products: 0 = the
                     time model decides, -1 = none, L > 0 = L levels (each needs
                     m, l, n to be multiples of 2048 at that level)               */
@@ -159,22 +161,34 @@ int fq_matmul_ex(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A,
 int fq_strassen_levels(int q, int64_t m, int64_t l, int64_t n, const fq_options *opt);
 
 /* ---- the tensor-core path in two stages -------------------------------------
- * FQ_PATH_MMA runs on the tcgen05 tensor cores (kind::f8f6f4: e4m3 operands,
- * fp32 accumulation) whenever l * ((p-1)/2)^2 < 2^24 (l < 2^24 for GF(4)):
- * the balanced residues 0, +-1, +-2, +-3 are exact in e4m3 and every partial
- * sum is an integer below 2^24, so the fp32 sums are exact and the product is
- * bit-exact.  Longer l, or fq_options.chunk > 0, or fq_options.kernel = 1
- * select the mma.sync s8 form with mod-p reduction every chunk.  fq_matmul
- * converts the operands into stream-ordered scratch; these calls expose the
- * two stages so that a caller can keep the converted operands:
- *   fq_tc_workspace_bytes: device bytes of the converted operands (A as m x la
- *     e4m3 bytes, B transposed as 64 * fq_pitch_words(n) x la, la = l rounded
- *     up to 128; three such pairs for GF(4), whose product is three F_2
- *     products by Section 4.3's Karatsuba form), or -1 outside the tcgen05
- *     form (bad q, negative size, l too long);
+ * FQ_PATH_MMA runs on the tcgen05 tensor cores whenever l * ((p-1)/2)^2 < 2^24
+ * (l < 2^24 for GF(4)), in one of two operand formats:
+ *   - kind::f8f6f4 with e4m3 operands (forms 2, 3, 4: single SMs, SM pairs
+ *     with 256 x 256 tiles, SM pairs with 256 x 512 tiles);
+ *   - kind::mxf4 with packed e2m1 operands, two to a byte, every block scale
+ *     factor 1.0 (form 5: SM pairs, 256 x 448 tiles), at twice the e4m3 rate.
+ * Both accumulate in fp32.  The balanced residues 0, +-1, +-2, +-3 are exact
+ * in e4m3 and in e2m1, and every partial sum is an integer below 2^24, so the
+ * sums are exact and the product is bit-exact.  By shape, products of at most
+ * 128 rows take form 2, products of more rows and l >= 2048 form 5, the rest
+ * form 3 (fq_tc_form); fq_options.kernel = 2 .. 5 forces a form.  Longer l, or
+ * fq_options.chunk > 0, or fq_options.kernel = 1 select the mma.sync s8 form
+ * with mod-p reduction every chunk.  fq_matmul converts the operands into
+ * stream-ordered scratch; these calls expose the two stages (in the shape's
+ * default form) so that a caller can keep the converted operands:
+ *   fq_tc_form: the form (2 .. 5) the shape takes, or -FQ_ENOTSUP outside the
+ *     tcgen05 path's range, -FQ_EINVAL for a bad q or size.  Host-only;
+ *   fq_tc_workspace_bytes: device bytes of the converted operands, or -1
+ *     outside the tcgen05 form (bad q, negative size, l too long).  Forms 2, 3,
+ *     4: A as m x la e4m3 bytes, B transposed as 64 * fq_pitch_words(n) x la,
+ *     la = l rounded up to 128.  Form 5: A as m rows and B transposed as
+ *     64 * fq_pitch_words(n) rows of la / 2 bytes, la = l rounded up to 256.
+ *     Three such pairs for GF(4), whose product is three F_2 products by
+ *     Section 4.3's Karatsuba form;
  *   fq_tc_prepare: A, B (planes buffers) -> workspace (16-byte aligned);
  *   fq_tc_multiply: workspace -> C (planes buffer, written entirely).
  * Both are asynchronous on `stream`; FQ_ENOTSUP outside the tcgen05 form. */
+int fq_tc_form(int q, int64_t m, int64_t l, int64_t n);
 int64_t fq_tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n);
 int fq_tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B,
                   void *workspace, void *stream);

@@ -223,6 +223,11 @@ int64_t fq_tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n) {
   return fqk::tc_workspace_bytes(q, m, l, n);
 }
 
+int fq_tc_form(int q, int64_t m, int64_t l, int64_t n) {
+  if (fq_tc_workspace_bytes(q, m, l, n) < 0) return base_q(q) && m >= 0 && l >= 0 && n >= 0 ? -FQ_ENOTSUP : -FQ_EINVAL;
+  return fqk::tc_form(m, l);
+}
+
 int fq_tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, void *workspace,
                   void *stream) {
   if (fq_tc_workspace_bytes(q, m, l, n) < 0) return base_q(q) && m >= 0 && l >= 0 && n >= 0 ? FQ_ENOTSUP : FQ_EINVAL;

@@ -23,19 +23,23 @@ int launch_mma(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const 
 // beyond the exact fp32 range of the field (tc_max_l).
 struct TcOptions {
   int form = 0;   // 0: by shape; 2: single SMs; 3: SM pairs, 256-column tiles; 4: SM pairs, 512-column tiles
+                  // (these three from e4m3 operands); 5: SM pairs, 448-column tiles from packed e2m1 (fp4)
   int group = 0;  // row blocks per group of the tile order (0: 8)
 };
 int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
               cudaStream_t s, const TcOptions &to = TcOptions());
 int64_t tc_max_l(int q);
 // Its two stages on a caller's workspace (bytes: tc_workspace_bytes, -1 if
-// the product is outside the tcgen05 form): operands to e4m3, then the product.
-int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n);
+// the product is outside the tcgen05 form): operands to e4m3 or packed e2m1
+// (by the form, which both stages must be given alike), then the product.
+int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n, const TcOptions &to = TcOptions());
 int tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, void *ws,
-               cudaStream_t s);
+               cudaStream_t s, const TcOptions &to = TcOptions());
 int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t *C, cudaStream_t s,
                 const TcOptions &to = TcOptions());
 double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms);
+// The tcgen05 product form a shape takes by default (2 .. 5, as TcOptions::form).
+int tc_form(int64_t m, int64_t l);
 
 // Batched products on the tcgen05 path.  The plan gives every product to one
 // of kTcCtas persistent CTAs (longest first, each to the least-loaded CTA).  A

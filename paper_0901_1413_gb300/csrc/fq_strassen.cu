@@ -112,13 +112,13 @@ int direct(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint
     }
   }
   if (path == FQ_PATH_MMA) {
-    // tcgen05 (e4m3, exact fp32 sums) unless a reduction chunk or the
-    // mma.sync s8 form (kernel = 1) is requested, or l is beyond its exact
-    // range; kernel = 2, 3, 4 force its single-SM, SM-pair or wide SM-pair
-    // kernel
+    // tcgen05 (e4m3 or packed e2m1, exact fp32 sums) unless a reduction
+    // chunk or the mma.sync s8 form (kernel = 1) is requested, or l is beyond
+    // its exact range; kernel = 2, 3, 4 force its single-SM, SM-pair or wide
+    // SM-pair e4m3 kernel, 5 the fp4 SM-pair kernel
     if (o.chunk == 0 && o.kernel != 1 && l <= tc_max_l(q)) {
       TcOptions to;
-      to.form = o.kernel >= 2 && o.kernel <= 4 ? o.kernel : 0;
+      to.form = o.kernel >= 2 && o.kernel <= 5 ? o.kernel : 0;
       to.group = o.variant;
       return launch_tc(q, m, l, n, A, B, C, s, to);
     }

@@ -281,6 +281,164 @@ __global__ void __launch_bounds__(256) planes_to_e4m3_t(const uint64_t *__restri
   transpose_block<Q, P>(X, rows, pitch, out + j0 * ld + off + k0, ld, kcols, int64_t(1) << 62, sel, k0, j0, tile);
 }
 
+// ------------------------------------------- packed e2m1 (fp4) operands --
+//
+// The fp4 form feeds the same balanced residues to tcgen05.mma kind::mxf4
+// (packed e2m1, two elements to a byte, block scale factors all 1.0), which
+// runs at twice the e4m3 rate and takes half the operand bytes.  e2m1 has a
+// sign bit, two exponent bits biased by 1 and one mantissa bit: 0, 1, 2, 3 are
+// 0000, 0010, 0100, 0101 and the sign is bit 3, so 0, +-1, +-2, +-3 are exact.
+// Both operands are K-major: element k of a row is nibble k of the row (the
+// low nibble of byte k / 2 for even k).  Which nibble the tensor core takes
+// first does not matter, since A and B pair the same positions.
+__host__ __device__ constexpr uint32_t e2m1_nibble(int v) {
+  return v == 0 ? 0u : ((v < 0 ? 8u : 0u) | ((v == 1 || v == -1) ? 2u : ((v == 2 || v == -2) ? 4u : 5u)));
+}
+
+// Bit b of the e2m1 nibble of a 3-bit code, as a LOP3 truth table of (plane
+// 2, plane 1, plane 0): the table's index is then the code itself.
+template <int Q>
+__host__ __device__ constexpr int nibble_lut(int b) {
+  int lut = 0;
+  for (int c = 0; c < 8; ++c) lut |= int((e2m1_nibble(code_value<Q>(c)) >> b) & 1u) << c;
+  return lut;
+}
+
+// Bits 0..7 of x spread to bits 0, 4, ..., 28.
+__device__ __forceinline__ uint32_t spread8(uint32_t x) {
+  x = (x | (x << 12)) & 0x000F000Fu;
+  x = (x | (x << 6)) & 0x03030303u;
+  return (x | (x << 3)) & 0x11111111u;
+}
+
+// 32 elements (bit i of the plane words t) as 32 packed e2m1 nibbles, element
+// i in bits 4 (i % 8) .. of word i / 8.  The nibble's bits are first formed
+// 32 elements at a time as bit-planes: F_2 (and a selected GF(4) plane) puts
+// the element in bit 1 (1.0); F_3 puts the unit in bit 1 and the sign in bit
+// 3 (the unused code 2 gives -0, which adds nothing); F_5 and F_7 take one
+// LOP3 per nibble bit over the three code planes.
+template <int Q, int P>
+__device__ __forceinline__ uint4 e2m1x32(const uint32_t (&t)[P]) {
+  uint32_t nb[4];
+  if constexpr (Q == 2) {
+    nb[0] = 0u; nb[1] = t[0]; nb[2] = 0u; nb[3] = 0u;
+  } else if constexpr (Q == 3) {
+    nb[0] = 0u; nb[1] = t[0]; nb[2] = 0u; nb[3] = t[1];
+  } else {
+    nb[0] = lop3<nibble_lut<Q>(0)>(t[2], t[1], t[0]);
+    nb[1] = lop3<nibble_lut<Q>(1)>(t[2], t[1], t[0]);
+    nb[2] = lop3<nibble_lut<Q>(2)>(t[2], t[1], t[0]);
+    nb[3] = lop3<nibble_lut<Q>(3)>(t[2], t[1], t[0]);
+  }
+  uint32_t o[4];
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    uint32_t x = 0u;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if ((Q == 2 || Q == 3) && (b == 0 || b == 2)) continue;
+      if (Q == 2 && b == 3) continue;
+      x |= spread8((nb[b] >> (8 * w)) & 0xFFu) << b;
+    }
+    o[w] = x;
+  }
+  return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+// Rows of a planes matrix to packed e2m1: byte c / 2 of out[r * ld ..] holds
+// elements c and c + 1 of row r, for c < cols (a multiple of 32, which may run
+// into the planes' zero padding, giving zeros).  One thread per 32 elements
+// (one 32-bit plane word in, a 16-byte store out, so that a warp writes 512
+// contiguous bytes); a thread loads the next group of RPT rows' words before
+// it converts the current one.
+template <int Q, int P>
+__global__ void rows_to_fp4(const uint64_t *__restrict__ X, int64_t rows, int64_t cols, int64_t pitch,
+                            uint8_t *__restrict__ out, int64_t ld, int sel) {
+  using CF = ConvField<Q>;
+  const int64_t piece = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // the 32-bit word of the row
+  if (piece * 32 >= cols) return;
+  const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
+  auto load = [&](int64_t r0, uint32_t (&t)[RPT][P]) {
+#pragma unroll
+    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        t[i][p] = r0 + i < rows ? __ldg(X32 + (p * rows + r0 + i) * pitch * 2 + piece) : 0u;
+  };
+  const int64_t step = int64_t(gridDim.y) * RPT;
+  int64_t r0 = int64_t(blockIdx.y) * RPT;
+  uint32_t t[RPT][P], nt[RPT][P];
+  if (r0 < rows) load(r0, t);
+  for (; r0 < rows; r0 += step) {
+    if (r0 + step < rows) load(r0 + step, nt);
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      if (r0 + i >= rows) break;
+      uint32_t o[CF::P2];
+      select_planes<Q, P>(t[i], sel, o);
+      *reinterpret_cast<uint4 *>(out + (r0 + i) * ld + piece * 16) = e2m1x32<CF::Q2, CF::P2>(o);
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+      for (int p = 0; p < P; ++p) t[i][p] = nt[i][p];
+  }
+}
+
+// Launch shape of rows_to_fp4 for rows x cols (cols a multiple of 32): one
+// wave of 256-thread blocks (8 per SM on 152 SMs), each walking row groups.
+inline dim3 rows_grid4(int64_t rows, int64_t cols) {
+  const int64_t pieces = cols / 32, xs = cdiv(pieces, 256), groups = cdiv(rows, RPT);
+  const int64_t want = cdiv(int64_t(152) * 8, xs);
+  const int64_t ys = groups < want ? groups : want;
+  return dim3(unsigned(xs), unsigned(ys < 65535 ? (ys > 0 ? ys : 1) : 65535));
+}
+
+// B^T as packed e2m1 straight from B's planes: row j of out (ld bytes) holds
+// B[k][j] in nibble k, for every column j of the planes' pitch (n_pad = 64
+// pitch) and k < kcols (a multiple of 256; rows k >= rows read as zero).  A
+// CTA of eight warps turns a 256 (k) x 256 (j) block around: warp w loads rows
+// k0 + 32 w + lane, all 256 columns (four words of every plane), transposes
+// each 32 x 32 bit block across the warp, converts lane j's 32 bits into 16
+// bytes and puts them at chunk w of row j of a shared 256 x 128-byte tile
+// (16-byte chunks XOR-swizzled by row, so that eight lanes hit eight bank
+// groups); the tile leaves in 128-byte rows.
+constexpr int TK4 = 256, TJ4 = 256;
+template <int Q, int P>
+__global__ void __launch_bounds__(256) planes_to_fp4_t(const uint64_t *__restrict__ X, int64_t rows, int64_t pitch,
+                                                       uint8_t *__restrict__ out, int64_t ld, int64_t kcols, int sel) {
+  using CF = ConvField<Q>;
+  __shared__ uint4 tile[TJ4 * 8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k0 = int64_t(blockIdx.x) * TK4, j0 = int64_t(blockIdx.y) * TJ4;
+  const int64_t k = k0 + 32 * warp + lane;
+  uint32_t t[8][P];  // group g: columns j0 + 32 g .. + 31
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(X + (p * rows + k) * pitch + j0 / 64);
+    const uint4 v0 = k < rows ? __ldg(src) : make_uint4(0u, 0u, 0u, 0u);
+    const uint4 v1 = k < rows ? __ldg(src + 1) : make_uint4(0u, 0u, 0u, 0u);
+    t[0][p] = v0.x; t[1][p] = v0.y; t[2][p] = v0.z; t[3][p] = v0.w;
+    t[4][p] = v1.x; t[5][p] = v1.y; t[6][p] = v1.z; t[7][p] = v1.w;
+  }
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    uint32_t o[CF::P2];
+    select_planes<Q, P>(t[g], sel, o);
+#pragma unroll
+    for (int p = 0; p < CF::P2; ++p) o[p] = transpose32(o[p], lane);
+    const int jl = 32 * g + lane;  // lane: column j0 + jl, bit i = row k0 + 32 warp + i
+    tile[jl * 8 + (warp ^ (jl & 7))] = e2m1x32<CF::Q2, CF::P2>(o);
+  }
+  __syncthreads();
+  uint8_t *blk = out + j0 * ld + k0 / 2;
+#pragma unroll
+  for (int i = threadIdx.x; i < TJ4 * 8; i += 256) {
+    const int jl = i >> 3, c = i & 7;
+    if (k0 + 32 * c < kcols) *reinterpret_cast<uint4 *>(blk + jl * ld + 16 * c) = tile[jl * 8 + (c ^ (jl & 7))];
+  }
+}
+
 // ------------------------------------------------------------------ GEMM --
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
@@ -380,10 +538,39 @@ __device__ __forceinline__ void tile_coords(const GemmParams &prm, int t, int &m
   nb = in / rows;
 }
 
+// 32 accumulator values of one row (exact integers in fp32) reduced mod p and
+// packed into one 32-bit word per plane (value i at bit i), through four
+// independent partial words so that the bit-or chains are short.
+template <int Q, int P>
+__device__ __forceinline__ void pack32(const uint32_t (&v)[32], uint32_t (&h)[P]) {
+  uint32_t part[P][4];
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) part[p][j] = 0u;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int x = int(__uint_as_float(v[i]));  // an exact integer
+    const int mod = Q == 4 ? 2 : Q;
+    int r = x % mod;
+    r += r < 0 ? mod : 0;
+    if constexpr (Q == 3) {
+      part[0][i & 3] |= uint32_t(r != 0) << i;
+      part[1][i & 3] |= uint32_t(r == 2) << i;
+    } else if constexpr (Q == 4 || Q == 2) {
+      part[0][i & 3] |= uint32_t(r) << i;
+    } else {
+#pragma unroll
+      for (int p = 0; p < P; ++p) part[p][i & 3] |= uint32_t((r >> p) & 1) << i;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) h[p] = (part[p][0] | part[p][1]) | (part[p][2] | part[p][3]);
+}
+
 // NW 64-column words of one accumulator row (this lane's TMEM lane, from
-// column address taddr), reduced mod p and packed into plane words.  Each
-// 32-value load is packed through four independent partial words, so that
-// the bit-or chains are short.
+// column address taddr), reduced mod p and packed into plane words (pack32
+// per 32-value load).
 template <int Q, int P, int NW = BN / 64>
 __device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&words)[P][NW], int live = 2 * NW) {
 #pragma unroll
@@ -398,32 +585,12 @@ __device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&wor
       }
       continue;
     }
-    uint32_t v[32];
+    uint32_t v[32], hw[P];
     tmem_ld32(taddr + uint32_t(c * 32), v);
-    uint32_t part[P][4];
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) part[p][j] = 0u;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const int x = int(__uint_as_float(v[i]));  // an exact integer
-      const int mod = Q == 4 ? 2 : Q;
-      int r = x % mod;
-      r += r < 0 ? mod : 0;
-      if constexpr (Q == 3) {
-        part[0][i & 3] |= uint32_t(r != 0) << i;
-        part[1][i & 3] |= uint32_t(r == 2) << i;
-      } else if constexpr (Q == 4 || Q == 2) {
-        part[0][i & 3] |= uint32_t(r) << i;
-      } else {
-#pragma unroll
-        for (int p = 0; p < P; ++p) part[p][i & 3] |= uint32_t((r >> p) & 1) << i;
-      }
-    }
+    pack32<Q, P>(v, hw);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      const uint64_t h = (part[p][0] | part[p][1]) | (part[p][2] | part[p][3]);
+      const uint64_t h = hw[p];
       if (c & 1)
         words[p][c >> 1] |= h << 32;
       else
@@ -826,6 +993,246 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairGeo<WIDE>::THREA
   }
 }
 
+// ------------------------------------------------- fp4 CTA-pair product --
+//
+// The product on SM pairs from packed e2m1 operands (tcgen05.mma.cta_group::2
+// kind::mxf4, twice the e4m3 rate).  A 128-byte k-slice is 256 elements deep
+// and feeds four MMAs of K = 64, the same 32 bytes per MMA as the e4m3 form,
+// so the descriptors, the swizzle and the stage layout do not change.  The
+// block-scaled kind reads scale factors from TMEM: columns 448..511 of both
+// CTAs are filled once with ue8m0 1.0 (0x7F) in every byte, so whichever
+// bytes the hardware takes, every block is scaled by 1.0 and the sums stay
+// the exact integers of the e4m3 form.  That leaves 448 columns for the
+// accumulator: a pair owns 256 x 448 tiles (7 words of C), computed as two
+// MMAs of N = 224 per 64-deep step, each CTA staging its 128 rows of A and
+// 112 rows of each of the two B^T halves (44 KB a stage, 5 stages).  The
+// last column tile of a product is narrower (w = 64 pitch - 448 nb, a
+// multiple of 64): its halves take N_j = min(w - 224 j, 224) columns, and
+// CTA r loads B^T rows 224 j + r N_j / 2 .., so that accumulator column c is
+// always tile column c.  The accumulator is not double-buffered; twice as
+// many epilogue warps as in the 256 x 256 pair form drain it.
+namespace f4 {
+constexpr int NB = 448, HALF = 224, BROWS = HALF / 2;  // tile columns, per MMA, B^T rows per CTA per half
+constexpr int B_BYTES = BROWS * BK;                     // 14 KB (a whole number of 1 KB swizzle atoms)
+constexpr int STAGE = A2_BYTES + 2 * B_BYTES;
+constexpr int STAGES = 5;
+constexpr int BAR_OFF = STAGES * STAGE;
+constexpr int NBARS = 2 * STAGES + 2 + 1;  // full, empty, accfull, accempty, the MMA drain
+constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;
+constexpr int EPI = 8;                      // epilogue warps: lane quadrant warp % 4, column group (warp - 4) / 4
+constexpr int THREADS = 128 + 32 * EPI;
+constexpr int CHUNKS = NB / 32;             // 32-column accumulator loads per tile row
+constexpr uint32_t SF_COL = NB;             // scale factors: columns 448 .. 511
+static_assert(SMEM <= 232448, "shared memory per CTA");
+}  // namespace f4
+
+// kind::mxf4 instruction descriptor: E2M1 A and B (format 1, bits 7-9 and
+// 10-12), both K-major, N >> 3 (bits 17-22), ue8m0 scale factors (bit 23),
+// M = 256 (bits 24-28), scale-factor ids 0, dense K = 64.
+__host__ __device__ constexpr uint32_t idesc_mxf4_pair(int n) {
+  return (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (1u << 23) | (uint32_t(256 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_fp4_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                             uint32_t accumulate, uint32_t sf) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate), "r"(sf), "r"(sf + 32u)
+      : "memory");
+}
+
+// 32 TMEM columns of this warp's lane quadrant set to v.
+__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(v)
+      : "memory");
+}
+
+// Columns of tile nb of the fp4 pair form: 448, or what is left of the pitch.
+__device__ __forceinline__ int f4_width(const GemmParams &prm, int nb) {
+  const int64_t left = 64 * prm.pc - int64_t(f4::NB) * nb;
+  return left < f4::NB ? int(left) : f4::NB;
+}
+
+// Store 32-bit halves h of one row's plane words (half-word index h32 of C's
+// row).  GF(4): plane < 0 writes the F_2 result into both planes, else XORs it
+// into that plane.
+template <int Q, int P>
+__device__ __forceinline__ void store_half(const GemmParams &prm, int64_t row, int64_t h32, const uint32_t (&h)[P]) {
+  if (!debug_ok(row < prm.m && h32 < 2 * prm.pc, prm.err)) return;
+  uint32_t *C32 = reinterpret_cast<uint32_t *>(prm.C);
+  if constexpr (Q == 4) {
+    if (prm.plane < 0) {
+      C32[(row)*2 * prm.pc + h32] = h[0];
+      C32[(prm.m + row) * 2 * prm.pc + h32] = h[0];
+    } else {
+      C32[(int64_t(prm.plane) * prm.m + row) * 2 * prm.pc + h32] ^= h[0];
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) C32[(int64_t(p) * prm.m + row) * 2 * prm.pc + h32] = h[p];
+  }
+}
+
+template <int Q, int P>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(f4::THREADS, 1)
+    tc_gemm4_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const GemmParams prm) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned (128-byte swizzle atoms)
+  unsigned char *smem = smem_raw + (base - raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const uint32_t full = base + f4::BAR_OFF, empty = full + 8 * f4::STAGES, accfull = empty + 8 * f4::STAGES,
+                 accempty = accfull + 8, drain = accempty + 8;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + f4::BAR_OFF + 8 * f4::NBARS);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + f4::BAR_OFF + 8 * f4::NBARS + 8);
+
+  if (tid == 0) {
+    *abort_flag = 0;
+    for (int s = 0; s < f4::STAGES; ++s) {
+      mbar_init(full + 8 * s, 1);   // the leader's producer arrives; both CTAs' bytes complete it
+      mbar_init(empty + 8 * s, 1);  // one multicast commit
+    }
+    mbar_init(accfull, 1);
+    mbar_init(accempty, 2 * f4::EPI);  // the epilogue warps of both CTAs (the leader's barrier)
+    mbar_init(drain, 1);               // the leader's MMA drain
+    fence_mbar_init();
+  }
+  if (warp == 2) {  // one warp of each CTA allocates the pair's columns together
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  cluster_sync();  // both CTAs' barriers initialised, the columns allocated
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  if (warp >= 4 && warp < 8) {  // scale factors 1.0 (ue8m0 0x7F) in columns 448..511 of every lane
+    const uint32_t q0 = tmem + (uint32_t((warp & 3) * 32) << 16) + f4::SF_COL;
+    tmem_fill32(q0, 0x7F7F7F7Fu);
+    tmem_fill32(q0 + 32u, 0x7F7F7F7Fu);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync();  // both CTAs' scale factors are in place before the first MMA
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int cl = int(blockIdx.x >> 1), ncl = int(gridDim.x >> 1);
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer (both CTAs): this CTA's rows of A and of each B^T half
+    int it = 0;
+    for (int t = cl; t < prm.tiles && !*abort_flag; t += ncl) {
+      int mb, nb;
+      tile_coords(prm, t, mb, nb);
+      const int w = f4_width(prm, nb);
+      const int n0 = w < f4::HALF ? w : f4::HALF, n1 = w - n0;
+      const int halves = n1 > 0 ? 2 : 1;
+      for (int ks = 0; ks < prm.ksteps; ++ks, ++it) {
+        const int s = it % f4::STAGES;
+        if (it >= f4::STAGES) wait_bar(empty + 8 * s, uint32_t((it / f4::STAGES - 1) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+        if (leader) mbar_expect_tx(full + 8 * s, 2 * (A2_BYTES + halves * f4::B_BYTES));
+        const uint32_t bar = map_to_rank(full + 8 * s, 0);
+        const uint32_t a_dst = base + uint32_t(s * f4::STAGE), b_dst = a_dst + A2_BYTES;
+        tma_load_2d_pair(a_dst, &tmA, bar, ks * BK, mb * 256 + 128 * int(rank));
+        tma_load_2d_pair(b_dst, &tmB, bar, ks * BK, nb * f4::NB + int(rank) * (n0 / 2));
+        if (halves == 2)
+          tma_load_2d_pair(b_dst + uint32_t(f4::B_BYTES), &tmB, bar, ks * BK,
+                           nb * f4::NB + f4::HALF + int(rank) * (n1 / 2));
+      }
+    }
+    // The last commits to this CTA's stage barriers have landed before it
+    // exits (see tc_gemm2_kernel: a stage is committed only after its copies
+    // have landed, and these waits run with the default bound).
+    for (int j = it > f4::STAGES ? it - f4::STAGES : 0; j < it; ++j)
+      mbar_wait_bounded(empty + 8 * uint32_t(j % f4::STAGES), uint32_t((j / f4::STAGES) & 1));
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---- MMA issuer (the leader CTA only)
+    int it = 0, li = 0;
+    const uint32_t sf = tmem + f4::SF_COL;
+    for (int t = cl; t < prm.tiles && !*abort_flag; t += ncl, ++li) {
+      int mb, nb;
+      tile_coords(prm, t, mb, nb);
+      const int w = f4_width(prm, nb);
+      const int n0 = w < f4::HALF ? w : f4::HALF, n1 = w - n0;
+      const uint32_t id0 = idesc_mxf4_pair(n0), id1 = idesc_mxf4_pair(n1 > 0 ? n1 : 32);
+      if (li >= 1) wait_bar_cluster(accempty, uint32_t((li - 1) & 1), abort_flag, prm.err);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int ks = 0; ks < prm.ksteps; ++ks, ++it) {
+        const int s = it % f4::STAGES;
+        wait_bar(full + 8 * s, uint32_t((it / f4::STAGES) & 1), abort_flag, prm.err);
+        if (*abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_src = base + uint32_t(s * f4::STAGE), b_src = a_src + A2_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / UK; ++kk) {
+          mma_fp4_pair(tmem, smem_desc(a_src + UK * kk), smem_desc(b_src + UK * kk), id0, (ks | kk) != 0, sf);
+          if (n1 > 0)
+            mma_fp4_pair(tmem + uint32_t(f4::HALF), smem_desc(a_src + UK * kk),
+                         smem_desc(b_src + uint32_t(f4::B_BYTES) + UK * kk), id1, (ks | kk) != 0, sf);
+        }
+        mma_commit_pair(empty + 8 * s);  // both CTAs' stage s is free once these MMAs have read it
+      }
+      mma_commit_pair(accfull);  // this tile's accumulator is complete in both CTAs
+    }
+    if (*abort_flag) {  // the pair's MMAs complete before either CTA frees its TMEM
+      asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(drain)
+                   : "memory");
+      mbar_wait_bounded(drain, 0);
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue (both CTAs): row 128 rank + 32 (warp % 4) + lane of the
+    // tile; column group g = (warp - 4) / 4 drains 32-column chunks
+    // [CHUNKS g / G, CHUNKS (g + 1) / G) and stores them as 32-bit halves of C's words
+    constexpr int G = f4::EPI / 4;
+    const int ew = warp & 3, grp = (warp - 4) >> 2;
+    const int c_lo = f4::CHUNKS * grp / G, c_hi = f4::CHUNKS * (grp + 1) / G;
+    const uint32_t back = leader ? accempty : map_to_rank(accempty, 0);
+    int li = 0;
+    for (int t = cl; t < prm.tiles; t += ncl, ++li) {
+      wait_bar(accfull, uint32_t(li & 1), abort_flag, prm.err);
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int mb, nb;
+      tile_coords(prm, t, mb, nb);
+      const int w = f4_width(prm, nb);
+      const int64_t row = int64_t(mb) * 256 + 128 * int(rank) + ew * 32 + lane;
+#pragma unroll 1
+      for (int c = c_lo; c < c_hi && 32 * c < w; ++c) {
+        uint32_t v[32], h[P];
+        tmem_ld32(tmem + (uint32_t(ew * 32) << 16) + uint32_t(32 * c), v);
+        pack32<Q, P>(v, h);
+        if (row < prm.m) store_half<Q, P>(prm, row, int64_t(nb) * (f4::NB / 32) + c, h);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        if (leader)
+          mbar_arrive_cta(accempty);
+        else
+          mbar_arrive_cluster(back);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync();  // neither CTA touches the other's memory any more
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
 // ---------------------------------------------------- batched products --
 //
 // One persistent CTA per slot (kTcCtas) works through its own products, in the
@@ -1169,29 +1576,62 @@ int make_map(CUtensorMap *map, const uint8_t *ptr, int64_t inner, int64_t rows, 
 }
 
 
+// Product forms: 2 single SMs (128 x 256 tiles), 3 SM pairs (256 x 256), 4
+// SM pairs (256 x 512), all from e4m3 operands; 5 SM pairs (256 x 448) from
+// packed e2m1 operands.  By shape: a product of at most 128 rows would leave
+// half of every pair idle, so it runs on single SMs; products at least
+// kFp4MinL deep take the fp4 form (twice the tensor rate, half the operand
+// bytes), whose unoverlapped epilogue a shallower product would not amortise;
+// the rest take the 256 x 256 pair form (or, from kWideKsteps k-slices, the
+// wide one).
+constexpr int64_t kFp4MinL = 2048;
+inline int form_for(int64_t m, int64_t l, const TcOptions &to) {
+  if (to.form) return to.form;
+  if (m <= BM) return 2;
+  if (l >= kFp4MinL) return 5;
+  return cdiv(l, BK) >= kWideKsteps ? 4 : 3;
+}
+
+// Prepared operands in a workspace: per product (GF(4) has three, the other
+// fields one) A as m rows, then B transposed as npad rows, each row `row`
+// bytes: la e4m3 bytes (la = l rounded up to 128), or la / 2 bytes of packed
+// e2m1 (la = l rounded up to 256) for the fp4 form.
+struct Layout {
+  int rounds;
+  bool fp4;
+  int64_t la, row, npad, pc, a_bytes, b_bytes;
+};
+
+inline Layout layout_for(int q, int64_t m, int64_t l, int64_t n, int form) {
+  Layout lo;
+  lo.rounds = q == 4 ? 3 : 1;
+  lo.fp4 = form == 5;
+  lo.la = cdiv(l, lo.fp4 ? 2 * BK : BK) * (lo.fp4 ? 2 * BK : BK);
+  lo.row = lo.fp4 ? lo.la / 2 : lo.la;
+  lo.pc = fq_pitch_words(n);
+  lo.npad = lo.pc * 64;
+  lo.a_bytes = m * lo.row;
+  lo.b_bytes = lo.npad * lo.row;
+  return lo;
+}
+
 template <int Q, int P>
-int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t la, int64_t npad, int64_t pc,
-         int plane, const TcOptions &to, cudaStream_t s) {
+int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, const Layout &lo, int form, int plane,
+         const TcOptions &to, cudaStream_t s) {
   unsigned *err = nullptr;
   if (int rc = status_word(&err)) return rc;
-  // SM pairs take 256 x 256 tiles; a product of at most 128 rows would leave
-  // half of every pair idle, so it runs on single SMs (128 x 256 tiles).  Deep
-  // products (at least kWideKsteps k-slices) take the wide pair form (256 x
-  // 512), whose extra latency cover outweighs its unoverlapped epilogue.
-  const int ksteps = int(la / BK);
-  const int form = to.form ? to.form : (m <= BM ? 2 : (ksteps >= kWideKsteps ? 4 : 3));
-  const bool pair = form == 3 || form == 4, wide = form == 4;
+  const bool pair = form == 3 || form == 4 || form == 5, wide = form == 4, fp4 = form == 5;
   const int rows = pair ? 2 * BM : BM;
   CUtensorMap ma, mb;
-  if (int rc = make_map(&ma, Ab, la, m, BM)) return rc;
-  if (int rc = make_map(&mb, Bt, la, npad, pair ? BM : BN)) return rc;
+  if (int rc = make_map(&ma, Ab, lo.row, m, BM)) return rc;
+  if (int rc = make_map(&mb, Bt, lo.row, lo.npad, fp4 ? f4::BROWS : (pair ? BM : BN))) return rc;
   GemmParams prm;
   prm.C = C;
   prm.m = m;
-  prm.pc = pc;
-  prm.ksteps = int(la / BK);
+  prm.pc = lo.pc;
+  prm.ksteps = int(lo.row / BK);
   prm.mblocks = int(cdiv(m, rows));
-  prm.nblocks = int(npad / (wide ? 2 * BN : BN));
+  prm.nblocks = int(fp4 ? cdiv(lo.npad, f4::NB) : lo.npad / (wide ? 2 * BN : BN));
   const int64_t tiles = int64_t(prm.mblocks) * prm.nblocks;
   if (tiles >= (int64_t(1) << 31)) return FQ_ENOTSUP;
   prm.tiles = int(tiles);
@@ -1204,7 +1644,10 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
   if (pair) {
     const int64_t pairs = sms / 2 > 0 ? sms / 2 : 1;
     const int grid = 2 * int(tiles < pairs ? tiles : pairs);
-    if (wide) {
+    if (fp4) {
+      FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm4_kernel<Q, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, f4::SMEM));
+      tc_gemm4_kernel<Q, P><<<grid, f4::THREADS, f4::SMEM, s>>>(ma, mb, prm);
+    } else if (wide) {
       FQ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm2_kernel<Q, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        PairGeo<true>::SMEM));
       tc_gemm2_kernel<Q, P, true><<<grid, PairGeo<true>::THREADS, PairGeo<true>::SMEM, s>>>(ma, mb, prm);
@@ -1222,24 +1665,6 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, int64_t l
   return FQ_OK;
 }
 
-// Prepared operands in a workspace: per product (GF(4) has three, the other
-// fields one) A as m x la e4m3 bytes, then B transposed as npad x la bytes.
-struct Layout {
-  int rounds;
-  int64_t la, npad, pc, a_elems, b_elems;
-};
-
-inline Layout layout_for(int q, int64_t m, int64_t l, int64_t n) {
-  Layout lo;
-  lo.rounds = q == 4 ? 3 : 1;
-  lo.la = cdiv(l, BK) * BK;
-  lo.pc = fq_pitch_words(n);
-  lo.npad = lo.pc * 64;
-  lo.a_elems = m * lo.la;
-  lo.b_elems = lo.npad * lo.la;
-  return lo;
-}
-
 // B^T (npad x ld bytes from offset off) from B's planes, k < kcols.
 template <int Q, int P>
 void transpose_to(const uint64_t *B, int64_t l, int64_t pitch, int64_t npad, uint8_t *out, int64_t ld, int64_t off,
@@ -1249,33 +1674,36 @@ void transpose_to(const uint64_t *B, int64_t l, int64_t pitch, int64_t npad, uin
 }
 
 template <int Q, int P>
-int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint8_t *ws, cudaStream_t s) {
-  const Layout lo = layout_for(Q, m, l, n);
+int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint8_t *ws, int form,
+            cudaStream_t s) {
+  const Layout lo = layout_for(Q, m, l, n, form);
   if (lo.npad / TJ > 65535) return FQ_ENOTSUP;
   const int64_t pa = fq_pitch_words(l);
-  if (Q == 4) {
-    // the operands of X, Y, Z: A0, A1, A0 + A1 and B0, B1, B0 + B1 (sel 0, 1, 2)
-    for (int r = 0; r < 3; ++r) {
-      uint8_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
+  // GF(4): the operands of X, Y, Z are A0, A1, A0 + A1 and B0, B1, B0 + B1 (sel 0, 1, 2)
+  for (int r = 0; r < lo.rounds; ++r) {
+    uint8_t *a = ws + r * (lo.a_bytes + lo.b_bytes), *b = a + lo.a_bytes;
+    if (lo.fp4) {
+      rows_to_fp4<Q, P><<<rows_grid4(m, lo.la), 256, 0, s>>>(A, m, lo.la, pa, a, lo.row, r);
+      const dim3 grid(unsigned(lo.la / TK4), unsigned(lo.npad / TJ4));
+      planes_to_fp4_t<Q, P><<<grid, 256, 0, s>>>(B, l, lo.pc, b, lo.row, lo.la, r);
+    } else {
       rows_to_e4m3<Q, P><<<rows_grid(m, lo.la), 256, 0, s>>>(A, m, lo.la, pa, a, lo.la, 0, r);
       transpose_to<Q, P>(B, l, lo.pc, lo.npad, b, lo.la, 0, lo.la, r, s);
     }
-  } else {
-    rows_to_e4m3<Q, P><<<rows_grid(m, lo.la), 256, 0, s>>>(A, m, lo.la, pa, ws, lo.la, 0, 0);
-    transpose_to<Q, P>(B, l, lo.pc, lo.npad, ws + lo.a_elems, lo.la, 0, lo.la, 0, s);
   }
   FQ_LAUNCH_CHECK();
   return FQ_OK;
 }
 
 template <int Q, int P>
-int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, const TcOptions &to, cudaStream_t s) {
-  const Layout lo = layout_for(Q, m, l, n);
+int multiply(int64_t m, int64_t l, int64_t n, const uint8_t *ws, uint64_t *C, int form, const TcOptions &to,
+             cudaStream_t s) {
+  const Layout lo = layout_for(Q, m, l, n, form);
   // GF(4): X into both planes, then Y added into plane 0 and Z into plane 1
   const int plane[3] = {-1, 0, 1};
   for (int r = 0; r < lo.rounds; ++r) {
-    const uint8_t *a = ws + r * (lo.a_elems + lo.b_elems), *b = a + lo.a_elems;
-    if (int rc = gemm<Q, P>(a, b, C, m, lo.la, lo.npad, lo.pc, plane[r], to, s)) return rc;
+    const uint8_t *a = ws + r * (lo.a_bytes + lo.b_bytes), *b = a + lo.a_bytes;
+    if (int rc = gemm<Q, P>(a, b, C, m, lo, form, plane[r], to, s)) return rc;
   }
   return FQ_OK;
 }
@@ -1312,36 +1740,50 @@ int64_t tc_max_l(int q) {
   return ((int64_t(1) << 24) - 1) / (b * b);
 }
 
-// Modelled time (SM cycles), fitted on GB300: the busiest CTA's tiles
-// (ceil(tiles / SMs), one persistent CTA per SM) times 128-deep k-steps at
-// about 760 cycles each, per product (GF(4) runs three); the operand
-// conversion's bytes at about 2.8 TB/s (1.7 TB/s for the three-plane fields);
+// Modelled time (SM cycles), fitted on GB300.  e4m3 forms: the busiest CTA's
+// tiles (ceil(tiles / SMs) of 128 x 256, one persistent CTA per SM) times
+// 128-deep k-steps at about 760 cycles each.  fp4 form: the busiest pair's
+// 256 x 448 tiles, each 256-deep k-step about 1120 cycles plus about 6000 for
+// the tile's epilogue.  Per product (GF(4) runs three), plus the operand
+// conversion's bytes at about 2.8 TB/s (1.7 TB/s for the three-plane fields)
 // and about 30 us of launches and set-up.
 double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms) {
-  const tc::Layout lo = tc::layout_for(q, m, l, n);
-  const int64_t tiles = (lo.npad / tc::BN) * cdiv(m, tc::BM);
-  const double gemm = double(lo.rounds) * double(cdiv(tiles, sms > 0 ? sms : 1)) * double(lo.la / tc::BK) * 760.0;
-  const double bytes = double(lo.rounds) * double(lo.a_elems + lo.b_elems);
+  const int form = tc::form_for(m, l, TcOptions());
+  const tc::Layout lo = tc::layout_for(q, m, l, n, form);
+  const int64_t units = sms > 0 ? sms : 1;
+  double gemm;
+  if (lo.fp4) {
+    const int64_t tiles = cdiv(lo.npad, tc::f4::NB) * cdiv(m, 2 * tc::BM);
+    const int64_t pairs = units / 2 > 0 ? units / 2 : 1;
+    gemm = double(cdiv(tiles, pairs)) * (double(lo.row / tc::BK) * 1120.0 + 6000.0);
+  } else {
+    const int64_t tiles = (lo.npad / tc::BN) * cdiv(m, tc::BM);
+    gemm = double(cdiv(tiles, units)) * double(lo.la / tc::BK) * 760.0;
+  }
+  const double bytes = double(lo.rounds) * double(lo.a_bytes + lo.b_bytes);
   const double rate = (q == 5 || q == 7) ? 1.7e12 : 2.8e12;
-  return gemm + bytes * 2.07e9 / rate + 62000.0;
+  return double(lo.rounds) * gemm + bytes * 2.07e9 / rate + 62000.0;
 }
 
-int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n) {
+int tc_form(int64_t m, int64_t l) { return tc::form_for(m, l, TcOptions()); }
+
+int64_t tc_workspace_bytes(int q, int64_t m, int64_t l, int64_t n, const TcOptions &to) {
   if (!(q == 2 || q == 3 || q == 4 || q == 5 || q == 7) || m < 0 || l < 0 || n < 0 || l > tc_max_l(q)) return -1;
-  const tc::Layout lo = tc::layout_for(q, m, l, n);
-  return int64_t(lo.rounds) * (lo.a_elems + lo.b_elems);
+  const tc::Layout lo = tc::layout_for(q, m, l, n, tc::form_for(m, l, to));
+  return int64_t(lo.rounds) * (lo.a_bytes + lo.b_bytes);
 }
 
 int tc_prepare(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, void *ws,
-               cudaStream_t s) {
+               cudaStream_t s, const TcOptions &to) {
   if (l == 0 || m == 0 || n == 0) return FQ_OK;
   uint8_t *w = static_cast<uint8_t *>(ws);
+  const int form = tc::form_for(m, l, to);
   switch (q) {
-    case 2: return tc::prepare<2, 1>(m, l, n, A, B, w, s);
-    case 3: return tc::prepare<3, 2>(m, l, n, A, B, w, s);
-    case 4: return tc::prepare<4, 2>(m, l, n, A, B, w, s);
-    case 5: return tc::prepare<5, 3>(m, l, n, A, B, w, s);
-    case 7: return tc::prepare<7, 3>(m, l, n, A, B, w, s);
+    case 2: return tc::prepare<2, 1>(m, l, n, A, B, w, form, s);
+    case 3: return tc::prepare<3, 2>(m, l, n, A, B, w, form, s);
+    case 4: return tc::prepare<4, 2>(m, l, n, A, B, w, form, s);
+    case 5: return tc::prepare<5, 3>(m, l, n, A, B, w, form, s);
+    case 7: return tc::prepare<7, 3>(m, l, n, A, B, w, form, s);
     default: return FQ_EINVAL;
   }
 }
@@ -1354,24 +1796,25 @@ int tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *ws, uint64_t
     return FQ_OK;
   }
   const uint8_t *w = static_cast<const uint8_t *>(ws);
+  const int form = tc::form_for(m, l, to);
   switch (q) {
-    case 2: return tc::multiply<2, 1>(m, l, n, w, C, to, s);
-    case 3: return tc::multiply<3, 2>(m, l, n, w, C, to, s);
-    case 4: return tc::multiply<4, 2>(m, l, n, w, C, to, s);
-    case 5: return tc::multiply<5, 3>(m, l, n, w, C, to, s);
-    case 7: return tc::multiply<7, 3>(m, l, n, w, C, to, s);
+    case 2: return tc::multiply<2, 1>(m, l, n, w, C, form, to, s);
+    case 3: return tc::multiply<3, 2>(m, l, n, w, C, form, to, s);
+    case 4: return tc::multiply<4, 2>(m, l, n, w, C, form, to, s);
+    case 5: return tc::multiply<5, 3>(m, l, n, w, C, form, to, s);
+    case 7: return tc::multiply<7, 3>(m, l, n, w, C, form, to, s);
     default: return FQ_EINVAL;
   }
 }
 
 int launch_tc(int q, int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *B, uint64_t *C,
               cudaStream_t s, const TcOptions &to) {
-  const int64_t bytes = tc_workspace_bytes(q, m, l, n);
+  const int64_t bytes = tc_workspace_bytes(q, m, l, n, to);
   if (bytes < 0) return FQ_ENOTSUP;
-  if (l == 0) return tc_multiply(q, m, l, n, nullptr, C, s);
+  if (l == 0) return tc_multiply(q, m, l, n, nullptr, C, s, to);
   void *mem = nullptr;
   if (int rc = scratch_alloc(&mem, size_t(bytes), s)) return rc;
-  int rc = tc_prepare(q, m, l, n, A, B, mem, s);
+  int rc = tc_prepare(q, m, l, n, A, B, mem, s, to);
   if (rc == FQ_OK) rc = tc_multiply(q, m, l, n, mem, C, s, to);
   const int fr = scratch_free(mem, s);
   return rc ? rc : fr;

@@ -100,6 +100,7 @@ def _bind(lib):
         "fq_auto_choice": (i32, [i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "fq_strassen_levels": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
         "fq_planned_kernel": (i32, [i32, i64, i64, i64, ctypes.POINTER(Options)]),
+        "fq_tc_form": (i32, [i32, i64, i64, i64]),
         "fq_tc_workspace_bytes": (i64, [i32, i64, i64, i64]),
         "fq_tc_prepare": (i32, [i32, i64, i64, i64, vp, vp, vp, vp]),
         "fq_tc_multiply": (i32, [i32, i64, i64, i64, vp, vp, vp]),
@@ -254,6 +255,15 @@ def auto_choice(q: int, m: int, l: int, n: int) -> tuple[int, int]:
     path, kernel = ctypes.c_int(), ctypes.c_int()
     _check(load().fq_auto_choice(q, m, l, n, ctypes.byref(path), ctypes.byref(kernel)), "fq_auto_choice")
     return path.value, kernel.value
+
+
+def tc_form(q: int, m: int, l: int, n: int) -> int:
+    """fq_tc_form: the tcgen05 product form of this shape (2 single SMs, 3 and 4
+    SM pairs from e4m3 operands, 5 SM pairs from packed e2m1 operands)."""
+    r = load().fq_tc_form(q, m, l, n)
+    if r < 0:
+        raise FqError(-r, "fq_tc_form")
+    return r
 
 
 class TensorOperands:

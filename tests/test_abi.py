@@ -285,6 +285,19 @@ def test_autotune_cache_host_side(lib):
     assert lib.fq_tc_workspace_bytes(6, 100, 200, 300) == -1
     assert lib.fq_tc_workspace_bytes(9, 100, 200, 300) == -1
     assert lib.fq_tc_workspace_bytes(7, 10, 2_000_000, 10) == -1                 # beyond exact fp32 sums
+    # packed e2m1 operands (form 5: more than 128 rows, l >= 2048): rows of
+    # la / 2 bytes, la = l up to a multiple of 256
+    assert lib.fq_tc_workspace_bytes(3, 300, 2100, 300) == (300 + 1024) * 2304 // 2
+    assert lib.fq_tc_workspace_bytes(4, 129, 2048, 1025) == 3 * (129 + 2048) * 1024
+    assert lib.fq_tc_workspace_bytes(3, 300, 2047, 300) == (300 + 1024) * 2048    # e4m3, form 3
+    # the form a shape takes (host-only)
+    assert lib.fq_tc_form(3, 128, 5000, 300) == 2
+    assert lib.fq_tc_form(3, 129, 2047, 300) == 3
+    assert lib.fq_tc_form(5, 129, 2048, 300) == 5
+    assert lib.fq_tc_form(7, 16384, 16384, 16384) == 5
+    assert lib.fq_tc_form(7, 10, 2_000_000, 10) == -fq.ENOTSUP
+    assert lib.fq_tc_form(6, 10, 10, 10) == -fq.EINVAL
+    assert lib.fq_tc_form(3, -1, 10, 10) == -fq.EINVAL
     vp = ctypes.c_void_p
     assert lib.fq_tc_prepare(7, 10, 2_000_000, 10, vp(16), vp(16), vp(16), None) == fq.ENOTSUP
     assert lib.fq_tc_multiply(6, 10, 10, 10, vp(16), vp(16), None) == fq.EINVAL

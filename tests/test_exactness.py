@@ -1,12 +1,13 @@
 """The exact tensor-core form's arithmetic, pinned on the CPU.
 
 The tcgen05 path feeds residues in their balanced form {-B, .., B} (B = (p-1)/2,
-B = 1 for the F_2 products of GF(4)) as e4m3 values and accumulates the
-products in fp32.  That is exact when (a) every balanced residue is an e4m3
+B = 1 for the F_2 products of GF(4)) as e4m3 or packed e2m1 values (the latter
+with block scale factors 1.0) and accumulates the products in fp32.  That is exact when (a) every balanced residue is an e4m3
 value and (b) every partial sum is an integer of magnitude below 2^24, which
 holds for any order of additions while l * B^2 < 2^24.  These tests check both
-facts with PyTorch's own e4m3 conversion and numpy's float32 arithmetic, and
-that the library's range for the form ends exactly there."""
+facts with PyTorch's own e4m3 conversion, the e2m1 format's definition and
+numpy's float32 arithmetic, and that the library's range for the form ends
+exactly there."""
 import numpy as np
 import pytest
 import torch
@@ -38,6 +39,30 @@ def test_e4m3_bytes_of_the_balanced_residues():
     r = torch.tensor([0.0, 1.0, 2.0, 3.0, -1.0, -2.0, -3.0])
     got = r.to(torch.float8_e4m3fn).view(torch.uint8).tolist()
     assert got == [0x00, 0x38, 0x40, 0x44, 0xB8, 0xC0, 0xC4]
+
+
+def e2m1_value(nib):
+    """The OCP MX E2M1 format: sign bit 3, exponent bits 2..1 biased by 1,
+    mantissa bit 0; exponent 0 holds the subnormals 0 and 0.5."""
+    sign = -1.0 if nib & 8 else 1.0
+    e, m = (nib >> 1) & 3, nib & 1
+    return sign * (0.5 * m if e == 0 else 2.0 ** (e - 1) * (1.0 + 0.5 * m))
+
+
+def test_e2m1_nibbles_of_the_balanced_residues():
+    """The nibble constants of the fp4 conversion (kind::mxf4 operands): 1 =
+    0x2, 2 = 0x4, 3 = 0x5, a negative value sets bit 3, zero is 0x0; and each
+    balanced residue has exactly that nibble (besides -0 for zero)."""
+    table = {0: 0x0, 1: 0x2, 2: 0x4, 3: 0x5, -1: 0xA, -2: 0xC, -3: 0xD}
+    for v, nib in table.items():
+        assert e2m1_value(nib) == v
+        assert [x for x in range(16) if e2m1_value(x) == v] == ([0x0, 0x8] if v == 0 else [nib])
+
+
+def test_unit_block_scale():
+    """The fp4 form's block scale factors are ue8m0 0x7F, 2^(127 - 127) = 1.0,
+    so every scaled block sum is the plain integer sum."""
+    assert 2.0 ** (0x7F - 127) == 1.0
 
 
 @pytest.mark.parametrize("q", (3, 5, 7))

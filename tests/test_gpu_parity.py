@@ -280,15 +280,16 @@ def test_mma_sync_form_matches_oracle(fq, q, mln):
     _check_product(fq, q, *mln, seed=sum(mln) + 11 * q, path=fq.PATH_MMA, kernel=1)
 
 
-@pytest.mark.parametrize("kernel", [2, 3, 4])
+@pytest.mark.parametrize("kernel", [2, 3, 4, 5])
 @pytest.mark.parametrize("q", FIELDS)
 @pytest.mark.parametrize("mln", [(1, 1, 1), (128, 300, 257), (129, 300, 257), (300, 500, 260), (513, 257, 1025),
                                  (260, 1300, 1100)])
 def test_tcgen05_forms_match_oracle(fq, q, mln, kernel):
-    """fq_options.kernel = 2, 3, 4: the single-SM tcgen05 kernel (128 x 256
+    """fq_options.kernel = 2, 3, 4, 5: the single-SM tcgen05 kernel (128 x 256
     tiles), the SM-pair kernel (256 x 256) and the wide SM-pair kernel (256 x
-    512), each forced whatever the shape; equal to the oracle and to the form
-    the shape takes by default."""
+    512) from e4m3 operands, and the SM-pair kernel from packed e2m1 operands
+    (kind::mxf4, 256 x 448 tiles), each forced whatever the shape; equal to
+    the oracle and to the form the shape takes by default."""
     got, c1 = _check_product(fq, q, *mln, seed=sum(mln) + 13 * q, path=fq.PATH_MMA, kernel=kernel)
     m, l, n = mln
     A = inputs.uniform(q, m, l, seed=sum(mln) + 13 * q, stream=inputs.STREAM_A)
@@ -320,35 +321,51 @@ def test_tensor_operands_prepared_once(fq, q):
     assert fq.status() == fq.OK
 
 
+# Every tcgen05 product kernel: (rows, forced kernel) -- single SMs, the two
+# e4m3 SM-pair forms and the fp4 SM-pair form (rows 260: the second half of
+# the pair's row block lies outside m).
+TC_KERNELS = [(3, 2), (260, 3), (260, 4), (260, 5)]
+
+
 @pytest.mark.slow
-def test_tcgen05_exact_near_its_range(fq):
+@pytest.mark.parametrize("m, kernel", TC_KERNELS)
+def test_tcgen05_exact_near_its_range(fq, m, kernel):
     """F_7 with every entry 3: each entry of C is 9 l before the reduction,
     9.4e6 for l = 2^20 (the fp32 sums must stay exact up to 2^24)."""
-    m, l, n = 3, 1 << 20, 70
+    l, n = 1 << 20, 70
     A = np.full((m, l), 3, np.uint8)
     B = np.full((l, n), 3, np.uint8)
-    got, _ = gpu_product(fq, 7, A, B, path=fq.PATH_MMA)
+    got, _ = gpu_product(fq, 7, A, B, path=fq.PATH_MMA, kernel=kernel)
     assert (got == (9 * l) % 7).all()
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("m", [3, 260])
+@pytest.mark.parametrize("m, kernel", TC_KERNELS)
 @pytest.mark.parametrize("q, l, codes", [(7, None, (1, 2, 3)), (3, 1 << 22, (0, 1))])
-def test_tcgen05_exact_with_random_low_bits(fq, q, l, codes, m):
+def test_tcgen05_exact_with_random_low_bits(fq, q, l, codes, m, kernel):
     """Rows of A all +3 (F_7) or all +1 (F_3) against random positive B: every
     step of the tensor-core sum adds a random amount, so an accumulation that
     dropped low bits anywhere on the way to 2^24 (F_7 at its longest exact l)
     or 2^22 (F_3) would change the residues.  C = A B is a column sum of B.
-    m = 3 runs the single-SM kernel, m = 260 the SM-pair kernel (its second
-    pair tile half outside m)."""
+    Every product kernel, e4m3 and packed e2m1 (block scale factors 1.0)."""
     l = l or _tc_max_l(fq, q)
     n = 70
     a = 3 if q == 7 else 1
     A = np.full((m, l), a, np.uint8)
     B = np.random.default_rng(q).choice(np.array(codes, np.uint8), size=(l, n))
-    got, _ = gpu_product(fq, q, A, B, path=fq.PATH_MMA)
+    got, _ = gpu_product(fq, q, A, B, path=fq.PATH_MMA, kernel=kernel)
     want = (a * B.sum(axis=0, dtype=np.int64)) % q
     assert (got == want[None, :]).all()
+
+
+@pytest.mark.parametrize("q", FIELDS)
+@pytest.mark.parametrize("k", range(1, 8))
+def test_fp4_form_every_last_tile_width(fq, q, k):
+    """The fp4 SM-pair form's column tiles are 448 wide; the last one takes
+    what is left of the 1024 k-column pitch: 128, 256, 384, 64, 192, 320 and
+    448 for k = 1 .. 7 (two MMA halves of up to 224 columns, the second one
+    narrower or absent).  n = 1024 k - 100 leaves padding columns too."""
+    _check_product(fq, q, 300, 600, 1024 * k - 100, seed=40 + k, path=fq.PATH_MMA, kernel=5)
 
 
 def _tc_max_l(fq, q):
