@@ -9,7 +9,8 @@ against the classical product's work).
 * ``value``: packed inputs resident in HBM, device time (CUDA events on the
   launching stream), L2 flushed before every step; each product runs in the
   form FQ_PATH_AUTO takes for its shape (for these F_3 shapes the tcgen05
-  tensor-core form: operand conversion, then the product kernel).
+  tensor-core form from packed e2m1 operands on SM pairs: operand
+  conversion, then the product kernel).
 * ``m4rm``: the same products by the plain bitsliced Four-Russians path, with
   ``speedup_vs_m4rm`` the factor between the two.
 * ``e2e``: the same products through the public API from pinned host residues:
@@ -17,9 +18,12 @@ against the classical product's work).
   by the host link: 1 byte per element up, about 210 GB/s on GB300).
 * ``e2e_packed``: the same with the host holding the library's bit-planes
   (the paper's representation): planes up, fq_matmul, C's planes down.
-* ``roofline``: the dominant kernel, the tcgen05 product (e4m3 operands), at
-  2 m l n flops per launch over its own event time, against the dense fp8
-  peak (the measured cuBLAS bf16 burst times the nominal fp8/bf16 ratio 2);
+* ``roofline``: the dominant kernel, the tcgen05 product, at 2 m l n flops
+  per launch over its own event time, against the dense peak of its operand
+  type: the measured cuBLAS bf16 burst times the nominal ratio (fp4 13.5 /
+  2.25 = 6, fp8 4.5 / 2.25 = 2), and beside it the instruction kind's own
+  pipe rate (fp4 kind::mxf4 32768, fp8 16384 ops/clk/SM, measured by the
+  microbenchmark) at the sampled SM clock;
   ``prepare``: the operand conversion's bytes over its time, against the
   measured HBM copy bandwidth;
   ``m4rm.roofline``: the M4RM kernels against the integer-logic (LOP3) issue
@@ -96,22 +100,40 @@ def cdiv(a, b):
     return -(-a // b)
 
 
-# Launches of one F_3 tensor-core product: A to e4m3, B's planes to e4m3 B^T,
-# the tcgen05 product.
+# Launches of one F_3 tensor-core product: A's planes converted, B's planes
+# converted to B^T, the tcgen05 product.
 TC_LAUNCHES = 3
+
+# The tcgen05 product forms (fq_tc_form): kernel, operand type, dense
+# ops/clk/SM of the instruction kind (the microbenchmark's measured pipe
+# rate), nominal peak as a multiple of the bf16 peak.
+TC_FORMS = {
+    2: ("tc_gemm_kernel (tcgen05.mma.cta_group::1 kind::f8f6f4, e4m3, single SMs, 128x256 tiles)", "fp8", 16384, 2.0),
+    3: ("tc_gemm2_kernel (tcgen05.mma.cta_group::2 kind::f8f6f4, e4m3, SM pairs, 256x256 tiles)", "fp8", 16384, 2.0),
+    4: ("tc_gemm2_kernel (tcgen05.mma.cta_group::2 kind::f8f6f4, e4m3, SM pairs, 256x512 tiles)", "fp8", 16384, 2.0),
+    5: ("tc_gemm4_kernel (tcgen05.mma.cta_group::2 kind::mxf4, packed e2m1, block scales 1.0, SM pairs, "
+        "256x448 tiles)", "fp4", 32768, 6.0),
+}
 
 
 def pitch_words(cols):
     return cdiv(max(cols, 1), 1024) * 16
 
 
-def prepare_bytes(m, l, n, q=3):
+def prepare_bytes(m, l, n, q=3, form=3):
     """Algorithmic DRAM bytes of the operand conversion: every plane of A and
-    of B read, e4m3 A and B^T written (GF(4): three rounds, one per F_2
-    product)."""
-    la, npad = cdiv(l, 128) * 128, pitch_words(n) * 64
+    of B read, A and B^T written, e4m3 (one byte per element, la = l rounded up
+    to 128) or, for form 5, packed e2m1 (half a byte, la = l rounded up to
+    256) (GF(4): three rounds, one per F_2 product)."""
+    if form == 5:
+        la = cdiv(l, 256) * 256
+        row = la // 2
+    else:
+        la = cdiv(l, 128) * 128
+        row = la
+    npad = pitch_words(n) * 64
     rounds = 3 if q == 4 else 1
-    return rounds * (PLANES[q] * (m * pitch_words(l) + l * pitch_words(n)) * 8 + (m + npad) * la)
+    return rounds * (PLANES[q] * (m * pitch_words(l) + l * pitch_words(n)) * 8 + (m + npad) * row)
 
 
 def tensor_flops(q, m, l, n):
@@ -286,6 +308,7 @@ def product_leg(torch, fq, inputs, dist, dev, flush, workload, prods, clk, reps=
         del A, B
         c_tc, c_m4 = fq.empty(q, m, n), fq.empty(q, m, n)
         ops = fq.TensorOperands(a, b)
+        form = fq.tc_form(q, m, l, n)
         t_prep, t_mul, t_m4 = [], [], []
         for r in range(warmup + reps):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -314,7 +337,7 @@ def product_leg(torch, fq, inputs, dist, dev, flush, workload, prods, clk, reps=
         m4_ms = dist.max(statistics.median(t_m4), dev)
         field_ops = 2.0 * m * l * n
         tflops = tensor_flops(q, m, l, n) / (mul_ms * 1e-3) / 1e12
-        pbytes = prepare_bytes(m, l, n, q)
+        pbytes = prepare_bytes(m, l, n, q, form)
         levels = fq.strassen_levels(q, m, l, n, path=fq.PATH_M4RM)
         leaf = (m >> levels, l >> levels, n >> levels)
         k = fq.planned_kernel(q, *leaf, path=fq.PATH_M4RM)["k"]
@@ -324,9 +347,7 @@ def product_leg(torch, fq, inputs, dist, dev, flush, workload, prods, clk, reps=
             "q": q, "m": m, "l": l, "n": n, "paths_agree": agree,
             "tensor": {"ms": prep_ms + mul_ms, "prepare_ms": prep_ms, "multiply_ms": mul_ms,
                        "field_ops_per_s": dist.world * field_ops / ((prep_ms + mul_ms) * 1e-3),
-                       "roofline": {"bound": "tensor", "achieved": tflops, "peak": peaks["fp8"], "unit": "TFLOP/s",
-                                    "frac": tflops / peaks["fp8"], "peak_note": peaks["note"],
-                                    "pipe": pipe_peak(tflops, clk)},
+                       "roofline": tc_roofline(peaks, form, tflops, clk),
                        "prepare_roofline": {"bound": "hbm", "achieved": pbytes / (prep_ms * 1e-3) / 1e9,
                                             "peak": peaks["hbm"], "unit": "GB/s",
                                             "frac": pbytes / (prep_ms * 1e-3) / 1e9 / peaks["hbm"],
@@ -510,34 +531,50 @@ def measured_traffic(name, digest):
 def measured_peaks():
     """Peaks for the rooflines: the measured dense bf16 burst of
     MEASURED_PEAKS.json (else 1900 TFLOP/s, an earlier GB300 measurement); the
-    dense fp8 (e4m3) peak as twice that, the nominal ratio of the two (4.5 and
-    2.25 PFLOP/s); the measured HBM copy bandwidth (else 6800 GB/s)."""
+    dense fp8 (e4m3) and fp4 (e2m1) peaks as 2 and 6 times that, the nominal
+    ratios (4.5 and 13.5 against 2.25 PFLOP/s); the measured HBM copy
+    bandwidth (else 6800 GB/s)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             rec = json.load(f)
         bf16, hbm = float(rec["bf16_tflops"]), float(rec["hbm_gbs"])
-        note = "of measured: cuBLAS bf16 burst x 2 (nominal fp8/bf16 ratio), MEASURED_PEAKS.json"
-        hbm_note = "of measured: HBM copy (MEASURED_PEAKS.json)"
+        src, hbm_note = "of measured: cuBLAS bf16 burst", "of measured: HBM copy (MEASURED_PEAKS.json)"
     except (OSError, ValueError, KeyError):
         bf16, hbm = 1900.0, 6800.0
-        note, hbm_note = "of fallback: 1.9 PFLOP/s bf16 x 2", "of fallback: 6.8 TB/s"
-    return {"bf16": bf16, "fp8": 2.0 * bf16, "note": note, "hbm": hbm, "hbm_note": hbm_note}
+        src, hbm_note = "of fallback: 1.9 PFLOP/s bf16", "of fallback: 6.8 TB/s"
+    return {"bf16": bf16, "fp8": 2.0 * bf16, "fp4": 6.0 * bf16,
+            "note": src + " x 2 (nominal fp8/bf16 ratio)",
+            "note_fp8": src + " x 2 (nominal fp8/bf16 ratio)",
+            "note_fp4": src + " x 6 (nominal fp4/bf16 ratio)",
+            "hbm": hbm, "hbm_note": hbm_note}
+
+
+def tc_roofline(peaks, form, achieved_tflops, clk):
+    """Roofline of a tcgen05 product kernel in `form`: against its operand
+    type's dense peak, and against its instruction kind's pipe at the sampled
+    SM clock."""
+    kernel, dtype, opc, _ = TC_FORMS[form]
+    return {"bound": "tensor", "achieved": achieved_tflops, "peak": peaks[dtype], "unit": "TFLOP/s",
+            "frac": achieved_tflops / peaks[dtype], "peak_note": peaks["note_" + dtype], "kernel": kernel,
+            "operands": dtype, "pipe": pipe_peak(achieved_tflops, clk, opc)}
 
 
 # The f8f6f4 tensor pipe's own peak, as the hardware counters state it
-# (sm__ops_path_tensor_op_utcqmma_src_fp8_dst_fp32...peak_sustained).
+# (sm__ops_path_tensor_op_utcqmma_src_fp8_dst_fp32...peak_sustained) and the
+# microbenchmark measures it; kind::mxf4 (packed e2m1) measured at twice that.
 FP8_OPS_PER_CLK_PER_SM = 16384
 SMS = 152
 
 
-def pipe_peak(achieved_tflops, clk):
-    """A second roofline denominator for the tensor-core product: the fp8 pipe's
-    peak at the SM clock sampled in the timed region (the measured bf16 figure
-    was taken at a lower, power-capped clock)."""
+def pipe_peak(achieved_tflops, clk, ops_per_clk=FP8_OPS_PER_CLK_PER_SM):
+    """A second roofline denominator for the tensor-core product: the
+    instruction kind's pipe peak at the SM clock sampled in the timed region
+    (the measured bf16 figure was taken at a lower, power-capped clock)."""
     mhz = (clk or {}).get("sm_mhz") or 2070.0
-    peak = FP8_OPS_PER_CLK_PER_SM * SMS * mhz * 1e6 / 1e12
+    peak = ops_per_clk * SMS * mhz * 1e6 / 1e12
     return {"peak": peak, "unit": "TFLOP/s", "frac": achieved_tflops / peak, "sm_mhz": mhz,
-            "note": "16384 fp8 ops/clk/SM (ncu peak_sustained) x 152 SMs x the median SM clock of the timed region"}
+            "note": "%d ops/clk/SM (tcgen05 microbenchmark, operands resident) x 152 SMs x the median SM clock "
+                    "of the timed region" % ops_per_clk}
 
 
 def make_inputs(torch, inputs, prods, seed=0):
@@ -652,6 +689,7 @@ def main():
     # tensor-core product runs as its two stages, operand conversion and the
     # tcgen05 product, so that the product kernel can be timed on its own.
     forms = ["tensor" if fq.auto_choice(Q, m, l, n)[0] == fq.PATH_MMA else "m4rm" for (m, l, n, _) in prods]
+    tc_forms = [fq.tc_form(Q, m, l, n) if f == "tensor" else None for f, (m, l, n, _) in zip(forms, prods)]
     tops = [fq.TensorOperands(a, b) if f == "tensor" else None for f, (a, b, c) in zip(forms, packed)]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -743,19 +781,26 @@ def main():
 
     pack_unpack = pack_unpack_ms()
 
-    # Roofline of the dominant kernel, the tcgen05 product: 2 m l n flops (e4m3
-    # operands, fp32 sums) per launch over the product stage's event time.
+    # Roofline of the dominant kernel, the tcgen05 product: 2 m l n flops per
+    # launch over the product stage's event time, for the form that takes the
+    # most product time (each form against its own operand type's peak).
     peaks = measured_peaks()
-    t_flops = sum(2.0 * m * l * n for f, (m, l, n, _) in zip(forms, prods) if f == "tensor")
-    t_ms = sum(t for f, t in zip(forms, product_ms) if f == "tensor")
+    form_ms = {}
+    for tf, t in zip(tc_forms, product_ms):
+        if tf is not None:
+            form_ms[tf] = form_ms.get(tf, 0.0) + t
+    main_form = max(form_ms, key=form_ms.get) if form_ms else None
+    t_flops = sum(2.0 * m * l * n for tf, (m, l, n, _) in zip(tc_forms, prods) if tf is not None and tf == main_form)
+    t_ms = form_ms.get(main_form, 0.0)
     achieved = t_flops / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
     # The conversion stage: e4m3 bytes written (A: m x la, B^T: 64 pitch(n) x
     # la) plus the planes read (A; B, then B^T's planes written and read).
     prep_ms = sum(sum(stage[s_][j][0] for s_ in range(args.steps)) / args.steps
                   for j, f in enumerate(forms) if f == "tensor")
-    prep_bytes = sum(prepare_bytes(m, l, n) for f, (m, l, n, _) in zip(forms, prods) if f == "tensor")
+    prep_bytes = sum(prepare_bytes(m, l, n, Q, tf) for tf, (m, l, n, _) in zip(tc_forms, prods) if tf is not None)
     prep_gbs = prep_bytes / (prep_ms * 1e-3) / 1e9 if prep_ms > 0 else 0.0
-    traffic_rec = measured_traffic("tc_f3_dram_traffic.json", tc_sources_digest())
+    traffic_rec = measured_traffic("tc_fp4_f3_dram_traffic.json" if main_form == 5 else "tc_f3_dram_traffic.json",
+                                   tc_sources_digest())
     traffic = traffic_rec.get("bytes_per_launch") if traffic_rec else None
 
     # ---- the plain bitsliced M4RM path on the same products, for the factor --
@@ -945,20 +990,18 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "e4m3 (exact integers, fp32 sums)", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": ("e2m1" if main_form == 5 else "e4m3") + " (exact integers, fp32 sums)",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.sizes else "F_3 square n=" + args.sizes,
                        "q": Q, "products": [list(p) for p in prods],
-                       "path": forms, "path_choice": "FQ_PATH_AUTO per shape (fq_auto_choice: the library's "
-                                                     "time model of M4RM and the tensor-core path)",
+                       "path": forms, "tc_form": tc_forms,
+                       "path_choice": "FQ_PATH_AUTO per shape (fq_auto_choice: the library's "
+                                      "time model of M4RM and the tensor-core path; fq_tc_form: the tcgen05 form)",
                        "l2": "flushed (256 MiB write) before every step",
                        "parallelism": "replicas" if dist.world > 1 else "single GPU"},
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["fp8"], "unit": "TFLOP/s",
-                         "frac": achieved / peaks["fp8"], "traffic": traffic,
-                         "peak_note": peaks["note"],
-                         "kernel": "tc_gemm2_kernel (tcgen05.mma.cta_group::2 kind::f8f6f4 e4m3 on SM pairs, "
-                                   "persistent; 256x512 tiles for l >= 4096, 256x256 below)",
-                         "kernel_ms_per_step": sum(product_ms),
-                         "pipe": pipe_peak(achieved, clk)},
+            "roofline": dict(tc_roofline(peaks, main_form, achieved, clk) if main_form else {},
+                             traffic=traffic, kernel_ms_per_step=t_ms),
             "prepare": {"bound": "hbm", "ms_per_step": prep_ms, "bytes": prep_bytes, "achieved": prep_gbs,
                         "peak": peaks["hbm"], "unit": "GB/s", "frac": prep_gbs / peaks["hbm"],
                         "peak_note": peaks["hbm_note"]},

@@ -538,11 +538,15 @@ __device__ __forceinline__ void tile_coords(const GemmParams &prm, int t, int &m
   nb = in / rows;
 }
 
-// 32 accumulator values of one row (exact integers in fp32) reduced mod p and
-// packed into one 32-bit word per plane (value i at bit i), through four
-// independent partial words so that the bit-or chains are short.
+// 32 accumulator values of one row (exact integers in fp32, |x| < 2^24)
+// reduced mod p and packed into one 32-bit word per plane (value i at bit i).
+// x + p 2^25 is positive and has x's residue, so the reduction is an unsigned
+// one (a multiply-high by the reciprocal); the bits are gathered through four
+// independent partial words (disjoint bits, so adds), keeping chains short.
 template <int Q, int P>
 __device__ __forceinline__ void pack32(const uint32_t (&v)[32], uint32_t (&h)[P]) {
+  constexpr int mod = Q == 4 ? 2 : Q;
+  constexpr int off = mod * (1 << 25);
   uint32_t part[P][4];
 #pragma unroll
   for (int p = 0; p < P; ++p)
@@ -550,18 +554,16 @@ __device__ __forceinline__ void pack32(const uint32_t (&v)[32], uint32_t (&h)[P]
     for (int j = 0; j < 4; ++j) part[p][j] = 0u;
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
-    const int x = int(__uint_as_float(v[i]));  // an exact integer
-    const int mod = Q == 4 ? 2 : Q;
-    int r = x % mod;
-    r += r < 0 ? mod : 0;
+    const int x = __float2int_rz(__uint_as_float(v[i]));  // an exact integer
+    const uint32_t r = mod == 2 ? (uint32_t(x) & 1u) : uint32_t(x + off) % uint32_t(mod);
     if constexpr (Q == 3) {
-      part[0][i & 3] |= uint32_t(r != 0) << i;
-      part[1][i & 3] |= uint32_t(r == 2) << i;
+      part[0][i & 3] += ((r + 1u) >> 1) << i;  // unit: r != 0
+      part[1][i & 3] += (r >> 1) << i;         // sign: r == 2
     } else if constexpr (Q == 4 || Q == 2) {
-      part[0][i & 3] |= uint32_t(r) << i;
+      part[0][i & 3] += r << i;
     } else {
 #pragma unroll
-      for (int p = 0; p < P; ++p) part[p][i & 3] |= uint32_t((r >> p) & 1) << i;
+      for (int p = 0; p < P; ++p) part[p][i & 3] += ((r >> p) & 1u) << i;
     }
   }
 #pragma unroll
@@ -1010,7 +1012,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairGeo<WIDE>::THREA
 // multiple of 64): its halves take N_j = min(w - 224 j, 224) columns, and
 // CTA r loads B^T rows 224 j + r N_j / 2 .., so that accumulator column c is
 // always tile column c.  The accumulator is not double-buffered; twice as
-// many epilogue warps as in the 256 x 256 pair form drain it.
+// many epilogue warps as in the 256 x 256 pair form drain it, each a
+// quarter of the row's words.
 namespace f4 {
 constexpr int NB = 448, HALF = 224, BROWS = HALF / 2;  // tile columns, per MMA, B^T rows per CTA per half
 constexpr int B_BYTES = BROWS * BK;                     // 14 KB (a whole number of 1 KB swizzle atoms)
@@ -1019,9 +1022,10 @@ constexpr int STAGES = 5;
 constexpr int BAR_OFF = STAGES * STAGE;
 constexpr int NBARS = 2 * STAGES + 2 + 1;  // full, empty, accfull, accempty, the MMA drain
 constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;
-constexpr int EPI = 8;                      // epilogue warps: lane quadrant warp % 4, column group (warp - 4) / 4
+constexpr int EPI = 16;                     // epilogue warps: lane quadrant warp % 4, column group (warp - 4) / 4
 constexpr int THREADS = 128 + 32 * EPI;
-constexpr int CHUNKS = NB / 32;             // 32-column accumulator loads per tile row
+constexpr int WORDS = NB / 64;              // 64-column words of C per tile row
+constexpr int GROUPS = EPI / 4, WPG = (WORDS + GROUPS - 1) / GROUPS;  // column groups, words per group
 constexpr uint32_t SF_COL = NB;             // scale factors: columns 448 .. 511
 static_assert(SMEM <= 232448, "shared memory per CTA");
 }  // namespace f4
@@ -1058,24 +1062,22 @@ __device__ __forceinline__ int f4_width(const GemmParams &prm, int nb) {
   return left < f4::NB ? int(left) : f4::NB;
 }
 
-// Store 32-bit halves h of one row's plane words (half-word index h32 of C's
-// row).  GF(4): plane < 0 writes the F_2 result into both planes, else XORs it
-// into that plane.
-template <int Q, int P>
-__device__ __forceinline__ void store_half(const GemmParams &prm, int64_t row, int64_t h32, const uint32_t (&h)[P]) {
-  if (!debug_ok(row < prm.m && h32 < 2 * prm.pc, prm.err)) return;
-  uint32_t *C32 = reinterpret_cast<uint32_t *>(prm.C);
-  if constexpr (Q == 4) {
-    if (prm.plane < 0) {
-      C32[(row)*2 * prm.pc + h32] = h[0];
-      C32[(prm.m + row) * 2 * prm.pc + h32] = h[0];
-    } else {
-      C32[(int64_t(prm.plane) * prm.m + row) * 2 * prm.pc + h32] ^= h[0];
-    }
-  } else {
+// Two 32-column TMEM loads (columns taddr .. + 63 of this warp's lanes), one
+// wait for both.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[2][32]) {
 #pragma unroll
-    for (int p = 0; p < P; ++p) C32[(int64_t(p) * prm.m + row) * 2 * prm.pc + h32] = h[p];
-  }
+  for (int h = 0; h < 2; ++h)
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[h][0]), "=r"(v[h][1]), "=r"(v[h][2]), "=r"(v[h][3]), "=r"(v[h][4]), "=r"(v[h][5]), "=r"(v[h][6]),
+          "=r"(v[h][7]), "=r"(v[h][8]), "=r"(v[h][9]), "=r"(v[h][10]), "=r"(v[h][11]), "=r"(v[h][12]),
+          "=r"(v[h][13]), "=r"(v[h][14]), "=r"(v[h][15]), "=r"(v[h][16]), "=r"(v[h][17]), "=r"(v[h][18]),
+          "=r"(v[h][19]), "=r"(v[h][20]), "=r"(v[h][21]), "=r"(v[h][22]), "=r"(v[h][23]), "=r"(v[h][24]),
+          "=r"(v[h][25]), "=r"(v[h][26]), "=r"(v[h][27]), "=r"(v[h][28]), "=r"(v[h][29]), "=r"(v[h][30]),
+          "=r"(v[h][31])
+        : "r"(taddr + uint32_t(32 * h)));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 template <int Q, int P>
@@ -1192,11 +1194,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(f4::THREADS, 1)
     }
   } else if (warp >= 4) {
     // ---- epilogue (both CTAs): row 128 rank + 32 (warp % 4) + lane of the
-    // tile; column group g = (warp - 4) / 4 drains 32-column chunks
-    // [CHUNKS g / G, CHUNKS (g + 1) / G) and stores them as 32-bit halves of C's words
-    constexpr int G = f4::EPI / 4;
+    // tile; column group g = (warp - 4) / 4 drains words [WPG g, WPG (g + 1))
+    // of the tile's seven (those inside its width)
     const int ew = warp & 3, grp = (warp - 4) >> 2;
-    const int c_lo = f4::CHUNKS * grp / G, c_hi = f4::CHUNKS * (grp + 1) / G;
+    const int w_lo = f4::WPG * grp, w_hi = w_lo + f4::WPG < f4::WORDS ? w_lo + f4::WPG : f4::WORDS;
     const uint32_t back = leader ? accempty : map_to_rank(accempty, 0);
     int li = 0;
     for (int t = cl; t < prm.tiles; t += ncl, ++li) {
@@ -1208,11 +1209,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(f4::THREADS, 1)
       const int w = f4_width(prm, nb);
       const int64_t row = int64_t(mb) * 256 + 128 * int(rank) + ew * 32 + lane;
 #pragma unroll 1
-      for (int c = c_lo; c < c_hi && 32 * c < w; ++c) {
-        uint32_t v[32], h[P];
-        tmem_ld32(tmem + (uint32_t(ew * 32) << 16) + uint32_t(32 * c), v);
-        pack32<Q, P>(v, h);
-        if (row < prm.m) store_half<Q, P>(prm, row, int64_t(nb) * (f4::NB / 32) + c, h);
+      for (int wd = w_lo; wd < w_hi && 64 * wd < w; ++wd) {
+        uint32_t v[2][32], h0[P], h1[P];
+        tmem_ld64(tmem + (uint32_t(ew * 32) << 16) + uint32_t(64 * wd), v);
+        pack32<Q, P>(v[0], h0);
+        pack32<Q, P>(v[1], h1);
+        uint64_t words[P][1];
+#pragma unroll
+        for (int p = 0; p < P; ++p) words[p][0] = uint64_t(h0[p]) | (uint64_t(h1[p]) << 32);
+        if (row < prm.m) store_words<Q, P, 1>(prm, row, int64_t(nb) * f4::WORDS + wd, words);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();

@@ -42,6 +42,25 @@ def test_prepare_bytes_counts_planes_in_and_e4m3_out():
     assert bench.prepare_bytes(100, 200, 300) == 2 * (100 * 16 + 200 * 16) * 8 + (100 + 1024) * 256
 
 
+def test_prepare_bytes_fp4_form():
+    bench = _bench()
+    # form 5: packed e2m1, half a byte per element, l rounded up to 256
+    assert bench.prepare_bytes(8192, 8192, 8192, 3, 5) == 2 * (2 * 8192 * 128 * 8) + 2 * 8192 * 4096
+    assert bench.prepare_bytes(300, 2100, 300, 3, 5) == 2 * (300 * 48 + 2100 * 16) * 8 + (300 + 1024) * 1152
+    assert bench.prepare_bytes(8192, 8192, 8192, 4, 5) == 3 * (2 * (2 * 8192 * 128 * 8) + 2 * 8192 * 4096)
+
+
+def test_tc_roofline_per_form():
+    bench = _bench()
+    peaks = {"fp8": 3000.0, "fp4": 9000.0, "note_fp8": "x2", "note_fp4": "x6"}
+    r4 = bench.tc_roofline(peaks, 5, 4500.0, {"sm_mhz": 2000.0})
+    assert r4["frac"] == 0.5 and r4["operands"] == "fp4" and "mxf4" in r4["kernel"]
+    assert abs(r4["pipe"]["peak"] - 32768 * 152 * 2000e6 / 1e12) < 1e-6
+    r8 = bench.tc_roofline(peaks, 4, 1500.0, {"sm_mhz": 2000.0})
+    assert r8["frac"] == 0.5 and r8["operands"] == "fp8"
+    assert abs(r8["pipe"]["peak"] - 16384 * 152 * 2000e6 / 1e12) < 1e-6
+
+
 def test_prepare_bytes_other_fields():
     bench = _bench()
     # F_5 / F_7: three planes read; GF(4): three rounds (one per F_2 product)
