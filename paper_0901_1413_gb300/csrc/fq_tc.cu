@@ -523,6 +523,7 @@ struct GemmParams {
   int mblocks, nblocks, tiles;
   int group;       // row blocks per group of the tile order
   int plane;       // GF(4): -1 writes both planes, 0 or 1 adds into that plane
+  bool small;      // every sum's magnitude is at most kSmallSum (l B^2 <= 2^22 - 8)
   unsigned *err;
 };
 
@@ -538,43 +539,88 @@ __device__ __forceinline__ void tile_coords(const GemmParams &prm, int t, int &m
   nb = in / rows;
 }
 
+// Bits 0, 2, ..., 30 of x gathered into bits 0..15.
+__device__ __forceinline__ uint32_t even16(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+  x = (x | (x >> 4)) & 0x00FF00FFu;
+  return (x | (x >> 8)) & 0x0000FFFFu;
+}
+
+// Bits 0, 4, ..., 28 of x gathered into bits 0..7.
+__device__ __forceinline__ uint32_t nib8(uint32_t x) {
+  x &= 0x11111111u;
+  x = (x | (x >> 3)) & 0x03030303u;
+  x = (x | (x >> 6)) & 0x000F000Fu;
+  return (x | (x >> 12)) & 0x000000FFu;
+}
+
+// Sums of magnitude at most kSmallSum leave the fp32 accumulator through one
+// add: for an integer x with |x| <= 2^22 - 8, residue_magic<p>() + x is exact
+// and lies in [2^23, 2^24), so its bit pattern is 0x4B000000 + (the constant
+// - 2^23) + x; the constant is 1.5 2^23 + d, d (0, 2, 1, 0 for p = 2, 3, 5, 7)
+// making that pattern congruent to x mod p.
+constexpr int64_t kSmallSum = (int64_t(1) << 22) - 8;
+template <int MOD>
+__device__ __forceinline__ float residue_magic() {
+  return MOD == 3 ? 12582914.0f : (MOD == 5 ? 12582913.0f : 12582912.0f);
+}
+
 // 32 accumulator values of one row (exact integers in fp32, |x| < 2^24)
 // reduced mod p and packed into one 32-bit word per plane (value i at bit i).
-// x + p 2^25 is positive and has x's residue, so the reduction is an unsigned
-// one (a multiply-high by the reciprocal); the bits are gathered through four
-// independent partial words (disjoint bits, so adds), keeping chains short.
+// Each value first becomes a non-negative 32-bit integer y with x's residue:
+// the bits of x + residue_magic (one add) when the caller knows |x| <=
+// kSmallSum (`small`), else the truncated integer plus p 2^25.  Then q =
+// floor(y / p) by a multiply-high (0x55555556 is exact for y < 2^31 at p =
+// 3, 0x24924925 for y < 2^32 / 3 at p = 7, 0xCCCCCCCD with a shift at p = 5),
+// and r = y - p q is added into 2-bit (p = 3) or 4-bit (p = 5, 7) fields,
+// whose bit-planes are gathered 16 or 8 values at a time.  p = 2 takes y's
+// low bit.  v is overwritten.
 template <int Q, int P>
-__device__ __forceinline__ void pack32(const uint32_t (&v)[32], uint32_t (&h)[P]) {
+__device__ __forceinline__ void pack32(uint32_t (&v)[32], uint32_t (&h)[P], bool small) {
   constexpr int mod = Q == 4 ? 2 : Q;
-  constexpr int off = mod * (1 << 25);
-  uint32_t part[P][4];
+  if (small) {
 #pragma unroll
-  for (int p = 0; p < P; ++p)
+    for (int i = 0; i < 32; ++i) v[i] = __float_as_uint(__uint_as_float(v[i]) + residue_magic<mod>());
+  } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) part[p][j] = 0u;
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int x = __float2int_rz(__uint_as_float(v[i]));  // an exact integer
-    const uint32_t r = mod == 2 ? (uint32_t(x) & 1u) : uint32_t(x + off) % uint32_t(mod);
-    if constexpr (Q == 3) {
-      part[0][i & 3] += ((r + 1u) >> 1) << i;  // unit: r != 0
-      part[1][i & 3] += (r >> 1) << i;         // sign: r == 2
-    } else if constexpr (Q == 4 || Q == 2) {
-      part[0][i & 3] += r << i;
-    } else {
-#pragma unroll
-      for (int p = 0; p < P; ++p) part[p][i & 3] += ((r >> p) & 1u) << i;
-    }
+    for (int i = 0; i < 32; ++i) v[i] = uint32_t(__float2int_rz(__uint_as_float(v[i])) + mod * (1 << 25));
   }
+  if constexpr (mod == 2) {
+    uint32_t part[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-  for (int p = 0; p < P; ++p) h[p] = (part[p][0] | part[p][1]) | (part[p][2] | part[p][3]);
+    for (int i = 0; i < 32; ++i) part[i & 3] += (v[i] & 1u) << i;
+    h[0] = (part[0] | part[1]) | (part[2] | part[3]);
+  } else if constexpr (mod == 3) {
+    uint32_t f[2] = {0u, 0u};  // value i in bits 2 (i % 16) .. of f[i / 16]
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const uint32_t q = __umulhi(v[i], 0x55555556u);
+      f[i >> 4] += (v[i] - 3u * q) << (2 * (i & 15));
+    }
+    // unit: r != 0 (either bit of the field); sign: r == 2 (its high bit)
+    h[0] = even16(f[0] | (f[0] >> 1)) | (even16(f[1] | (f[1] >> 1)) << 16);
+    h[1] = even16(f[0] >> 1) | (even16(f[1] >> 1) << 16);
+  } else {
+    uint32_t f[4] = {0u, 0u, 0u, 0u};  // value i in bits 4 (i % 8) .. of f[i / 8]
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const uint32_t q = mod == 5 ? (__umulhi(v[i], 0xCCCCCCCDu) >> 2) : __umulhi(v[i], 0x24924925u);
+      f[i >> 3] += (v[i] - uint32_t(mod) * q) << (4 * (i & 7));
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      h[p] = nib8(f[0] >> p) | (nib8(f[1] >> p) << 8) | (nib8(f[2] >> p) << 16) | (nib8(f[3] >> p) << 24);
+  }
 }
 
 // NW 64-column words of one accumulator row (this lane's TMEM lane, from
 // column address taddr), reduced mod p and packed into plane words (pack32
 // per 32-value load).
 template <int Q, int P, int NW = BN / 64>
-__device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&words)[P][NW], int live = 2 * NW) {
+__device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&words)[P][NW], bool small,
+                                                  int live = 2 * NW) {
 #pragma unroll
   for (int c = 0; c < 2 * NW; ++c) {
     if (c >= live) {  // columns past the product's n (warp-uniform): nothing to read
@@ -589,7 +635,7 @@ __device__ __forceinline__ void drain_accumulator(uint32_t taddr, uint64_t (&wor
     }
     uint32_t v[32], hw[P];
     tmem_ld32(taddr + uint32_t(c * 32), v);
-    pack32<Q, P>(v, hw);
+    pack32<Q, P>(v, hw, small);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       const uint64_t h = hw[p];
@@ -727,7 +773,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tile_coords(prm, t, mb, nb);
       const int64_t row = int64_t(mb) * BM + ew * 32 + lane;
       uint64_t words[P][BN / 64];
-      drain_accumulator<Q, P>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN), words);
+      drain_accumulator<Q, P>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * BN), words, prm.small);
       // the accumulator has been read: hand it back to the MMA warp
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -972,7 +1018,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairGeo<WIDE>::THREA
       for (int j = 0; j < G::BBLK; ++j) {  // one 256-column block at a time
         uint64_t words[P][CW / 64];
         drain_accumulator<Q, P, CW / 64>(
-            tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * G::NB + 256 * j + CW * grp), words);
+            tmem + (uint32_t(ew * 32) << 16) + uint32_t(b * G::NB + 256 * j + CW * grp), words, prm.small);
         if (row < prm.m)
           store_words<Q, P, CW / 64>(prm, row, int64_t(nb) * (G::NB / 64) + 4 * j + (CW / 64) * grp, words);
       }
@@ -1212,8 +1258,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(f4::THREADS, 1)
       for (int wd = w_lo; wd < w_hi && 64 * wd < w; ++wd) {
         uint32_t v[2][32], h0[P], h1[P];
         tmem_ld64(tmem + (uint32_t(ew * 32) << 16) + uint32_t(64 * wd), v);
-        pack32<Q, P>(v[0], h0);
-        pack32<Q, P>(v[1], h1);
+        pack32<Q, P>(v[0], h0, prm.small);
+        pack32<Q, P>(v[1], h1, prm.small);
         uint64_t words[P][1];
 #pragma unroll
         for (int p = 0; p < P; ++p) words[p][0] = uint64_t(h0[p]) | (uint64_t(h1[p]) << 32);
@@ -1520,7 +1566,8 @@ __global__ void __launch_bounds__(THREADS_F, 1)
         const int64_t rest = bo.n - col0;
         const int live = rest <= 0 ? 0 : (rest >= 128 ? 4 : int((rest + 31) / 32));
         uint64_t words[P][2];
-        drain_accumulator<Q, P, 2>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(ab * BN + half * 128), words, live);
+        drain_accumulator<Q, P, 2>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(ab * BN + half * 128), words, false,
+                                   live);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive_cta(accempty + 8 * ab);
@@ -1604,6 +1651,7 @@ inline int form_for(int64_t m, int64_t l, const TcOptions &to) {
 struct Layout {
   int rounds;
   bool fp4;
+  bool small;  // l B^2 <= kSmallSum: every partial sum leaves the accumulator through one add
   int64_t la, row, npad, pc, a_bytes, b_bytes;
 };
 
@@ -1611,6 +1659,8 @@ inline Layout layout_for(int q, int64_t m, int64_t l, int64_t n, int form) {
   Layout lo;
   lo.rounds = q == 4 ? 3 : 1;
   lo.fp4 = form == 5;
+  const int64_t b = q == 2 || q == 4 ? 1 : (q - 1) / 2;  // the largest balanced magnitude
+  lo.small = l * b * b <= kSmallSum;
   lo.la = cdiv(l, lo.fp4 ? 2 * BK : BK) * (lo.fp4 ? 2 * BK : BK);
   lo.row = lo.fp4 ? lo.la / 2 : lo.la;
   lo.pc = fq_pitch_words(n);
@@ -1641,6 +1691,7 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, const Lay
   if (tiles >= (int64_t(1) << 31)) return FQ_ENOTSUP;
   prm.tiles = int(tiles);
   prm.plane = plane;
+  prm.small = lo.small;
   prm.err = err;
   prm.group = to.group > 0 ? to.group : GROUP_M;
   int dev = 0, sms = 0;

@@ -358,6 +358,30 @@ def test_tcgen05_exact_with_random_low_bits(fq, q, l, codes, m, kernel):
     assert (got == want[None, :]).all()
 
 
+SMALL_SUM = (1 << 22) - 8   # the epilogue's one-add conversion covers |sum| <= 2^22 - 8
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("m, kernel", [(3, 2), (260, 5)])
+@pytest.mark.parametrize("q, a, top", [(3, 1, 1), (3, 2, 1), (7, 3, 3), (7, 4, 3)])
+@pytest.mark.parametrize("extra", [0, 1])
+def test_tcgen05_sums_at_the_epilogue_boundary(fq, q, a, top, m, kernel, extra):
+    """Every row of A is a (balanced +-top) and column 0 of B is all +top,
+    column 1 all -top, so the two sums are +-l top^2: exactly +-(2^22 - 8) at
+    the longest l whose sums the epilogue reads through one add, and one term
+    past it (extra = 1), where it reads them through the truncating
+    conversion; the other columns are random.  C = a colsum(B) mod q."""
+    l = SMALL_SUM // (top * top) + extra
+    n = 70
+    A = np.full((m, l), a, np.uint8)
+    B = np.random.default_rng(l + q).integers(0, q, size=(l, n), dtype=np.uint8)
+    B[:, 0] = top
+    B[:, 1] = q - top
+    got, _ = gpu_product(fq, q, A, B, path=fq.PATH_MMA, kernel=kernel)
+    want = (a * B.sum(axis=0, dtype=np.int64)) % q
+    assert (got == want[None, :]).all()
+
+
 @pytest.mark.parametrize("q", FIELDS)
 @pytest.mark.parametrize("k", range(1, 8))
 def test_fp4_form_every_last_tile_width(fq, q, k):
