@@ -386,58 +386,84 @@ __global__ void rows_to_fp4(const uint64_t *__restrict__ X, int64_t rows, int64_
 }
 
 // Launch shape of rows_to_fp4 for rows x cols (cols a multiple of 32): one
-// wave of 256-thread blocks (8 per SM on 152 SMs), each walking row groups.
-inline dim3 rows_grid4(int64_t rows, int64_t cols) {
+// wave of 256-thread blocks (`per_sm` resident per SM, from the occupancy
+// calculator), each walking row groups.
+inline dim3 rows_grid4(int64_t rows, int64_t cols, int sms, int per_sm) {
   const int64_t pieces = cols / 32, xs = cdiv(pieces, 256), groups = cdiv(rows, RPT);
-  const int64_t want = cdiv(int64_t(152) * 8, xs);
+  const int64_t want = cdiv(int64_t(sms) * per_sm, xs);
   const int64_t ys = groups < want ? groups : want;
   return dim3(unsigned(xs), unsigned(ys < 65535 ? (ys > 0 ? ys : 1) : 65535));
 }
 
 // B^T as packed e2m1 straight from B's planes: row j of out (ld bytes) holds
 // B[k][j] in nibble k, for every column j of the planes' pitch (n_pad = 64
-// pitch) and k < kcols (a multiple of 256; rows k >= rows read as zero).  A
-// CTA of eight warps turns a 256 (k) x 256 (j) block around: warp w loads rows
-// k0 + 32 w + lane, all 256 columns (four words of every plane), transposes
-// each 32 x 32 bit block across the warp, converts lane j's 32 bits into 16
-// bytes and puts them at chunk w of row j of a shared 256 x 128-byte tile
-// (16-byte chunks XOR-swizzled by row, so that eight lanes hit eight bank
-// groups); the tile leaves in 128-byte rows.
-constexpr int TK4 = 256, TJ4 = 256;
+// pitch) and k < kcols (a multiple of 64; rows k >= rows read as zero).  The
+// work is in blocks of 64 (k) x 256 (j), taken by a persistent grid (k
+// fastest, so that neighbouring CTAs fill neighbouring bytes of the same
+// output rows).  In a block, warp w loads rows k0 + 32 (w % 2) + lane, one
+// word (64 columns) j0 / 64 + w / 2 of every plane, transposes its two 32 x 32
+// bit blocks across the warp and converts lane j's 32 bits into 16 bytes,
+// chunk w % 2 of row j of a shared 256 x 32-byte tile (the chunk index XORed
+// with bit 2 of the row, so that the eight lanes of a store phase hit eight
+// bank groups); the tile leaves in 32-byte row pieces.
+constexpr int TK4 = 64, TJ4 = 256;
 template <int Q, int P>
 __global__ void __launch_bounds__(256) planes_to_fp4_t(const uint64_t *__restrict__ X, int64_t rows, int64_t pitch,
-                                                       uint8_t *__restrict__ out, int64_t ld, int64_t kcols, int sel) {
+                                                       uint8_t *__restrict__ out, int64_t ld, int sel,
+                                                       int64_t kblocks, int64_t blocks) {
   using CF = ConvField<Q>;
-  __shared__ uint4 tile[TJ4 * 8];
+  __shared__ uint4 tile[TJ4 * 2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t k0 = int64_t(blockIdx.x) * TK4, j0 = int64_t(blockIdx.y) * TJ4;
-  const int64_t k = k0 + 32 * warp + lane;
-  uint32_t t[8][P];  // group g: columns j0 + 32 g .. + 31
+  const int kq = warp & 1, jq = warp >> 1;
+  for (int64_t blk = blockIdx.x; blk < blocks; blk += gridDim.x) {
+    const int64_t k0 = (blk % kblocks) * TK4, j0 = (blk / kblocks) * TJ4;
+    const int64_t k = k0 + 32 * kq + lane;
+    uint32_t t[2][P];  // half g: columns j0 + 64 jq + 32 g .. + 31
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(X + (p * rows + k) * pitch + j0 / 64);
-    const uint4 v0 = k < rows ? __ldg(src) : make_uint4(0u, 0u, 0u, 0u);
-    const uint4 v1 = k < rows ? __ldg(src + 1) : make_uint4(0u, 0u, 0u, 0u);
-    t[0][p] = v0.x; t[1][p] = v0.y; t[2][p] = v0.z; t[3][p] = v0.w;
-    t[4][p] = v1.x; t[5][p] = v1.y; t[6][p] = v1.z; t[7][p] = v1.w;
-  }
+    for (int p = 0; p < P; ++p) {
+      const uint64_t w = k < rows ? __ldg(X + (p * rows + k) * pitch + j0 / 64 + jq) : 0ull;
+      t[0][p] = uint32_t(w);
+      t[1][p] = uint32_t(w >> 32);
+    }
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
-    uint32_t o[CF::P2];
-    select_planes<Q, P>(t[g], sel, o);
+    for (int g = 0; g < 2; ++g) {
+      uint32_t o[CF::P2];
+      select_planes<Q, P>(t[g], sel, o);
 #pragma unroll
-    for (int p = 0; p < CF::P2; ++p) o[p] = transpose32(o[p], lane);
-    const int jl = 32 * g + lane;  // lane: column j0 + jl, bit i = row k0 + 32 warp + i
-    tile[jl * 8 + (warp ^ (jl & 7))] = e2m1x32<CF::Q2, CF::P2>(o);
-  }
-  __syncthreads();
-  uint8_t *blk = out + j0 * ld + k0 / 2;
+      for (int p = 0; p < CF::P2; ++p) o[p] = transpose32(o[p], lane);
+      const int jl = 64 * jq + 32 * g + lane;  // lane: column j0 + jl, bit i = row k0 + 32 kq + i
+      tile[jl * 2 + (kq ^ ((jl >> 2) & 1))] = e2m1x32<CF::Q2, CF::P2>(o);
+    }
+    __syncthreads();
 #pragma unroll
-  for (int i = threadIdx.x; i < TJ4 * 8; i += 256) {
-    const int jl = i >> 3, c = i & 7;
-    if (k0 + 32 * c < kcols) *reinterpret_cast<uint4 *>(blk + jl * ld + 16 * c) = tile[jl * 8 + (c ^ (jl & 7))];
+    for (int i = threadIdx.x; i < TJ4 * 2; i += 256) {
+      const int jl = i >> 1, c = i & 1;
+      *reinterpret_cast<uint4 *>(out + (j0 + jl) * ld + k0 / 2 + 16 * c) = tile[jl * 2 + (c ^ ((jl >> 2) & 1))];
+    }
+    __syncthreads();
   }
 }
+
+// Resident 256-thread blocks per SM of a kernel (the occupancy calculator).
+template <class K>
+int occupancy256(K kernel) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 256, 0) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
+// The fp4 conversions' resident blocks per SM, computed once per field.
+template <int Q, int P>
+struct Fp4Occupancy {
+  static int rows() {
+    static const int n = occupancy256(rows_to_fp4<Q, P>);
+    return n;
+  }
+  static int transpose() {
+    static const int n = occupancy256(planes_to_fp4_t<Q, P>);
+    return n;
+  }
+};
 
 // ------------------------------------------------------------------ GEMM --
 
@@ -1735,13 +1761,18 @@ int prepare(int64_t m, int64_t l, int64_t n, const uint64_t *A, const uint64_t *
   const Layout lo = layout_for(Q, m, l, n, form);
   if (lo.npad / TJ > 65535) return FQ_ENOTSUP;
   const int64_t pa = fq_pitch_words(l);
+  int dev = 0, sms = 0;
+  FQ_CUDA_TRY(cudaGetDevice(&dev));
+  FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   // GF(4): the operands of X, Y, Z are A0, A1, A0 + A1 and B0, B1, B0 + B1 (sel 0, 1, 2)
   for (int r = 0; r < lo.rounds; ++r) {
     uint8_t *a = ws + r * (lo.a_bytes + lo.b_bytes), *b = a + lo.a_bytes;
     if (lo.fp4) {
-      rows_to_fp4<Q, P><<<rows_grid4(m, lo.la), 256, 0, s>>>(A, m, lo.la, pa, a, lo.row, r);
-      const dim3 grid(unsigned(lo.la / TK4), unsigned(lo.npad / TJ4));
-      planes_to_fp4_t<Q, P><<<grid, 256, 0, s>>>(B, l, lo.pc, b, lo.row, lo.la, r);
+      const int per_a = Fp4Occupancy<Q, P>::rows(), per_b = Fp4Occupancy<Q, P>::transpose();
+      rows_to_fp4<Q, P><<<rows_grid4(m, lo.la, sms, per_a), 256, 0, s>>>(A, m, lo.la, pa, a, lo.row, r);
+      const int64_t kblocks = lo.la / TK4, blocks = kblocks * (lo.npad / TJ4);
+      const int64_t grid = blocks < int64_t(sms) * per_b ? blocks : int64_t(sms) * per_b;
+      planes_to_fp4_t<Q, P><<<unsigned(grid), 256, 0, s>>>(B, l, lo.pc, b, lo.row, r, kblocks, blocks);
     } else {
       rows_to_e4m3<Q, P><<<rows_grid(m, lo.la), 256, 0, s>>>(A, m, lo.la, pa, a, lo.la, 0, r);
       transpose_to<Q, P>(B, l, lo.pc, lo.npad, b, lo.la, 0, lo.la, r, s);
