@@ -112,7 +112,8 @@ typedef struct fq_options {
   int k;         /* M4RM block size: 0 = planner, else 6..10 (Section 2's k)       */
   int64_t chunk; /* MMA path: l-chunk length between mod-p reductions; 0 = largest */
   int variant;   /* M4RM rows per CTA: 0 = planner, else 1 .. the kernel's maximum;
-                    tcgen05 path: row blocks per group of the tile order (0 = 8) */
+                    tcgen05 path: row blocks per group of the tile order (0 = 8,
+                    16 for the fp4 form)                                     */
   int kernel;    /* M4RM kernel: 0 = planner, i + 1 = compiled kernel i of field q;
                     tensor-core path: 0 = tcgen05 by shape, 1 = the mma.sync
                     s8 form, 2 = tcgen05 on single SMs (128 x 256 tiles),

@@ -50,6 +50,7 @@ constexpr int SMEM = BAR_OFF + 8 * NBARS + 16 + 1024;  // + alignment slack
 constexpr int TMEM_COLS = ACC * BN;
 constexpr int THREADS = 256;
 constexpr int GROUP_M = 8;                     // tile order: default row blocks per group (L2 reuse)
+constexpr int GROUP_M4 = 16;                   // the same for the fp4 form (its operands are half the bytes)
 constexpr int THREADS_B = 640;                 // batched kernel: sixteen epilogue warps
 
 // ---------------------------------------------------------- conversions --
@@ -1719,7 +1720,7 @@ int gemm(const uint8_t *Ab, const uint8_t *Bt, uint64_t *C, int64_t m, const Lay
   prm.plane = plane;
   prm.small = lo.small;
   prm.err = err;
-  prm.group = to.group > 0 ? to.group : GROUP_M;
+  prm.group = to.group > 0 ? to.group : (fp4 ? GROUP_M4 : GROUP_M);
   int dev = 0, sms = 0;
   FQ_CUDA_TRY(cudaGetDevice(&dev));
   FQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
