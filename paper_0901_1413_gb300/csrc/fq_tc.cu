@@ -1593,8 +1593,9 @@ __global__ void __launch_bounds__(THREADS_F, 1)
         const int64_t rest = bo.n - col0;
         const int live = rest <= 0 ? 0 : (rest >= 128 ? 4 : int((rest + 31) / 32));
         uint64_t words[P][2];
-        drain_accumulator<Q, P, 2>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(ab * BN + half * 128), words, false,
-                                   live);
+        constexpr int64_t bb = Q == 4 || Q == 2 ? 1 : (Q - 1) / 2;  // the largest balanced magnitude
+        drain_accumulator<Q, P, 2>(tmem + (uint32_t(ew * 32) << 16) + uint32_t(ab * BN + half * 128), words,
+                                   int64_t(bp.l) * bb * bb <= kSmallSum, live);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive_cta(accempty + 8 * ab);
