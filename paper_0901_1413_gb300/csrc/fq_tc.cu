@@ -204,16 +204,32 @@ inline dim3 rows_grid(int64_t rows, int64_t cols) {
 
 // 32 x 32 bit transpose across a warp: afterwards bit i of lane j's word is
 // bit j of lane i's word before.  Five stages swap the off-diagonal s x s
-// blocks between lanes l and l ^ s (s = 16, 8, 4, 2, 1).
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+// blocks between lanes l and l ^ s (s = 16, 8, 4, 2, 1): a lane keeps its
+// bits under `keep` (the mask m of the stage's low blocks, or ~m when bit s of
+// the lane is set) and takes the rest from the partner's word rotated left by
+// s (or right by s): the bits a rotation wraps around land under `keep`.
+struct Transpose32 {
+  uint32_t rot[5], keep[5];
+  __device__ __forceinline__ explicit Transpose32(int lane) {
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const uint32_t m = s == 16 ? 0x0000FFFFu : (s == 8 ? 0x00FF00FFu : (s == 4 ? 0x0F0F0F0Fu : (s == 2 ? 0x33333333u : 0x55555555u)));
-    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, s);
-    x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+    for (int k = 0; k < 5; ++k) {
+      const int s = 16 >> k;
+      const uint32_t m = s == 16 ? 0x0000FFFFu : (s == 8 ? 0x00FF00FFu : (s == 4 ? 0x0F0F0F0Fu : (s == 2 ? 0x33333333u : 0x55555555u)));
+      rot[k] = (lane & s) ? uint32_t(32 - s) : uint32_t(s);
+      keep[k] = (lane & s) ? ~m : m;
+    }
   }
-  return x;
-}
+  __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, 16 >> k);
+      x = lop3<0xE4>(x, __funnelshift_l(y, y, rot[k]), keep[k]);  // (x & keep) | (rot & ~keep)
+    }
+    return x;
+  }
+};
+
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) { return Transpose32(lane)(x); }
 
 // B^T as e4m3 bytes straight from B's planes: out[j * ld + off + k] = the byte
 // of B[k][j] for every column j of the planes' pitch (n_pad = 64 pitch) and
@@ -416,6 +432,7 @@ __global__ void __launch_bounds__(256) planes_to_fp4_t(const uint64_t *__restric
   __shared__ uint4 tile[TJ4 * 2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kq = warp & 1, jq = warp >> 1;
+  const Transpose32 tr(lane);
   for (int64_t blk = blockIdx.x; blk < blocks; blk += gridDim.x) {
     const int64_t k0 = (blk % kblocks) * TK4, j0 = (blk / kblocks) * TJ4;
     const int64_t k = k0 + 32 * kq + lane;
@@ -431,7 +448,7 @@ __global__ void __launch_bounds__(256) planes_to_fp4_t(const uint64_t *__restric
       uint32_t o[CF::P2];
       select_planes<Q, P>(t[g], sel, o);
 #pragma unroll
-      for (int p = 0; p < CF::P2; ++p) o[p] = transpose32(o[p], lane);
+      for (int p = 0; p < CF::P2; ++p) o[p] = tr(o[p]);
       const int jl = 64 * jq + 32 * g + lane;  // lane: column j0 + jl, bit i = row k0 + 32 kq + i
       tile[jl * 2 + (kq ^ ((jl >> 2) & 1))] = e2m1x32<CF::Q2, CF::P2>(o);
     }
