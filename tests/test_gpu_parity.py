@@ -341,16 +341,17 @@ def test_tcgen05_exact_near_its_range(fq, m, kernel):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("m, kernel", TC_KERNELS)
-@pytest.mark.parametrize("q, l, codes", [(7, None, (1, 2, 3)), (3, 1 << 22, (0, 1))])
+@pytest.mark.parametrize("q, l, codes", [(7, None, (1, 2, 3)), (5, None, (1, 2)), (3, 1 << 22, (0, 1))])
 def test_tcgen05_exact_with_random_low_bits(fq, q, l, codes, m, kernel):
-    """Rows of A all +3 (F_7) or all +1 (F_3) against random positive B: every
-    step of the tensor-core sum adds a random amount, so an accumulation that
-    dropped low bits anywhere on the way to 2^24 (F_7 at its longest exact l)
-    or 2^22 (F_3) would change the residues.  C = A B is a column sum of B.
-    Every product kernel, e4m3 and packed e2m1 (block scale factors 1.0)."""
+    """Rows of A all +3 (F_7), +2 (F_5) or +1 (F_3) against random positive B:
+    every step of the tensor-core sum adds a random amount, so an
+    accumulation that dropped low bits anywhere on the way to 2^24 (F_7 and
+    F_5 at their longest exact l) or 2^22 (F_3) would change the residues.
+    C = A B is a column sum of B.  Every product kernel, e4m3 and packed e2m1
+    (block scale factors 1.0)."""
     l = l or _tc_max_l(fq, q)
     n = 70
-    a = 3 if q == 7 else 1
+    a = {7: 3, 5: 2, 3: 1}[q]
     A = np.full((m, l), a, np.uint8)
     B = np.random.default_rng(q).choice(np.array(codes, np.uint8), size=(l, n))
     got, _ = gpu_product(fq, q, A, B, path=fq.PATH_MMA, kernel=kernel)
@@ -363,7 +364,7 @@ SMALL_SUM = (1 << 22) - 8   # the epilogue's one-add conversion covers |sum| <= 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("m, kernel", [(3, 2), (260, 5)])
-@pytest.mark.parametrize("q, a, top", [(3, 1, 1), (3, 2, 1), (7, 3, 3), (7, 4, 3)])
+@pytest.mark.parametrize("q, a, top", [(3, 1, 1), (3, 2, 1), (5, 2, 2), (5, 3, 2), (7, 3, 3), (7, 4, 3)])
 @pytest.mark.parametrize("extra", [0, 1])
 def test_tcgen05_sums_at_the_epilogue_boundary(fq, q, a, top, m, kernel, extra):
     """Every row of A is a (balanced +-top) and column 0 of B is all +top,
