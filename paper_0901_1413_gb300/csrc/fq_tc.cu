@@ -2,14 +2,14 @@
 //
 // The same product C = A B as the Four-Russians path, as a dense contraction
 // of small integers.  The integer tcgen05 kind is not available on sm_103a, so
-// residues enter kind::f8f6f4 with e4m3 operands and fp32 accumulation, which
-// is exact here: balanced residues |a|, |b| <= (p - 1) / 2 <= 3 are exact in
-// e4m3 (1, 2, 3 = 1.000, 1.000 x 2, 1.100 x 2 in binary), every product is an
-// exact small integer, and every partial sum of l of them stays an integer
-// below 2^24 in magnitude (the launcher checks l * B^2 < 2^24 and otherwise
-// takes the mma.sync s8 path), so no rounding ever happens.  The epilogue
-// reads the fp32 accumulators from TMEM, reduces mod p and packs the residues
-// into bit-planes.
+// residues enter as balanced small floats with fp32 accumulation, which is
+// exact here: balanced residues |a|, |b| <= (p - 1) / 2 <= 3 are exact in e4m3
+// (1, 2, 3 = 1.000, 1.000 x 2, 1.100 x 2 in binary) and in e2m1 (0010, 0100,
+// 0101), every product is an exact small integer, and every partial sum of l
+// of them stays an integer below 2^24 in magnitude (the launcher checks
+// l * B^2 < 2^24 and otherwise takes the mma.sync s8 path), so no rounding
+// ever happens.  The epilogue reads the fp32 accumulators from TMEM, reduces
+// mod p and packs the residues into bit-planes.
 //
 // GF(4) follows Section 4.3 at matrix level with three F_2 products (the
 // Karatsuba form): X = A0 B0, Y = A1 B1, Z = (A0 + A1)(B0 + B1), each read mod
@@ -17,20 +17,26 @@
 // the coefficient of alpha once alpha^2 = alpha + 1 is folded in).  The first
 // product writes X into both planes, the other two add theirs in (XOR).
 //
-// Layout.  The operands are first converted from planes to e4m3 bytes: A as m
-// rows of la = roundup(l, 128) values, B transposed to n_pad rows of la values
-// (K contiguous for both, as the tensor core reads them), zero past l.  Three
-// persistent product kernels read them through TMA (128-byte swizzle) and keep
-// their fp32 sums in TMEM; one thread issues the MMAs and a group of warps
-// drains the accumulators (tcgen05.ld) and writes the packed codes:
-//   - single SMs (m <= 128): 128 x 256 tiles, two 256-column accumulators, so
-//     a tile's epilogue overlaps the next tile's products;
-//   - SM pairs (cta_group::2): 256 x 256 tiles, each CTA staging its own
-//     halves of A and B^T, also double-buffered;
-//   - SM pairs, wide (from 32 k-slices): 256 x 512 tiles, two MMAs per step
-//     into one 512-column accumulator, for a third more load-latency cover.
-// The batched form converts many products into two shared arenas and runs
-// one persistent kernel over all their tiles.  Every mbarrier wait is bounded.
+// Layout.  The operands are first converted from planes to K-contiguous rows
+// (A as m rows, B transposed to n_pad rows, zero past l), as the tensor core
+// reads them, in one of two formats, and persistent product kernels read them
+// through TMA (128-byte swizzle) and keep their fp32 sums in TMEM; one thread
+// issues the MMAs and a group of warps drains the accumulators (tcgen05.ld)
+// and writes the packed codes:
+//   - e4m3 bytes, la = roundup(l, 128) per row, kind::f8f6f4:
+//     - single SMs (m <= 128): 128 x 256 tiles, two 256-column accumulators,
+//       so a tile's epilogue overlaps the next tile's products;
+//     - SM pairs (cta_group::2): 256 x 256 tiles, each CTA staging its own
+//       halves of A and B^T, also double-buffered;
+//     - SM pairs, wide: 256 x 512 tiles, two MMAs per step into one
+//       512-column accumulator, for a third more load-latency cover;
+//   - packed e2m1, la / 2 bytes per row (la = roundup(l, 256)), kind::mxf4
+//     with block scale factors 1.0 held in TMEM, at twice the e4m3 rate: SM
+//     pairs, 256 x 448 tiles (the default for m > 128 and l >= 2048).
+// The batched form gives whole products to persistent CTAs whose converter
+// warps write each product's e4m3 operands into the CTA's own two scratch
+// buffers while its tensor-core warps compute the previous product.  Every
+// mbarrier wait is bounded.
 #include <cstring>
 
 #include "../../include/fq.h"
