@@ -41,6 +41,7 @@
 
 #include "../../include/fq.h"
 #include "fq_common.cuh"
+#include "fq_e4m3.cuh"
 #include "fq_internal.h"
 
 namespace fqk {
@@ -61,13 +62,6 @@ constexpr int THREADS_B = 640;                 // batched kernel: sixteen epilog
 
 // ---------------------------------------------------------- conversions --
 
-// e4m3 byte of a small integer (sign, 4 exponent bits biased by 7, 3 mantissa
-// bits): 0, +-1, +-2, +-3 are exact.
-__host__ __device__ constexpr uint32_t e4m3_byte(int v) {
-  return v == 0 ? 0u
-                : ((v < 0 ? 0x80u : 0u) | ((v == 1 || v == -1) ? 0x38u : ((v == 2 || v == -2) ? 0x40u : 0x44u)));
-}
-
 // Balanced value of a code (the bits of the element in planes 0, 1, 2).
 // F_3: unit | sign << 1 (code 2 is unused); F_5, F_7: any 3-bit code, read mod
 // p; F_2 and the GF(4) planes: the bit.
@@ -79,53 +73,6 @@ __host__ __device__ constexpr int code_value(int code) {
     return r > Q / 2 ? r - Q : r;
   }
   return code & 1;
-}
-
-// The e4m3 bytes of codes 4 g .. 4 g + 3, one per byte.
-template <int Q>
-__host__ __device__ constexpr uint32_t table_word(int g) {
-  uint32_t w = 0;
-  for (int i = 0; i < 4; ++i) w |= e4m3_byte(code_value<Q>(4 * g + i)) << (8 * i);
-  return w;
-}
-
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-  uint32_t d;
-  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-  return d;
-}
-
-// Bits 0..3 of b spread to bits 0, 4, 8, 12: bits 2, 3 move up by 6, then the
-// odd bits of each pair move up by 3.
-__device__ __forceinline__ uint32_t spread4(uint32_t b) {
-  const uint32_t x = (b | (b << 6)) & 0x0303u;
-  return (x | (x << 3)) & 0x1111u;
-}
-
-// Bits 0..3 of b to the low bit of bytes 0..3: b times 1 + 2^7 + 2^14 + 2^21
-// puts bit i at bit 8 i, and the four shifted copies of b do not overlap.
-__device__ __forceinline__ uint32_t bytes_of_bits(uint32_t b) { return (b * 0x204081u) & 0x01010101u; }
-
-// Elements e .. e + 3 as four e4m3 bytes, from 32-bit plane words t (element
-// i at bit i).  Q = 2 takes one plane (F_2, and a selected GF(4) plane): 1 ->
-// 0x38.  Q = 3: unit u, sign s -> u 0x38 | s 0x80 (u = 0, s = 1 gives -0,
-// which adds nothing, as code 2 stands for 0).  F_5, F_7: the 3-bit codes
-// become a byte-permute selector into the table (nibbles below 8, so no sign
-// replication).
-template <int Q, int P>
-__device__ __forceinline__ uint32_t e4m3x4(const uint32_t (&t)[P], int e) {
-  if constexpr (Q == 2) {
-    return bytes_of_bits((t[0] >> e) & 0xFu) * 0x38u;
-  } else if constexpr (Q == 3) {
-    const uint32_t u = (t[0] >> e) & 0xFu, sg = (t[1] >> e) & 0xFu;
-    return (bytes_of_bits(u) * 0x38u) | ((sg * 0x10204080u) & 0x80808080u);
-  } else {
-    uint32_t c = 0;
-#pragma unroll
-    for (int p = 0; p < P; ++p) c |= spread4((t[p] >> e) & 0xFu) << p;
-    constexpr uint32_t T0 = table_word<Q>(0), T1 = table_word<Q>(1);
-    return prmt(T0, T1, c);
-  }
 }
 
 // The planes a conversion reads: GF(4) becomes one F_2 plane, `sel` 0, 1 or
@@ -145,39 +92,29 @@ __device__ __forceinline__ void select_planes(const uint32_t (&t)[P], int sel, u
   }
 }
 
-// Sixteen elements b0 .. b0 + 15 of the plane words as a 16-byte vector.
-template <int Q, int P>
-__device__ __forceinline__ uint4 e4m3x16(const uint32_t (&t)[P], int b0) {
-  using CF = ConvField<Q>;
-  return make_uint4(e4m3x4<CF::Q2, P>(t, b0), e4m3x4<CF::Q2, P>(t, b0 + 4), e4m3x4<CF::Q2, P>(t, b0 + 8),
-                    e4m3x4<CF::Q2, P>(t, b0 + 12));
-}
-
 // Rows of a planes matrix to e4m3 bytes: out[r * ld + off + c] for c < cols,
-// cols and off multiples of 16 (cols may run into the planes' zero padding,
-// which gives zeros).  One thread per 16 elements (a 16-byte store), so that a
-// warp writes 512 contiguous bytes; a thread loads RPT rows' words before it
-// converts any of them.
+// cols a multiple of 32 and off of 16 (cols may run into the planes' zero
+// padding, which gives zeros).  One thread per 32 elements (one 32-bit plane
+// word, two 16-byte stores), so that a warp writes 1024 contiguous bytes; a
+// thread loads RPT rows' words before it converts any of them.
 constexpr int RPT = 4;
 template <int Q, int P>
 __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64_t cols, int64_t pitch,
                              uint8_t *__restrict__ out, int64_t ld, int64_t off, int sel) {
   using CF = ConvField<Q>;
-  // grid: x over the 16-byte pieces of a row, y over groups of RPT rows
+  // grid: x over the 32-element pieces of a row, y over groups of RPT rows
   // (grid-stride); the next group's words are loaded before this group is
   // converted and stored
-  const int64_t piece = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t c0 = piece * 16;
+  const int64_t piece = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // the 32-bit plane word
+  const int64_t c0 = piece * 32;
   if (c0 >= cols) return;
   const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
-  const int64_t half = piece >> 1;    // the 32-bit half word holding the 16 elements
-  const int b0 = 16 * int(piece & 1);
   auto load = [&](int64_t r0, uint32_t (&t)[RPT][P]) {
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
 #pragma unroll
       for (int p = 0; p < P; ++p)
-        t[i][p] = r0 + i < rows ? __ldg(X32 + (p * rows + r0 + i) * pitch * 2 + half) : 0u;
+        t[i][p] = r0 + i < rows ? __ldg(X32 + (p * rows + r0 + i) * pitch * 2 + piece) : 0u;
   };
   const int64_t step = int64_t(gridDim.y) * RPT;
   int64_t r0 = int64_t(blockIdx.y) * RPT;
@@ -190,7 +127,11 @@ __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64
       if (r0 + i >= rows) break;
       uint32_t o[CF::P2];
       select_planes<Q, P>(t[i], sel, o);
-      *reinterpret_cast<uint4 *>(out + (r0 + i) * ld + off + c0) = e4m3x16<Q, CF::P2>(o, b0);
+      uint4 lo, hi;
+      e4m3x32<CF::Q2, CF::P2>(o, lo, hi);
+      uint4 *dst = reinterpret_cast<uint4 *>(out + (r0 + i) * ld + off + c0);
+      dst[0] = lo;
+      dst[1] = hi;
     }
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
@@ -199,10 +140,10 @@ __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64
   }
 }
 
-// Launch shape of rows_to_e4m3 for rows x cols (cols a multiple of 16): one
+// Launch shape of rows_to_e4m3 for rows x cols (cols a multiple of 32): one
 // wave of 256-thread blocks (8 per SM on 152 SMs), each walking row groups.
 inline dim3 rows_grid(int64_t rows, int64_t cols) {
-  const int64_t pieces = cols / 16, xs = cdiv(pieces, 256), groups = cdiv(rows, RPT);
+  const int64_t pieces = cols / 32, xs = cdiv(pieces, 256), groups = cdiv(rows, RPT);
   const int64_t want = cdiv(int64_t(152) * 8, xs);
   const int64_t ys = groups < want ? groups : want;
   return dim3(unsigned(xs), unsigned(ys < 65535 ? (ys > 0 ? ys : 1) : 65535));
@@ -275,8 +216,10 @@ __device__ __forceinline__ void transpose_block(const uint64_t *__restrict__ X, 
     for (int p = 0; p < CF::P2; ++p) o[p] = transpose32(o[p], lane);
     // lane: column jl of the tile, bit i = row k0 + 32 kq + i
     const int jl = 128 * jh + 32 * g + lane, c0 = 2 * kq;
-    tile[jl * 8 + (c0 ^ (jl & 7))] = e4m3x16<Q, CF::P2>(o, 0);
-    tile[jl * 8 + ((c0 + 1) ^ (jl & 7))] = e4m3x16<Q, CF::P2>(o, 16);
+    uint4 lo, hi;
+    e4m3x32<CF::Q2, CF::P2>(o, lo, hi);
+    tile[jl * 8 + (c0 ^ (jl & 7))] = lo;
+    tile[jl * 8 + ((c0 + 1) ^ (jl & 7))] = hi;
   }
   __syncthreads();
 #pragma unroll
@@ -1394,18 +1337,18 @@ __device__ __forceinline__ void mma_e4m3_mn(uint32_t d_tmem, uint64_t a, uint64_
 // A planes matrix of `rows_valid` rows (pitch words, P planes; rows up to
 // `rows` read as zero) as e4m3 bytes in 128-element chunks: chunk c of row r
 // (c < chunks) becomes the 128-byte scratch row row_of(r, c).  The work is
-// split in 16-element pieces, eight to a chunk, so that eight consecutive
-// threads write one 128-byte row (a warp's 16-byte stores cover four whole
-// rows).  Converter thread ct takes the pieces ct, ct + CONV_THREADS, ...
-// (row-major), UNR at a time with all their words loaded first; a thread's
-// (row, piece) advances by the stride's quotient and remainder, so no
-// division runs per piece.
+// split in 32-element pieces (one 32-bit plane word in, 32 bytes out), four
+// to a chunk, so that four consecutive threads write one 128-byte row (a
+// warp's stores cover eight whole rows).  Converter thread ct takes the
+// pieces ct, ct + CONV_THREADS, ... (row-major), UNR at a time with all their
+// words loaded first; a thread's (row, piece) advances by the stride's
+// quotient and remainder, so no division runs per piece.
 template <int Q, int P, class RowOf>
 __device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int rows_valid, int rows, int64_t pitch,
                                              int chunks, uint8_t *buf, int ct, RowOf row_of) {
   using CF = ConvField<Q>;
   constexpr int UNR = 4;
-  const int per_row = 8 * chunks;
+  const int per_row = 4 * chunks;
   const int radv = CONV_THREADS / per_row, padv = CONV_THREADS % per_row;
   const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
   int r = ct / per_row, piece = ct % per_row;
@@ -1418,7 +1361,7 @@ __device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int
       pp[u] = piece;
 #pragma unroll
       for (int p = 0; p < P; ++p)
-        t[u][p] = r < rows_valid ? __ldg(X32 + (p * int64_t(rows_valid) + r) * pitch * 2 + (piece >> 1)) : 0u;
+        t[u][p] = r < rows_valid ? __ldg(X32 + (p * int64_t(rows_valid) + r) * pitch * 2 + piece) : 0u;
       r += radv;
       piece += padv;
       if (piece >= per_row) {
@@ -1431,8 +1374,11 @@ __device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int
       if (rr[u] >= rows) break;
       uint32_t o[CF::P2];
       select_planes<Q, P>(t[u], 0, o);
-      *reinterpret_cast<uint4 *>(buf + row_of(rr[u], pp[u] >> 3) * 128 + (pp[u] & 7) * 16) =
-          e4m3x16<Q, CF::P2>(o, 16 * (pp[u] & 1));
+      uint4 lo, hi;
+      e4m3x32<CF::Q2, CF::P2>(o, lo, hi);
+      uint4 *dst = reinterpret_cast<uint4 *>(buf + row_of(rr[u], pp[u] >> 2) * 128 + (pp[u] & 3) * 32);
+      dst[0] = lo;
+      dst[1] = hi;
     }
   }
 }

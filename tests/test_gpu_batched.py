@@ -80,6 +80,26 @@ def test_batched_mixed_paths_in_one_plan(fq, q):
     check(fq, q, A, B, c)
 
 
+@pytest.mark.parametrize("q", [3, 5, 7])
+def test_batched_tensor_core_depth_and_width_edges(fq, q):
+    """The tcgen05 batch kernel's operands are padded to 128-deep k-slices and
+    256-column tiles, and C is cleared past n: depths from 1 to 257 around
+    multiples of 32, widths from 1 to 513 (a last tile holding one to eight
+    32-column words, in the first, second and third column block) and row
+    counts about one and two 128-row blocks, all in one plan."""
+    depths = (1, 31, 32, 33, 64, 65, 96, 97, 127, 128, 129, 200, 255, 257)
+    widths = (1, 31, 32, 33, 96, 128, 160, 192, 224, 255, 256, 257, 288, 513)
+    rows = (1, 127, 128, 129, 255, 300)
+    shapes = [(rows[i % len(rows)], d, widths[(3 * i) % len(widths)]) for i, d in enumerate(depths)]
+    shapes += [(rows[(i + 2) % len(rows)], depths[(5 * i) % len(depths)], w) for i, w in enumerate(widths)]
+    A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=q + 60)
+    plan = fq.BatchPlan(q, shapes, path=fq.PATH_MMA)
+    assert plan.tc_products == len(shapes) and plan.items == 0
+    plan.run(pa, pb, pc)
+    assert fq.status() == fq.OK
+    check(fq, q, A, B, c)
+
+
 @pytest.mark.parametrize("path", ["m4rm", "mma"])
 @pytest.mark.parametrize("q", [3, 5])
 def test_batched_graph_capture_and_replay(fq, q, path):
