@@ -511,7 +511,7 @@ def kernel_sources_digest():
 def tc_sources_digest():
     """Digest of the sources the tcgen05 product kernel is compiled from."""
     csrc = os.path.join(ROOT, "paper_0901_1413_gb300", "csrc")
-    return sources_digest([os.path.join(csrc, n) for n in ("fq_tc.cu", "fq_common.cuh")])
+    return sources_digest([os.path.join(csrc, n) for n in ("fq_tc.cu", "fq_common.cuh", "fq_e4m3.cuh")])
 
 
 def measured_traffic(name, digest):

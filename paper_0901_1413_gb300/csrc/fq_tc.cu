@@ -93,28 +93,30 @@ __device__ __forceinline__ void select_planes(const uint32_t (&t)[P], int sel, u
 }
 
 // Rows of a planes matrix to e4m3 bytes: out[r * ld + off + c] for c < cols,
-// cols a multiple of 32 and off of 16 (cols may run into the planes' zero
-// padding, which gives zeros).  One thread per 32 elements (one 32-bit plane
-// word, two 16-byte stores), so that a warp writes 1024 contiguous bytes; a
-// thread loads RPT rows' words before it converts any of them.
+// cols and off multiples of 16 (cols may run into the planes' zero padding,
+// which gives zeros).  One thread per 16 elements (a 16-byte store), so that a
+// warp writes 512 contiguous bytes; a thread loads RPT rows' words before it
+// converts any of them.
 constexpr int RPT = 4;
 template <int Q, int P>
 __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64_t cols, int64_t pitch,
                              uint8_t *__restrict__ out, int64_t ld, int64_t off, int sel) {
   using CF = ConvField<Q>;
-  // grid: x over the 32-element pieces of a row, y over groups of RPT rows
+  // grid: x over the 16-byte pieces of a row, y over groups of RPT rows
   // (grid-stride); the next group's words are loaded before this group is
   // converted and stored
-  const int64_t piece = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // the 32-bit plane word
-  const int64_t c0 = piece * 32;
+  const int64_t piece = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t c0 = piece * 16;
   if (c0 >= cols) return;
   const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
+  const int64_t word = piece >> 1;    // the 32-bit plane word holding the 16 elements
+  const int half = int(piece & 1);
   auto load = [&](int64_t r0, uint32_t (&t)[RPT][P]) {
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
 #pragma unroll
       for (int p = 0; p < P; ++p)
-        t[i][p] = r0 + i < rows ? __ldg(X32 + (p * rows + r0 + i) * pitch * 2 + piece) : 0u;
+        t[i][p] = r0 + i < rows ? __ldg(X32 + (p * rows + r0 + i) * pitch * 2 + word) : 0u;
   };
   const int64_t step = int64_t(gridDim.y) * RPT;
   int64_t r0 = int64_t(blockIdx.y) * RPT;
@@ -127,11 +129,7 @@ __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64
       if (r0 + i >= rows) break;
       uint32_t o[CF::P2];
       select_planes<Q, P>(t[i], sel, o);
-      uint4 lo, hi;
-      e4m3x32<CF::Q2, CF::P2>(o, lo, hi);
-      uint4 *dst = reinterpret_cast<uint4 *>(out + (r0 + i) * ld + off + c0);
-      dst[0] = lo;
-      dst[1] = hi;
+      *reinterpret_cast<uint4 *>(out + (r0 + i) * ld + off + c0) = e4m3x16<CF::Q2, CF::P2>(o, half);
     }
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
@@ -140,10 +138,10 @@ __global__ void rows_to_e4m3(const uint64_t *__restrict__ X, int64_t rows, int64
   }
 }
 
-// Launch shape of rows_to_e4m3 for rows x cols (cols a multiple of 32): one
+// Launch shape of rows_to_e4m3 for rows x cols (cols a multiple of 16): one
 // wave of 256-thread blocks (8 per SM on 152 SMs), each walking row groups.
 inline dim3 rows_grid(int64_t rows, int64_t cols) {
-  const int64_t pieces = cols / 32, xs = cdiv(pieces, 256), groups = cdiv(rows, RPT);
+  const int64_t pieces = cols / 16, xs = cdiv(pieces, 256), groups = cdiv(rows, RPT);
   const int64_t want = cdiv(int64_t(152) * 8, xs);
   const int64_t ys = groups < want ? groups : want;
   return dim3(unsigned(xs), unsigned(ys < 65535 ? (ys > 0 ? ys : 1) : 65535));
@@ -1337,18 +1335,18 @@ __device__ __forceinline__ void mma_e4m3_mn(uint32_t d_tmem, uint64_t a, uint64_
 // A planes matrix of `rows_valid` rows (pitch words, P planes; rows up to
 // `rows` read as zero) as e4m3 bytes in 128-element chunks: chunk c of row r
 // (c < chunks) becomes the 128-byte scratch row row_of(r, c).  The work is
-// split in 32-element pieces (one 32-bit plane word in, 32 bytes out), four
-// to a chunk, so that four consecutive threads write one 128-byte row (a
-// warp's stores cover eight whole rows).  Converter thread ct takes the
-// pieces ct, ct + CONV_THREADS, ... (row-major), UNR at a time with all their
-// words loaded first; a thread's (row, piece) advances by the stride's
-// quotient and remainder, so no division runs per piece.
+// split in 16-element pieces, eight to a chunk, so that eight consecutive
+// threads write one 128-byte row (a warp's 16-byte stores cover four whole
+// rows).  Converter thread ct takes the pieces ct, ct + CONV_THREADS, ...
+// (row-major), UNR at a time with all their words loaded first; a thread's
+// (row, piece) advances by the stride's quotient and remainder, so no
+// division runs per piece.
 template <int Q, int P, class RowOf>
 __device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int rows_valid, int rows, int64_t pitch,
                                              int chunks, uint8_t *buf, int ct, RowOf row_of) {
   using CF = ConvField<Q>;
   constexpr int UNR = 4;
-  const int per_row = 4 * chunks;
+  const int per_row = 8 * chunks;
   const int radv = CONV_THREADS / per_row, padv = CONV_THREADS % per_row;
   const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
   int r = ct / per_row, piece = ct % per_row;
@@ -1361,7 +1359,7 @@ __device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int
       pp[u] = piece;
 #pragma unroll
       for (int p = 0; p < P; ++p)
-        t[u][p] = r < rows_valid ? __ldg(X32 + (p * int64_t(rows_valid) + r) * pitch * 2 + piece) : 0u;
+        t[u][p] = r < rows_valid ? __ldg(X32 + (p * int64_t(rows_valid) + r) * pitch * 2 + (piece >> 1)) : 0u;
       r += radv;
       piece += padv;
       if (piece >= per_row) {
@@ -1374,11 +1372,8 @@ __device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int
       if (rr[u] >= rows) break;
       uint32_t o[CF::P2];
       select_planes<Q, P>(t[u], 0, o);
-      uint4 lo, hi;
-      e4m3x32<CF::Q2, CF::P2>(o, lo, hi);
-      uint4 *dst = reinterpret_cast<uint4 *>(buf + row_of(rr[u], pp[u] >> 2) * 128 + (pp[u] & 3) * 32);
-      dst[0] = lo;
-      dst[1] = hi;
+      *reinterpret_cast<uint4 *>(buf + row_of(rr[u], pp[u] >> 3) * 128 + (pp[u] & 7) * 16) =
+          e4m3x16<CF::Q2, CF::P2>(o, pp[u] & 1);
     }
   }
 }

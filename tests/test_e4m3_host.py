@@ -1,7 +1,7 @@
-"""The plane-word to e4m3 conversion of the tensor-core operands (e4m3x32 in
-csrc/fq_e4m3.cuh), built for the host with nvcc and checked on the CPU byte
-for byte against PyTorch's own e4m3 conversion of each element's balanced
-value.  The element codes are those of the library's planes (Sections 4.1
+"""The plane-word to e4m3 conversion of the tensor-core operands (e4m3x32
+and its 16-element form e4m3x16 in csrc/fq_e4m3.cuh), built for the host
+with nvcc and checked on the CPU byte for byte against PyTorch's own e4m3
+conversion of each element's balanced value.  The element codes are those of the library's planes (Sections 4.1
 and 4.2): F_3 unit | sign << 1, F_5 and F_7 a 3-bit code read mod p, and F_2
 (each F_2 product of GF(4)) one bit."""
 import os
@@ -27,7 +27,9 @@ void run(int words) {
     for (int p = 0; p < P; ++p) if (std::scanf("%%x", &t[p]) != 1) return;
     uint4 lo, hi;
     fqk::e4m3x32<Q, P>(t, lo, hi);
-    std::printf("%%08x %%08x %%08x %%08x %%08x %%08x %%08x %%08x\n", lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w);
+    const uint4 h0 = fqk::e4m3x16<Q, P>(t, 0), h1 = fqk::e4m3x16<Q, P>(t, 1);
+    std::printf("%%08x %%08x %%08x %%08x %%08x %%08x %%08x %%08x ", lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w);
+    std::printf("%%08x %%08x %%08x %%08x %%08x %%08x %%08x %%08x\n", h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w);
   }
 }
 int main() {
@@ -77,12 +79,13 @@ def test_e4m3x32_matches_the_e4m3_format(harness, q):
     t[1] = 0xFFFFFFFF
     text = "%d %d\n" % (q, words) + "\n".join(" ".join("%x" % int(v) for v in row) for row in t)
     out = subprocess.run([harness], input=text, capture_output=True, text=True, check=True).stdout.split()
-    got = np.array([int(x, 16) for x in out], dtype=np.uint64).reshape(words, 8)
-    got_bytes = got.astype("<u4").view(np.uint8).reshape(words, 32)
+    got = np.array([int(x, 16) for x in out], dtype=np.uint64).reshape(words, 2, 8)
+    got_bytes = got.astype("<u4").view(np.uint8).reshape(words, 2, 32)
     bits = (t[:, :, None] >> np.arange(32, dtype=np.uint64)) & np.uint64(1)        # words x P x 32
     codes = sum(bits[:, p, :].astype(np.int64) << p for p in range(P))              # words x 32
     table = torch.tensor([float(balanced(q, c)) for c in range(1 << P)])
     want_of_code = table.to(torch.float8_e4m3fn).view(torch.uint8).numpy()
     if q == 3:
         want_of_code[2] = 0x80
-    assert np.array_equal(got_bytes, want_of_code[codes])
+    assert np.array_equal(got_bytes[:, 0], want_of_code[codes])      # 32 elements at once
+    assert np.array_equal(got_bytes[:, 1], want_of_code[codes])      # the two 16-element halves
