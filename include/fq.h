@@ -203,14 +203,15 @@ int fq_tc_multiply(int q, int64_t m, int64_t l, int64_t n, const void *workspace
  *   - Four Russians: work items (rows x a column tile of one product) with a
  *     block size k chosen per item by the planner's cost model, longest first;
  *   - tcgen05 (F_3, F_5, F_7 with 0 < l within the exact range and
- *     n <= 2^30): whole products are given to 152 persistent CTAs (longest
- *     first, each to the least-loaded CTA by the model; a CTA then takes its
- *     products smallest first).  A CTA's converter warps write each
- *     product's A and B^T as e4m3 bytes into one of the CTA's two scratch
- *     buffers in the workspace while its tensor-core warps compute the
- *     previous product's 128 x 256 tiles from the other, so the operands
- *     stay in L2.  A product runs on one SM: a batch of a few very large
- *     products is better served by fq_matmul.
+ *     n <= 2^30): whole products are given to 76 groups of two persistent
+ *     CTAs (one thread-block cluster each; longest first, each to the
+ *     least-loaded group by the model; a group then takes its products
+ *     smallest first).  A group's converter warps write each product's A
+ *     and B as e4m3 bytes into one of the group's two scratch buffers in
+ *     the workspace while its tensor-core warps compute the previous
+ *     product's 128 x 256 tiles from the other, the two CTAs taking
+ *     alternate tiles.  A product runs on two SMs: a batch of a few very
+ *     large products is better served by fq_matmul.
  * The plan is host memory owned by the library. */
 typedef struct fq_batch_plan fq_batch_plan;
 
@@ -228,9 +229,9 @@ int fq_batched_plan_create_ex(int q, int count, const int64_t *m, const int64_t 
                               fq_batch_plan **plan);
 
 /* Bytes of device workspace the plan needs (64-byte aligned, caller-owned:
- * the work lists, and for tcgen05 products each CTA's two scratch buffers,
+ * the work lists, and for tcgen05 products each group's two scratch buffers,
  * buffer b holding (m rounded up to 128 + n rounded up to 256) x (l rounded up
- * to 128) bytes for the largest of the CTA's products b, b + 2, ...), the
+ * to 128) bytes for the largest of the group's products b, b + 2, ...), the
  * number of Four-Russians work items, of products on the tcgen05 path and of
  * their 128 x 256 tiles; -1 for a NULL plan. */
 int64_t fq_batched_workspace_bytes(const fq_batch_plan *plan);

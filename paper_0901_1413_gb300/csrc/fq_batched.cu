@@ -262,11 +262,11 @@ struct fq_batch_plan {
   std::vector<fqk::batched::Shape> shapes;
   std::vector<fqk::batched::Item> items;      // Four-Russians items
   std::vector<fqk::BatchProd> tc_prods;       // products on the tcgen05 path
-  std::vector<int32_t> tc_cta_begin;          // kTcCtas + 1
-  std::vector<int32_t> tc_cta_list;           // product indices, each CTA's in the order it computes them
-  std::vector<int64_t> tc_cta_rows;           // kTcCtas x 2: first scratch row of each CTA's buffers
+  std::vector<int32_t> tc_cta_begin;          // kTcGroups + 1
+  std::vector<int32_t> tc_cta_list;           // product indices, each group's in the order it computes them
+  std::vector<int64_t> tc_cta_rows;           // kTcGroups x 2: first scratch row of each group's buffers
   int64_t tc_tiles = 0;                       // 128 x 256 tiles of the tcgen05 products
-  int64_t scratch_rows = 0;                   // 128-byte rows of all CTAs' buffers
+  int64_t scratch_rows = 0;                   // 128-byte rows of all groups' buffers
   int64_t off_prods = 0, off_cta_begin = 0, off_cta_list = 0, off_cta_rows = 0, off_scratch = 0;
   int64_t table_bytes = 0;      // header .. CTA rows (uploaded)
   int64_t workspace_bytes = 0;  // plus the scratch buffers
@@ -442,13 +442,14 @@ int plan_create(int q, int count, const int64_t *m, const int64_t *l, const int6
     host_alloc_point();
     plan->items.push_back(c.second);
   }
-  // tcgen05 work: whole products to the kTcCtas persistent CTAs, longest
-  // first, each to the least-loaded CTA by the modelled cost; a CTA then takes
-  // its products smallest first (the first one's conversion is the only one
-  // no MMA overlaps).  Each CTA owns two scratch buffers, buffer b sized for
+  // tcgen05 work: whole products to the kTcGroups groups of persistent CTAs
+  // (kTcGroup CTAs, one cluster, share each product), longest first, each to
+  // the least-loaded group by the modelled cost; a group then takes its
+  // products smallest first (the first one's conversion is the only one no
+  // MMA overlaps).  Each group owns two scratch buffers, buffer b sized for
   // the largest of its products b, b + 2, ...
   const int T = int(plan->tc_prods.size());
-  constexpr int NC = fqk::kTcCtas;
+  constexpr int NC = fqk::kTcGroups;
   plan->tc_cta_begin.assign(NC + 1, 0);
   plan->tc_cta_rows.assign(2 * NC, 0);
   if (T > 0) {

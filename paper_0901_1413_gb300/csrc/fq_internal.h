@@ -41,15 +41,19 @@ double tc_estimate(int q, int64_t m, int64_t l, int64_t n, int sms);
 // The tcgen05 product form a shape takes by default (2 .. 5, as TcOptions::form).
 int tc_form(int64_t m, int64_t l);
 
-// Batched products on the tcgen05 path.  The plan gives every product to one
-// of kTcCtas persistent CTAs (longest first, each to the least-loaded CTA).  A
-// CTA works through its products in turn: its converter warps write a
-// product's A and B^T as e4m3 bytes into one of the CTA's two scratch buffers
-// (K-blocked rows of 128 bytes: a 128-row block of A, or a 256-row block of
-// B^T, holds its 128-deep k-slices one after another) while its TMA, MMA and
-// epilogue warps compute the previous product's 128 x 256 tiles from the
-// other buffer.  The buffers are small enough to stay in L2.
+// Batched products on the tcgen05 path.  The kTcCtas persistent CTAs work in
+// groups of kTcGroup (one thread-block cluster), and the plan gives every
+// product to one group (longest first, each to the least-loaded group).  A
+// group works through its products in turn: its converter warps (of all its
+// CTAs) write a product's A and B as e4m3 bytes into one of the group's two
+// scratch buffers (K-blocked rows of 128 bytes: a 128-row block of A, or a
+// 128-column block of B, holds its 128-deep k-slices one after another) while
+// its TMA, MMA and epilogue warps compute the previous product's 128 x 256
+// tiles from the other, CTA r of the group taking tiles r, r + kTcGroup, ...
 constexpr int kTcCtas = 152;
+constexpr int kTcGroup = 2;
+constexpr int kTcGroups = kTcCtas / kTcGroup;
+static_assert(kTcCtas % kTcGroup == 0, "whole groups");
 struct BatchProd {
   int32_t p;              // index into the caller's pointer arrays
   int32_t m, l, n;
@@ -61,11 +65,11 @@ struct BatchProd {
 struct TcBatch {
   int q = 0;
   int nprod = 0;
-  int64_t scratch_rows = 0;            // rows of 128 bytes of all CTAs' buffers together
+  int64_t scratch_rows = 0;            // rows of 128 bytes of all groups' buffers together
   const BatchProd *prods = nullptr;    // device
-  const int32_t *cta_begin = nullptr;  // device, kTcCtas + 1: products of CTA c are cta_list[begin[c] .. begin[c+1])
-  const int32_t *cta_list = nullptr;   // device, nprod product indices, each CTA's in the order it computes them
-  const int64_t *cta_rows = nullptr;   // device, kTcCtas x 2: first scratch row of each CTA's buffers 0 and 1
+  const int32_t *cta_begin = nullptr;  // device, kTcGroups + 1: products of group g are cta_list[begin[g] .. begin[g+1])
+  const int32_t *cta_list = nullptr;   // device, nprod product indices, each group's in the order it computes them
+  const int64_t *cta_rows = nullptr;   // device, kTcGroups x 2: first scratch row of each group's buffers 0 and 1
   uint8_t *scratch = nullptr;          // device, scratch_rows x 128 bytes (1024-byte aligned)
 };
 // Rows of 128 bytes a product's operands take in a scratch buffer: A, then B^T.

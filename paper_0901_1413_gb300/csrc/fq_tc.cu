@@ -1277,8 +1277,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(f4::THREADS, 1)
 
 // ---------------------------------------------------- batched products --
 //
-// One persistent CTA per slot (kTcCtas) works through its own products, in the
-// order the plan lists them.  Product i of a CTA uses the CTA's scratch buffer
+// The persistent CTAs work in groups of kTcGroup (one thread-block cluster);
+// each group works through its own products, in the order the plan lists
+// them, and the group's CTAs share every product: all of them convert parts
+// of its operands into the group's scratch buffer, and CTA r of the group
+// computes the product's tiles r, r + kTcGroup, ...  Sharing halves the
+// operand bytes the GPU keeps live at a time (two products per group instead
+// of two per SM), so that more of the converted operands are read back from
+// L2 rather than DRAM.  Product i of a group uses the group's scratch buffer
 // i mod 2, rows of 128 bytes, both operands K-blocked in 128-row blocks:
 //   A (K-major): the 128-element chunk c of k of row r at row
 //       ((r / 128) * kb + c) * 128 + r % 128        (kb = la / 128 k-slices);
@@ -1288,19 +1294,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(f4::THREADS, 1)
 // A stage of the tile kernel is one 128-row block of A and two of B (the two
 // 128-column halves of a 256-column tile), 16 KB each, so every TMA copy is
 // one contiguous 16 KB block.  Converter warps fill one buffer while the
-// TMA, MMA and epilogue warps compute the previous product from the other,
-// so the operands are written and read back through L2 instead of a DRAM
-// arena.
+// TMA, MMA and epilogue warps compute the previous product from the other.
 //
 // Warps: 0 (one thread) TMA loads, 1 (one thread) MMAs, 2 TMEM allocation,
 // 4..11 epilogue (TMEM lane quadrant warp % 4, 128-column half (warp - 4) /
-// 4), 12..27 converters.  Hand-overs between them:
-//   conv_full[b]   converters -> TMA thread: the product's operands are in
+// 4), 12..27 converters.  Hand-overs, on mbarriers in every CTA of the group
+// with cluster-scope release and acquire:
+//   conv_full[b]   converters -> TMA threads: the product's operands are in
 //                  buffer b (each converter thread orders its global writes
-//                  before the async proxy's reads, then arrives);
-//   conv_empty[b]  MMA thread -> converters: every copy out of buffer b has
-//                  landed in shared memory (arrived after the product's last
-//                  full-stage wait), so the buffer may be refilled.
+//                  before the async proxy's reads, then arrives on every
+//                  CTA's barrier);
+//   conv_empty[b]  MMA threads -> converters: every copy out of buffer b has
+//                  landed in shared memory (each MMA thread arrives on every
+//                  CTA's barrier after its last full-stage wait of the
+//                  product), so the buffer may be refilled.
+// A group's CTAs leave together (a cluster barrier), so no arrival reaches a
+// CTA that has exited.
 constexpr int EPI_WARPS_B = 8;
 constexpr int CONV_WARPS = 16, CONV_THREADS = 32 * CONV_WARPS;
 constexpr int FIRST_CONV_WARP = 4 + EPI_WARPS_B;
@@ -1337,17 +1346,17 @@ __device__ __forceinline__ void mma_e4m3_mn(uint32_t d_tmem, uint64_t a, uint64_
 // (c < chunks) becomes the 128-byte scratch row row_of(r, c).  The work is
 // split in 16-element pieces, eight to a chunk, so that eight consecutive
 // threads write one 128-byte row (a warp's 16-byte stores cover four whole
-// rows).  Converter thread ct takes the pieces ct, ct + CONV_THREADS, ...
-// (row-major), UNR at a time with all their words loaded first; a thread's
-// (row, piece) advances by the stride's quotient and remainder, so no
-// division runs per piece.
+// rows).  Converter thread ct of the nct converting threads takes the pieces
+// ct, ct + nct, ... (row-major), UNR at a time with all their words loaded
+// first; a thread's (row, piece) advances by the stride's quotient and
+// remainder, so no division runs per piece.
 template <int Q, int P, class RowOf>
 __device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int rows_valid, int rows, int64_t pitch,
-                                             int chunks, uint8_t *buf, int ct, RowOf row_of) {
+                                             int chunks, uint8_t *buf, int ct, int nct, RowOf row_of) {
   using CF = ConvField<Q>;
   constexpr int UNR = 4;
   const int per_row = 8 * chunks;
-  const int radv = CONV_THREADS / per_row, padv = CONV_THREADS % per_row;
+  const int radv = nct / per_row, padv = nct % per_row;
   const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
   int r = ct / per_row, piece = ct % per_row;
   while (r < rows) {
@@ -1389,8 +1398,8 @@ __device__ __forceinline__ void prefetch_l2(const void *p, int64_t bytes) {
 
 struct BatchParams {
   const BatchProd *prods;
-  const int32_t *cta_begin, *cta_list;  // products of CTA c: cta_list[cta_begin[c] .. cta_begin[c + 1])
-  const int64_t *cta_rows;              // kTcCtas x 2: first tensor-map row of each CTA's buffer 0 and buffer 1
+  const int32_t *cta_begin, *cta_list;  // products of group g: cta_list[cta_begin[g] .. cta_begin[g + 1])
+  const int64_t *cta_rows;              // kTcGroups x 2: first tensor-map row of each group's buffer 0 and buffer 1
   uint8_t *scratch;
   const uint64_t *const *A;
   const uint64_t *const *B;
@@ -1426,11 +1435,12 @@ __device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, i
   }
 }
 
-// The persistent batched kernel: CTA c computes the products of its list, one
-// after another, 128 x 256 tiles each (row block by row block), from the e4m3
-// operands its converter warps write into its two scratch buffers.
+// The persistent batched kernel: group g (cluster g) computes the products of
+// its list, one after another, 128 x 256 tiles each (row block by row block),
+// from the e4m3 operands its converter warps write into its two scratch
+// buffers; CTA r of the group takes tiles r, r + kTcGroup, ... of each.
 template <int Q, int P>
-__global__ void __launch_bounds__(THREADS_F, 1)
+__global__ void __cluster_dims__(kTcGroup, 1, 1) __launch_bounds__(THREADS_F, 1)
     tc_batched_kernel(const __grid_constant__ CUtensorMap tmA, const BatchParams prm) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -1442,6 +1452,7 @@ __global__ void __launch_bounds__(THREADS_F, 1)
                  conv_empty = conv_full + 16;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + BAR_OFF + 8 * NBARS_F);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + BAR_OFF + 8 * NBARS_F + 8);
+  const int rank = int(cluster_rank());
 
   if (tid == 0) {
     *abort_flag = 0;
@@ -1455,8 +1466,8 @@ __global__ void __launch_bounds__(THREADS_F, 1)
     }
     mbar_init(drain, 1);  // the MMA drain
     for (int b = 0; b < 2; ++b) {
-      mbar_init(conv_full + 8 * b, CONV_THREADS);
-      mbar_init(conv_empty + 8 * b, 1);
+      mbar_init(conv_full + 8 * b, kTcGroup * CONV_THREADS);  // every converter thread of the group
+      mbar_init(conv_empty + 8 * b, kTcGroup);                // every MMA thread of the group
     }
     fence_mbar_init();
   }
@@ -1467,46 +1478,53 @@ __global__ void __launch_bounds__(THREADS_F, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
-  __syncthreads();
+  cluster_sync();  // every CTA's barriers initialised before any arrival from another CTA
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int cta = blockIdx.x;
-  const int first = prm.cta_begin[cta], count = prm.cta_begin[cta + 1] - first;
-  const int64_t row_buf[2] = {prm.cta_rows[2 * cta], prm.cta_rows[2 * cta + 1]};
+  const int grp = blockIdx.x / kTcGroup;
+  const int first = prm.cta_begin[grp], count = prm.cta_begin[grp + 1] - first;
+  const int64_t row_buf[2] = {prm.cta_rows[2 * grp], prm.cta_rows[2 * grp + 1]};
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA: the tiles of each product, from its buffer once it is filled
+    // ---- TMA: this CTA's tiles of each product, from its buffer once it is filled
     int it = 0;
     for (int i = 0; i < count && !*abort_flag; ++i) {
       const int b = i & 1;
-      wait_bar(conv_full + 8 * b, uint32_t((i >> 1) & 1), abort_flag, prm.err);
+      wait_bar_cluster(conv_full + 8 * b, uint32_t((i >> 1) & 1), abort_flag, prm.err);
       if (*abort_flag) break;
       const BatchProd bp = prm.prods[prm.cta_list[first + i]];
-      const int kb = bp.la >> 7, mbs = (bp.m + 127) >> 7, nbs = bp.nr >> 8;
+      const int kb = bp.la >> 7, nbs = bp.nr >> 8, tiles = ((bp.m + 127) >> 7) * nbs;
       const int ya = int(row_buf[b]), yb = int(row_buf[b] + batch_a_rows(bp.m, bp.la));
-      for (int mb = 0; mb < mbs && !*abort_flag; ++mb)
-        for (int nb = 0; nb < nbs && !*abort_flag; ++nb)
-          for (int ks = 0; ks < kb; ++ks, ++it) {
-            const int s = it % STAGES;
-            if (it >= STAGES) wait_bar(empty + 8 * s, uint32_t((it / STAGES - 1) & 1), abort_flag, prm.err);
-            if (*abort_flag) break;
-            const uint32_t a_dst = base + uint32_t(s * STAGE_BYTES), b_dst = a_dst + A_BYTES;
-            mbar_expect_tx(full + 8 * s, STAGE_BYTES);
-            // three contiguous 16 KB blocks: A's rows, then B's two 128-column halves
-            tma_load_2d(a_dst, &tmA, full + 8 * s, 0, ya + (mb * kb + ks) * 128);
-            tma_load_2d(b_dst, &tmA, full + 8 * s, 0, yb + ((2 * nb) * kb + ks) * 128);
-            tma_load_2d(b_dst + 16384, &tmA, full + 8 * s, 0, yb + ((2 * nb + 1) * kb + ks) * 128);
-          }
+      for (int t = rank; t < tiles && !*abort_flag; t += kTcGroup) {
+        const int mb = t / nbs, nb = t - mb * nbs;
+        for (int ks = 0; ks < kb; ++ks, ++it) {
+          const int s = it % STAGES;
+          if (it >= STAGES) wait_bar(empty + 8 * s, uint32_t((it / STAGES - 1) & 1), abort_flag, prm.err);
+          if (*abort_flag) break;
+          const uint32_t a_dst = base + uint32_t(s * STAGE_BYTES), b_dst = a_dst + A_BYTES;
+          mbar_expect_tx(full + 8 * s, STAGE_BYTES);
+          // three contiguous 16 KB blocks: A's rows, then B's two 128-column halves
+          tma_load_2d(a_dst, &tmA, full + 8 * s, 0, ya + (mb * kb + ks) * 128);
+          tma_load_2d(b_dst, &tmA, full + 8 * s, 0, yb + ((2 * nb) * kb + ks) * 128);
+          tma_load_2d(b_dst + 16384, &tmA, full + 8 * s, 0, yb + ((2 * nb + 1) * kb + ks) * 128);
+        }
+      }
     }
     if (*abort_flag) drain_copies(full, it, STAGES);
   } else if (warp == 1 && lane == 0) {
-    // ---- MMAs; after a product's last stage has landed its buffer is free
+    // ---- MMAs; after this CTA's last stage of a product has landed, its part
+    // of the buffer is free (arrivals on every CTA of the group).  The thread
+    // first waits for the product's operands, as the TMA thread does: a CTA
+    // with no tiles in two products of the same buffer would otherwise arrive
+    // twice in one phase of conv_empty, before another CTA had read the first.
     int it = 0, li = 0;
     bool issued = false;
     for (int i = 0; i < count && !*abort_flag; ++i) {
+      wait_bar_cluster(conv_full + 8 * (i & 1), uint32_t((i >> 1) & 1), abort_flag, prm.err);
+      if (*abort_flag) break;
       const BatchProd bp = prm.prods[prm.cta_list[first + i]];
       const int kb = bp.la >> 7, tiles = ((bp.m + 127) >> 7) * (bp.nr >> 8);
-      for (int t = 0; t < tiles && !*abort_flag; ++t, ++li) {
+      for (int t = rank; t < tiles && !*abort_flag; t += kTcGroup, ++li) {
         const int ab = li % ACC;
         if (li >= ACC) wait_bar(accempty + 8 * ab, uint32_t((li / ACC - 1) & 1), abort_flag, prm.err);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1525,7 +1543,8 @@ __global__ void __launch_bounds__(THREADS_F, 1)
         }
         mma_commit(accfull + 8 * ab);
       }
-      if (!*abort_flag) mbar_arrive_cta(conv_empty + 8 * (i & 1));
+      if (!*abort_flag)
+        for (int r = 0; r < kTcGroup; ++r) mbar_arrive_cluster(map_to_rank(conv_empty + 8 * (i & 1), uint32_t(r)));
     }
     if (*abort_flag && issued) {  // the MMAs issued so far complete before TMEM is freed
       mma_commit(drain);
@@ -1544,7 +1563,7 @@ __global__ void __launch_bounds__(THREADS_F, 1)
       bo.pc = bp.pc;
       bo.C = prm.C[bp.p];
       const int nbs = bp.nr >> 8, tiles = ((bp.m + 127) >> 7) * nbs;
-      for (int t = 0; t < tiles; ++t, ++li) {
+      for (int t = rank; t < tiles; t += kTcGroup, ++li) {
         const int ab = li % ACC;
         wait_bar(accfull + 8 * ab, uint32_t((li / ACC) & 1), abort_flag, prm.err);
         if (*abort_flag) break;
@@ -1567,32 +1586,35 @@ __global__ void __launch_bounds__(THREADS_F, 1)
       }
     }
   } else if (warp >= FIRST_CONV_WARP) {
-    // ---- converters: product i into buffer i mod 2, once the product two
-    // before it has left that buffer; the next product's planes are fetched
-    // into L2 meanwhile
-    const int ct = tid - 32 * FIRST_CONV_WARP;
+    // ---- converters: product i into buffer i mod 2, once every CTA of the
+    // group has finished reading the product two before it from that buffer;
+    // the group's converter threads share each product's pieces, and the
+    // next product's planes are fetched into L2 meanwhile (A by CTA 0, B by
+    // the last CTA of the group)
+    const int ct = tid - 32 * FIRST_CONV_WARP, gct = rank * CONV_THREADS + ct;
+    constexpr int nct = kTcGroup * CONV_THREADS;
     for (int i = 0; i < count && !*abort_flag; ++i) {
       const int b = i & 1;
       if (i >= 2) {
-        wait_bar(conv_empty + 8 * b, uint32_t(((i - 2) >> 1) & 1), abort_flag, prm.err);
+        wait_bar_cluster(conv_empty + 8 * b, uint32_t(((i - 2) >> 1) & 1), abort_flag, prm.err);
         if (*abort_flag) break;
       }
       const BatchProd bp = prm.prods[prm.cta_list[first + i]];
       if (ct == 0 && i + 1 < count) {
         const BatchProd nx = prm.prods[prm.cta_list[first + i + 1]];
-        prefetch_l2(prm.A[nx.p], int64_t(P) * nx.m * nx.pa * 8);
-        prefetch_l2(prm.B[nx.p], int64_t(P) * nx.l * nx.pb * 8);
+        if (rank == 0) prefetch_l2(prm.A[nx.p], int64_t(P) * nx.m * nx.pa * 8);
+        if (rank == kTcGroup - 1) prefetch_l2(prm.B[nx.p], int64_t(P) * nx.l * nx.pb * 8);
       }
       uint8_t *buf = prm.scratch + row_buf[b] * 128;
       const int kb = bp.la >> 7;
-      convert_rows<Q, P>(prm.A[bp.p], bp.m, bp.m, bp.pa, kb, buf, ct, [kb](int r, int c) {
+      convert_rows<Q, P>(prm.A[bp.p], bp.m, bp.m, bp.pa, kb, buf, gct, nct, [kb](int r, int c) {
         return int64_t((r >> 7) * kb + c) * 128 + (r & 127);
       });
-      convert_rows<Q, P>(prm.B[bp.p], bp.l, bp.la, bp.pb, bp.nr >> 7, buf + batch_a_rows(bp.m, bp.la) * 128, ct,
-                         [kb](int r, int c) { return int64_t(c * kb + (r >> 7)) * 128 + (r & 127); });
+      convert_rows<Q, P>(prm.B[bp.p], bp.l, bp.la, bp.pb, bp.nr >> 7, buf + batch_a_rows(bp.m, bp.la) * 128, gct,
+                         nct, [kb](int r, int c) { return int64_t(c * kb + (r >> 7)) * 128 + (r & 127); });
       // this thread's writes are visible to the TMA loads that follow the hand-over
       asm volatile("fence.proxy.async.global;" ::: "memory");
-      mbar_arrive_cta(conv_full + 8 * b);
+      for (int r = 0; r < kTcGroup; ++r) mbar_arrive_cluster(map_to_rank(conv_full + 8 * b, uint32_t(r)));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1601,6 +1623,7 @@ __global__ void __launch_bounds__(THREADS_F, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
+  cluster_sync();  // no CTA leaves while another may still arrive on its barriers
 }
 
 // ------------------------------------------------------------------ host --

@@ -96,12 +96,13 @@ def _plan_layout_model(q, shapes, path):
     forced onto one path, from the layout include/fq.h describes: header 64,
     shapes 24 each (64-aligned), Four-Russians items 32 each (tiles of C's
     pitch: 512 rows x 512 columns for F_3 and GF(4), 256 x 1024 for F_5 and
-    F_7); for tcgen05 products 64-byte records, the 153 CTA list starts and
-    the product list (4 bytes each), the 2 x 152 buffer starts (8 bytes), each
-    part 64-aligned; then the CTAs' scratch buffers, 1024-aligned, of 128-byte
-    rows.  Products go to 152 CTAs longest first, each to the least-loaded
-    one by the plan's cost model; a CTA takes its products in the reverse
-    order, and its buffer b holds the largest of its products b, b + 2, ...:
+    F_7); for tcgen05 products 64-byte records, the 77 group list starts and
+    the product list (4 bytes each), the 2 x 76 buffer starts (8 bytes), each
+    part 64-aligned; then the groups' scratch buffers, 1024-aligned, of
+    128-byte rows.  Products go to 76 groups (pairs of CTAs) longest first,
+    each to the least-loaded one by the plan's cost model; a group takes its
+    products in the reverse order, and its buffer b holds the largest of its
+    products b, b + 2, ...:
     m rounded up to 128 plus n rounded up to 256, times l rounded up to 128
     over 128, rows."""
     from paper_0901_1413_gb300 import fq
@@ -125,16 +126,16 @@ def _plan_layout_model(q, shapes, path):
     off = 64 + up(24 * len(shapes), 64) + 32 * items
     if tc:
         order = sorted(range(len(tc)), key=lambda i: -tc[i][0])
-        load, per = [0.0] * 152, [[] for _ in range(152)]
+        load, per = [0.0] * 76, [[] for _ in range(76)]
         for i in order:
-            c = min(range(152), key=lambda k: (load[k], k))
+            c = min(range(76), key=lambda k: (load[k], k))
             per[c].append(i)
             load[c] += tc[i][0]
         rows = 0
-        for c in range(152):
+        for c in range(76):
             lst = per[c][::-1]
             rows += max([tc[i][1] for i in lst[0::2]] or [0]) + max([tc[i][1] for i in lst[1::2]] or [0])
-        for size in (64 * len(tc), 4 * 153, 4 * len(tc), 8 * 304):
+        for size in (64 * len(tc), 4 * 77, 4 * len(tc), 8 * 152):
             off = up(off, 64) + size
         off = up(off, 1024) + 128 * rows
     return off, items, len(tc), tiles
@@ -213,16 +214,16 @@ def test_batch_plan_host_side(lib):
     # every product the tcgen05 form takes (l > 0; m = 0 needs no work): 100 x 70
     # x 600 (1 x 3 tiles of 128 x 256) and 2000 x 64 x 64 (16 x 1); l = 0 stays
     # a Four-Russians product (4 zero-fill items).  Tables: header 64, shapes 128,
-    # items 4 x 32, products 2 x 64, CTA list starts 153 x 4, CTA lists 2 x 4,
-    # buffer starts 304 x 8, each part 64-byte aligned -> 3456 bytes; scratch
+    # items 4 x 32, products 2 x 64, group list starts 77 x 4, group lists 2 x 4,
+    # buffer starts 152 x 8, each part 64-byte aligned -> 1440 bytes; scratch
     # (1024-aligned): the larger product (2000 x 64 x 64: 16 row blocks x 128
-    # rows of A + 256 rows of B^T) on CTA 0, the other on CTA 1, each in its
+    # rows of A + 256 rows of B^T) on group 0, the other on group 1, each in its
     # buffer 0: 2304 and 128 + 768 rows of 128 bytes.
     assert lib.fq_batched_plan_create_ex(3, 4, i64p(m), i64p(l), i64p(n), fq.PATH_MMA, ctypes.byref(h)) == fq.OK
     assert lib.fq_batched_items(h) == 4
     assert lib.fq_batched_tc_products(h) == 2
     assert lib.fq_batched_tc_tiles(h) == 3 + 16
-    assert lib.fq_batched_workspace_bytes(h) == 4096 + (2304 + 896) * 128
+    assert lib.fq_batched_workspace_bytes(h) == 2048 + (2304 + 896) * 128
     assert [lib.fq_batched_product_path(h, p) for p in range(4)] == [fq.PATH_MMA, fq.PATH_MMA, fq.PATH_M4RM,
                                                                      fq.PATH_M4RM]
     assert lib.fq_batched_product_path(h, 4) == -fq.EINVAL
