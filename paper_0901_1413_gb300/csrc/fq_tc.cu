@@ -1435,8 +1435,22 @@ __device__ __forceinline__ void store_batched(const BatchOut &bp, uint64_t *C, i
   }
 }
 
+// Row block and column block of tile t of a product with mbs x nbs tiles.
+// The operand that the tile walk streams again and again should be the
+// smaller one: row blocks outer (A's block stays while all of B streams)
+// when A is the larger operand, column blocks outer otherwise.
+__device__ __forceinline__ void batch_tile(int t, int mbs, int nbs, int nr, int &mb, int &nb) {
+  if (mbs * BM < nr) {  // A (mbs 128 rows) smaller than B (nr columns), per k-slice
+    nb = t / mbs;
+    mb = t - nb * mbs;
+  } else {
+    mb = t / nbs;
+    nb = t - mb * nbs;
+  }
+}
+
 // The persistent batched kernel: group g (cluster g) computes the products of
-// its list, one after another, 128 x 256 tiles each (row block by row block),
+// its list, one after another, 128 x 256 tiles each (in batch_tile's order),
 // from the e4m3 operands its converter warps write into its two scratch
 // buffers; CTA r of the group takes tiles r, r + kTcGroup, ... of each.
 template <int Q, int P>
@@ -1496,7 +1510,8 @@ __global__ void __cluster_dims__(kTcGroup, 1, 1) __launch_bounds__(THREADS_F, 1)
       const int kb = bp.la >> 7, nbs = bp.nr >> 8, tiles = ((bp.m + 127) >> 7) * nbs;
       const int ya = int(row_buf[b]), yb = int(row_buf[b] + batch_a_rows(bp.m, bp.la));
       for (int t = rank; t < tiles && !*abort_flag; t += kTcGroup) {
-        const int mb = t / nbs, nb = t - mb * nbs;
+        int mb, nb;
+        batch_tile(t, (bp.m + 127) >> 7, nbs, bp.nr, mb, nb);
         for (int ks = 0; ks < kb; ++ks, ++it) {
           const int s = it % STAGES;
           if (it >= STAGES) wait_bar(empty + 8 * s, uint32_t((it / STAGES - 1) & 1), abort_flag, prm.err);
@@ -1568,7 +1583,8 @@ __global__ void __cluster_dims__(kTcGroup, 1, 1) __launch_bounds__(THREADS_F, 1)
         wait_bar(accfull + 8 * ab, uint32_t((li / ACC) & 1), abort_flag, prm.err);
         if (*abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int mb = t / nbs, nb = t - mb * nbs;
+        int mb, nb;
+        batch_tile(t, (bp.m + 127) >> 7, nbs, bp.nr, mb, nb);
         const int64_t row = int64_t(mb) * BM + ew * 32 + lane;
         const int64_t w0 = int64_t(nb) * (BN / 64);
         const int64_t col0 = (w0 + 2 * half) * 64;
