@@ -126,7 +126,7 @@ def main():
     ap.add_argument("--case", help="time one product only: q,m,l,n[,path[,kernel]]")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--strassen", action="store_true", help="direct vs Strassen-Winograd levels only")
-    ap.add_argument("--batched", help="the 4096-product batch only: q[,auto|m4rm|mma]")
+    ap.add_argument("--batched", help="the batch only: q[,auto|m4rm|mma[,count]] (4096 products by default)")
     args = ap.parse_args()
     fq.load()
     if args.case:
@@ -139,9 +139,10 @@ def main():
         parts = args.batched.split(",")
         q = int(parts[0])
         path = {"auto": fq.PATH_AUTO, "m4rm": fq.PATH_M4RM, "mma": fq.PATH_MMA}[parts[1] if len(parts) > 1 else "auto"]
-        t, pps, ops, items = batched_row(q, reps=args.reps, path=path)
-        print("| batched F_%d (%s) | %.3f ms | %.3e products/s | %.3e field-ops/s | %d items |" % (
-            q, parts[1] if len(parts) > 1 else "auto", t, pps, ops, items))
+        count = int(parts[2]) if len(parts) > 2 else 4096
+        t, pps, ops, items = batched_row(q, count=count, reps=args.reps, path=path)
+        print("| batched F_%d (%s, %d products) | %.3f ms | %.3e products/s | %.3e field-ops/s | %d items |" % (
+            q, parts[1] if len(parts) > 1 else "auto", count, t, pps, ops, items))
         return
     print("| configuration | path | ms | field-ops/s |")
     print("|---|---|---:|---:|")
