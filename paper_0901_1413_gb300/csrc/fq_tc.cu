@@ -1298,7 +1298,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(f4::THREADS, 1)
 //
 // Warps: 0 (one thread) TMA loads, 1 (one thread) MMAs, 2 TMEM allocation,
 // 4..11 epilogue (TMEM lane quadrant warp % 4, 128-column half (warp - 4) /
-// 4), 12..27 converters.  Hand-overs, on mbarriers in every CTA of the group
+// 4), 12..27 and, once the TMEM is allocated, 2 and 3 converters.  Hand-overs, on mbarriers in every CTA of the group
 // with cluster-scope release and acquire:
 //   conv_full[b]   converters -> TMA threads: the product's operands are in
 //                  buffer b (each converter thread orders its global writes
@@ -1311,9 +1311,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(f4::THREADS, 1)
 // A group's CTAs leave together (a cluster barrier), so no arrival reaches a
 // CTA that has exited.
 constexpr int EPI_WARPS_B = 8;
-constexpr int CONV_WARPS = 16, CONV_THREADS = 32 * CONV_WARPS;
+constexpr int CONV_WARPS = 16;                  // warps 12..27
 constexpr int FIRST_CONV_WARP = 4 + EPI_WARPS_B;
-constexpr int THREADS_F = 32 * FIRST_CONV_WARP + CONV_THREADS;
+constexpr int THREADS_F = 32 * FIRST_CONV_WARP + 32 * CONV_WARPS;
+constexpr int CONV_THREADS = 32 * (CONV_WARPS + 2);  // and warps 2, 3 once the TMEM is allocated
 constexpr int NBARS_F = NBARS + 4;  // + conv_full[2], conv_empty[2]
 constexpr int SMEM_F = BAR_OFF + 8 * NBARS_F + 16 + 1024;
 // kind::f8f6f4, fp32 accumulator, e4m3 A (K-major) and B (N-major), N = 256, M = 128
@@ -1601,13 +1602,14 @@ __global__ void __cluster_dims__(kTcGroup, 1, 1) __launch_bounds__(THREADS_F, 1)
         if (row < bo.m) store_batched<Q, P>(bo, bo.C, row, w0, half, words, prm.err);
       }
     }
-  } else if (warp >= FIRST_CONV_WARP) {
+  } else if (warp >= FIRST_CONV_WARP || warp == 2 || warp == 3) {
     // ---- converters: product i into buffer i mod 2, once every CTA of the
     // group has finished reading the product two before it from that buffer;
     // the group's converter threads share each product's pieces, and the
     // next product's planes are fetched into L2 meanwhile (A by CTA 0, B by
     // the last CTA of the group)
-    const int ct = tid - 32 * FIRST_CONV_WARP, gct = rank * CONV_THREADS + ct;
+    const int ct = warp >= FIRST_CONV_WARP ? tid - 32 * FIRST_CONV_WARP : 32 * CONV_WARPS + tid - 64;
+    const int gct = rank * CONV_THREADS + ct;
     constexpr int nct = kTcGroup * CONV_THREADS;
     for (int i = 0; i < count && !*abort_flag; ++i) {
       const int b = i & 1;
