@@ -1355,7 +1355,7 @@ template <int Q, int P, class RowOf>
 __device__ __forceinline__ void convert_rows(const uint64_t *__restrict__ X, int rows_valid, int rows, int64_t pitch,
                                              int chunks, uint8_t *buf, int ct, int nct, RowOf row_of) {
   using CF = ConvField<Q>;
-  constexpr int UNR = 4;
+  constexpr int UNR = P == 2 ? 8 : 4;  // pieces whose loads are in flight together (registers allow 8 for two planes)
   const int per_row = 8 * chunks;
   const int radv = nct / per_row, padv = nct % per_row;
   const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
