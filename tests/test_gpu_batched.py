@@ -100,6 +100,36 @@ def test_batched_tensor_core_depth_and_width_edges(fq, q):
     check(fq, q, A, B, c)
 
 
+@pytest.mark.parametrize("q", [3, 5])
+def test_batched_tensor_core_pairs_with_single_tile_products(fq, q):
+    """The tcgen05 batch kernel gives each product to a pair of CTAs that take
+    alternate 128 x 256 tiles, so in a one-tile product one CTA of the pair
+    has nothing to compute yet takes part in the buffer hand-overs.  Nine
+    hundred such products (and a few with several tiles in between) put about
+    a dozen on every pair, with runs of one-tile products in the same scratch
+    buffer; run twice with new inputs behind the same pointers."""
+    rng = np.random.default_rng(70 + q)
+    shapes = [(int(rng.choice([1, 37, 64, 100, 128])), int(rng.choice([1, 64, 130, 300])),
+               int(rng.choice([1, 64, 200, 256]))) for _ in range(900)]
+    shapes[::97] = [(300, 200, 600)] * len(shapes[::97])
+    A, B, a, b, c, pa, pb, pc = make_batch(fq, q, shapes, seed=q + 80)
+    plan = fq.BatchPlan(q, shapes, path=fq.PATH_MMA)
+    assert plan.tc_products == len(shapes) and plan.items == 0
+    plan.run(pa, pb, pc)
+    assert fq.status() == fq.OK
+    sample = list(range(0, len(shapes), 7)) + list(range(0, len(shapes), 97))
+    check(fq, q, [A[i] for i in sample], [B[i] for i in sample], [c[i] for i in sample])
+    A2, B2 = [], []
+    for p, (m, l, n) in enumerate(shapes):
+        A2.append(inputs.uniform(q, m, l, seed=5, stream=2 * p))
+        B2.append(inputs.uniform(q, l, n, seed=5, stream=2 * p + 1))
+        fq.pack(q, torch.from_numpy(A2[-1]).cuda(), out=a[p])
+        fq.pack(q, torch.from_numpy(B2[-1]).cuda(), out=b[p])
+    plan.run(pa, pb, pc)
+    assert fq.status() == fq.OK
+    check(fq, q, [A2[i] for i in sample], [B2[i] for i in sample], [c[i] for i in sample])
+
+
 @pytest.mark.parametrize("path", ["m4rm", "mma"])
 @pytest.mark.parametrize("q", [3, 5])
 def test_batched_graph_capture_and_replay(fq, q, path):
