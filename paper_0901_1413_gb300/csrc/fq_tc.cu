@@ -33,10 +33,10 @@
 //   - packed e2m1, la / 2 bytes per row (la = roundup(l, 256)), kind::mxf4
 //     with block scale factors 1.0 held in TMEM, at twice the e4m3 rate: SM
 //     pairs, 256 x 448 tiles (the default for m > 128 and l >= 2048).
-// The batched form gives whole products to persistent CTAs whose converter
-// warps write each product's e4m3 operands into the CTA's own two scratch
-// buffers while its tensor-core warps compute the previous product.  Every
-// mbarrier wait is bounded.
+// The batched form gives whole products to pairs of persistent CTAs (one
+// cluster each) whose converter warps write each product's e4m3 operands
+// into the pair's two scratch buffers while their tensor-core warps compute
+// the previous product's tiles.  Every mbarrier wait is bounded.
 #include <cstring>
 
 #include "../../include/fq.h"
@@ -1298,8 +1298,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(f4::THREADS, 1)
 //
 // Warps: 0 (one thread) TMA loads, 1 (one thread) MMAs, 2 TMEM allocation,
 // 4..11 epilogue (TMEM lane quadrant warp % 4, 128-column half (warp - 4) /
-// 4), 12..27 and, once the TMEM is allocated, 2 and 3 converters.  Hand-overs, on mbarriers in every CTA of the group
-// with cluster-scope release and acquire:
+// 4), 12..27 and, once the TMEM is allocated, 2 and 3 converters.
+// Hand-overs, on mbarriers in every CTA of the group with cluster-scope
+// release and acquire:
 //   conv_full[b]   converters -> TMA threads: the product's operands are in
 //                  buffer b (each converter thread orders its global writes
 //                  before the async proxy's reads, then arrives on every
